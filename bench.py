@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of one SPH-with-boids step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (default): the large tank -- 2,097,152 fluid particles uniform in
+the lower 40% of a 4x2x2 tank, settled for 200 steps, then 16,384 boids in 8
+schools released; K timed steps.  A step is one call of sph_step: binning,
+density, forces + integration, boid binning and rules (all in the library's
+CUDA kernels).  Each timed step is bracketed by CUDA events on the step's
+stream; L2 is flushed (a 256 MiB write) between timed steps, outside the
+events.  ``value`` = fluid particles x steps / summed step time (max over
+ranks; under torchrun every rank runs its own replica: weak scaling).
+
+Also reported: per-pass times (library event hook), the roofline of the
+dominant pass, the CPU oracle on a bounded sample, an end-to-end figure
+through host buffers, kernel launches and SM clocks.
+
+``--impl reference`` times the CPU oracle (the reference program of this
+method) on the same workload: each step is the full oracle step on a
+bounded spatial sample of the tank.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2311_15088_gb300 import scenes  # noqa: E402
+
+METRIC = "particle-steps/sec at 2M particles (HBM roofline %)"
+UNIT = "particle-steps/s"
+SETTLE = 200
+
+# FP32 peak of the ALU-bound passes: 152 SMs x 128 FP32 lanes x 2 flops (FMA)
+# x 2070 MHz (maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic work per particle-step: a candidate test is 3 sub + 1 mul +
+# 2 fma = 8 flops; an accepted density pair 4 flops; a force pair 30 flops.
+FLOP_CAND, FLOP_DENS_PAIR, FLOP_FORCE_PAIR = 8, 4, 30
+# Compulsory bytes per particle of each pass (float4 pos/vel, float rho ...):
+BYTES = {"scatter": 12, "sort": 68, "density": 24, "forces": 112}
+BYTES_PER_CELL_SCAN = 12
+
+# DRAM traffic of the force pass from one ncu capture (bytes per launch) and
+# the sha256 of the kernel source it was taken on; null once the source moved.
+FORCES_TRAFFIC = None  # {"bytes": ..., "source_sha256": ...}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=("large", "column", "small"), default="large")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="approximate CPU time of the oracle baseline sample")
+    ap.add_argument("--reference-budget", type=float, default=150.0,
+                    help="seconds the reference arm may spend on its K + W sample steps")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(name):
+    if name == "large":
+        sc = scenes.large_tank()
+        desc = ("large tank: 2,097,152 fluid particles uniform in the lower 40% of a 4x2x2 tank, "
+                f"settled {SETTLE} steps, then 16,384 boids in 8 schools")
+        return sc, desc, SETTLE
+    if name == "column":
+        sc = scenes.dam_break_column()
+        return sc, "dam-break column: 262,144 particles (64^3 lattice) in a 2x1x1 tank, 1,024 boids", 0
+    sc = scenes.dam_break_small()
+    return sc, "dam-break: 4,096 particles (16^3 lattice) in the unit box, 16 boids", 0
+
+
+def _params(sc):
+    p = dict(sc["params"])
+    if p.get("mass") is None:
+        from paper_2311_15088_gb300 import sph
+
+        p["mass"] = sph.sph_lattice_mass(p, sc["lattice_spacing"])
+    return p
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read only)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(1.0)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------- work counts
+
+def _candidates_and_pairs(cell_start, dims, nbr_count):
+    """Total 27-cell candidates (self included) and neighbour pairs of a step."""
+    counts = np.diff(cell_start.astype(np.int64)).reshape(dims[2], dims[1], dims[0])
+    pad = np.pad(counts, 1)
+    box = np.zeros_like(counts)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                box += pad[dz:dz + dims[2], dy:dy + dims[1], dx:dx + dims[0]]
+    cand = int((counts * box).sum())
+    pairs = int(nbr_count.astype(np.int64).sum())
+    return cand, pairs
+
+
+def _work_snapshot(s):
+    cs = s.field("cell_start").cpu().numpy().view(np.uint32)
+    nbr = s.field("nbr_count").cpu().numpy()
+    cand, pairs = _candidates_and_pairs(cs, s.dims, nbr)
+    return {"candidates": cand, "pairs": pairs, "nbr_mean": float(nbr.mean()), "nbr_max": int(nbr.max())}
+
+
+def _source_sha(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def _slab(fp, fv, bp, bv, lo, hi):
+    m = (fp[:, 0] >= lo) & (fp[:, 0] < hi)
+    mb = (bp[:, 0] >= lo) & (bp[:, 0] < hi)
+    return fp[m], fv[m], bp[mb], bv[mb]
+
+
+def _oracle_rate(p, fp, fv, bp, bv, step_seconds, min_seconds=0.0, steps=None):
+    """Full oracle steps on a centred x-slab of the state.  The slab is grown
+    until one step takes about ``step_seconds``; then ``steps`` steps (or as
+    many as fill ``min_seconds``) are timed.  Returns (particle-steps/s,
+    threads, description, steps, particles, seconds)."""
+    import oracle
+
+    oracle.build()
+    x0, x1 = float(p["box_min"][0]), float(p["box_max"][0])
+    full = x1 - x0
+    w = full * min(1.0, 20000.0 / max(len(fp), 1))
+    for _ in range(8):
+        lo = x0 + 0.5 * (full - w)
+        sample = _slab(fp, fv, bp, bv, lo, lo + w)
+        t = time.perf_counter()
+        oracle.step(p, *sample)
+        t = time.perf_counter() - t
+        if t >= 0.6 * step_seconds or w >= full:
+            break
+        w = min(full, w * min(4.0, step_seconds / max(t, 1e-6)))
+    n_steps, done, t0 = 0, 0, time.perf_counter()
+    while True:
+        oracle.step(p, *sample)
+        n_steps += 1
+        done += len(sample[0])
+        el = time.perf_counter() - t0
+        if (steps is not None and n_steps >= steps) or (steps is None and el >= min_seconds):
+            break
+    desc = (f"full oracle step on the x-slab [{lo:.3f}, {lo + w:.3f}) of the tank: {len(sample[0])} fluid "
+            f"particles and {len(sample[2])} boids, {n_steps} step(s)")
+    return done / el, oracle.num_threads(), desc, n_steps, len(sample[0]), el
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    sc, desc, _settle = _workload(a.workload)
+    p = dict(sc["params"])
+    if p.get("mass") is None:
+        import oracle
+
+        p["mass"] = float(np.float32(oracle.lattice_mass(p, sc["lattice_spacing"])))
+    fp, fv, bp, bv = sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"]
+    per_step = a.reference_budget / max(a.steps + a.warmup, 1)
+    # warm-up sample steps are part of the budget but not of the figure
+    if a.warmup:
+        _oracle_rate(p, fp, fv, bp, bv, per_step, steps=a.warmup)
+    rate, cores, sdesc, steps, npart, el = _oracle_rate(p, fp, fv, bp, bv, per_step, steps=a.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / max(steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc + " (initial state: the oracle does not settle it)"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+
+    from paper_2311_15088_gb300 import sph
+    from paper_2311_15088_gb300.sph import Scene
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    sc, desc, settle = _workload(a.workload)
+    p = _params(sc)
+    nf, nb = len(sc["fluid_pos"]), len(sc["boid_pos"])
+    z = np.zeros((0, 4), np.float32)
+
+    # settle the fluid alone, then release the boids
+    if settle:
+        s0 = Scene(p, nf, 0, device=dev)
+        s0.set_state(sc["fluid_pos"], sc["fluid_vel"], z, z)
+        s0.step(settle)
+        fp, fv, _, _ = s0.get_state()
+        del s0
+    else:
+        fp, fv = sc["fluid_pos"], sc["fluid_vel"]
+    s = Scene(p, nf, nb, device=dev)
+    s.set_state(fp, fv, sc["boid_pos"], sc["boid_vel"])
+    for _ in range(a.warmup):
+        s.step(1)
+    torch.cuda.synchronize(dev)
+    work0 = _work_snapshot(s)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    sph.sph_profile_enable(s.handle, a.steps * len(sph.KINDS) + 16)
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = s.launches
+    for k in range(a.steps):
+        flush.zero_()
+        ev0[k].record()
+        s.step(1)
+        ev1[k].record()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    launches = s.launches - launches0
+    clk = clocks.stop()
+    prof = sph.sph_profile_read(s.handle)
+    sph.sph_profile_enable(s.handle, 0)
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]
+    t = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    value = nf * a.steps * world / t
+    work1 = _work_snapshot(s)
+    status = s.status()
+
+    # ---- roofline of the dominant pass and the HBM view of the step
+    cand = 0.5 * (work0["candidates"] + work1["candidates"])
+    pairs = 0.5 * (work0["pairs"] + work1["pairs"])
+    n_all = nf + nb
+    passes = {k: {"ms_per_step": ms / max(cnt, 1), "launch_groups": cnt} for k, (ms, cnt) in prof.items() if cnt}
+    f_ms = passes["forces"]["ms_per_step"]
+    d_ms = passes["density"]["ms_per_step"]
+    force_flops = FLOP_CAND * cand + FLOP_FORCE_PAIR * pairs
+    dens_flops = FLOP_CAND * cand + FLOP_DENS_PAIR * (pairs + n_all)
+    achieved = force_flops / (f_ms * 1e-3) / 1e12
+    src = os.path.join(ROOT, "paper_2311_15088_gb300", "csrc", "sph_physics.cu")
+    traffic = None
+    if FORCES_TRAFFIC and FORCES_TRAFFIC.get("source_sha256") == _source_sha(src):
+        traffic = FORCES_TRAFFIC["bytes"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    ncells = s.dims[0] * s.dims[1] * s.dims[2]
+    step_bytes = n_all * sum(BYTES.values()) + ncells * BYTES_PER_CELL_SCAN
+    ms_per_step = 1e3 * t / a.steps
+    hbm_pass = {}
+    for k in ("scatter", "sort", "density", "forces"):
+        if k in passes:
+            gbs = n_all * BYTES[k] / (passes[k]["ms_per_step"] * 1e-3) / 1e9
+            hbm_pass[k] = {"GB/s": gbs, "frac": gbs / hbm_peak}
+    roofline = {
+        "bound": "alu", "kernel": "k_forces (pair forces + integration)", "achieved": achieved,
+        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+        "flops_per_launch": force_flops,
+        "density_pass": {"achieved": dens_flops / (d_ms * 1e-3) / 1e12,
+                         "frac": dens_flops / (d_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
+    }
+    hbm = {"algorithmic_bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (ms_per_step * 1e-3) / 1e9,
+           "peak_GBps": hbm_peak, "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak,
+           "peak_source": hbm_src, "per_pass": hbm_pass}
+
+    # ---- end to end through host buffers
+    host = [torch.empty((n, 4), dtype=torch.float32).pin_memory() for n in (nf, nf, nb, nb)]
+    sph.sph_get_state(s.handle, *[h.data_ptr() if h.numel() else None for h in host], 1, s.stream)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        s.set_state_host(*host)
+        s.step(1)
+        s.get_state_host(host)
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": nf * a.e2e_steps * world / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in host)),
+           "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in host)), "steps": a.e2e_steps}
+
+    # ---- CPU oracle on a bounded sample of the same (settled) workload
+    cpu = None
+    if world == 1 and rank == 0 and not a.no_cpu_baseline:
+        st = [x.cpu().numpy() if hasattr(x, "cpu") else x for x in s.get_state()]
+        rate, cores, sdesc, _steps, _np, _el = _oracle_rate(p, *st, step_seconds=a.cpu_seconds / 3,
+                                                            min_seconds=a.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "fluid_particles": nf, "boids": nb, "settle_steps": settle,
+                       "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "neighbours_mean": 0.5 * (work0["nbr_mean"] + work1["nbr_mean"]),
+                       "neighbours_max": max(work0["nbr_max"], work1["nbr_max"]),
+                       "candidates_per_particle": cand / n_all},
+            "roofline": roofline, "hbm": hbm, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk, "device_status": status,
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

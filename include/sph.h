@@ -1,0 +1,240 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) SPH-with-boids step library.
+ *
+ * The library advances the method of "A GPU-based Hydrodynamic Simulator with
+ * Boid Interactions" (Liu, Kayar, Perlin, arXiv 2311.15088) by whole steps:
+ * uniform-grid binning with a counting sort (sections "Neighborhood Search",
+ * "Neighbor Search with Sorting"), poly6 density and the equation of state
+ * (sections "Smoothed Particle Hydrodynamics", "Pressure and Viscosity"),
+ * symmetrised pressure + viscosity pair forces with the boid-touch counters
+ * (section "Pressure and Viscosity", listing "Compute acceleration"), the boid
+ * rules with two-way coupling (section "Boid Motion and Agent Fluid
+ * Interaction") and Euler-Cromer integration with damped walls (section
+ * "Governing Equations" frame loop, section "Background").
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: SPH_OK (0) or one of the SPH_ERR_* codes; the message of
+ *     the last failure is sph_last_error(handle) (or sph_last_error(NULL)
+ *     for failures before a handle exists).
+ *   - Pointers are device pointers unless an `on_host` argument says
+ *     otherwise.  Host pointers given with on_host = 1 should be pinned for
+ *     asynchronous copies; the call then synchronises `stream` before it
+ *     returns so that the host buffer is complete.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - The caller owns every buffer, including the workspace; the library
+ *     never allocates or frees device memory.  sph_destroy frees only the
+ *     host-side handle.
+ *   - float4 arrays are (x, y, z, w) with w ignored on input and 0 on output.
+ *   - Particle ids: ids 0 .. n_boid-1 are the particles attached to boids
+ *     (boid b <-> particle b), ids n_boid .. n_boid+n_fluid-1 are the fluid
+ *     particles (fluid index f <-> id n_boid + f), as the paper's
+ *     initialize_particle kernel assigns them.
+ *   - No entry point falls back to the CPU.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SPH_OK           0
+#define SPH_ERR_ARG      1  /* invalid parameter, size, pointer or alignment   */
+#define SPH_ERR_CUDA     2  /* a CUDA runtime call or launch failed            */
+#define SPH_ERR_OVERFLOW 3  /* a size does not fit the library's index types   */
+#define SPH_ERR_TIMEOUT  4  /* a bounded device wait gave up                   */
+#define SPH_ERR_STATE    5  /* call out of order (e.g. fields before a step)   */
+
+/* Constant sets of the spiky-gradient / viscosity-Laplacian prefactors. */
+#define SPH_MULLER3D      0  /* 45/(pi h^5) for both: the 3-D normalised kernels (default) */
+#define SPH_PAPER_LITERAL 1  /* 30/(pi h^4) and 40/(pi h^4), as printed in the paper      */
+
+/* Fluid -> boid coupling modes. */
+#define SPH_COUPLE_FORCE 0   /* v_b += sph_factor * dt * F_b (the only mode implemented) */
+
+/* Bits of the sticky device error word (sph_status). */
+#define SPH_DEV_NONFINITE 1u  /* a density, position or velocity became NaN/Inf  */
+#define SPH_DEV_CLAMPED   2u  /* a position lay outside the grid and was clamped */
+
+/* Fields that sph_get_fields can return (one per call). */
+#define SPH_FIELD_RHO         0  /* float[n_tot]   density, by particle id                 */
+#define SPH_FIELD_PRESSURE    1  /* float[n_tot]   k (rho - rho0), by particle id          */
+#define SPH_FIELD_ACC         2  /* float4[n_tot]  acceleration, by particle id            */
+#define SPH_FIELD_TOUCHED     3  /* int[n_tot]     touched_by_boid, by particle id          */
+#define SPH_FIELD_INFLUENCE   4  /* float4[n_tot]  boid_influence, by particle id           */
+#define SPH_FIELD_NBR_COUNT   5  /* int[n_tot]     neighbour count (self excluded), by id   */
+#define SPH_FIELD_KEYS        6  /* uint[n_tot]    cell key of the step's binning, by id    */
+#define SPH_FIELD_PERM        7  /* int[n_tot]     id at each sorted slot                   */
+#define SPH_FIELD_CELL_START  8  /* uint[ncells+1] first sorted slot of each cell           */
+#define SPH_FIELD_FB          9  /* float4[n_boid] fluid force F_b on each boid             */
+#define SPH_FIELD_BOID_KEYS  10  /* uint[n_boid]   boid-grid cell key, by boid id           */
+#define SPH_FIELD_BOID_PERM  11  /* int[n_boid]    boid id at each sorted boid slot         */
+#define SPH_FIELD_BOID_CELL_START 12 /* uint[nbcells+1] first sorted boid slot per cell    */
+
+/*
+ * Parameters of a scene.  Paper notation: h smoothing length, rho0 rest
+ * density, k gas constant (p = k (rho - rho0)), mu viscosity, mass particle
+ * mass (every particle, attached ones included), d = cell_size the grid
+ * cell (d >= h: the 27-cell stencil then holds every neighbour), boid radii
+ * r_sep ("protect_range") and r_vis ("visible_range"), rule weights w_sep
+ * ("sep"), w_align ("mat"), w_coh ("cen"), sph_factor, the speed limits
+ * v_min / v_max, edge_turn (edge avoidance), boid_cell_size (>= r_vis).
+ * The paper gives no value for the boid weights, the wall restitution or
+ * the edge turn; they are free parameters.
+ */
+typedef struct sph_params {
+    float h, rho0, k, mu, dt, gx, gy, gz, mass;
+    float box_min[3], box_max[3];
+    float cell_size;
+    int   const_set;           /* SPH_MULLER3D | SPH_PAPER_LITERAL */
+    float wall_restitution;    /* walls: x reflected, v_n <- -wall_restitution v_n */
+    float r_sep, r_vis, w_sep, w_align, w_coh, sph_factor, v_min, v_max, edge_turn;
+    float boid_cell_size;
+    int   coupling_mode;       /* SPH_COUPLE_FORCE */
+} sph_params;
+
+typedef struct sph_handle sph_handle;
+
+/*
+ * Bytes of device workspace a scene of n_fluid + n_boid particles needs
+ * (all per-step arrays, the double-buffered SoA state and the grids).
+ * Errors: SPH_ERR_ARG for invalid parameters (see sph_create), a NULL
+ * `bytes` or negative counts; SPH_ERR_OVERFLOW if the grid or the counts
+ * exceed 2^31 - 1.
+ */
+int sph_workspace_size(const sph_params* p, int n_fluid, int n_boid, size_t* bytes);
+
+/*
+ * Grid dimensions dim = ceil((box_max - box_min) / cell), per axis, of the
+ * particle grid (which = 0, cell = cell_size) or the boid grid (which = 1,
+ * cell = boid_cell_size) (section "Neighborhood Search").
+ */
+int sph_grid_dims(const sph_params* p, int which, int dims[3]);
+
+/*
+ * Particle mass that makes the density of an infinite cubic lattice of the
+ * given spacing equal rho0 under the poly6 kernel (self term included):
+ * mass = rho0 / sum_o W_poly6(|o| spacing), o over integer offsets with
+ * |o| spacing < h.  Host-side computation in double; no device work.
+ */
+int sph_lattice_mass(const sph_params* p, float spacing, float* mass);
+
+/*
+ * Create a scene handle on a caller-owned device workspace of ws_bytes
+ * (>= sph_workspace_size, 256-byte aligned).  The current CUDA device must
+ * be the workspace's device.  The state is undefined until sph_set_state.
+ * Errors: SPH_ERR_ARG if h, rho0, mass, dt <= 0, cell_size < h,
+ * boid_cell_size < r_vis, r_sep > r_vis, box_max <= box_min on an axis,
+ * an unknown const_set / coupling_mode, a small or misaligned workspace.
+ */
+int sph_create(const sph_params* p, int n_fluid, int n_boid, void* workspace,
+               size_t ws_bytes, sph_handle** out);
+
+/*
+ * Load the state: fluid_pos4 / fluid_vel4 hold n_fluid float4 (fluid order),
+ * boid_pos4 / boid_vel4 hold n_boid float4 (boid order).  on_host = 1: host
+ * buffers (copied on `stream`, which is synchronised before returning);
+ * on_host = 0: device buffers, 16-byte aligned.  Any pointer of an empty
+ * set may be NULL.  Errors: SPH_ERR_ARG (NULL or misaligned pointer),
+ * SPH_ERR_CUDA.
+ */
+int sph_set_state(sph_handle* h, const float* fluid_pos4, const float* fluid_vel4,
+                  const float* boid_pos4, const float* boid_vel4, int on_host, void* stream);
+
+/* Store the current state into the same layouts as sph_set_state. */
+int sph_get_state(sph_handle* h, float* fluid_pos4, float* fluid_vel4,
+                  float* boid_pos4, float* boid_vel4, int on_host, void* stream);
+
+/*
+ * Advance nsteps whole steps on `stream` (asynchronous; no host sync, no
+ * allocation).  One step: attach particles to boids; bin (keys, counting
+ * sort by cell then particle id); density + pressure; pair forces,
+ * touched_by_boid, boid_influence and the fluid force F_b on each boid;
+ * boid rules (start-of-step snapshot, rules in the listed order, then
+ * v_b += sph_factor dt F_b, edge avoidance, speed limit, x_b += v_b dt);
+ * Euler-Cromer integration of the fluid with damped wall reflection.
+ * Errors: SPH_ERR_ARG (nsteps < 0), SPH_ERR_STATE (no state loaded),
+ * SPH_ERR_CUDA.  Device-side anomalies set bits of the error word.
+ */
+int sph_step(sph_handle* h, int nsteps, void* stream);
+
+/*
+ * Fluid force on every boid for the CURRENT state (mode 0 = exact SPH
+ * coupling): F_b = (1/rho_b) sum_j f_bj over fluid neighbours j of the
+ * boid's attached particle (section "Boid Motion and Agent Fluid
+ * Interaction").  Writes n_boid float4 to out_f4 (device).  Does not
+ * change the state.  Errors: SPH_ERR_ARG (mode != 0, NULL out),
+ * SPH_ERR_STATE, SPH_ERR_CUDA.
+ */
+int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream);
+
+/*
+ * Copy one field of the most recent step (SPH_FIELD_*) to `out` (device,
+ * or host with on_host = 1), sized as listed with the SPH_FIELD_* codes.
+ * Errors: SPH_ERR_ARG (unknown field, NULL out), SPH_ERR_STATE (no step
+ * since the last sph_set_state), SPH_ERR_CUDA.
+ */
+int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* stream);
+
+/*
+ * Test hook: bin the CURRENT state and write every particle's neighbour
+ * list, N(i) = { j != i : not both attached, r_ij^2 < h^2 } with the float32
+ * predicate, in the order the 27-cell walk visits them (cells dz, dy, dx
+ * ascending; particles of a cell by id).  counts: int[n_tot] by id (device).
+ * If offsets (int64[n_tot + 1], device, by id) and list (int[offsets[n_tot]],
+ * device) are non-NULL, list[offsets[i] ..] receives the ids.  State is
+ * unchanged.  Errors: SPH_ERR_ARG, SPH_ERR_STATE, SPH_ERR_CUDA.
+ */
+int sph_debug_neighbors(sph_handle* h, int* counts, const long long* offsets, int* list,
+                        void* stream);
+
+/*
+ * Read (and keep) the sticky device error word into *bits; synchronises the
+ * handle's last stream.  sph_clear_status zeroes it (asynchronously).
+ */
+int sph_status(sph_handle* h, unsigned* bits);
+int sph_clear_status(sph_handle* h, void* stream);
+
+/* Message of the last failure on h (or of handle-less calls if h is NULL). */
+const char* sph_last_error(sph_handle* h);
+
+/* Number of kernels this handle has launched since creation. */
+long long sph_launch_count(sph_handle* h);
+
+/*
+ * Per-pass CUDA-event timing of sph_step (the library's tracing hook).
+ * Kinds: SPH_KIND_KEYS (cell keys of a freshly loaded state), SPH_KIND_SCAN
+ * (exclusive scan of the cell counts), SPH_KIND_SCATTER, SPH_KIND_SORT
+ * (per-cell sort + gather), SPH_KIND_DENSITY, SPH_KIND_FORCES (pair forces
+ * + integration + next keys), SPH_KIND_BOID_BIN (boid-grid binning),
+ * SPH_KIND_BOID_RULES.  sph_profile_enable(h, n) creates a host-side pool
+ * of 2n events (n = 0 disables and frees it); while enabled, each pass of
+ * sph_step is bracketed by two events recorded on the step's stream, up to
+ * n passes.  sph_profile_read synchronises on the last event and writes,
+ * per kind (nkinds entries), the summed milliseconds and the number of
+ * passes, then restarts the record.  Errors: SPH_ERR_ARG, SPH_ERR_CUDA.
+ */
+#define SPH_KIND_KEYS       0
+#define SPH_KIND_SCAN       1
+#define SPH_KIND_SCATTER    2
+#define SPH_KIND_SORT       3
+#define SPH_KIND_DENSITY    4
+#define SPH_KIND_FORCES     5
+#define SPH_KIND_BOID_BIN   6
+#define SPH_KIND_BOID_RULES 7
+#define SPH_NUM_KINDS       8
+int sph_profile_enable(sph_handle* h, int max_passes);
+int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds);
+
+/* Free the host-side handle (the workspace stays the caller's). */
+void sph_destroy(sph_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_GB300_H */

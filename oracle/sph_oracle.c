@@ -362,7 +362,13 @@ int or_brute_neighbors(const or_params *p, int n, int n_att, const float *pos3,
  * r_ij = x_i - x_j, v_ij = v_i - v_j, q = |r_ij| / h:
  *   f_ij = m/rho_j * [ C_p (p_i + p_j)/2 (1-q)^2/q r_ij - C_v mu (1-q) v_ij ]
  * Returns 0 for r2 >= h^2 or r2 == 0 (listing "Compute acceleration").
- * abs_out receives |f_ij| for the error scale. */
+ *
+ * abs_out receives the error scale of a float32 evaluation of f_ij: for each
+ * term its magnitude plus r^2 |d(term)/d(r^2)|, the forward-error factor of a
+ * relative rounding of the float32 squared distance (1 - q cancels near the
+ * kernel's edge), with the equation-of-state sum taken as (|p_i| + |p_j|)/2
+ * (it cancels where rho_i < rho0 < rho_j):
+ *   m/rho_j [ C_p (|p_i| + |p_j|)/2 h (1-q) + C_v mu |v_ij| (1 - q/2) ]. */
 static void pair_force(const or_params *p, double cp, double cv,
                        const double *xi, const double *xj,
                        const double *vi, const double *vj,
@@ -380,7 +386,9 @@ static void pair_force(const or_params *p, double cp, double cv,
     double pres = cp * 0.5 * (pi + pj) * (1.0 - q) * (1.0 - q) / q;
     double visc = cv * p->mu * (1.0 - q);
     for (int a = 0; a < 3; ++a) f[a] = p->mass / rho_j * (pres * r[a] - visc * v[a]);
-    *abs_out = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    *abs_out = p->mass / rho_j * (cp * 0.5 * (fabs(pi) + fabs(pj)) * p->h * (1.0 - q) +
+                                  cv * p->mu * vmag * (1.0 - 0.5 * q));
 }
 
 int or_step(const or_params *p, int n_fluid, int n_boid,

@@ -1,0 +1,756 @@
+// sph_api.cu -- the C ABI declared in include/sph.h: parameter validation,
+// the workspace layout, state upload/download, step orchestration and the
+// field accessors.  All device work is enqueued on the caller's stream;
+// nothing here allocates device memory.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "sph_internal.cuh"
+
+using namespace sphk;
+
+struct sph_handle {
+    sph_params p;
+    StepConst c;
+    int n_fluid, n_boid, n;
+    // state (storage order) and the sorted scratch copy
+    float4 *pos, *vel, *pos_s, *vel_s;
+    unsigned *key, *rank;
+    int* tmp;
+    unsigned *count, *cell_start, *scan_part;
+    int* big_list;
+    unsigned* big_count;
+    float* rho;
+    int* nbr;
+    float4* acc;
+    int* touched;
+    float4* infl;
+    int* slot_of_boid;
+    float4 *bpos, *bvel, *bpos_s, *bvel_s;
+    unsigned *bkey, *brank;
+    int* btmp;
+    unsigned *bcount, *bstart, *bscan_part;
+    int* bbig_list;
+    unsigned* bbig_count;
+    float4* fb;
+    unsigned* err;
+    bool has_state, keys_ready, has_step;
+    long long launches;
+    cudaStream_t last_stream;
+    // per-pass event timing (sph_profile_enable)
+    cudaEvent_t* prof_ev;
+    int* prof_kind;
+    int prof_cap, prof_n;
+    char msg[512];
+};
+
+static void prof_begin(sph_handle* h, int kind, cudaStream_t s)
+{
+    if (h->prof_n < h->prof_cap) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_n], s);
+        h->prof_kind[h->prof_n] = kind;
+    }
+}
+
+static void prof_end(sph_handle* h, cudaStream_t s)
+{
+    if (h->prof_n < h->prof_cap) {
+        cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], s);
+        ++h->prof_n;
+    }
+}
+
+static thread_local char g_msg[512] = "";
+
+static int fail(sph_handle* h, int code, const char* fmt, ...)
+{
+    char* dst = h ? h->msg : g_msg;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_TRY(h, expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail((h), SPH_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),  \
+                        __FILE__, __LINE__);                                                \
+    } while (0)
+
+// ------------------------------------------------------------ parameters
+
+static bool finite_pos(float v) { return isfinite(v) && v > 0.0f; }
+
+static int make_grid(const float mn[3], const float mx[3], float d, GridDesc* g)
+{
+    long long cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        double n = ceil(((double)mx[a] - (double)mn[a]) / (double)d);
+        if (n < 1.0) n = 1.0;
+        if (n > 2147483647.0) return SPH_ERR_OVERFLOW;
+        g->dim[a] = (int)n;
+        g->minf[a] = mn[a];
+        cells *= (long long)n;
+        if (cells > 2147483646LL) return SPH_ERR_OVERFLOW;
+    }
+    g->ncells = (int)cells;
+    g->inv_d = 1.0f / d;
+    return SPH_OK;
+}
+
+static int validate(const sph_params* p, int n_fluid, int n_boid)
+{
+    if (!p) return fail(nullptr, SPH_ERR_ARG, "params is NULL");
+    if (n_fluid < 0 || n_boid < 0) return fail(nullptr, SPH_ERR_ARG, "negative particle count");
+    if ((long long)n_fluid + n_boid > 2147483647LL) return fail(nullptr, SPH_ERR_OVERFLOW, "too many particles");
+    if (!finite_pos(p->h) || !finite_pos(p->rho0) || !finite_pos(p->mass) || !finite_pos(p->dt))
+        return fail(nullptr, SPH_ERR_ARG, "h, rho0, mass and dt must be finite and > 0");
+    if (!(isfinite(p->cell_size) && p->cell_size >= p->h))
+        return fail(nullptr, SPH_ERR_ARG, "cell_size must be >= h (27-cell stencil)");
+    if (!(isfinite(p->k) && p->k >= 0.0f) || !(isfinite(p->mu) && p->mu >= 0.0f))
+        return fail(nullptr, SPH_ERR_ARG, "k and mu must be finite and >= 0");
+    for (int a = 0; a < 3; ++a)
+        if (!(isfinite(p->box_min[a]) && isfinite(p->box_max[a]) && p->box_max[a] > p->box_min[a]))
+            return fail(nullptr, SPH_ERR_ARG, "box_max must exceed box_min on every axis");
+    if (!(isfinite(p->gx) && isfinite(p->gy) && isfinite(p->gz)))
+        return fail(nullptr, SPH_ERR_ARG, "gravity must be finite");
+    if (p->const_set != SPH_MULLER3D && p->const_set != SPH_PAPER_LITERAL)
+        return fail(nullptr, SPH_ERR_ARG, "unknown const_set %d", p->const_set);
+    if (p->coupling_mode != SPH_COUPLE_FORCE)
+        return fail(nullptr, SPH_ERR_ARG, "unsupported coupling_mode %d", p->coupling_mode);
+    if (!(isfinite(p->wall_restitution) && p->wall_restitution >= 0.0f))
+        return fail(nullptr, SPH_ERR_ARG, "wall_restitution must be >= 0");
+    if (!(p->r_sep >= 0.0f && p->r_vis >= p->r_sep && isfinite(p->r_vis)))
+        return fail(nullptr, SPH_ERR_ARG, "need 0 <= r_sep <= r_vis");
+    if (!(isfinite(p->boid_cell_size) && p->boid_cell_size > 0.0f && p->boid_cell_size >= p->r_vis))
+        return fail(nullptr, SPH_ERR_ARG, "boid_cell_size must be > 0 and >= r_vis");
+    if (!(p->v_min >= 0.0f && p->v_max >= p->v_min && isfinite(p->v_max)))
+        return fail(nullptr, SPH_ERR_ARG, "need 0 <= v_min <= v_max");
+    if (!(isfinite(p->w_sep) && isfinite(p->w_align) && isfinite(p->w_coh) && isfinite(p->sph_factor) &&
+          isfinite(p->edge_turn)))
+        return fail(nullptr, SPH_ERR_ARG, "boid weights must be finite");
+    GridDesc g;
+    if (make_grid(p->box_min, p->box_max, p->cell_size, &g) != SPH_OK)
+        return fail(nullptr, SPH_ERR_OVERFLOW, "particle grid has more than 2^31 cells");
+    if (make_grid(p->box_min, p->box_max, p->boid_cell_size, &g) != SPH_OK)
+        return fail(nullptr, SPH_ERR_OVERFLOW, "boid grid has more than 2^31 cells");
+    return SPH_OK;
+}
+
+static void make_const(const sph_params* p, int n_fluid, int n_boid, StepConst* c)
+{
+    memset(c, 0, sizeof(*c));
+    make_grid(p->box_min, p->box_max, p->cell_size, &c->g);
+    make_grid(p->box_min, p->box_max, p->boid_cell_size, &c->gb);
+    c->n = n_fluid + n_boid;
+    c->nb = n_boid;
+    const double pi = 3.14159265358979323846;
+    const double h = p->h;
+    c->h2 = p->h * p->h;
+    c->mC6 = (float)((double)p->mass * 315.0 / (64.0 * pi * pow(h, 9)));
+    double cp, cv;
+    if (p->const_set == SPH_PAPER_LITERAL) {
+        cp = 30.0 / (pi * pow(h, 4));
+        cv = 40.0 / (pi * pow(h, 4));
+    } else {
+        cp = 45.0 / (pi * pow(h, 5));
+        cv = cp;
+    }
+    c->half_cp_h = (float)(0.5 * cp * h);
+    c->cv_mu = (float)(cv * (double)p->mu);
+    c->inv_h = (float)(1.0 / h);
+    c->mass = p->mass;
+    c->k = p->k;
+    c->rho0 = p->rho0;
+    c->dt = p->dt;
+    c->grav[0] = p->gx;
+    c->grav[1] = p->gy;
+    c->grav[2] = p->gz;
+    for (int a = 0; a < 3; ++a) {
+        c->box_min[a] = p->box_min[a];
+        c->box_max[a] = p->box_max[a];
+    }
+    c->restitution = p->wall_restitution;
+    c->rs = p->r_sep;
+    c->rs2 = p->r_sep * p->r_sep;
+    c->rv2 = p->r_vis * p->r_vis;
+    c->w_sep = p->w_sep;
+    c->w_align = p->w_align;
+    c->w_coh = p->w_coh;
+    c->sph_dt = (float)((double)p->sph_factor * (double)p->dt);
+    c->v_min = p->v_min;
+    c->v_max = p->v_max;
+    c->edge_turn = p->edge_turn;
+}
+
+// ------------------------------------------------------------- workspace
+
+struct Carver {
+    uintptr_t base, off;
+    template <class T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~(uintptr_t)255;
+        T* ptr = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T) + 16;  // + guard so that empty arrays stay distinct
+        return ptr;
+    }
+};
+
+static size_t carve(sph_handle* h, uintptr_t base)
+{
+    Carver cv{base, 0};
+    const size_t n = (size_t)h->n, nb = (size_t)h->n_boid;
+    const size_t C = (size_t)h->c.g.ncells, Cb = (size_t)h->c.gb.ncells;
+    h->pos = cv.take<float4>(n);
+    h->vel = cv.take<float4>(n);
+    h->pos_s = cv.take<float4>(n);
+    h->vel_s = cv.take<float4>(n);
+    h->key = cv.take<unsigned>(n);
+    h->rank = cv.take<unsigned>(n);
+    h->tmp = cv.take<int>(n > C ? n : C);
+    h->count = cv.take<unsigned>(C);
+    h->cell_start = cv.take<unsigned>(C + 1);
+    h->scan_part = cv.take<unsigned>((size_t)scan_parts((int)C) + 1);
+    h->big_list = cv.take<int>(C);
+    h->big_count = cv.take<unsigned>(1);
+    h->rho = cv.take<float>(n);
+    h->nbr = cv.take<int>(n);
+    h->acc = cv.take<float4>(n);
+    h->touched = cv.take<int>(n);
+    h->infl = cv.take<float4>(n);
+    h->slot_of_boid = cv.take<int>(nb);
+    h->bpos = cv.take<float4>(nb);
+    h->bvel = cv.take<float4>(nb);
+    h->bpos_s = cv.take<float4>(nb);
+    h->bvel_s = cv.take<float4>(nb);
+    h->bkey = cv.take<unsigned>(nb);
+    h->brank = cv.take<unsigned>(nb);
+    h->btmp = cv.take<int>(nb > Cb ? nb : Cb);
+    h->bcount = cv.take<unsigned>(Cb);
+    h->bstart = cv.take<unsigned>(Cb + 1);
+    h->bscan_part = cv.take<unsigned>((size_t)scan_parts((int)Cb) + 1);
+    h->bbig_list = cv.take<int>(Cb);
+    h->bbig_count = cv.take<unsigned>(1);
+    h->fb = cv.take<float4>(nb);
+    h->err = cv.take<unsigned>(4);
+    return (size_t)((cv.off + 255) & ~(uintptr_t)255);
+}
+
+// ---------------------------------------------------------- state kernels
+
+__global__ void k_load_state(const float4* __restrict__ fpos, const float4* __restrict__ fvel,
+                             const float4* __restrict__ bpos_in, const float4* __restrict__ bvel_in,
+                             int nf, int nb, float4* __restrict__ pos, float4* __restrict__ vel,
+                             float4* __restrict__ bpos, float4* __restrict__ bvel, int* __restrict__ slot_of_boid)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf + nb) return;
+    float4 p, v;
+    if (i < nb) {
+        p = bpos_in[i];
+        v = bvel_in[i];
+        p.w = __int_as_float(i);
+        v.w = 0.0f;
+        bpos[i] = p;
+        bvel[i] = v;
+        slot_of_boid[i] = i;
+    } else {
+        p = fpos[i - nb];
+        v = fvel[i - nb];
+        p.w = __int_as_float(i);
+        v.w = 0.0f;
+    }
+    pos[i] = p;
+    vel[i] = v;
+}
+
+__global__ void k_store_state(const float4* __restrict__ pos, const float4* __restrict__ vel,
+                              const float4* __restrict__ bpos, const float4* __restrict__ bvel, int n, int nb,
+                              float4* __restrict__ fpos, float4* __restrict__ fvel, float4* __restrict__ opos,
+                              float4* __restrict__ ovel)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float4 p = pos[i];
+        int id = __float_as_int(p.w);
+        if (id >= nb) {
+            float4 v = vel[i];
+            fpos[id - nb] = make_float4(p.x, p.y, p.z, 0.0f);
+            fvel[id - nb] = make_float4(v.x, v.y, v.z, 0.0f);
+        }
+    } else if (i < n + nb) {
+        int b = i - n;
+        float4 p = bpos[b], v = bvel[b];
+        opos[b] = make_float4(p.x, p.y, p.z, 0.0f);
+        ovel[b] = make_float4(v.x, v.y, v.z, 0.0f);
+    }
+}
+
+// out[id(slot)] = field[slot] for 4-, 16-byte fields
+template <class T>
+__global__ void k_by_id(const float4* __restrict__ pos, const T* __restrict__ field, int n,
+                        T* __restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[__float_as_int(pos[i].w)] = field[i];
+}
+
+__global__ void k_pressure_by_id(const float4* __restrict__ pos, const float* __restrict__ rho, int n,
+                                 float k, float rho0, float* __restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[__float_as_int(pos[i].w)] = k * (rho[i] - rho0);
+}
+
+__global__ void k_ids(const float4* __restrict__ pos, int n, int* __restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float_as_int(pos[i].w);
+}
+
+// ------------------------------------------------------------------ API
+
+extern "C" {
+
+const char* sph_last_error(sph_handle* h) { return h ? h->msg : g_msg; }
+
+long long sph_launch_count(sph_handle* h) { return h ? h->launches : 0; }
+
+int sph_grid_dims(const sph_params* p, int which, int dims[3])
+{
+    if (!p || !dims || (which != 0 && which != 1)) return fail(nullptr, SPH_ERR_ARG, "bad arguments");
+    GridDesc g;
+    float d = which ? p->boid_cell_size : p->cell_size;
+    if (!(d > 0.0f)) return fail(nullptr, SPH_ERR_ARG, "cell size must be > 0");
+    if (make_grid(p->box_min, p->box_max, d, &g) != SPH_OK) return fail(nullptr, SPH_ERR_OVERFLOW, "grid too large");
+    for (int a = 0; a < 3; ++a) dims[a] = g.dim[a];
+    return SPH_OK;
+}
+
+int sph_lattice_mass(const sph_params* p, float spacing, float* mass)
+{
+    if (!p || !mass || !(spacing > 0.0f) || !(p->h > 0.0f) || !(p->rho0 > 0.0f))
+        return fail(nullptr, SPH_ERR_ARG, "bad arguments");
+    const double h = p->h, s = spacing, pi = 3.14159265358979323846;
+    const int R = (int)ceil(h / s) + 1;
+    double acc = 0.0;
+    for (int z = -R; z <= R; ++z)
+        for (int y = -R; y <= R; ++y)
+            for (int x = -R; x <= R; ++x) {
+                double r2 = (double)(x * x + y * y + z * z) * s * s;
+                if (r2 < h * h) {
+                    double t = h * h - r2;
+                    acc += t * t * t;
+                }
+            }
+    *mass = (float)((double)p->rho0 / (315.0 / (64.0 * pi * pow(h, 9)) * acc));
+    return SPH_OK;
+}
+
+int sph_workspace_size(const sph_params* p, int n_fluid, int n_boid, size_t* bytes)
+{
+    int rc = validate(p, n_fluid, n_boid);
+    if (rc != SPH_OK) return rc;
+    if (!bytes) return fail(nullptr, SPH_ERR_ARG, "bytes is NULL");
+    sph_handle tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.n_fluid = n_fluid;
+    tmp.n_boid = n_boid;
+    tmp.n = n_fluid + n_boid;
+    make_const(p, n_fluid, n_boid, &tmp.c);
+    *bytes = carve(&tmp, 0);
+    return SPH_OK;
+}
+
+int sph_create(const sph_params* p, int n_fluid, int n_boid, void* workspace, size_t ws_bytes,
+               sph_handle** out)
+{
+    int rc = validate(p, n_fluid, n_boid);
+    if (rc != SPH_OK) return rc;
+    if (!out) return fail(nullptr, SPH_ERR_ARG, "out is NULL");
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(nullptr, SPH_ERR_ARG, "workspace must be non-NULL and 256-byte aligned");
+    sph_handle* h = new (std::nothrow) sph_handle;
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "out of host memory");
+    memset(h, 0, sizeof(*h));
+    h->p = *p;
+    h->n_fluid = n_fluid;
+    h->n_boid = n_boid;
+    h->n = n_fluid + n_boid;
+    make_const(p, n_fluid, n_boid, &h->c);
+    size_t need = carve(h, (uintptr_t)workspace);
+    if (ws_bytes < need) {
+        delete h;
+        return fail(nullptr, SPH_ERR_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+    }
+    cudaError_t e = cudaMemsetAsync(h->err, 0, 4 * sizeof(unsigned), 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(nullptr, SPH_ERR_CUDA, "cudaMemset of the error word: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return SPH_OK;
+}
+
+static void prof_free(sph_handle* h)
+{
+    for (int i = 0; i < 2 * h->prof_cap; ++i) cudaEventDestroy(h->prof_ev[i]);
+    free(h->prof_ev);
+    free(h->prof_kind);
+    h->prof_ev = nullptr;
+    h->prof_kind = nullptr;
+    h->prof_cap = h->prof_n = 0;
+}
+
+void sph_destroy(sph_handle* h)
+{
+    if (!h) return;
+    prof_free(h);
+    delete h;
+}
+
+int sph_profile_enable(sph_handle* h, int max_passes)
+{
+    if (!h || max_passes < 0) return fail(h, SPH_ERR_ARG, "bad arguments");
+    prof_free(h);
+    if (max_passes == 0) return SPH_OK;
+    h->prof_ev = (cudaEvent_t*)calloc((size_t)max_passes * 2, sizeof(cudaEvent_t));
+    h->prof_kind = (int*)calloc((size_t)max_passes, sizeof(int));
+    if (!h->prof_ev || !h->prof_kind) {
+        prof_free(h);
+        return fail(h, SPH_ERR_ARG, "out of host memory");
+    }
+    for (int i = 0; i < 2 * max_passes; ++i) {
+        cudaError_t e = cudaEventCreate(&h->prof_ev[i]);
+        if (e != cudaSuccess) {
+            h->prof_cap = i / 2;
+            prof_free(h);
+            return fail(h, SPH_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+        }
+        h->prof_cap = (i + 1) / 2;
+    }
+    h->prof_cap = max_passes;
+    h->prof_n = 0;
+    return SPH_OK;
+}
+
+int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds)
+{
+    if (!h || !ms || !passes || nkinds < 0) return fail(h, SPH_ERR_ARG, "bad arguments");
+    for (int k = 0; k < nkinds; ++k) {
+        ms[k] = 0.0;
+        passes[k] = 0;
+    }
+    if (h->prof_n > 0) CUDA_TRY(h, cudaEventSynchronize(h->prof_ev[2 * h->prof_n - 1]));
+    for (int i = 0; i < h->prof_n; ++i) {
+        float t = 0.0f;
+        CUDA_TRY(h, cudaEventElapsedTime(&t, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+        int k = h->prof_kind[i];
+        if (k < nkinds) {
+            ms[k] += t;
+            passes[k] += 1;
+        }
+    }
+    h->prof_n = 0;
+    return SPH_OK;
+}
+
+static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15) == 0; }
+
+int sph_set_state(sph_handle* h, const float* fluid_pos4, const float* fluid_vel4, const float* boid_pos4,
+                  const float* boid_vel4, int on_host, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    const int nf = h->n_fluid, nb = h->n_boid;
+    if ((nf && (!fluid_pos4 || !fluid_vel4)) || (nb && (!boid_pos4 || !boid_vel4)))
+        return fail(h, SPH_ERR_ARG, "state pointer is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const float4 *fp = (const float4*)fluid_pos4, *fv = (const float4*)fluid_vel4;
+    const float4 *bp = (const float4*)boid_pos4, *bv = (const float4*)boid_vel4;
+    if (on_host) {
+        // stage in the sorted scratch arrays: fluid at [0, nf), boids at [nf, nf + nb)
+        if (nf) {
+            CUDA_TRY(h, cudaMemcpyAsync(h->pos_s, fluid_pos4, (size_t)nf * 16, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(h, cudaMemcpyAsync(h->vel_s, fluid_vel4, (size_t)nf * 16, cudaMemcpyHostToDevice, s));
+        }
+        if (nb) {
+            CUDA_TRY(h, cudaMemcpyAsync(h->pos_s + nf, boid_pos4, (size_t)nb * 16, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(h, cudaMemcpyAsync(h->vel_s + nf, boid_vel4, (size_t)nb * 16, cudaMemcpyHostToDevice, s));
+        }
+        fp = h->pos_s;
+        fv = h->vel_s;
+        bp = h->pos_s + nf;
+        bv = h->vel_s + nf;
+    } else if (!aligned16(fp) || !aligned16(fv) || !aligned16(bp) || !aligned16(bv)) {
+        return fail(h, SPH_ERR_ARG, "device state pointers must be 16-byte aligned");
+    }
+    if (h->n > 0) {
+        k_load_state<<<(h->n + 255) / 256, 256, 0, s>>>(fp, fv, bp, bv, nf, nb, h->pos, h->vel, h->bpos, h->bvel,
+                                                         h->slot_of_boid);
+        ++h->launches;
+        CUDA_TRY(h, cudaGetLastError());
+    }
+    if (on_host) CUDA_TRY(h, cudaStreamSynchronize(s));
+    h->has_state = true;
+    h->keys_ready = false;
+    h->has_step = false;
+    return SPH_OK;
+}
+
+int sph_get_state(sph_handle* h, float* fluid_pos4, float* fluid_vel4, float* boid_pos4, float* boid_vel4,
+                  int on_host, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    const int nf = h->n_fluid, nb = h->n_boid;
+    if ((nf && (!fluid_pos4 || !fluid_vel4)) || (nb && (!boid_pos4 || !boid_vel4)))
+        return fail(h, SPH_ERR_ARG, "state pointer is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    float4 *fp = (float4*)fluid_pos4, *fv = (float4*)fluid_vel4, *bp = (float4*)boid_pos4, *bv = (float4*)boid_vel4;
+    if (on_host) {
+        fp = h->pos_s;
+        fv = h->vel_s;
+        bp = h->pos_s + nf;
+        bv = h->vel_s + nf;
+    } else if (!aligned16(fp) || !aligned16(fv) || !aligned16(bp) || !aligned16(bv)) {
+        return fail(h, SPH_ERR_ARG, "device state pointers must be 16-byte aligned");
+    }
+    if (h->n + nb > 0) {
+        k_store_state<<<(h->n + nb + 255) / 256, 256, 0, s>>>(h->pos, h->vel, h->bpos, h->bvel, h->n, nb, fp, fv,
+                                                               bp, bv);
+        ++h->launches;
+        CUDA_TRY(h, cudaGetLastError());
+    }
+    if (on_host) {
+        if (nf) {
+            CUDA_TRY(h, cudaMemcpyAsync(fluid_pos4, h->pos_s, (size_t)nf * 16, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(h, cudaMemcpyAsync(fluid_vel4, h->vel_s, (size_t)nf * 16, cudaMemcpyDeviceToHost, s));
+        }
+        if (nb) {
+            CUDA_TRY(h, cudaMemcpyAsync(boid_pos4, h->pos_s + nf, (size_t)nb * 16, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(h, cudaMemcpyAsync(boid_vel4, h->vel_s + nf, (size_t)nb * 16, cudaMemcpyDeviceToHost, s));
+        }
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        h->has_step = false;  // the scratch arrays held the staged copy
+    }
+    return SPH_OK;
+}
+
+// Keys (if needed), scan, scatter and per-cell sort + gather of the state
+// into the sorted scratch arrays.  consume = true zeroes the counts for the
+// next step's keys.
+static int bin_state(sph_handle* h, cudaStream_t s, bool consume)
+{
+    const StepConst& c = h->c;
+    if (!h->keys_ready) {
+        prof_begin(h, SPH_KIND_KEYS, s);
+        CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)c.g.ncells * sizeof(unsigned), s));
+        CUDA_TRY(h, launch_keys(h->pos, c.n, c.g, h->key, h->rank, h->count, h->err, s, &h->launches));
+        prof_end(h, s);
+        h->keys_ready = true;
+    }
+    prof_begin(h, SPH_KIND_SCAN, s);
+    CUDA_TRY(h, launch_scan(h->count, c.g.ncells, h->scan_part, h->cell_start, s, &h->launches));
+    prof_end(h, s);
+    prof_begin(h, SPH_KIND_SCATTER, s);
+    CUDA_TRY(h, launch_scatter(h->key, h->rank, h->cell_start, c.n, h->tmp, s, &h->launches));
+    prof_end(h, s);
+    prof_begin(h, SPH_KIND_SORT, s);
+    CUDA_TRY(h, launch_cellsort_gather(h->cell_start, c.g.ncells, h->tmp, h->pos, h->vel, h->pos_s, h->vel_s, c.nb,
+                                       h->slot_of_boid, h->big_list, h->big_count, s, &h->launches));
+    prof_end(h, s);
+    if (consume) {
+        CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)c.g.ncells * sizeof(unsigned), s));
+        h->keys_ready = false;
+    }
+    return SPH_OK;
+}
+
+int sph_step(sph_handle* h, int nsteps, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, SPH_ERR_ARG, "nsteps < 0");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const StepConst& c = h->c;
+    for (int it = 0; it < nsteps; ++it) {
+        int rc = bin_state(h, s, true);
+        if (rc != SPH_OK) return rc;
+        prof_begin(h, SPH_KIND_DENSITY, s);
+        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, c, h->rho, h->nbr, h->err, s, &h->launches));
+        prof_end(h, s);
+        prof_begin(h, SPH_KIND_FORCES, s);
+        CUDA_TRY(h, launch_forces(0, h->pos_s, h->vel_s, h->rho, h->cell_start, c, h->acc, h->touched, h->infl,
+                                  h->fb, h->pos, h->vel, h->key, h->rank, h->count, h->err, s, &h->launches));
+        prof_end(h, s);
+        if (c.nb > 0) {
+            prof_begin(h, SPH_KIND_BOID_BIN, s);
+            CUDA_TRY(h, cudaMemsetAsync(h->bcount, 0, (size_t)c.gb.ncells * sizeof(unsigned), s));
+            CUDA_TRY(h, launch_boid_keys(h->bpos, c.nb, c.gb, h->bkey, h->brank, h->bcount, s, &h->launches));
+            CUDA_TRY(h, launch_scan(h->bcount, c.gb.ncells, h->bscan_part, h->bstart, s, &h->launches));
+            CUDA_TRY(h, launch_scatter(h->bkey, h->brank, h->bstart, c.nb, h->btmp, s, &h->launches));
+            CUDA_TRY(h, launch_cellsort_gather(h->bstart, c.gb.ncells, h->btmp, h->bpos, h->bvel, h->bpos_s,
+                                               h->bvel_s, 0, nullptr, h->bbig_list, h->bbig_count, s,
+                                               &h->launches));
+            prof_end(h, s);
+            prof_begin(h, SPH_KIND_BOID_RULES, s);
+            CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, c, h->fb, h->bpos, h->bvel, h->pos,
+                                          h->vel, h->slot_of_boid, h->key, h->rank, h->count, h->err, s,
+                                          &h->launches));
+            prof_end(h, s);
+        }
+        h->keys_ready = true;  // the force and boid kernels emitted the next keys
+        h->has_step = true;
+    }
+    return SPH_OK;
+}
+
+int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (mode != 0) return fail(h, SPH_ERR_ARG, "unsupported mode %d", mode);
+    if (h->n_boid && (!out_f4 || !aligned16(out_f4))) return fail(h, SPH_ERR_ARG, "out must be 16-byte aligned");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    if (h->n_boid == 0) return SPH_OK;
+    int rc = bin_state(h, s, false);
+    if (rc != SPH_OK) return rc;
+    const StepConst& c = h->c;
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, c, h->rho, h->nbr, h->err, s, &h->launches));
+    CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, c, nullptr, nullptr, nullptr,
+                              (float4*)out_f4, nullptr, nullptr, nullptr, nullptr, nullptr, h->err, s,
+                              &h->launches));
+    h->has_step = false;
+    return SPH_OK;
+}
+
+int sph_debug_neighbors(sph_handle* h, int* counts, const long long* offsets, int* list, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (!counts || ((offsets == nullptr) != (list == nullptr)))
+        return fail(h, SPH_ERR_ARG, "counts must be given; offsets and list together");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    int rc = bin_state(h, s, false);
+    if (rc != SPH_OK) return rc;
+    CUDA_TRY(h, launch_neighbor_list(h->pos_s, h->cell_start, h->c, counts, offsets, list, s, &h->launches));
+    h->has_step = false;
+    return SPH_OK;
+}
+
+int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (!out) return fail(h, SPH_ERR_ARG, "out is NULL");
+    if (!h->has_step) return fail(h, SPH_ERR_STATE, "no step since the state was loaded or staged");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const int n = h->n, nb = h->n_boid;
+    const int blocks = (n + 255) / 256;
+    size_t bytes = 0;
+    void* dst = on_host ? (void*)h->pos_s : out;  // staging: the sorted scratch array
+    switch (field) {
+    case SPH_FIELD_RHO:
+        if (n) k_by_id<float><<<blocks, 256, 0, s>>>(h->pos, h->rho, n, (float*)dst);
+        bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_PRESSURE:
+        if (n) k_pressure_by_id<<<blocks, 256, 0, s>>>(h->pos, h->rho, n, h->c.k, h->c.rho0, (float*)dst);
+        bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_ACC:
+        if (n) k_by_id<float4><<<blocks, 256, 0, s>>>(h->pos, h->acc, n, (float4*)dst);
+        bytes = (size_t)n * 16;
+        break;
+    case SPH_FIELD_TOUCHED:
+        if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->touched, n, (int*)dst);
+        bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_INFLUENCE:
+        if (n) k_by_id<float4><<<blocks, 256, 0, s>>>(h->pos, h->infl, n, (float4*)dst);
+        bytes = (size_t)n * 16;
+        break;
+    case SPH_FIELD_NBR_COUNT:
+        if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->nbr, n, (int*)dst);
+        bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_KEYS:
+        CUDA_TRY(h, launch_slot_keys(h->cell_start, h->c.g.ncells, (unsigned*)h->tmp, s, &h->launches));
+        if (n) k_by_id<unsigned><<<blocks, 256, 0, s>>>(h->pos, (const unsigned*)h->tmp, n, (unsigned*)dst);
+        bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_PERM:
+        if (n) k_ids<<<blocks, 256, 0, s>>>(h->pos, n, (int*)dst);
+        bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_CELL_START:
+        dst = out;
+        bytes = ((size_t)h->c.g.ncells + 1) * 4;
+        CUDA_TRY(h, cudaMemcpyAsync(out, h->cell_start, bytes, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+        if (on_host) CUDA_TRY(h, cudaStreamSynchronize(s));
+        return SPH_OK;
+    case SPH_FIELD_FB:
+        bytes = (size_t)nb * 16;
+        if (nb) CUDA_TRY(h, cudaMemcpyAsync(dst, h->fb, bytes, cudaMemcpyDeviceToDevice, s));
+        break;
+    case SPH_FIELD_BOID_PERM:
+        if (nb) k_ids<<<(nb + 255) / 256, 256, 0, s>>>(h->bpos_s, nb, (int*)dst);
+        bytes = (size_t)nb * 4;
+        break;
+    case SPH_FIELD_BOID_KEYS:
+        CUDA_TRY(h, launch_slot_keys(h->bstart, h->c.gb.ncells, (unsigned*)h->btmp, s, &h->launches));
+        if (nb) k_by_id<unsigned><<<(nb + 255) / 256, 256, 0, s>>>(h->bpos_s, (const unsigned*)h->btmp, nb, (unsigned*)dst);
+        bytes = (size_t)nb * 4;
+        break;
+    case SPH_FIELD_BOID_CELL_START:
+        bytes = ((size_t)h->c.gb.ncells + 1) * 4;
+        CUDA_TRY(h, cudaMemcpyAsync(out, h->bstart, bytes, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+        if (on_host) CUDA_TRY(h, cudaStreamSynchronize(s));
+        return SPH_OK;
+    default:
+        return fail(h, SPH_ERR_ARG, "unknown field %d", field);
+    }
+    if (field != SPH_FIELD_FB && field != SPH_FIELD_KEYS && field != SPH_FIELD_BOID_KEYS) ++h->launches;
+    if (field == SPH_FIELD_KEYS || field == SPH_FIELD_BOID_KEYS) ++h->launches;
+    CUDA_TRY(h, cudaGetLastError());
+    if (on_host) {
+        if (bytes) CUDA_TRY(h, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+    }
+    return SPH_OK;
+}
+
+int sph_status(sph_handle* h, unsigned* bits)
+{
+    if (!h || !bits) return fail(h, SPH_ERR_ARG, "bad arguments");
+    unsigned v = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&v, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->last_stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->last_stream));
+    *bits = v;
+    return SPH_OK;
+}
+
+int sph_clear_status(sph_handle* h, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    h->last_stream = (cudaStream_t)stream;
+    CUDA_TRY(h, cudaMemsetAsync(h->err, 0, sizeof(unsigned), (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,306 @@
+"""ctypes binding of the step library (include/sph.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of ``libsph_gb300.so``.  Importing this module fails loudly if the
+library has not been built (``python -m paper_2311_15088_gb300.build``);
+there is no CPU fallback.
+
+:class:`Scene` is a thin convenience wrapper that keeps the workspace in a
+torch tensor and passes torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsph_gb300.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_2311_15088_gb300.build`")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+SPH_OK, SPH_ERR_ARG, SPH_ERR_CUDA, SPH_ERR_OVERFLOW, SPH_ERR_TIMEOUT, SPH_ERR_STATE = range(6)
+SPH_MULLER3D, SPH_PAPER_LITERAL = 0, 1
+SPH_COUPLE_FORCE = 0
+SPH_DEV_NONFINITE, SPH_DEV_CLAMPED = 1, 2
+
+FIELDS = {
+    "rho": (0, np.float32, 1), "pressure": (1, np.float32, 1), "acc": (2, np.float32, 4),
+    "touched": (3, np.int32, 1), "influence": (4, np.float32, 4), "nbr_count": (5, np.int32, 1),
+    "keys": (6, np.uint32, 1), "perm": (7, np.int32, 1), "cell_start": (8, np.uint32, 1),
+    "fb": (9, np.float32, 4), "boid_keys": (10, np.uint32, 1), "boid_perm": (11, np.int32, 1),
+    "boid_cell_start": (12, np.uint32, 1),
+}
+
+
+class SphParams(ctypes.Structure):
+    _fields_ = [
+        ("h", ctypes.c_float), ("rho0", ctypes.c_float), ("k", ctypes.c_float), ("mu", ctypes.c_float),
+        ("dt", ctypes.c_float), ("gx", ctypes.c_float), ("gy", ctypes.c_float), ("gz", ctypes.c_float),
+        ("mass", ctypes.c_float), ("box_min", ctypes.c_float * 3), ("box_max", ctypes.c_float * 3),
+        ("cell_size", ctypes.c_float), ("const_set", ctypes.c_int), ("wall_restitution", ctypes.c_float),
+        ("r_sep", ctypes.c_float), ("r_vis", ctypes.c_float), ("w_sep", ctypes.c_float),
+        ("w_align", ctypes.c_float), ("w_coh", ctypes.c_float), ("sph_factor", ctypes.c_float),
+        ("v_min", ctypes.c_float), ("v_max", ctypes.c_float), ("edge_turn", ctypes.c_float),
+        ("boid_cell_size", ctypes.c_float), ("coupling_mode", ctypes.c_int),
+    ]
+
+
+_vp, _i, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+_P = ctypes.POINTER(SphParams)
+_sig = {
+    "sph_workspace_size": (_i, [_P, _i, _i, ctypes.POINTER(_sz)]),
+    "sph_grid_dims": (_i, [_P, _i, _vp]),
+    "sph_lattice_mass": (_i, [_P, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "sph_create": (_i, [_P, _i, _i, _vp, _sz, ctypes.POINTER(_vp)]),
+    "sph_set_state": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp]),
+    "sph_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp]),
+    "sph_step": (_i, [_vp, _i, _vp]),
+    "sph_boid_forces": (_i, [_vp, _i, _vp, _vp]),
+    "sph_get_fields": (_i, [_vp, _i, _vp, _i, _vp]),
+    "sph_debug_neighbors": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "sph_status": (_i, [_vp, ctypes.POINTER(ctypes.c_uint)]),
+    "sph_clear_status": (_i, [_vp, _vp]),
+    "sph_last_error": (ctypes.c_char_p, [_vp]),
+    "sph_launch_count": (ctypes.c_longlong, [_vp]),
+    "sph_destroy": (None, [_vp]),
+    "sph_profile_enable": (_i, [_vp, _i]),
+    "sph_profile_read": (_i, [_vp, _vp, _vp, _i]),
+}
+for _name, (_res, _args) in _sig.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sph error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc, handle=None):
+    if rc != SPH_OK:
+        raise SphError(rc, (_lib.sph_last_error(handle) or b"").decode())
+
+
+def make_params(p: dict) -> SphParams:
+    """Fill the library's parameter struct from a parameter dict."""
+    if p.get("mass") is None:
+        raise ValueError("params['mass'] must be set")
+    s = SphParams()
+    for name, ctype in SphParams._fields_:
+        if name in ("box_min", "box_max"):
+            getattr(s, name)[:] = [float(v) for v in p[name]]
+        elif ctype is ctypes.c_int:
+            setattr(s, name, int(p[name]))
+        else:
+            setattr(s, name, float(p[name]))
+    return s
+
+
+# ----------------------------------------------------------- C-ABI names
+
+def sph_workspace_size(params: dict, n_fluid: int, n_boid: int) -> int:
+    out = _sz()
+    _check(_lib.sph_workspace_size(ctypes.byref(make_params(params)), n_fluid, n_boid, ctypes.byref(out)))
+    return int(out.value)
+
+
+def sph_grid_dims(params: dict, which: int = 0):
+    d = (ctypes.c_int * 3)()
+    _check(_lib.sph_grid_dims(ctypes.byref(make_params(params)), which, ctypes.cast(d, _vp)))
+    return tuple(d)
+
+
+def sph_lattice_mass(params: dict, spacing: float) -> float:
+    q = dict(params)
+    if q.get("mass") is None:
+        q["mass"] = 1.0
+    m = ctypes.c_float()
+    _check(_lib.sph_lattice_mass(ctypes.byref(make_params(q)), float(spacing), ctypes.byref(m)))
+    return float(m.value)
+
+
+def sph_create(params: dict, n_fluid: int, n_boid: int, workspace_ptr: int, ws_bytes: int):
+    h = _vp()
+    _check(_lib.sph_create(ctypes.byref(make_params(params)), n_fluid, n_boid, workspace_ptr, ws_bytes,
+                           ctypes.byref(h)))
+    return h
+
+
+def sph_set_state(h, fluid_pos, fluid_vel, boid_pos, boid_vel, on_host: int, stream: int):
+    _check(_lib.sph_set_state(h, fluid_pos, fluid_vel, boid_pos, boid_vel, on_host, stream), h)
+
+
+def sph_get_state(h, fluid_pos, fluid_vel, boid_pos, boid_vel, on_host: int, stream: int):
+    _check(_lib.sph_get_state(h, fluid_pos, fluid_vel, boid_pos, boid_vel, on_host, stream), h)
+
+
+def sph_step(h, nsteps: int, stream: int):
+    _check(_lib.sph_step(h, nsteps, stream), h)
+
+
+def sph_boid_forces(h, mode: int, out_ptr: int, stream: int):
+    _check(_lib.sph_boid_forces(h, mode, out_ptr, stream), h)
+
+
+def sph_get_fields(h, field: int, out_ptr: int, on_host: int, stream: int):
+    _check(_lib.sph_get_fields(h, field, out_ptr, on_host, stream), h)
+
+
+def sph_debug_neighbors(h, counts_ptr: int, offsets_ptr, list_ptr, stream: int):
+    _check(_lib.sph_debug_neighbors(h, counts_ptr, offsets_ptr, list_ptr, stream), h)
+
+
+def sph_status(h) -> int:
+    bits = ctypes.c_uint()
+    _check(_lib.sph_status(h, ctypes.byref(bits)), h)
+    return int(bits.value)
+
+
+def sph_clear_status(h, stream: int):
+    _check(_lib.sph_clear_status(h, stream), h)
+
+
+def sph_last_error(h) -> str:
+    return (_lib.sph_last_error(h) or b"").decode()
+
+
+def sph_launch_count(h) -> int:
+    return int(_lib.sph_launch_count(h))
+
+
+def sph_destroy(h):
+    _lib.sph_destroy(h)
+
+
+KINDS = ("keys", "scan", "scatter", "sort", "density", "forces", "boid_bin", "boid_rules")
+
+
+def sph_profile_enable(h, max_passes: int):
+    _check(_lib.sph_profile_enable(h, max_passes), h)
+
+
+def sph_profile_read(h) -> dict:
+    """Summed milliseconds and pass counts per kind since the last read."""
+    ms = (ctypes.c_double * len(KINDS))()
+    n = (ctypes.c_longlong * len(KINDS))()
+    _check(_lib.sph_profile_read(h, ctypes.cast(ms, _vp), ctypes.cast(n, _vp), len(KINDS)), h)
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KINDS)}
+
+
+# ------------------------------------------------------ torch convenience
+
+class Scene:
+    """A scene whose workspace and state live in torch tensors on ``device``.
+
+    Inputs are float32 ``(n, 4)`` arrays (numpy or torch); outputs are torch
+    tensors on the device.  All calls use torch's current stream."""
+
+    def __init__(self, params: dict, n_fluid: int, n_boid: int, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.params = dict(params)
+        self.n_fluid, self.n_boid = int(n_fluid), int(n_boid)
+        self.n = self.n_fluid + self.n_boid
+        self.device = torch.device(device)
+        nbytes = sph_workspace_size(self.params, self.n_fluid, self.n_boid)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self.handle = sph_create(self.params, self.n_fluid, self.n_boid, self._ws_ptr, nbytes)
+        self.dims = sph_grid_dims(self.params, 0)
+        self.bdims = sph_grid_dims(self.params, 1)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            sph_destroy(h)
+            self.handle = None
+
+    @property
+    def stream(self) -> int:
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def _dev4(self, a, n):
+        t = self.torch.as_tensor(np.asarray(a, np.float32) if not self.torch.is_tensor(a) else a)
+        t = t.to(device=self.device, dtype=self.torch.float32).reshape(n, 4).contiguous()
+        return t
+
+    def set_state(self, fluid_pos, fluid_vel, boid_pos, boid_vel):
+        ts = [self._dev4(fluid_pos, self.n_fluid), self._dev4(fluid_vel, self.n_fluid),
+              self._dev4(boid_pos, self.n_boid), self._dev4(boid_vel, self.n_boid)]
+        self._keep = ts
+        sph_set_state(self.handle, *[t.data_ptr() if t.numel() else None for t in ts], 0, self.stream)
+
+    def set_state_host(self, fluid_pos, fluid_vel, boid_pos, boid_vel):
+        """Upload from (preferably pinned) host tensors; synchronises the stream."""
+        ts = [fluid_pos, fluid_vel, boid_pos, boid_vel]
+        sph_set_state(self.handle, *[t.data_ptr() if t.numel() else None for t in ts], 1, self.stream)
+
+    def get_state(self):
+        t = self.torch
+        out = [t.empty((self.n_fluid, 4), dtype=t.float32, device=self.device),
+               t.empty((self.n_fluid, 4), dtype=t.float32, device=self.device),
+               t.empty((self.n_boid, 4), dtype=t.float32, device=self.device),
+               t.empty((self.n_boid, 4), dtype=t.float32, device=self.device)]
+        sph_get_state(self.handle, *[o.data_ptr() if o.numel() else None for o in out], 0, self.stream)
+        return out
+
+    def get_state_host(self, outs):
+        """Download into host tensors (pinned for speed); synchronises the stream."""
+        sph_get_state(self.handle, *[o.data_ptr() if o.numel() else None for o in outs], 1, self.stream)
+
+    def step(self, nsteps: int = 1):
+        sph_step(self.handle, nsteps, self.stream)
+
+    def field(self, name: str):
+        t = self.torch
+        code, dtype, width = FIELDS[name]
+        if name == "cell_start":
+            n = self.dims[0] * self.dims[1] * self.dims[2] + 1
+        elif name == "boid_cell_start":
+            n = self.bdims[0] * self.bdims[1] * self.bdims[2] + 1
+        elif name in ("fb", "boid_keys", "boid_perm"):
+            n = self.n_boid
+        else:
+            n = self.n
+        tdtype = {np.float32: t.float32, np.int32: t.int32, np.uint32: t.int32}[dtype]
+        out = t.empty((n, width) if width > 1 else (n,), dtype=tdtype, device=self.device)
+        if out.numel():
+            sph_get_fields(self.handle, code, out.data_ptr(), 0, self.stream)
+        return out
+
+    def boid_forces(self):
+        t = self.torch
+        out = t.empty((self.n_boid, 4), dtype=t.float32, device=self.device)
+        sph_boid_forces(self.handle, 0, out.data_ptr() if out.numel() else None, self.stream)
+        return out
+
+    def neighbors(self, lists: bool = True):
+        t = self.torch
+        counts = t.zeros(self.n, dtype=t.int32, device=self.device)
+        sph_debug_neighbors(self.handle, counts.data_ptr(), None, None, self.stream)
+        if not lists:
+            return counts, None, None
+        offsets = t.zeros(self.n + 1, dtype=t.int64, device=self.device)
+        offsets[1:] = t.cumsum(counts.to(t.int64), 0)
+        total = int(offsets[-1].item())
+        lst = t.zeros(max(total, 1), dtype=t.int32, device=self.device)
+        sph_debug_neighbors(self.handle, counts.data_ptr(), offsets.data_ptr(), lst.data_ptr(), self.stream)
+        return counts, offsets, lst[:total]
+
+    def status(self) -> int:
+        return sph_status(self.handle)
+
+    def clear_status(self):
+        sph_clear_status(self.handle, self.stream)
+
+    @property
+    def launches(self) -> int:
+        return sph_launch_count(self.handle)

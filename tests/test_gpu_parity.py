@@ -1,0 +1,200 @@
+"""GPU step vs the CPU oracle, element by element (needs a GB300).
+
+Every case runs the CUDA path through the C ABI (via the ctypes binding)
+and the oracle on the same seeded float32 state, then compares every field
+of one step with the tolerances listed in tests/parity.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_15088_gb300 import scenes
+from paper_2311_15088_gb300.sph import Scene
+
+from parity import compare_step, gpu_outputs, lattice_params, oracle_step, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _state_of(s, p):
+    fp, fv, bp, bv = (t.cpu().numpy() for t in s.get_state())
+    return dict(params=p, fluid_pos=fp, fluid_vel=fv, boid_pos=bp, boid_vel=bv)
+
+
+def _check(p, sc):
+    nb = len(sc["boid_pos"])
+    s = run_gpu(p, sc, steps=1)
+    g = gpu_outputs(s)
+    o = oracle_step(p, sc)
+    compare_step(p, g, o, nb)
+    assert s.status() & 1 == 0
+    return s, g, o
+
+
+def test_dam_break_4096_first_step():
+    sc = scenes.dam_break_small()
+    p = lattice_params(sc)
+    _check(p, sc)
+
+
+def test_dam_break_4096_after_80_gpu_steps():
+    """Run the GPU 80 steps (the column collapses and compresses), then one
+    more step on the GPU and in the oracle from the GPU's state."""
+    sc = scenes.dam_break_small()
+    p = lattice_params(sc)
+    s = run_gpu(p, sc, steps=80)
+    st = _state_of(s, p)
+    _check(p, st)
+
+
+@pytest.mark.parametrize("const_set", [0, 1])
+def test_fluid_with_boids_inside(const_set):
+    """12k particles with 300 boids moving through the fluid: coupling,
+    touched_by_boid and boid_influence are all exercised."""
+    sc = scenes.scaled_block(12000, 300, (0.6, 0.6, 0.6), (0.6, 0.4, 0.6), seed=77)
+    sc["boid_pos"][:, 1] *= np.float32(0.4 / 0.6)
+    p = dict(sc["params"], const_set=const_set)
+    _s, _g, o = _check(p, sc)
+    assert o["touched"].sum() > 1000
+
+
+def test_column_262144_first_step():
+    sc = scenes.dam_break_column()
+    p = lattice_params(sc)
+    _check(p, sc)
+
+
+def test_neighbor_lists_bit_exact():
+    sc = scenes.scaled_block(6000, 40, (0.5, 0.5, 0.5), (0.5, 0.5, 0.5), seed=3)
+    p = sc["params"]
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    counts, offsets, lst = s.neighbors()
+    pos = np.concatenate([sc["boid_pos"], sc["fluid_pos"]])
+    c2, o2, l2 = oracle.neighbors(p, pos, n_att=len(sc["boid_pos"]))
+    assert np.array_equal(counts.cpu().numpy(), c2)
+    assert np.array_equal(offsets.cpu().numpy(), o2)
+    assert np.array_equal(lst.cpu().numpy(), l2)
+
+
+def test_crowded_cells_sort_paths():
+    """Cells with more than 32 and more than 512 particles take the other
+    two paths of the per-cell sort; order and sums must still match."""
+    rng = np.random.default_rng(5)
+    p = scenes.default_params(mass=scenes.f32(0.001))
+    h = p["h"]
+    a = 0.5 + rng.uniform(0, 0.9 * h, size=(700, 3))        # one cell, > 512
+    b = 0.2 + rng.uniform(0, 0.9 * h, size=(100, 3))        # one cell, 33..512
+    c = rng.uniform(0.05, 0.95, size=(3000, 3))             # sparse background
+    pos = np.zeros((3800, 4), np.float32)
+    pos[:, :3] = np.concatenate([a, b, c])
+    sc = dict(fluid_pos=pos, fluid_vel=np.zeros_like(pos), boid_pos=np.zeros((0, 4), np.float32),
+              boid_vel=np.zeros((0, 4), np.float32))
+    _check(p, sc)
+
+
+def test_edge_cases_small_scenes():
+    p = scenes.default_params(mass=scenes.f32(0.01))
+    z = np.zeros((0, 4), np.float32)
+    one = np.array([[0.5, 0.5, 0.5, 0]], np.float32)
+    # a single fluid particle
+    _check(p, dict(fluid_pos=one, fluid_vel=np.zeros_like(one), boid_pos=z, boid_vel=z))
+    # boids only (their attached particles have no fluid neighbours)
+    bp, bv = scenes.boids_uniform(50, (0, 0, 0), (1, 1, 1), seed=9)
+    _check(p, dict(fluid_pos=z, fluid_vel=z, boid_pos=bp, boid_vel=bv))
+    # coincident particles and particles outside the box (clamped cells)
+    pts = np.array([[0.3, 0.3, 0.3, 0], [0.3, 0.3, 0.3, 0], [0.31, 0.3, 0.3, 0], [-0.05, 0.5, 0.5, 0],
+                    [1.02, 0.99, 0.5, 0], [0.99, 1.03, 0.5, 0]], np.float32)
+    _check(p, dict(fluid_pos=pts, fluid_vel=np.zeros_like(pts), boid_pos=z, boid_vel=z))
+
+
+def test_unjittered_lattice_ties():
+    p = scenes.default_params()
+    s = np.float32(p["h"]) / np.float32(2)
+    p["mass"] = scenes.f32(oracle.lattice_mass(p, s))
+    n = 12
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    pos = np.zeros((n ** 3, 4), np.float32)
+    pos[:, :3] = np.stack([i.ravel(), j.ravel(), k.ravel()], 1) * s + np.float32(0.2)
+    z = np.zeros((0, 4), np.float32)
+    _check(p, dict(fluid_pos=pos, fluid_vel=np.zeros_like(pos), boid_pos=z, boid_vel=z))
+
+
+def test_deterministic_and_resumable():
+    """Two runs agree bit for bit; stopping, reading the state back and
+    loading it again continues bit-identically."""
+    sc = scenes.dam_break_small()
+    p = lattice_params(sc)
+    a = run_gpu(p, sc, steps=30)
+    b = run_gpu(p, sc, steps=15)
+    fp, fv, bp, bv = b.get_state()
+    c = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    c.set_state(fp, fv, bp, bv)
+    c.step(15)
+    sa = [t.cpu().numpy() for t in a.get_state()]
+    sc_ = [t.cpu().numpy() for t in c.get_state()]
+    for x, y in zip(sa, sc_):
+        assert np.array_equal(x, y)
+    d = run_gpu(p, sc, steps=30)
+    for x, y in zip(sa, [t.cpu().numpy() for t in d.get_state()]):
+        assert np.array_equal(x, y)
+
+
+def test_boid_forces_entry_point_matches_step():
+    sc = scenes.scaled_block(8000, 200, (0.5, 0.5, 0.5), (0.5, 0.3, 0.5), seed=12)
+    sc["boid_pos"][:, 1] *= np.float32(0.3 / 0.5)
+    p = sc["params"]
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    f_now = s.boid_forces().cpu().numpy()
+    s.step(1)
+    f_step = s.field("fb").cpu().numpy()
+    assert np.array_equal(f_now, f_step)
+    o = oracle_step(p, sc)
+    assert np.all(np.abs(f_now[:, :3] - o["fb"]).max(1) <= 1e-5 * o["acc_scale"][:len(f_now)])
+
+
+def test_host_buffers_round_trip():
+    sc = scenes.dam_break_small(n_side=10, n_boid=8)
+    p = lattice_params(sc)
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    host = [torch.from_numpy(a).pin_memory() for a in (sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])]
+    s.set_state_host(*host)
+    s.step(3)
+    outs = [torch.empty_like(t).pin_memory() for t in host]
+    s.get_state_host(outs)
+    dev = run_gpu(p, sc, steps=3).get_state()
+    for a, b in zip(outs, dev):
+        assert np.array_equal(a.numpy(), b.cpu().numpy())
+
+
+def test_nonfinite_input_sets_status_bit():
+    sc = scenes.dam_break_small(n_side=8, n_boid=4)
+    p = lattice_params(sc)
+    fp = sc["fluid_pos"].copy()
+    fp[7, 0] = np.nan
+    s = Scene(p, len(fp), len(sc["boid_pos"]))
+    s.set_state(fp, sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    s.step(1)
+    assert s.status() & 1
+    s.clear_status()
+    assert s.status() == 0
+
+
+def test_large_tank_settled_step_full_size():
+    """The 2,097,152-particle tank of the benchmark: 200 settling steps on
+    the GPU, boids released, 20 more steps, then one step compared with the
+    oracle on every particle."""
+    sc = scenes.large_tank()
+    p = dict(sc["params"])
+    z = np.zeros((0, 4), np.float32)
+    s = Scene(p, len(sc["fluid_pos"]), 0)
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], z, z)
+    s.step(200)
+    fp, fv, _, _ = s.get_state()
+    s2 = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    s2.set_state(fp, fv, sc["boid_pos"], sc["boid_vel"])
+    s2.step(20)
+    st = _state_of(s2, p)
+    _check(p, st)

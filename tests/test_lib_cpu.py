@@ -1,0 +1,88 @@
+"""CPU-side checks of the step library: it loads, exports every entry point
+of include/sph.h, validates its arguments and agrees with the oracle on the
+host-side set-up values.  No compute call needs a GPU here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2311_15088_gb300 import scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_15088_gb300 import build
+
+    build.build()
+    from paper_2311_15088_gb300 import sph
+
+    return sph
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "sph.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib._lib, name), f"{name} is declared in include/sph.h but not exported"
+        assert name in lib.EXPORTED, f"{name} has no Python binding"
+
+
+def test_library_is_independent_of_the_oracle(lib):
+    data = open(lib._LIB_PATH, "rb").read()
+    assert b"or_step" not in data and b"liboracle" not in data
+
+
+def _p(**kw):
+    p = scenes.default_params(**kw)
+    if p["mass"] is None:
+        p["mass"] = 0.01
+    return p
+
+
+def test_workspace_size_grows_with_particles(lib):
+    a = lib.sph_workspace_size(_p(), 1000, 10)
+    b = lib.sph_workspace_size(_p(), 100000, 10)
+    assert b - a >= 99000 * 110  # about 120 bytes of per-particle arrays
+
+
+@pytest.mark.parametrize("bad", [
+    dict(h=0.0), dict(cell_size=0.04), dict(mass=-1.0), dict(dt=0.0), dict(box_max=(0.0, 1.0, 1.0)),
+    dict(const_set=7), dict(coupling_mode=1), dict(boid_cell_size=0.1), dict(r_sep=0.5),
+    dict(v_min=2.0), dict(k=float("nan")), dict(wall_restitution=-1.0),
+])
+def test_invalid_parameters_are_rejected(lib, bad):
+    with pytest.raises(lib.SphError) as e:
+        lib.sph_workspace_size(_p(**bad), 100, 4)
+    assert e.value.code == lib.SPH_ERR_ARG
+
+
+def test_negative_counts_and_huge_grids(lib):
+    with pytest.raises(lib.SphError) as e:
+        lib.sph_workspace_size(_p(), -1, 0)
+    assert e.value.code == lib.SPH_ERR_ARG
+    with pytest.raises(lib.SphError) as e:
+        lib.sph_workspace_size(_p(box_max=(2000.0, 2000.0, 2000.0)), 10, 0)
+    assert e.value.code == lib.SPH_ERR_OVERFLOW
+
+
+def test_grid_dims_match_oracle(lib, orc):
+    for p in (_p(), _p(box_max=(2.0, 1.0, 1.0)), _p(box_max=(4.0, 2.0, 2.0))):
+        assert lib.sph_grid_dims(p, 0) == orc.grid_dims(p, 0)
+        assert lib.sph_grid_dims(p, 1) == orc.grid_dims(p, 1)
+    assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0)), 0) == (88, 44, 44)
+    assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0)), 1) == (22, 11, 11)
+
+
+@pytest.mark.parametrize("spacing", [0.02285, 1.0 / 64, 0.03])
+def test_lattice_mass_matches_oracle(lib, orc, spacing):
+    p = _p()
+    assert lib.sph_lattice_mass(p, spacing) == pytest.approx(orc.lattice_mass(p, np.float32(spacing)), rel=1e-6)
