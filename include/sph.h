@@ -233,6 +233,38 @@ int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds);
 /* Free the host-side handle (the workspace stays the caller's). */
 void sph_destroy(sph_handle* h);
 
+/*
+ * Allocation-free binning.  The paper has no counterpart to this entry point;
+ * it exists for callers that cannot allocate device memory: code that runs
+ * inside another framework's hook and owns only its input and output buffers
+ * (the framework's allocator holds the rest of the device memory), or a
+ * real-time loop where a cudaMalloc, which may synchronise the device, would
+ * stall other streams.
+ *
+ * For n particles at pos4 (device float4, 16-byte aligned, by index; w
+ * ignored) it computes what sph_step's binning computes, with the grid of
+ * p->box_min/box_max/cell_size: keys_out[n] the cell key of each particle
+ * (by index), perm_out[n] the particle index at each sorted slot (sorted by
+ * key, then index), cell_start_out[ncells + 1] the first sorted slot of each
+ * cell (device arrays owned by the caller).  Work is enqueued on `stream`.
+ *
+ * Its scratch is one file-scope device array of SPH_STATIC_SCRATCH_BYTES
+ * (about 21 MiB) that every GPU which loads this library holds until the
+ * process exits.  Limits: n <= SPH_STATIC_MAX_PARTICLES and a grid of at most
+ * SPH_STATIC_MAX_CELLS cells; larger requests return SPH_ERR_ARG (message in
+ * sph_last_error(NULL)) before any device work.  The array is shared by all
+ * calls on a device and keeps the last call's contents; each call zeroes
+ * what must start at zero.  Calls that overlap on the GPU race on it:
+ * serialise them.  The first call on a device (with that device current)
+ * looks up the array's device address once; make it before any stream
+ * capture.  No device memory is allocated or freed.
+ */
+#define SPH_STATIC_MAX_PARTICLES (1 << 22)
+#define SPH_STATIC_MAX_CELLS     (1 << 20)
+#define SPH_STATIC_SCRATCH_BYTES (21u << 20)
+int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys_out, int* perm_out,
+                   unsigned* cell_start_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ static void prof_end(sph_handle* h, cudaStream_t s)
 
 static thread_local char g_msg[512] = "";
 
+void sphk::set_handleless_error(const char* msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
+
 static int fail(sph_handle* h, int code, const char* fmt, ...)
 {
     char* dst = h ? h->msg : g_msg;

@@ -128,4 +128,7 @@ cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const 
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches);
 
+// Set the message that sph_last_error(NULL) returns on this thread.
+void set_handleless_error(const char* msg);
+
 }  // namespace sphk

@@ -67,6 +67,7 @@ _sig = {
     "sph_destroy": (None, [_vp]),
     "sph_profile_enable": (_i, [_vp, _i]),
     "sph_profile_read": (_i, [_vp, _vp, _vp, _i]),
+    "sph_bin_static": (_i, [_P, _i, _vp, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -191,6 +192,18 @@ def sph_profile_read(h) -> dict:
     n = (ctypes.c_longlong * len(KINDS))()
     _check(_lib.sph_profile_read(h, ctypes.cast(ms, _vp), ctypes.cast(n, _vp), len(KINDS)), h)
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KINDS)}
+
+
+SPH_STATIC_MAX_PARTICLES = 1 << 22
+SPH_STATIC_MAX_CELLS = 1 << 20
+
+
+def sph_bin_static(params: dict, n: int, pos_ptr, keys_ptr, perm_ptr, cell_start_ptr, stream: int):
+    """Allocation-free binning (no device allocation; fixed static scratch)."""
+    q = dict(params)
+    if q.get("mass") is None:
+        q["mass"] = 1.0
+    _check(_lib.sph_bin_static(ctypes.byref(make_params(q)), n, pos_ptr, keys_ptr, perm_ptr, cell_start_ptr, stream))
 
 
 # ------------------------------------------------------ torch convenience
