@@ -192,22 +192,28 @@ static void force_constants(const or_params *p, double *cp, double *cv)
 
 /* ------------------------------------------------------ neighbour walk */
 
-/* The 27-cell stencil around the particle's own cell, out-of-grid cells
- * skipped (get_nearby_key), visited dz outer, dy, dx inner; particles of a
- * cell in sorted (id) order.  Calls visit(j) for every candidate j. */
+/* The stencil around the particle's own cell (get_nearby_key: 27 cells for
+ * d >= h), out-of-grid cells skipped, visited dz outer, dy, dx inner;
+ * particles of a cell in sorted (id) order.  The stencil reaches
+ * reach = ceil(h/d) + 1 cells: one more than ceil(h/d), so that a neighbour
+ * whose float32 cell index rounded across a cell face is still visited. */
 typedef struct {
     const or_grid *g;
     const int *perm, *cell_start;
+    int reach;
 } or_walk;
+
+static int walk_reach(double h, double d) { return (int)ceil(h / d) + 1; }
 
 #define FOR_EACH_CANDIDATE(W, XI, J, ...)                                        \
     do {                                                                         \
         int cx_ = cell_coord((W)->g, 0, (XI)[0]);                                \
         int cy_ = cell_coord((W)->g, 1, (XI)[1]);                                \
         int cz_ = cell_coord((W)->g, 2, (XI)[2]);                                \
-        for (int dz_ = -1; dz_ <= 1; ++dz_)                                      \
-            for (int dy_ = -1; dy_ <= 1; ++dy_)                                  \
-                for (int dx_ = -1; dx_ <= 1; ++dx_) {                            \
+        const int R_ = (W)->reach;                                               \
+        for (int dz_ = -R_; dz_ <= R_; ++dz_)                                    \
+            for (int dy_ = -R_; dy_ <= R_; ++dy_)                                \
+                for (int dx_ = -R_; dx_ <= R_; ++dx_) {                          \
                     int x_ = cx_ + dx_, y_ = cy_ + dy_, z_ = cz_ + dz_;          \
                     if (x_ < 0 || x_ >= (W)->g->dim[0] || y_ < 0 ||              \
                         y_ >= (W)->g->dim[1] || z_ < 0 || z_ >= (W)->g->dim[2])  \
@@ -321,7 +327,7 @@ int or_neighbors(const or_params *p, int n, int n_att, const float *pos3,
     int *perm = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     int *cs = (int *)malloc(sizeof(int) * (size_t)(g.ncells + 1));
     counting_sort(&g, n, pos3, keys, perm, cs);
-    or_walk w = {&g, perm, cs};
+    or_walk w = {&g, perm, cs, walk_reach(p->h, p->cell_size)};
     float hf = (float)p->h, h2f = hf * hf;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < n; ++i) {
@@ -421,7 +427,7 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
     int *perm = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     int *cs = (int *)malloc(sizeof(int) * (size_t)(g.ncells + 1));
     counting_sort(&g, n, x32, keys, perm, cs);
-    or_walk w = {&g, perm, cs};
+    or_walk w = {&g, perm, cs, walk_reach(p->h, p->cell_size)};
     float hf = (float)p->h, h2f = hf * hf;
 
     /* 3. density (self term included) and pressure. */

@@ -101,16 +101,17 @@ def _sets(counts, offsets, lst):
     return [set(lst[offsets[i]:offsets[i + 1]].tolist()) for i in range(len(counts))]
 
 
-@pytest.mark.parametrize("n,n_att", [(2500, 0), (2000, 40)])
-def test_grid_neighbors_equal_brute_force(orc, n, n_att):
-    """The 27-cell walk finds exactly the pairs an all-pairs scan finds,
-    including particles pushed into the corner and edge cells."""
+@pytest.mark.parametrize("n,n_att,cell", [(2500, 0, 1.0), (2000, 40, 1.0), (2500, 30, 0.5), (1500, 10, 0.34)])
+def test_grid_neighbors_equal_brute_force(orc, n, n_att, cell):
+    """The grid walk finds exactly the pairs an all-pairs scan finds, for
+    cells of h, h/2 and about h/3, including particles pushed into the corner
+    and edge cells."""
     sc = scenes.scaled_block(n, 0, (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), seed=5)
     pos = sc["fluid_pos"].copy()
     # squeeze a third of them against the corners of the box
     k = n // 3
     pos[:k, :3] = np.where(pos[:k, :3] < 0.5, pos[:k, :3] * 0.08, 1.0 - (1.0 - pos[:k, :3]) * 0.08)
-    p = dict(sc["params"])
+    p = dict(sc["params"], cell_size=scenes.f32(sc["params"]["h"] * cell))
     c1, o1, l1 = orc.neighbors(p, pos, n_att)
     c2, o2, l2 = orc.neighbors(p, pos, n_att, brute=True)
     assert np.array_equal(c1, c2)
