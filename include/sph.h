@@ -74,15 +74,17 @@ extern "C" {
 #define SPH_FIELD_BOID_KEYS  10  /* uint[n_boid]   boid-grid cell key, by boid id           */
 #define SPH_FIELD_BOID_PERM  11  /* int[n_boid]    boid id at each sorted boid slot         */
 #define SPH_FIELD_BOID_CELL_START 12 /* uint[nbcells+1] first sorted boid slot per cell    */
+#define SPH_FIELD_NCAND      13  /* int[n_tot]     candidates the density pass tested, by id */
 
 /*
  * Parameters of a scene.  Paper notation: h smoothing length, rho0 rest
  * density, k gas constant (p = k (rho - rho0)), mu viscosity, mass particle
  * mass (every particle, attached ones included), d = cell_size the grid
- * cell (d >= h: the 27-cell stencil then holds every neighbour), boid radii
+ * cell (d >= h/4; the walk visits every cell the h-sphere can reach, 27 of
+ * them for d >= h, clipped per particle for smaller cells), boid radii
  * r_sep ("protect_range") and r_vis ("visible_range"), rule weights w_sep
  * ("sep"), w_align ("mat"), w_coh ("cen"), sph_factor, the speed limits
- * v_min / v_max, edge_turn (edge avoidance), boid_cell_size (>= r_vis).
+ * v_min / v_max, edge_turn (edge avoidance), boid_cell_size (>= r_vis/4).
  * The paper gives no value for the boid weights, the wall restitution or
  * the edge turn; they are free parameters.
  */
@@ -127,12 +129,40 @@ int sph_lattice_mass(const sph_params* p, float spacing, float* mass);
  * Create a scene handle on a caller-owned device workspace of ws_bytes
  * (>= sph_workspace_size, 256-byte aligned).  The current CUDA device must
  * be the workspace's device.  The state is undefined until sph_set_state.
- * Errors: SPH_ERR_ARG if h, rho0, mass, dt <= 0, cell_size < h,
- * boid_cell_size < r_vis, r_sep > r_vis, box_max <= box_min on an axis,
+ * Errors: SPH_ERR_ARG if h, rho0, mass, dt <= 0, cell_size < h/4,
+ * boid_cell_size < r_vis/4, r_sep > r_vis, box_max <= box_min on an axis,
  * an unknown const_set / coupling_mode, a small or misaligned workspace.
  */
 int sph_create(const sph_params* p, int n_fluid, int n_boid, void* workspace,
                size_t ws_bytes, sph_handle** out);
+
+/*
+ * Batched scenes: S independent scenes (own parameters, own counts) in one
+ * handle.  Every pass of sph_step then runs as one launch over the particles
+ * (or boids, or cells) of all scenes, and each scene's result is bitwise the
+ * result of that scene run alone.  The state arrays of sph_set_state /
+ * sph_get_state are the scenes' arrays concatenated in scene order (fluid:
+ * scene 0's n_fluid[0] particles, then scene 1's ...; boids likewise).
+ * Particle ids of the fields are global: the attached particle of boid b
+ * (b counted over the concatenated boids) has id b, fluid particle f (over the
+ * concatenated fluid) has id n_boid_total + f; cell keys are global (scene
+ * k's cells follow scene k-1's).  For S = 1 this is exactly sph_create.
+ * Errors: as sph_create for any scene, SPH_ERR_ARG for S < 1 or NULL arrays,
+ * SPH_ERR_OVERFLOW beyond 2^31 - 1 particles or cells in total.
+ */
+int sph_batch_workspace_size(const sph_params* params, const int* n_fluid, const int* n_boid, int S,
+                             size_t* bytes);
+int sph_batch_create(const sph_params* params, const int* n_fluid, const int* n_boid, int S,
+                     void* workspace, size_t ws_bytes, sph_handle** out);
+
+/*
+ * Launch shape of the two neighbour passes: `block` threads per block (64,
+ * 128, 256 or 512) and whether the force pass reuses the candidate bits the
+ * density pass records (use_stream = 1) or tests the candidates again
+ * (0, the default).  Neither changes any result bit: the per-particle
+ * arithmetic and its order are the same.  Errors: SPH_ERR_ARG.
+ */
+int sph_set_tuning(sph_handle* h, int block, int use_stream);
 
 /*
  * Load the state: fluid_pos4 / fluid_vel4 hold n_fluid float4 (fluid order),
@@ -161,6 +191,15 @@ int sph_get_state(sph_handle* h, float* fluid_pos4, float* fluid_vel4,
  * SPH_ERR_CUDA.  Device-side anomalies set bits of the error word.
  */
 int sph_step(sph_handle* h, int nsteps, void* stream);
+
+/*
+ * sph_step through a CUDA graph: the first call captures one step on
+ * `stream` (which must not be the legacy default stream) and later calls
+ * replay it, nsteps times, with the same results as sph_step.  A change of
+ * stream or tuning recaptures.  Per-pass event timing is not recorded in
+ * graph mode.  Errors: SPH_ERR_ARG, SPH_ERR_STATE, SPH_ERR_CUDA.
+ */
+int sph_graph_step(sph_handle* h, int nsteps, void* stream);
 
 /*
  * Fluid force on every boid for the CURRENT state (mode 0 = exact SPH

@@ -15,9 +15,16 @@
 using namespace sphk;
 
 struct sph_handle {
-    sph_params p;
-    StepConst c;
-    int n_fluid, n_boid, n;
+    int S;                    // scenes (1 for sph_create)
+    sph_params* params;       // host copies, S entries
+    StepConst* consts;        // host copies, S entries
+    unsigned *h_pbase, *h_bbase;
+    StepConst* d_consts;      // device copies (in the workspace)
+    unsigned *d_pbase, *d_bbase;
+    Scenes sc;                // what the kernels receive
+    Tuning tune;
+    int n_fluid, n_boid, n;   // totals over the scenes
+    int ncells, nbcells;      // totals over the scenes
     // state (storage order) and the sorted scratch copy
     float4 *pos, *vel, *pos_s, *vel_s;
     unsigned *key, *rank;
@@ -27,6 +34,8 @@ struct sph_handle {
     unsigned* big_count;
     float* rho;
     int* nbr;
+    unsigned* bits;
+    int* ncand;
     float4* acc;
     int* touched;
     float4* infl;
@@ -46,6 +55,10 @@ struct sph_handle {
     cudaEvent_t* prof_ev;
     int* prof_kind;
     int prof_cap, prof_n;
+    // captured step (sph_graph_step)
+    cudaGraphExec_t graph;
+    cudaStream_t graph_stream;
+    long long graph_launches;
     char msg[512];
 };
 
@@ -115,8 +128,8 @@ static int validate(const sph_params* p, int n_fluid, int n_boid)
     if ((long long)n_fluid + n_boid > 2147483647LL) return fail(nullptr, SPH_ERR_OVERFLOW, "too many particles");
     if (!finite_pos(p->h) || !finite_pos(p->rho0) || !finite_pos(p->mass) || !finite_pos(p->dt))
         return fail(nullptr, SPH_ERR_ARG, "h, rho0, mass and dt must be finite and > 0");
-    if (!(isfinite(p->cell_size) && p->cell_size >= p->h))
-        return fail(nullptr, SPH_ERR_ARG, "cell_size must be >= h (27-cell stencil)");
+    if (!(isfinite(p->cell_size) && p->cell_size >= 0.25f * p->h))
+        return fail(nullptr, SPH_ERR_ARG, "cell_size must be >= h/4");
     if (!(isfinite(p->k) && p->k >= 0.0f) || !(isfinite(p->mu) && p->mu >= 0.0f))
         return fail(nullptr, SPH_ERR_ARG, "k and mu must be finite and >= 0");
     for (int a = 0; a < 3; ++a)
@@ -132,8 +145,8 @@ static int validate(const sph_params* p, int n_fluid, int n_boid)
         return fail(nullptr, SPH_ERR_ARG, "wall_restitution must be >= 0");
     if (!(p->r_sep >= 0.0f && p->r_vis >= p->r_sep && isfinite(p->r_vis)))
         return fail(nullptr, SPH_ERR_ARG, "need 0 <= r_sep <= r_vis");
-    if (!(isfinite(p->boid_cell_size) && p->boid_cell_size > 0.0f && p->boid_cell_size >= p->r_vis))
-        return fail(nullptr, SPH_ERR_ARG, "boid_cell_size must be > 0 and >= r_vis");
+    if (!(isfinite(p->boid_cell_size) && p->boid_cell_size > 0.0f && p->boid_cell_size >= 0.25f * p->r_vis))
+        return fail(nullptr, SPH_ERR_ARG, "boid_cell_size must be > 0 and >= r_vis/4");
     if (!(p->v_min >= 0.0f && p->v_max >= p->v_min && isfinite(p->v_max)))
         return fail(nullptr, SPH_ERR_ARG, "need 0 <= v_min <= v_max");
     if (!(isfinite(p->w_sep) && isfinite(p->w_align) && isfinite(p->w_coh) && isfinite(p->sph_factor) &&
@@ -147,13 +160,32 @@ static int validate(const sph_params* p, int n_fluid, int n_boid)
     return SPH_OK;
 }
 
+// Search bounds of a walk with radius^2 r2 (the float32 predicate bound) on
+// cells of size d: reach2 = r2 (1 + 1e-5) exceeds the exact squared
+// distance of any pair that passes the float32 predicate, and margin covers
+// the rounding of cell boundaries (8 ulps of the largest coordinate + 1e-5 d).
+static WalkBounds make_bounds(const sph_params* p, float r2, float d)
+{
+    float extent = d;
+    for (int a = 0; a < 3; ++a) extent = fmaxf(extent, fmaxf(fabsf(p->box_min[a]), fabsf(p->box_max[a])) + d);
+    const float ulp = nextafterf(extent, INFINITY) - extent;
+    WalkBounds w;
+    w.margin = 8.0f * ulp + 1e-5f * d;
+    w.reach2 = r2 * (1.0f + 1e-5f);
+    w.reach = sqrtf(w.reach2) + w.margin;
+    w.d = d;
+    return w;
+}
+
 static void make_const(const sph_params* p, int n_fluid, int n_boid, StepConst* c)
 {
     memset(c, 0, sizeof(*c));
     make_grid(p->box_min, p->box_max, p->cell_size, &c->g);
     make_grid(p->box_min, p->box_max, p->boid_cell_size, &c->gb);
+    c->wg = make_bounds(p, p->h * p->h, p->cell_size);
+    c->wb = make_bounds(p, p->r_vis * p->r_vis, p->boid_cell_size);
     c->n = n_fluid + n_boid;
-    c->nb = n_boid;
+    c->nb = n_boid;  // bases and nb_all are filled in by layout_scenes
     const double pi = 3.14159265358979323846;
     const double h = p->h;
     c->h2 = p->h * p->h;
@@ -211,7 +243,10 @@ static size_t carve(sph_handle* h, uintptr_t base)
 {
     Carver cv{base, 0};
     const size_t n = (size_t)h->n, nb = (size_t)h->n_boid;
-    const size_t C = (size_t)h->c.g.ncells, Cb = (size_t)h->c.gb.ncells;
+    const size_t C = (size_t)h->ncells, Cb = (size_t)h->nbcells;
+    h->d_consts = cv.take<StepConst>((size_t)h->S);
+    h->d_pbase = cv.take<unsigned>((size_t)h->S + 1);
+    h->d_bbase = cv.take<unsigned>((size_t)h->S + 1);
     h->pos = cv.take<float4>(n);
     h->vel = cv.take<float4>(n);
     h->pos_s = cv.take<float4>(n);
@@ -226,6 +261,8 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->big_count = cv.take<unsigned>(1);
     h->rho = cv.take<float>(n);
     h->nbr = cv.take<int>(n);
+    h->bits = cv.take<unsigned>(n * (size_t)NBR_WORDS);
+    h->ncand = cv.take<int>(n);
     h->acc = cv.take<float4>(n);
     h->touched = cv.take<int>(n);
     h->infl = cv.take<float4>(n);
@@ -249,26 +286,34 @@ static size_t carve(sph_handle* h, uintptr_t base)
 
 // ---------------------------------------------------------- state kernels
 
+// Storage slot i of scene k: its first n_boid(k) slots hold the scene's
+// attached particles, then its fluid particles.  Attached particle of global
+// boid b gets id b; fluid particle f (global fluid index) gets id nb_all + f.
 __global__ void k_load_state(const float4* __restrict__ fpos, const float4* __restrict__ fvel,
                              const float4* __restrict__ bpos_in, const float4* __restrict__ bvel_in,
-                             int nf, int nb, float4* __restrict__ pos, float4* __restrict__ vel,
+                             Scenes sc, float4* __restrict__ pos, float4* __restrict__ vel,
                              float4* __restrict__ bpos, float4* __restrict__ bvel, int* __restrict__ slot_of_boid)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf + nb) return;
+    if (i >= sc.n_all) return;
+    const int k = scene_of(sc.pbase, sc.S, (unsigned)i);
+    const unsigned local = (unsigned)i - sc.pbase[k];
+    const unsigned nbk = sc.bbase[k + 1] - sc.bbase[k];
     float4 p, v;
-    if (i < nb) {
-        p = bpos_in[i];
-        v = bvel_in[i];
-        p.w = __int_as_float(i);
+    if (local < nbk) {
+        const int b = (int)(sc.bbase[k] + local);
+        p = bpos_in[b];
+        v = bvel_in[b];
+        p.w = __int_as_float(b);
         v.w = 0.0f;
-        bpos[i] = p;
-        bvel[i] = v;
-        slot_of_boid[i] = i;
+        bpos[b] = p;
+        bvel[b] = v;
+        slot_of_boid[b] = i;
     } else {
-        p = fpos[i - nb];
-        v = fvel[i - nb];
-        p.w = __int_as_float(i);
+        const int f = (int)(sc.pbase[k] - sc.bbase[k] + (local - nbk));
+        p = fpos[f];
+        v = fvel[f];
+        p.w = __int_as_float(sc.nb_all + f);
         v.w = 0.0f;
     }
     pos[i] = p;
@@ -306,11 +351,14 @@ __global__ void k_by_id(const float4* __restrict__ pos, const T* __restrict__ fi
     if (i < n) out[__float_as_int(pos[i].w)] = field[i];
 }
 
-__global__ void k_pressure_by_id(const float4* __restrict__ pos, const float* __restrict__ rho, int n,
-                                 float k, float rho0, float* __restrict__ out)
+__global__ void k_pressure_by_id(const float4* __restrict__ pos, const float* __restrict__ rho, Scenes sc,
+                                 float* __restrict__ out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[__float_as_int(pos[i].w)] = k * (rho[i] - rho0);
+    if (i < sc.n_all) {
+        const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+        out[__float_as_int(pos[i].w)] = c.k * (rho[i] - c.rho0);
+    }
 }
 
 __global__ void k_ids(const float4* __restrict__ pos, int n, int* __restrict__ out)
@@ -358,49 +406,132 @@ int sph_lattice_mass(const sph_params* p, float spacing, float* mass)
     return SPH_OK;
 }
 
-int sph_workspace_size(const sph_params* p, int n_fluid, int n_boid, size_t* bytes)
+// Fill the host-side scene tables of h (S scenes) and the totals.
+static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_fluid, const int* n_boid, int S)
 {
-    int rc = validate(p, n_fluid, n_boid);
-    if (rc != SPH_OK) return rc;
-    if (!bytes) return fail(nullptr, SPH_ERR_ARG, "bytes is NULL");
-    sph_handle tmp;
-    memset(&tmp, 0, sizeof(tmp));
-    tmp.n_fluid = n_fluid;
-    tmp.n_boid = n_boid;
-    tmp.n = n_fluid + n_boid;
-    make_const(p, n_fluid, n_boid, &tmp.c);
-    *bytes = carve(&tmp, 0);
+    if (S < 1 || !params || !n_fluid || !n_boid) return fail(nullptr, SPH_ERR_ARG, "need S >= 1 and the arrays");
+    h->S = S;
+    h->params = new (std::nothrow) sph_params[S];
+    h->consts = new (std::nothrow) StepConst[S];
+    h->h_pbase = new (std::nothrow) unsigned[S + 1];
+    h->h_bbase = new (std::nothrow) unsigned[S + 1];
+    if (!h->params || !h->consts || !h->h_pbase || !h->h_bbase) return fail(nullptr, SPH_ERR_ARG, "out of host memory");
+    long long n = 0, nb = 0, nf = 0, C = 0, Cb = 0;
+    for (int k = 0; k < S; ++k) {
+        int rc = validate(&params[k], n_fluid[k], n_boid[k]);
+        if (rc != SPH_OK) return rc;
+        h->params[k] = params[k];
+        make_const(&params[k], n_fluid[k], n_boid[k], &h->consts[k]);
+        h->h_pbase[k] = (unsigned)n;
+        h->h_bbase[k] = (unsigned)nb;
+        h->consts[k].p_base = (int)n;
+        h->consts[k].b_base = (int)nb;
+        h->consts[k].c_base = (int)C;
+        h->consts[k].cb_base = (int)Cb;
+        n += (long long)n_fluid[k] + n_boid[k];
+        nb += n_boid[k];
+        nf += n_fluid[k];
+        C += h->consts[k].g.ncells;
+        Cb += h->consts[k].gb.ncells;
+        if (n > 2147483647LL || C > 2147483646LL || Cb > 2147483646LL)
+            return fail(nullptr, SPH_ERR_OVERFLOW, "the batch exceeds 2^31 particles or cells");
+    }
+    h->h_pbase[S] = (unsigned)n;
+    h->h_bbase[S] = (unsigned)nb;
+    for (int k = 0; k < S; ++k) h->consts[k].nb_all = (int)nb;
+    h->n = (int)n;
+    h->n_boid = (int)nb;
+    h->n_fluid = (int)nf;
+    h->ncells = (int)C;
+    h->nbcells = (int)Cb;
+    h->tune.block = 256;
+    h->tune.use_stream = 0;
     return SPH_OK;
 }
 
-int sph_create(const sph_params* p, int n_fluid, int n_boid, void* workspace, size_t ws_bytes,
-               sph_handle** out)
+static void free_tables(sph_handle* h)
 {
-    int rc = validate(p, n_fluid, n_boid);
-    if (rc != SPH_OK) return rc;
+    delete[] h->params;
+    delete[] h->consts;
+    delete[] h->h_pbase;
+    delete[] h->h_bbase;
+}
+
+int sph_batch_workspace_size(const sph_params* params, const int* n_fluid, const int* n_boid, int S,
+                             size_t* bytes)
+{
+    if (!bytes) return fail(nullptr, SPH_ERR_ARG, "bytes is NULL");
+    sph_handle tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    int rc = layout_scenes(&tmp, params, n_fluid, n_boid, S);
+    if (rc == SPH_OK) *bytes = carve(&tmp, 0);
+    free_tables(&tmp);
+    return rc;
+}
+
+int sph_workspace_size(const sph_params* p, int n_fluid, int n_boid, size_t* bytes)
+{
+    return sph_batch_workspace_size(p, &n_fluid, &n_boid, 1, bytes);
+}
+
+int sph_batch_create(const sph_params* params, const int* n_fluid, const int* n_boid, int S, void* workspace,
+                     size_t ws_bytes, sph_handle** out)
+{
     if (!out) return fail(nullptr, SPH_ERR_ARG, "out is NULL");
     if (!workspace || ((uintptr_t)workspace & 255))
         return fail(nullptr, SPH_ERR_ARG, "workspace must be non-NULL and 256-byte aligned");
     sph_handle* h = new (std::nothrow) sph_handle;
     if (!h) return fail(nullptr, SPH_ERR_ARG, "out of host memory");
     memset(h, 0, sizeof(*h));
-    h->p = *p;
-    h->n_fluid = n_fluid;
-    h->n_boid = n_boid;
-    h->n = n_fluid + n_boid;
-    make_const(p, n_fluid, n_boid, &h->c);
+    int rc = layout_scenes(h, params, n_fluid, n_boid, S);
+    if (rc != SPH_OK) {
+        free_tables(h);
+        delete h;
+        return rc;
+    }
     size_t need = carve(h, (uintptr_t)workspace);
     if (ws_bytes < need) {
+        free_tables(h);
         delete h;
         return fail(nullptr, SPH_ERR_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
     }
-    cudaError_t e = cudaMemsetAsync(h->err, 0, 4 * sizeof(unsigned), 0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    cudaError_t e = cudaMemcpy(h->d_consts, h->consts, sizeof(StepConst) * (size_t)S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_pbase, h->h_pbase, sizeof(unsigned) * (size_t)(S + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_bbase, h->h_bbase, sizeof(unsigned) * (size_t)(S + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->err, 0, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = prepare_kernels();
     if (e != cudaSuccess) {
+        free_tables(h);
         delete h;
-        return fail(nullptr, SPH_ERR_CUDA, "cudaMemset of the error word: %s", cudaGetErrorString(e));
+        return fail(nullptr, SPH_ERR_CUDA, "uploading the scene tables: %s", cudaGetErrorString(e));
     }
+    h->sc.c = h->d_consts;
+    h->sc.pbase = h->d_pbase;
+    h->sc.bbase = h->d_bbase;
+    h->sc.S = S;
+    h->sc.n_all = h->n;
+    h->sc.nb_all = h->n_boid;
     *out = h;
+    return SPH_OK;
+}
+
+int sph_create(const sph_params* p, int n_fluid, int n_boid, void* workspace, size_t ws_bytes, sph_handle** out)
+{
+    return sph_batch_create(p, &n_fluid, &n_boid, 1, workspace, ws_bytes, out);
+}
+
+int sph_set_tuning(sph_handle* h, int block, int use_stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (block != 64 && block != 128 && block != 256 && block != 512)
+        return fail(h, SPH_ERR_ARG, "block must be 64, 128, 256 or 512");
+    if (use_stream != 0 && use_stream != 1) return fail(h, SPH_ERR_ARG, "use_stream must be 0 or 1");
+    h->tune.block = block;
+    h->tune.use_stream = use_stream;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     return SPH_OK;
 }
 
@@ -418,6 +549,8 @@ void sph_destroy(sph_handle* h)
 {
     if (!h) return;
     prof_free(h);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    free_tables(h);
     delete h;
 }
 
@@ -498,7 +631,7 @@ int sph_set_state(sph_handle* h, const float* fluid_pos4, const float* fluid_vel
         return fail(h, SPH_ERR_ARG, "device state pointers must be 16-byte aligned");
     }
     if (h->n > 0) {
-        k_load_state<<<(h->n + 255) / 256, 256, 0, s>>>(fp, fv, bp, bv, nf, nb, h->pos, h->vel, h->bpos, h->bvel,
+        k_load_state<<<(h->n + 255) / 256, 256, 0, s>>>(fp, fv, bp, bv, h->sc, h->pos, h->vel, h->bpos, h->bvel,
                                                          h->slot_of_boid);
         ++h->launches;
         CUDA_TRY(h, cudaGetLastError());
@@ -553,30 +686,67 @@ int sph_get_state(sph_handle* h, float* fluid_pos4, float* fluid_vel4, float* bo
 // Keys (if needed), scan, scatter and per-cell sort + gather of the state
 // into the sorted scratch arrays.  consume = true zeroes the counts for the
 // next step's keys.
+// Keys (if needed), scan, scatter and per-cell sort + gather of the state
+// into the sorted scratch arrays.  consume = true zeroes the counts for the
+// next step's keys.
 static int bin_state(sph_handle* h, cudaStream_t s, bool consume)
 {
-    const StepConst& c = h->c;
     if (!h->keys_ready) {
         prof_begin(h, SPH_KIND_KEYS, s);
-        CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)c.g.ncells * sizeof(unsigned), s));
-        CUDA_TRY(h, launch_keys(h->pos, c.n, c.g, h->key, h->rank, h->count, h->err, s, &h->launches));
+        CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)h->ncells * sizeof(unsigned), s));
+        CUDA_TRY(h, launch_scene_keys(h->pos, h->sc, h->key, h->rank, h->count, h->err, s, &h->launches));
         prof_end(h, s);
         h->keys_ready = true;
     }
     prof_begin(h, SPH_KIND_SCAN, s);
-    CUDA_TRY(h, launch_scan(h->count, c.g.ncells, h->scan_part, h->cell_start, s, &h->launches));
+    CUDA_TRY(h, launch_scan(h->count, h->ncells, h->scan_part, h->cell_start, s, &h->launches));
     prof_end(h, s);
     prof_begin(h, SPH_KIND_SCATTER, s);
-    CUDA_TRY(h, launch_scatter(h->key, h->rank, h->cell_start, c.n, h->tmp, s, &h->launches));
+    CUDA_TRY(h, launch_scatter(h->key, h->rank, h->cell_start, h->n, h->tmp, s, &h->launches));
     prof_end(h, s);
     prof_begin(h, SPH_KIND_SORT, s);
-    CUDA_TRY(h, launch_cellsort_gather(h->cell_start, c.g.ncells, h->tmp, h->pos, h->vel, h->pos_s, h->vel_s, c.nb,
-                                       h->slot_of_boid, h->big_list, h->big_count, s, &h->launches));
+    CUDA_TRY(h, launch_cellsort_slots(h->cell_start, h->key, h->n, h->ncells, h->tmp, h->pos, h->vel, h->pos_s,
+                                      h->vel_s, h->n_boid, h->slot_of_boid, h->big_list, h->big_count, s,
+                                      &h->launches));
     prof_end(h, s);
     if (consume) {
-        CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)c.g.ncells * sizeof(unsigned), s));
+        CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)h->ncells * sizeof(unsigned), s));
         h->keys_ready = false;
     }
+    return SPH_OK;
+}
+
+// Enqueue one step (keys must be ready or are computed first).
+static int enqueue_step(sph_handle* h, cudaStream_t s)
+{
+    int rc = bin_state(h, s, true);
+    if (rc != SPH_OK) return rc;
+    prof_begin(h, SPH_KIND_DENSITY, s);
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand, h->err,
+                               s, &h->launches));
+    prof_end(h, s);
+    prof_begin(h, SPH_KIND_FORCES, s);
+    CUDA_TRY(h, launch_forces(0, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+                              h->acc, h->touched, h->infl, h->fb, h->pos, h->vel, h->key, h->rank, h->count, h->err,
+                              s, &h->launches));
+    prof_end(h, s);
+    if (h->n_boid > 0) {
+        prof_begin(h, SPH_KIND_BOID_BIN, s);
+        CUDA_TRY(h, cudaMemsetAsync(h->bcount, 0, (size_t)h->nbcells * sizeof(unsigned), s));
+        CUDA_TRY(h, launch_boid_keys(h->bpos, h->sc, h->bkey, h->brank, h->bcount, s, &h->launches));
+        CUDA_TRY(h, launch_scan(h->bcount, h->nbcells, h->bscan_part, h->bstart, s, &h->launches));
+        CUDA_TRY(h, launch_scatter(h->bkey, h->brank, h->bstart, h->n_boid, h->btmp, s, &h->launches));
+        CUDA_TRY(h, launch_cellsort_gather(h->bstart, h->nbcells, h->btmp, h->bpos, h->bvel, h->bpos_s, h->bvel_s,
+                                           0, nullptr, h->bbig_list, h->bbig_count, s, &h->launches));
+        prof_end(h, s);
+        prof_begin(h, SPH_KIND_BOID_RULES, s);
+        CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, h->sc, h->fb, h->bpos, h->bvel, h->pos,
+                                      h->vel, h->slot_of_boid, h->key, h->rank, h->count, h->err, s,
+                                      &h->launches));
+        prof_end(h, s);
+    }
+    h->keys_ready = true;  // the force and boid kernels emitted the next keys
+    h->has_step = true;
     return SPH_OK;
 }
 
@@ -587,36 +757,63 @@ int sph_step(sph_handle* h, int nsteps, void* stream)
     if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
-    const StepConst& c = h->c;
     for (int it = 0; it < nsteps; ++it) {
-        int rc = bin_state(h, s, true);
+        int rc = enqueue_step(h, s);
         if (rc != SPH_OK) return rc;
-        prof_begin(h, SPH_KIND_DENSITY, s);
-        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, c, h->rho, h->nbr, h->err, s, &h->launches));
-        prof_end(h, s);
-        prof_begin(h, SPH_KIND_FORCES, s);
-        CUDA_TRY(h, launch_forces(0, h->pos_s, h->vel_s, h->rho, h->cell_start, c, h->acc, h->touched, h->infl,
-                                  h->fb, h->pos, h->vel, h->key, h->rank, h->count, h->err, s, &h->launches));
-        prof_end(h, s);
-        if (c.nb > 0) {
-            prof_begin(h, SPH_KIND_BOID_BIN, s);
-            CUDA_TRY(h, cudaMemsetAsync(h->bcount, 0, (size_t)c.gb.ncells * sizeof(unsigned), s));
-            CUDA_TRY(h, launch_boid_keys(h->bpos, c.nb, c.gb, h->bkey, h->brank, h->bcount, s, &h->launches));
-            CUDA_TRY(h, launch_scan(h->bcount, c.gb.ncells, h->bscan_part, h->bstart, s, &h->launches));
-            CUDA_TRY(h, launch_scatter(h->bkey, h->brank, h->bstart, c.nb, h->btmp, s, &h->launches));
-            CUDA_TRY(h, launch_cellsort_gather(h->bstart, c.gb.ncells, h->btmp, h->bpos, h->bvel, h->bpos_s,
-                                               h->bvel_s, 0, nullptr, h->bbig_list, h->bbig_count, s,
-                                               &h->launches));
-            prof_end(h, s);
-            prof_begin(h, SPH_KIND_BOID_RULES, s);
-            CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, c, h->fb, h->bpos, h->bvel, h->pos,
-                                          h->vel, h->slot_of_boid, h->key, h->rank, h->count, h->err, s,
-                                          &h->launches));
-            prof_end(h, s);
-        }
-        h->keys_ready = true;  // the force and boid kernels emitted the next keys
-        h->has_step = true;
     }
+    return SPH_OK;
+}
+
+int sph_graph_step(sph_handle* h, int nsteps, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (nsteps < 0) return fail(h, SPH_ERR_ARG, "nsteps < 0");
+    if (!stream) return fail(h, SPH_ERR_ARG, "a CUDA graph needs a non-default stream");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    if (nsteps == 0) return SPH_OK;
+    if (!h->keys_ready) {  // the captured step starts from emitted keys
+        int rc = enqueue_step(h, s);
+        if (rc != SPH_OK) return rc;
+        --nsteps;
+    }
+    if (h->graph && h->graph_stream != s) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (!h->graph && nsteps > 0) {
+        const int cap = h->prof_cap;
+        h->prof_cap = 0;  // no event records inside the graph
+        const long long before = h->launches;
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_step(h, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        h->prof_cap = cap;
+        h->launches = before;
+        if (rc != SPH_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(h, SPH_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+        size_t nodes = 0;
+        cudaGraphGetNodes(g, nullptr, &nodes);
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->graph = nullptr;
+            return fail(h, SPH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        h->graph_stream = s;
+        h->graph_launches = (long long)nodes;
+    }
+    for (int it = 0; it < nsteps; ++it) {
+        CUDA_TRY(h, cudaGraphLaunch(h->graph, s));
+        h->launches += h->graph_launches;
+    }
+    h->keys_ready = true;
+    h->has_step = true;
     return SPH_OK;
 }
 
@@ -631,11 +828,11 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
     if (h->n_boid == 0) return SPH_OK;
     int rc = bin_state(h, s, false);
     if (rc != SPH_OK) return rc;
-    const StepConst& c = h->c;
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, c, h->rho, h->nbr, h->err, s, &h->launches));
-    CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, c, nullptr, nullptr, nullptr,
-                              (float4*)out_f4, nullptr, nullptr, nullptr, nullptr, nullptr, h->err, s,
-                              &h->launches));
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand,
+                               h->err, s, &h->launches));
+    CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+                              nullptr, nullptr, nullptr, (float4*)out_f4, nullptr, nullptr, nullptr, nullptr,
+                              nullptr, h->err, s, &h->launches));
     h->has_step = false;
     return SPH_OK;
 }
@@ -650,7 +847,7 @@ int sph_debug_neighbors(sph_handle* h, int* counts, const long long* offsets, in
     h->last_stream = s;
     int rc = bin_state(h, s, false);
     if (rc != SPH_OK) return rc;
-    CUDA_TRY(h, launch_neighbor_list(h->pos_s, h->cell_start, h->c, counts, offsets, list, s, &h->launches));
+    CUDA_TRY(h, launch_neighbor_list(h->pos_s, h->cell_start, h->sc, counts, offsets, list, s, &h->launches));
     h->has_step = false;
     return SPH_OK;
 }
@@ -672,7 +869,7 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
         bytes = (size_t)n * 4;
         break;
     case SPH_FIELD_PRESSURE:
-        if (n) k_pressure_by_id<<<blocks, 256, 0, s>>>(h->pos, h->rho, n, h->c.k, h->c.rho0, (float*)dst);
+        if (n) k_pressure_by_id<<<blocks, 256, 0, s>>>(h->pos, h->rho, h->sc, (float*)dst);
         bytes = (size_t)n * 4;
         break;
     case SPH_FIELD_ACC:
@@ -691,8 +888,12 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
         if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->nbr, n, (int*)dst);
         bytes = (size_t)n * 4;
         break;
+    case SPH_FIELD_NCAND:
+        if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->ncand, n, (int*)dst);
+        bytes = (size_t)n * 4;
+        break;
     case SPH_FIELD_KEYS:
-        CUDA_TRY(h, launch_slot_keys(h->cell_start, h->c.g.ncells, (unsigned*)h->tmp, s, &h->launches));
+        CUDA_TRY(h, launch_slot_keys(h->cell_start, h->ncells, (unsigned*)h->tmp, s, &h->launches));
         if (n) k_by_id<unsigned><<<blocks, 256, 0, s>>>(h->pos, (const unsigned*)h->tmp, n, (unsigned*)dst);
         bytes = (size_t)n * 4;
         break;
@@ -702,7 +903,7 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
         break;
     case SPH_FIELD_CELL_START:
         dst = out;
-        bytes = ((size_t)h->c.g.ncells + 1) * 4;
+        bytes = ((size_t)h->ncells + 1) * 4;
         CUDA_TRY(h, cudaMemcpyAsync(out, h->cell_start, bytes, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
         if (on_host) CUDA_TRY(h, cudaStreamSynchronize(s));
         return SPH_OK;
@@ -715,12 +916,12 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
         bytes = (size_t)nb * 4;
         break;
     case SPH_FIELD_BOID_KEYS:
-        CUDA_TRY(h, launch_slot_keys(h->bstart, h->c.gb.ncells, (unsigned*)h->btmp, s, &h->launches));
+        CUDA_TRY(h, launch_slot_keys(h->bstart, h->nbcells, (unsigned*)h->btmp, s, &h->launches));
         if (nb) k_by_id<unsigned><<<(nb + 255) / 256, 256, 0, s>>>(h->bpos_s, (const unsigned*)h->btmp, nb, (unsigned*)dst);
         bytes = (size_t)nb * 4;
         break;
     case SPH_FIELD_BOID_CELL_START:
-        bytes = ((size_t)h->c.gb.ncells + 1) * 4;
+        bytes = ((size_t)h->nbcells + 1) * 4;
         CUDA_TRY(h, cudaMemcpyAsync(out, h->bstart, bytes, on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
         if (on_host) CUDA_TRY(h, cudaStreamSynchronize(s));
         return SPH_OK;

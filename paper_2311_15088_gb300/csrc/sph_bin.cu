@@ -41,6 +41,36 @@ cudaError_t launch_keys(const float4* pos, int n, const GridDesc& g, unsigned* k
     return cudaGetLastError();
 }
 
+// Keys of every scene's particles: the thread of storage slot i finds its
+// scene and emits the global key c_base + hash(get_cell(p)).
+__global__ void __launch_bounds__(256)
+k_scene_keys(const float4* __restrict__ pos, Scenes sc, unsigned* __restrict__ key,
+             unsigned* __restrict__ rank, unsigned* __restrict__ count, unsigned* __restrict__ err)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active = i < sc.n_all;
+    unsigned k = 0;
+    bool clamped = false;
+    if (active) {
+        const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+        float4 p = pos[i];
+        k = (unsigned)c.c_base + cell_key(c.g, p.x, p.y, p.z, &clamped);
+        key[i] = k;
+    }
+    unsigned r = agg_increment(count, k, active);
+    if (active) rank[i] = r;
+    if (__any_sync(FULL, clamped) && (threadIdx.x & 31) == 0) atomicOr(err, SPH_DEV_CLAMPED);
+}
+
+cudaError_t launch_scene_keys(const float4* pos, const Scenes& sc, unsigned* key, unsigned* rank,
+                              unsigned* count, unsigned* err, cudaStream_t s, long long* launches)
+{
+    if (sc.n_all <= 0) return cudaSuccess;
+    k_scene_keys<<<(sc.n_all + 255) / 256, 256, 0, s>>>(pos, sc, key, rank, count, err);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ scan
 
 constexpr int SCAN_THREADS = 256;
@@ -327,24 +357,83 @@ k_cellsort_big(const unsigned* __restrict__ start, const int* __restrict__ big_l
     }
 }
 
+// One-time kernel attributes (the block sort's 128 KiB of shared memory);
+// called when a handle is created, before any stream capture.
+cudaError_t prepare_kernels()
+{
+    static bool done = false;
+    if (done) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_cellsort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         BIG_CAP * (int)sizeof(unsigned long long));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
 cudaError_t launch_cellsort_gather(const unsigned* start, int ncells, const int* tmp,
                                    const float4* pos_in, const float4* vel_in, float4* pos_out,
                                    float4* vel_out, int nb, int* slot_of_boid, int* big_list,
                                    unsigned* big_count, cudaStream_t s, long long* launches)
 {
     if (ncells <= 0) return cudaSuccess;
-    static bool smem_set = false;
-    if (!smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_cellsort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             BIG_CAP * (int)sizeof(unsigned long long));
-        if (e != cudaSuccess) return e;
-        smem_set = true;
-    }
-    cudaError_t e = cudaMemsetAsync(big_count, 0, sizeof(unsigned), s);
+    cudaError_t e = prepare_kernels();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(big_count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     int blocks = (ncells + SORT_WARPS - 1) / SORT_WARPS;
     k_cellsort_gather<<<blocks, SORT_WARPS * 32, 0, s>>>(start, ncells, tmp, pos_in, vel_in, pos_out,
                                                          vel_out, nb, slot_of_boid, big_list, big_count);
+    k_cellsort_big<<<BIG_BLOCKS, BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
+        start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+// One thread per sorted slot: the thread of slot s takes the storage index
+// tmp[s] of its cell, ranks it by particle id against the cell's other
+// entries and moves pos/vel to start[c] + rank.  Cells with more than
+// SLOT_SMALL entries are queued (by the thread of their first slot) for
+// k_cellsort_big.  Suited to grids of small cells (a few particles each).
+constexpr int SLOT_SMALL = 64;
+
+__global__ void __launch_bounds__(256)
+k_cellsort_slots(const unsigned* __restrict__ start, const unsigned* __restrict__ key, int n,
+                 const int* __restrict__ tmp, const float4* __restrict__ pos_in,
+                 const float4* __restrict__ vel_in, float4* __restrict__ pos_out,
+                 float4* __restrict__ vel_out, int nb, int* __restrict__ slot_of_boid,
+                 int* __restrict__ big_list, unsigned* __restrict__ big_count)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int src = tmp[s];
+    const unsigned c = key[src];
+    const unsigned s0 = start[c];
+    const int nc = (int)(start[c + 1] - s0);
+    if (nc > SLOT_SMALL) {
+        if ((unsigned)s == s0) big_list[atomicAdd(big_count, 1u)] = (int)c;
+        return;
+    }
+    const float4 p = pos_in[src];
+    const int id = id_of(p);
+    int r = 0;
+    for (int k = 0; k < nc; ++k) r += id_of(pos_in[tmp[s0 + k]]) < id;
+    const unsigned dst = s0 + (unsigned)r;
+    pos_out[dst] = p;
+    vel_out[dst] = vel_in[src];
+    if (id < nb && slot_of_boid) slot_of_boid[id] = (int)dst;
+}
+
+cudaError_t launch_cellsort_slots(const unsigned* start, const unsigned* key, int n, int ncells,
+                                  const int* tmp, const float4* pos_in, const float4* vel_in,
+                                  float4* pos_out, float4* vel_out, int nb, int* slot_of_boid,
+                                  int* big_list, unsigned* big_count, cudaStream_t s, long long* launches)
+{
+    if (n <= 0 || ncells <= 0) return cudaSuccess;
+    cudaError_t e = prepare_kernels();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(big_count, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_cellsort_slots<<<(n + 255) / 256, 256, 0, s>>>(start, key, n, tmp, pos_in, vel_in, pos_out, vel_out, nb,
+                                                     slot_of_boid, big_list, big_count);
     k_cellsort_big<<<BIG_BLOCKS, BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
         start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid);
     *launches += 2;

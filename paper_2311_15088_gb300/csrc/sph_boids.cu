@@ -11,34 +11,35 @@
 //
 // Every boid reads the start-of-step snapshot (sorted copies), so the result
 // does not depend on the order boids are processed in.  Lanes stride over
-// the candidates of the 27 boid cells and the warp sums with a fixed
-// butterfly, so the float32 result is deterministic.
+// the candidates of the boid cells within r_vis (RowWalk) and the warp
+// sums with a fixed butterfly, so the float32 result is deterministic.
 #include "sph_internal.cuh"
 
 namespace sphk {
 
 __global__ void __launch_bounds__(256)
-k_boid_keys(const float4* __restrict__ bpos, int nb, GridDesc gb, unsigned* __restrict__ bkey,
+k_boid_keys(const float4* __restrict__ bpos, Scenes sc, unsigned* __restrict__ bkey,
             unsigned* __restrict__ brank, unsigned* __restrict__ bcount)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    bool active = b < nb;
+    bool active = b < sc.nb_all;
     unsigned k = 0;
     bool clamped = false;
     if (active) {
+        const StepConst& c = sc.c[scene_of(sc.bbase, sc.S, (unsigned)b)];
         float4 p = bpos[b];
-        k = cell_key(gb, p.x, p.y, p.z, &clamped);
+        k = (unsigned)c.cb_base + cell_key(c.gb, p.x, p.y, p.z, &clamped);
         bkey[b] = k;
     }
     unsigned r = agg_increment(bcount, k, active);
     if (active) brank[b] = r;
 }
 
-cudaError_t launch_boid_keys(const float4* bpos, int nb, const GridDesc& gb, unsigned* bkey,
-                             unsigned* brank, unsigned* bcount, cudaStream_t s, long long* launches)
+cudaError_t launch_boid_keys(const float4* bpos, const Scenes& sc, unsigned* bkey, unsigned* brank,
+                             unsigned* bcount, cudaStream_t s, long long* launches)
 {
-    if (nb <= 0) return cudaSuccess;
-    k_boid_keys<<<(nb + 255) / 256, 256, 0, s>>>(bpos, nb, gb, bkey, brank, bcount);
+    if (sc.nb_all <= 0) return cudaSuccess;
+    k_boid_keys<<<(sc.nb_all + 255) / 256, 256, 0, s>>>(bpos, sc, bkey, brank, bcount);
     ++*launches;
     return cudaGetLastError();
 }
@@ -61,7 +62,7 @@ constexpr int BOID_WARPS = 8;
 
 __global__ void __launch_bounds__(BOID_WARPS * 32)
 k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_s,
-             const unsigned* __restrict__ bstart, StepConst c, const float4* __restrict__ fb,
+             const unsigned* __restrict__ bstart, Scenes sc, const float4* __restrict__ fb,
              float4* __restrict__ bpos, float4* __restrict__ bvel, float4* __restrict__ pos_next,
              float4* __restrict__ vel_next, const int* __restrict__ slot_of_boid,
              unsigned* __restrict__ key, unsigned* __restrict__ rank, unsigned* __restrict__ count,
@@ -69,54 +70,41 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
 {
     const int lane = threadIdx.x & 31;
     const int s = blockIdx.x * BOID_WARPS + (threadIdx.x >> 5);
-    if (s >= c.nb) return;  // whole warp
+    if (s >= sc.nb_all) return;  // whole warp
+    const StepConst& c = sc.c[scene_of(sc.bbase, sc.S, (unsigned)s)];
     const float4 pb = bpos_s[s];
     const float4 vb = bvel_s[s];
     const int b = id_of(pb);
-    const GridDesc& g = c.gb;
-    bool clamped = false;
-    const int cx = cell_coord(pb.x, g.minf[0], g.inv_d, g.dim[0], &clamped);
-    const int cy = cell_coord(pb.y, g.minf[1], g.inv_d, g.dim[1], &clamped);
-    const int cz = cell_coord(pb.z, g.minf[2], g.inv_d, g.dim[2], &clamped);
-
     float cl[3] = {0.f, 0.f, 0.f};  // separation: sum of d (1 - |d|/r_sep), d = p_b - p_j
     float vs[3] = {0.f, 0.f, 0.f};  // alignment: sum of v_j
     float ps[3] = {0.f, 0.f, 0.f};  // cohesion: sum of (p_j - p_b)
     int nv = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        if (z < 0 || z >= g.dim[2]) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= g.dim[1]) continue;
-            int x0 = cx > 0 ? cx - 1 : 0;
-            int x1 = cx + 1 < g.dim[0] ? cx + 1 : g.dim[0] - 1;
-            unsigned row = (unsigned)g.dim[0] * ((unsigned)y + (unsigned)g.dim[1] * (unsigned)z);
-            unsigned s0 = bstart[row + x0], s1 = bstart[row + x1 + 1];
-            for (unsigned j = s0 + lane; j < s1; j += 32) {
-                if (j == (unsigned)s) continue;
-                const float4 pj = bpos_s[j];
-                const float dx = __fsub_rn(pj.x, pb.x);
-                const float dy_ = __fsub_rn(pj.y, pb.y);
-                const float dz_ = __fsub_rn(pj.z, pb.z);
-                const float r2 = pair_r2(dx, dy_, dz_);
-                if (r2 < c.rs2) {
-                    float w = 1.0f - sqrtf(r2) / c.rs;
-                    w = fminf(fmaxf(w, 0.0f), 1.0f);
-                    cl[0] -= dx * w;
-                    cl[1] -= dy_ * w;
-                    cl[2] -= dz_ * w;
-                }
-                if (r2 < c.rv2) {
-                    const float4 vj = bvel_s[j];
-                    vs[0] += vj.x;
-                    vs[1] += vj.y;
-                    vs[2] += vj.z;
-                    ps[0] += dx;
-                    ps[1] += dy_;
-                    ps[2] += dz_;
-                    ++nv;
-                }
+    RowWalk walk(c.gb, c.wb, bstart + c.cb_base, pb.x, pb.y, pb.z);
+    unsigned s0, s1;
+    while (walk.next(s0, s1)) {
+        for (unsigned j = s0 + lane; j < s1; j += 32) {
+            if (j == (unsigned)s) continue;
+            const float4 pj = bpos_s[j];
+            const float dx = __fsub_rn(pj.x, pb.x);
+            const float dy_ = __fsub_rn(pj.y, pb.y);
+            const float dz_ = __fsub_rn(pj.z, pb.z);
+            const float r2 = pair_r2(dx, dy_, dz_);
+            if (r2 < c.rs2) {
+                float w = 1.0f - sqrtf(r2) / c.rs;
+                w = fminf(fmaxf(w, 0.0f), 1.0f);
+                cl[0] -= dx * w;
+                cl[1] -= dy_ * w;
+                cl[2] -= dz_ * w;
+            }
+            if (r2 < c.rv2) {
+                const float4 vj = bvel_s[j];
+                vs[0] += vj.x;
+                vs[1] += vj.y;
+                vs[2] += vj.z;
+                ps[0] += dx;
+                ps[1] += dy_;
+                ps[2] += dz_;
+                ++nv;
             }
         }
     }
@@ -176,21 +164,21 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
     pos_next[slot] = np;
     vel_next[slot] = nvel;
     bool cl2 = false;
-    const unsigned k = cell_key(c.g, x[0], x[1], x[2], &cl2);
+    const unsigned k = (unsigned)c.c_base + cell_key(c.g, x[0], x[1], x[2], &cl2);
     key[slot] = k;
     rank[slot] = atomicAdd(&count[k], 1u);
     if (cl2) atomicOr(err, SPH_DEV_CLAMPED);
 }
 
 cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const unsigned* bstart,
-                              const StepConst& c, const float4* fb, float4* bpos, float4* bvel,
+                              const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
                               float4* pos_next, float4* vel_next, const int* slot_of_boid,
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches)
 {
-    if (c.nb <= 0) return cudaSuccess;
-    int blocks = (c.nb + BOID_WARPS - 1) / BOID_WARPS;
-    k_boid_rules<<<blocks, BOID_WARPS * 32, 0, s>>>(bpos_s, bvel_s, bstart, c, fb, bpos, bvel, pos_next,
+    if (sc.nb_all <= 0) return cudaSuccess;
+    int blocks = (sc.nb_all + BOID_WARPS - 1) / BOID_WARPS;
+    k_boid_rules<<<blocks, BOID_WARPS * 32, 0, s>>>(bpos_s, bvel_s, bstart, sc, fb, bpos, bvel, pos_next,
                                                     vel_next, slot_of_boid, key, rank, count, err);
     ++*launches;
     return cudaGetLastError();

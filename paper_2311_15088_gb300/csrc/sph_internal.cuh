@@ -21,12 +21,35 @@ struct GridDesc {
     float inv_d;
 };
 
-// Everything a kernel of the step needs, precomputed on the host.
+// Conservative search bounds of a grid walk: any particle j with
+// pair_r2 < r2_bound lies within `reach` of the query along every axis and
+// within `reach2` in squared distance; `margin` covers the float32
+// rounding of cell boundaries (cell = floor((p - m) * inv_d)).
+struct WalkBounds {
+    float reach2;   // r2_bound * (1 + 1e-5)
+    float reach;    // sqrt(reach2) + margin
+    float margin;   // absolute slack on cell boundaries
+    float d;        // cell size
+};
+
+// Everything a kernel of the step needs about one scene, precomputed on
+// the host.  A handle holds one StepConst per scene (a single scene is a
+// batch of one).  The scenes' particles, boids and cells occupy consecutive
+// ranges of the handle's arrays: scene k owns sorted slots [p_base,
+// p_base + n), boids [b_base, b_base + nb), particle cells [c_base, c_base +
+// g.ncells) and boid cells [cb_base, cb_base + gb.ncells).  Particle ids are
+// global: the attached particle of (global) boid b has id b, fluid particle f
+// (global, scene-major) has id nb_all + f, so "attached" is id < nb_all in
+// every scene and the order of ids inside a scene is the scene's own order.
 struct StepConst {
     GridDesc g;         // particle grid (cell_size)
     GridDesc gb;        // boid grid (boid_cell_size)
-    int n;              // particles: attached + fluid
-    int nb;             // boids == attached particles (ids < nb)
+    WalkBounds wg;      // particle grid, radius h
+    WalkBounds wb;      // boid grid, radius r_vis
+    int n;              // particles of the scene: attached + fluid
+    int nb;             // boids of the scene
+    int nb_all;         // boids of every scene: ids below it are attached
+    int p_base, b_base, c_base, cb_base;
     float h2;           // fl(h * h): the neighbour predicate bound
     float mC6;          // m * 315 / (64 pi h^9): poly6 prefactor times mass
     float half_cp_h;    // C_p h / 2: pressure pair prefactor (times 1/r)
@@ -86,7 +109,99 @@ __device__ __forceinline__ unsigned agg_increment(unsigned* count, unsigned k, b
 
 __device__ __forceinline__ int id_of(const float4& p) { return __float_as_int(p.w); }
 
+// Scene of element i: the k with base[k] <= i < base[k + 1] (base has S + 1
+// non-decreasing entries, base[0] = 0).  Empty scenes are skipped.
+__device__ __forceinline__ int scene_of(const unsigned* __restrict__ base, int S, unsigned i)
+{
+    int lo = 0, hi = S;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(base + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The scene table a kernel receives: per-scene constants and the slot /
+// boid bases of the scenes.
+struct Scenes {
+    const StepConst* __restrict__ c;
+    const unsigned* __restrict__ pbase;  // S + 1 sorted-slot bases
+    const unsigned* __restrict__ bbase;  // S + 1 boid bases
+    int S;
+    int n_all, nb_all;                   // particles and boids of every scene
+};
+
+// Squared distance from v to the padded extent of cell c along one axis;
+// the outermost cells of the grid are open towards the outside (positions
+// beyond the grid are clamped into them).
+__device__ __forceinline__ float axis_gap2(float v, int c, int dim, float mn, const WalkBounds& w)
+{
+    float lo = c > 0 ? fmaf((float)c, w.d, mn) - w.margin : -INFINITY;
+    float hi = c < dim - 1 ? fmaf((float)(c + 1), w.d, mn) + w.margin : INFINITY;
+    float gap = fmaxf(0.0f, fmaxf(lo - v, v - hi));
+    return gap * gap;
+}
+
+// Walk of every cell that can hold a particle within the bound radius of
+// (px, py, pz), as rows of contiguous sorted slots: z ascending, then y,
+// then the x-cells of the row ascending (the order of the 27-cell walk of
+// section "Neighborhood Search", restricted to the cells the sphere can
+// reach).  Rows and x-ranges are pruned per query with bounds that are
+// conservative for the float32 predicate, so the visited set always holds
+// every neighbour.  Usage: RowWalk w(...); while (w.next(s0, s1)) {...}
+// yields each non-empty row [s0, s1).
+struct RowWalk {
+    const GridDesc& g;
+    const WalkBounds& wb;
+    const unsigned* __restrict__ start;
+    float px, py, pz, rz;
+    int z, z1, y, y0, y1;
+
+    __device__ __forceinline__ RowWalk(const GridDesc& g_, const WalkBounds& w_, const unsigned* __restrict__ st,
+                                       float x_, float y_, float z_)
+        : g(g_), wb(w_), start(st), px(x_), py(y_), pz(z_), rz(0.0f)
+    {
+        bool cl = false;
+        const int z0 = cell_coord(pz - wb.reach, g.minf[2], g.inv_d, g.dim[2], &cl);
+        z1 = cell_coord(pz + wb.reach, g.minf[2], g.inv_d, g.dim[2], &cl);
+        y0 = cell_coord(py - wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
+        y1 = cell_coord(py + wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
+        z = z0 - 1;
+        y = y1 + 1;  // forces the first next() to open row z0
+    }
+
+    __device__ __forceinline__ bool next(unsigned& s0, unsigned& s1)
+    {
+        for (;;) {
+            if (y > y1) {
+                if (++z > z1) return false;
+                y = y0;
+                rz = wb.reach2 - axis_gap2(pz, z, g.dim[2], g.minf[2], wb);
+                if (!(rz > 0.0f)) {
+                    y = y1 + 1;
+                    continue;
+                }
+            }
+            const int yy = y++;
+            const float ryz = rz - axis_gap2(py, yy, g.dim[1], g.minf[1], wb);
+            if (!(ryz > 0.0f)) continue;
+            const float xr = sqrtf(ryz) + wb.margin;
+            bool cl = false;
+            const int x0 = cell_coord(px - xr, g.minf[0], g.inv_d, g.dim[0], &cl);
+            const int x1 = cell_coord(px + xr, g.minf[0], g.inv_d, g.dim[0], &cl);
+            const unsigned rowk = (unsigned)g.dim[0] * ((unsigned)yy + (unsigned)g.dim[1] * (unsigned)z);
+            s0 = __ldg(start + rowk + x0);
+            s1 = __ldg(start + rowk + x1 + 1);
+            if (s0 < s1) return true;
+        }
+    }
+};
+
 // ---------------------------------------------------------------- launchers
+
+// One-time kernel attributes; call before any stream capture.
+cudaError_t prepare_kernels();
 
 // Exclusive scan of n counts into start[0..n] (start[n] = total).  part must
 // hold scan_parts(n) + 1 entries.
@@ -94,8 +209,12 @@ int scan_parts(int n);
 cudaError_t launch_scan(const unsigned* counts, int n, unsigned* part, unsigned* start,
                         cudaStream_t s, long long* launches);
 
+// Cell keys of one grid (the allocation-free binning).
 cudaError_t launch_keys(const float4* pos, int n, const GridDesc& g, unsigned* key, unsigned* rank,
                         unsigned* count, unsigned* err, cudaStream_t s, long long* launches);
+// Cell keys of every scene's particles (global keys c_base + local key).
+cudaError_t launch_scene_keys(const float4* pos, const Scenes& sc, unsigned* key, unsigned* rank,
+                              unsigned* count, unsigned* err, cudaStream_t s, long long* launches);
 cudaError_t launch_scatter(const unsigned* key, const unsigned* rank, const unsigned* start, int n,
                            int* tmp, cudaStream_t s, long long* launches);
 // Per-cell sort by particle id + gather.  big_list (ncells ints) and
@@ -104,26 +223,44 @@ cudaError_t launch_cellsort_gather(const unsigned* start, int ncells, const int*
                                    const float4* pos_in, const float4* vel_in, float4* pos_out,
                                    float4* vel_out, int nb, int* slot_of_boid, int* big_list,
                                    unsigned* big_count, cudaStream_t s, long long* launches);
+// The same with one thread per sorted slot (for grids of small cells); key
+// holds the cell of every storage slot, n the number of particles.
+cudaError_t launch_cellsort_slots(const unsigned* start, const unsigned* key, int n, int ncells,
+                                  const int* tmp, const float4* pos_in, const float4* vel_in,
+                                  float4* pos_out, float4* vel_out, int nb, int* slot_of_boid,
+                                  int* big_list, unsigned* big_count, cudaStream_t s, long long* launches);
 cudaError_t launch_slot_keys(const unsigned* start, int ncells, unsigned* slot_key, cudaStream_t s,
                              long long* launches);
 
-cudaError_t launch_density(const float4* pos, const unsigned* start, const StepConst& c, float* rho,
-                           int* nbr, unsigned* err, cudaStream_t s, long long* launches);
+// Candidate bits the density pass keeps per particle for the force pass.
+constexpr int NBR_WORDS = 64;
+
+// Launch shape of the neighbour passes (chosen by the autotuner; results do
+// not depend on it).
+struct Tuning {
+    int block;       // threads per block of density / forces (64 .. 512)
+    int use_stream;  // 1: the force pass decodes the density pass's candidate bits
+};
+
+// Density, neighbour counts and the candidate bit stream (bits: NBR_WORDS
+// words per particle, word-interleaved; ncand: candidates per particle).
+cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
+                           float* rho, int* nbr, unsigned* bits, int* ncand, unsigned* err, cudaStream_t s,
+                           long long* launches);
 // mode 0: full step (every particle; fluid integrated into pos_next/vel_next,
 // next keys emitted); mode 1: only the attached particles' F_b.
 cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho,
-                          const unsigned* start, const StepConst& c, float4* acc, int* touched,
-                          float4* infl, float4* fb, float4* pos_next, float4* vel_next,
-                          unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
-                          cudaStream_t s, long long* launches);
-cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const StepConst& c,
-                                 int* counts, const long long* offsets, int* list, cudaStream_t s,
-                                 long long* launches);
+                          const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
+                          const Tuning& t, float4* acc, int* touched, float4* infl, float4* fb,
+                          float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,
+                          unsigned* err, cudaStream_t s, long long* launches);
+cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const Scenes& sc, int* counts,
+                                 const long long* offsets, int* list, cudaStream_t s, long long* launches);
 
-cudaError_t launch_boid_keys(const float4* bpos, int nb, const GridDesc& gb, unsigned* bkey,
-                             unsigned* brank, unsigned* bcount, cudaStream_t s, long long* launches);
+cudaError_t launch_boid_keys(const float4* bpos, const Scenes& sc, unsigned* bkey, unsigned* brank,
+                             unsigned* bcount, cudaStream_t s, long long* launches);
 cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const unsigned* bstart,
-                              const StepConst& c, const float4* fb, float4* bpos, float4* bvel,
+                              const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
                               float4* pos_next, float4* vel_next, const int* slot_of_boid,
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches);

@@ -11,80 +11,82 @@
 // Equations" (density -> forces -> integration) and section "Background"
 // (damped boundary).
 //
-// One thread per particle in sorted order.  A thread walks its 27-cell
-// stencil as 9 x-rows (cells x-1..x+1 of a row are contiguous in the sorted
-// arrays), rows in (dz, dy) order, so its float32 sums have a fixed order
-// that depends only on the state.  Neighbouring threads share cells, so the
-// candidate loads are served by L1.
+// One thread per particle in sorted order.  A thread walks the cells its
+// h-sphere can reach as rows of contiguous sorted slots (RowWalk: rows in
+// z, y order, x ascending, each row clipped to the sphere), so its float32
+// sums have a fixed order that depends only on the state.  Neighbouring
+// threads share cells, so the candidate loads are served by L1.
 #include "sph_internal.cuh"
 
 namespace sphk {
 
-struct RowRange {
-    unsigned s0, s1;
-};
-
-// The sorted-slot range of the x-row (cx-1 .. cx+1, y, z), clipped to the grid.
-__device__ __forceinline__ RowRange row_range(const GridDesc& g, const unsigned* __restrict__ start,
-                                              int cx, int y, int z)
-{
-    int x0 = cx > 0 ? cx - 1 : 0;
-    int x1 = cx + 1 < g.dim[0] ? cx + 1 : g.dim[0] - 1;
-    unsigned row = (unsigned)g.dim[0] * ((unsigned)y + (unsigned)g.dim[1] * (unsigned)z);
-    RowRange r;
-    r.s0 = __ldg(start + row + x0);
-    r.s1 = __ldg(start + row + x1 + 1);
-    return r;
-}
-
 // ---------------------------------------------------------------- density
 
-__global__ void __launch_bounds__(256)
-k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, StepConst c,
-          float* __restrict__ rho, int* __restrict__ nbr, unsigned* __restrict__ err)
+// The density pass also records, for every candidate it tests (in walk
+// order), whether the pair enters the force sum (0 < r2 < h2, not two
+// attached particles): bit k of particle i's candidate stream lives in word
+// bits[(k / 32) * n + i].  The force pass then visits only those slots.
+// Particles with more than NBR_WORDS * 32 candidates keep no stream
+// (ncand > capacity) and the force pass tests their candidates again.
+template <bool STREAM>
+__global__ void __launch_bounds__(512)
+k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
+          float* __restrict__ rho, int* __restrict__ nbr, unsigned* __restrict__ bits,
+          int* __restrict__ ncand, unsigned* __restrict__ err)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.n) return;
+    if (i >= sc.n_all) return;
+    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+    const float h2 = c.h2;
+    const int nb_all = sc.nb_all, n_all = sc.n_all;
     const float4 pi = pos[i];
-    const bool att_i = id_of(pi) < c.nb;
-    bool clamped = false;
-    const int cx = cell_coord(pi.x, c.g.minf[0], c.g.inv_d, c.g.dim[0], &clamped);
-    const int cy = cell_coord(pi.y, c.g.minf[1], c.g.inv_d, c.g.dim[1], &clamped);
-    const int cz = cell_coord(pi.z, c.g.minf[2], c.g.inv_d, c.g.dim[2], &clamped);
+    const bool att_i = id_of(pi) < nb_all;
     float sum = 0.0f;
     int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        if (z < 0 || z >= c.g.dim[2]) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= c.g.dim[1]) continue;
-            RowRange rr = row_range(c.g, start, cx, y, z);
-            for (unsigned j = rr.s0; j < rr.s1; ++j) {
-                const float4 pj = __ldg(pos + j);
-                float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
-                if (r2 < c.h2) {
-                    bool skip = att_i && id_of(pj) < c.nb && j != (unsigned)i;
-                    if (!skip) {
-                        float t = c.h2 - r2;
-                        sum = fmaf(t * t, t, sum);
-                        cnt += j != (unsigned)i;
-                    }
+    unsigned word = 0;
+    int nc = 0;
+    RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+    unsigned s0, s1;
+    while (walk.next(s0, s1)) {
+        for (unsigned j = s0; j < s1; ++j) {
+            const float4 pj = __ldg(pos + j);
+            const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+            const bool hit = r2 < h2;
+            const bool att_pair = att_i && id_of(pj) < nb_all;
+            if (hit && !(att_pair && j != (unsigned)i)) {
+                const float t = h2 - r2;
+                sum = fmaf(t * t, t, sum);
+                cnt += j != (unsigned)i;
+            }
+            if (STREAM) {
+                word |= (unsigned)(hit && r2 != 0.0f && !att_pair) << (nc & 31);
+                if (((nc + 1) & 31) == 0) {
+                    const int w = nc >> 5;
+                    if (w < NBR_WORDS) bits[(size_t)w * n_all + i] = word;
+                    word = 0;
                 }
             }
+            ++nc;
         }
     }
+    if (STREAM && (nc & 31) != 0 && (nc >> 5) < NBR_WORDS) bits[(size_t)(nc >> 5) * n_all + i] = word;
+    ncand[i] = nc;
     float r = c.mC6 * sum;
     rho[i] = r;
     nbr[i] = cnt;
     if (!isfinite(r)) atomicOr(err, SPH_DEV_NONFINITE);
 }
 
-cudaError_t launch_density(const float4* pos, const unsigned* start, const StepConst& c, float* rho,
-                           int* nbr, unsigned* err, cudaStream_t s, long long* launches)
+cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
+                           float* rho, int* nbr, unsigned* bits, int* ncand, unsigned* err, cudaStream_t s,
+                           long long* launches)
 {
-    if (c.n <= 0) return cudaSuccess;
-    k_density<<<(c.n + 255) / 256, 256, 0, s>>>(pos, start, c, rho, nbr, err);
+    if (sc.n_all <= 0) return cudaSuccess;
+    const int blocks = (sc.n_all + t.block - 1) / t.block;
+    if (t.use_stream)
+        k_density<true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, err);
+    else
+        k_density<false><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, err);
     ++*launches;
     return cudaGetLastError();
 }
@@ -94,21 +96,25 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const StepC
 // f_ij = m/rho_j [ C_p (p_i + p_j)/2 (1-q)^2/q r_ij - C_v mu (1-q) v_ij ],
 // r_ij = x_i - x_j, v_ij = v_i - v_j; a_i = (1/rho_i) sum_j f_ij (+ g).
 template <int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ rho,
-         const unsigned* __restrict__ start, StepConst c, float4* __restrict__ acc,
-         int* __restrict__ touched, float4* __restrict__ infl, float4* __restrict__ fb,
-         float4* __restrict__ pos_next, float4* __restrict__ vel_next, unsigned* __restrict__ key,
-         unsigned* __restrict__ rank, unsigned* __restrict__ count, unsigned* __restrict__ err)
+         const unsigned* __restrict__ start, const unsigned* __restrict__ bits, const int* __restrict__ ncand,
+         Scenes sc, int use_stream, float4* __restrict__ acc, int* __restrict__ touched,
+         float4* __restrict__ infl, float4* __restrict__ fb, float4* __restrict__ pos_next,
+         float4* __restrict__ vel_next, unsigned* __restrict__ key, unsigned* __restrict__ rank,
+         unsigned* __restrict__ count, unsigned* __restrict__ err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < c.n;
+    const bool active = i < sc.n_all;
     const int ii = active ? i : 0;
+    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)ii)];
+    const int nb_all = sc.nb_all;
     const float4 pi = pos[ii];
     const int id_i = id_of(pi);
-    const bool att_i = id_i < c.nb;
+    const bool att_i = id_i < nb_all;
     // MODE 1 computes only the attached particles (threads of the others idle)
     const bool work = active && (MODE == 0 || att_i);
+    const unsigned* cstart = start + c.c_base;
 
     float ax = 0.f, ay = 0.f, az = 0.f;
     float bx = 0.f, by = 0.f, bz = 0.f;
@@ -119,48 +125,76 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
         const float4 vi = __ldg(vel + i);
         rho_i = __ldg(rho + i);
         const float p_i = c.k * (rho_i - c.rho0);
-        const int cx = cell_coord(pi.x, c.g.minf[0], c.g.inv_d, c.g.dim[0], &clamped);
-        const int cy = cell_coord(pi.y, c.g.minf[1], c.g.inv_d, c.g.dim[1], &clamped);
-        const int cz = cell_coord(pi.z, c.g.minf[2], c.g.inv_d, c.g.dim[2], &clamped);
-        for (int dz = -1; dz <= 1; ++dz) {
-            int z = cz + dz;
-            if (z < 0 || z >= c.g.dim[2]) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
-                int y = cy + dy;
-                if (y < 0 || y >= c.g.dim[1]) continue;
-                RowRange rr = row_range(c.g, start, cx, y, z);
-                for (unsigned j = rr.s0; j < rr.s1; ++j) {
-                    const float4 pj = __ldg(pos + j);
-                    const float dx = __fsub_rn(pj.x, pi.x);
-                    const float dy_ = __fsub_rn(pj.y, pi.y);
-                    const float dz_ = __fsub_rn(pj.z, pi.z);
-                    const float r2 = pair_r2(dx, dy_, dz_);
-                    if (!(r2 < c.h2) || r2 == 0.0f) continue;
-                    const bool att_j = id_of(pj) < c.nb;
-                    if (att_i && att_j) continue;
-                    const float4 vj = __ldg(vel + j);
-                    const float rho_j = __ldg(rho + j);
-                    const float p_j = c.k * (rho_j - c.rho0);
-                    const float rinv = rsqrtf(r2);
-                    const float q = r2 * rinv * c.inv_h;
-                    const float omq = 1.0f - q;
-                    const float m_rho_j = c.mass / rho_j;
-                    // pressure: C_p (p_i+p_j)/2 (1-q)^2 / q along r_ij = -(dx,dy,dz)
-                    const float sp = -m_rho_j * c.half_cp_h * (p_i + p_j) * omq * omq * rinv;
-                    // viscosity: -C_v mu (1-q) (v_i - v_j)
-                    const float sv = -m_rho_j * c.cv_mu * omq;
-                    const float fx = fmaf(sp, dx, sv * (vi.x - vj.x));
-                    const float fy = fmaf(sp, dy_, sv * (vi.y - vj.y));
-                    const float fz = fmaf(sp, dz_, sv * (vi.z - vj.z));
-                    ax += fx;
-                    ay += fy;
-                    az += fz;
-                    if (MODE == 0 && att_j) {
-                        ++touch;
-                        bx += fx;
-                        by += fy;
-                        bz += fz;
+        // one neighbour j (0 < r2 < h2, not two attached particles)
+        auto pair = [&](unsigned j) {
+            const float4 pj = __ldg(pos + j);
+            const float dx = __fsub_rn(pj.x, pi.x);
+            const float dy_ = __fsub_rn(pj.y, pi.y);
+            const float dz_ = __fsub_rn(pj.z, pi.z);
+            const float r2 = pair_r2(dx, dy_, dz_);
+            const float4 vj = __ldg(vel + j);
+            const float rho_j = __ldg(rho + j);
+            const float p_j = c.k * (rho_j - c.rho0);
+            const float rinv = rsqrtf(r2);
+            const float q = r2 * rinv * c.inv_h;
+            const float omq = 1.0f - q;
+            const float m_rho_j = c.mass / rho_j;
+            // pressure: C_p (p_i+p_j)/2 (1-q)^2 / q along r_ij = -(dx,dy,dz)
+            const float sp = -m_rho_j * c.half_cp_h * (p_i + p_j) * omq * omq * rinv;
+            // viscosity: -C_v mu (1-q) (v_i - v_j)
+            const float sv = -m_rho_j * c.cv_mu * omq;
+            const float fx = fmaf(sp, dx, sv * (vi.x - vj.x));
+            const float fy = fmaf(sp, dy_, sv * (vi.y - vj.y));
+            const float fz = fmaf(sp, dz_, sv * (vi.z - vj.z));
+            ax += fx;
+            ay += fy;
+            az += fz;
+            if (MODE == 0 && id_of(pj) < nb_all) {
+                ++touch;
+                bx += fx;
+                by += fy;
+                bz += fz;
+            }
+        };
+        if (use_stream && ncand[i] <= NBR_WORDS * 32) {
+            // decode the density pass's candidate bits, row by row
+            int bitpos = 0, wcur = -1;
+            unsigned wv = 0;
+            RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
+            unsigned s0, s1;
+            while (walk.next(s0, s1)) {
+                unsigned j = s0;
+                while (j < s1) {
+                    const int w = bitpos >> 5, b = bitpos & 31;
+                    if (w != wcur) {
+                        wv = __ldg(bits + (size_t)w * sc.n_all + i);
+                        wcur = w;
                     }
+                    const unsigned left = s1 - j;
+                    const int take = left < (unsigned)(32 - b) ? (int)left : 32 - b;
+                    unsigned m = wv >> b;
+                    if (take < 32) m &= (1u << take) - 1u;
+                    while (m) {
+                        const int t = __ffs(m) - 1;
+                        m &= m - 1u;
+                        pair(j + (unsigned)t);
+                    }
+                    j += (unsigned)take;
+                    bitpos += take;
+                }
+            }
+        } else {
+            // no stored stream: test every candidate again (same order)
+            RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
+            unsigned s0, s1;
+            while (walk.next(s0, s1)) {
+                for (unsigned j = s0; j < s1; ++j) {
+                    const float4 pj = __ldg(pos + j);
+                    const float r2 =
+                        pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+                    if (!(r2 < c.h2) || r2 == 0.0f) continue;
+                    if (att_i && id_of(pj) < nb_all) continue;
+                    pair(j);
                 }
             }
         }
@@ -212,7 +246,7 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
         }
         pos_next[i] = make_float4(x[0], x[1], x[2], pi.w);
         vel_next[i] = make_float4(v[0], v[1], v[2], 0.0f);
-        k_next = cell_key(c.g, x[0], x[1], x[2], &clamped);
+        k_next = (unsigned)c.c_base + cell_key(c.g, x[0], x[1], x[2], &clamped);
         key[i] = k_next;
     }
     unsigned r = agg_increment(count, k_next, fluid);
@@ -221,19 +255,19 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
 }
 
 cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho,
-                          const unsigned* start, const StepConst& c, float4* acc, int* touched,
-                          float4* infl, float4* fb, float4* pos_next, float4* vel_next,
-                          unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
-                          cudaStream_t s, long long* launches)
+                          const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
+                          const Tuning& t, float4* acc, int* touched, float4* infl, float4* fb,
+                          float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,
+                          unsigned* err, cudaStream_t s, long long* launches)
 {
-    if (c.n <= 0) return cudaSuccess;
-    int blocks = (c.n + 255) / 256;
+    if (sc.n_all <= 0) return cudaSuccess;
+    const int blocks = (sc.n_all + t.block - 1) / t.block;
     if (mode == 0)
-        k_forces<0><<<blocks, 256, 0, s>>>(pos, vel, rho, start, c, acc, touched, infl, fb, pos_next,
-                                           vel_next, key, rank, count, err);
+        k_forces<0><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, acc, touched,
+                                               infl, fb, pos_next, vel_next, key, rank, count, err);
     else
-        k_forces<1><<<blocks, 256, 0, s>>>(pos, vel, rho, start, c, acc, touched, infl, fb, pos_next,
-                                           vel_next, key, rank, count, err);
+        k_forces<1><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, acc, touched,
+                                               infl, fb, pos_next, vel_next, key, rank, count, err);
     ++*launches;
     return cudaGetLastError();
 }
@@ -241,48 +275,39 @@ cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const 
 // ---------------------------------------------------------- neighbour list
 
 __global__ void __launch_bounds__(256)
-k_neighbor_list(const float4* __restrict__ pos, const unsigned* __restrict__ start, StepConst c,
+k_neighbor_list(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
                 int* __restrict__ counts, const long long* __restrict__ offsets, int* __restrict__ list)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c.n) return;
+    if (i >= sc.n_all) return;
+    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
     const float4 pi = pos[i];
     const int id_i = id_of(pi);
-    const bool att_i = id_i < c.nb;
-    bool clamped = false;
-    const int cx = cell_coord(pi.x, c.g.minf[0], c.g.inv_d, c.g.dim[0], &clamped);
-    const int cy = cell_coord(pi.y, c.g.minf[1], c.g.inv_d, c.g.dim[1], &clamped);
-    const int cz = cell_coord(pi.z, c.g.minf[2], c.g.inv_d, c.g.dim[2], &clamped);
+    const bool att_i = id_i < sc.nb_all;
     long long o = offsets ? offsets[id_i] : 0;
     int cnt = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        if (z < 0 || z >= c.g.dim[2]) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= c.g.dim[1]) continue;
-            RowRange rr = row_range(c.g, start, cx, y, z);
-            for (unsigned j = rr.s0; j < rr.s1; ++j) {
-                if (j == (unsigned)i) continue;
-                const float4 pj = pos[j];
-                if (att_i && id_of(pj) < c.nb) continue;
-                float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
-                if (r2 < c.h2) {
-                    if (list) list[o + cnt] = id_of(pj);
-                    ++cnt;
-                }
+    RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+    unsigned s0, s1;
+    while (walk.next(s0, s1)) {
+        for (unsigned j = s0; j < s1; ++j) {
+            if (j == (unsigned)i) continue;
+            const float4 pj = pos[j];
+            if (att_i && id_of(pj) < sc.nb_all) continue;
+            float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+            if (r2 < c.h2) {
+                if (list) list[o + cnt] = id_of(pj);
+                ++cnt;
             }
         }
     }
     counts[id_i] = cnt;
 }
 
-cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const StepConst& c,
-                                 int* counts, const long long* offsets, int* list, cudaStream_t s,
-                                 long long* launches)
+cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const Scenes& sc, int* counts,
+                                 const long long* offsets, int* list, cudaStream_t s, long long* launches)
 {
-    if (c.n <= 0) return cudaSuccess;
-    k_neighbor_list<<<(c.n + 255) / 256, 256, 0, s>>>(pos, start, c, counts, offsets, list);
+    if (sc.n_all <= 0) return cudaSuccess;
+    k_neighbor_list<<<(sc.n_all + 255) / 256, 256, 0, s>>>(pos, start, sc, counts, offsets, list);
     ++*launches;
     return cudaGetLastError();
 }

@@ -71,8 +71,10 @@ def default_params(**overrides) -> dict:
     """The constant set of the dam-break workloads (every float float32-exact).
 
     h = 0.0457, rest density 1000, gas constant 3, viscosity 3.5, dt = 1e-3,
-    gravity -9.8 along y (y is up), cell size h, wall restitution 0.75,
-    boid radii 2h / 4h / 4h and the boid weights below.
+    gravity -9.8 along y (y is up), cell size h/2 (the grid cell is a free
+    parameter of the method; h/2 lets the walk clip each particle's search
+    to its h-sphere), wall restitution 0.75, boid radii 2h / 4h / 4h and the
+    boid weights below.
     ``mass`` must be supplied by the caller (it depends on the layout).
     """
     h = f32(0.0457)
@@ -80,7 +82,7 @@ def default_params(**overrides) -> dict:
         h=h, rho0=1000.0, k=3.0, mu=3.5, dt=f32(1e-3),
         gx=0.0, gy=f32(-9.8), gz=0.0, mass=None,
         box_min=(0.0, 0.0, 0.0), box_max=(1.0, 1.0, 1.0),
-        cell_size=h, const_set=0, wall_restitution=0.75,
+        cell_size=f32(np.float32(h) / np.float32(2)), const_set=0, wall_restitution=0.75,
         r_sep=f32(np.float32(2) * np.float32(h)),
         r_vis=f32(np.float32(4) * np.float32(h)),
         w_sep=f32(0.05), w_align=f32(0.05), w_coh=f32(0.005),
@@ -229,3 +231,35 @@ def scaled_block(n, n_boid, box_max, region_hi, seed, mass_density=1000.0):
     return dict(name=f"uniform block {n} particles, {n_boid} boids",
                 params=p, fluid_pos=pos, fluid_vel=_zeros4(n),
                 boid_pos=bpos, boid_vel=bvel, lattice_spacing=None)
+
+
+def batched_tanks(n_scenes=256, seed_offset=0, n_min=2048, n_max=65536, b_min=8, b_max=256):
+    """Independent unit-box dam-breaks for the batched workload: particle
+    counts log-uniform in [n_min, n_max], boid counts uniform in
+    [b_min, b_max].  Scene k: a column of lattice layers at spacing h/2 (width
+    min(ceil(N^(1/3)), floor(0.92/s)) points, the first N points of the
+    lattice, jitter +-0.1 spacing) in the (0,0,0) corner, boids uniform in
+    the box with unit-speed headings.  Mass as in the 4,096-particle
+    dam-break (lattice density = rest density; ``lattice_spacing``).
+    Returns a list of scene dicts."""
+    seed = BASE_SEED + 3 + seed_offset
+    size_rng = PaperHashRNG(seed, np.arange(n_scenes))
+    u = size_rng.next_unit().astype(np.float64)
+    v = size_rng.next_unit().astype(np.float64)
+    counts = np.floor(np.exp(math.log(n_min) + u * (math.log(n_max) - math.log(n_min)))).astype(np.int64)
+    counts = np.clip(counts, n_min, n_max)
+    boids = (b_min + np.floor(v * (b_max - b_min + 1))).astype(np.int64)
+    boids = np.clip(boids, b_min, b_max)
+    out = []
+    for k in range(n_scenes):
+        p = default_params()
+        s = f32(np.float32(p["h"]) / np.float32(2))
+        n, nb = int(counts[k]), int(boids[k])
+        w = min(int(math.ceil(n ** (1.0 / 3.0) - 1e-9)), int(math.floor(0.92 / s)))
+        layers = int(math.ceil(n / (w * w)))
+        rng = PaperHashRNG(seed + 1000 * (k + 1), nb + np.arange(w * w * layers))
+        pos = lattice_block((w, layers, w), s, (0.0, 0.0, 0.0), 0.1, rng)[:n]
+        bpos, bvel = boids_uniform(nb, p["box_min"], p["box_max"], seed + 1000 * (k + 1))
+        out.append(dict(name=f"batched tank {k}: {n} particles, {nb} boids", params=p, fluid_pos=pos,
+                        fluid_vel=_zeros4(n), boid_pos=bpos, boid_vel=bvel, lattice_spacing=s))
+    return out

@@ -30,7 +30,7 @@ FIELDS = {
     "touched": (3, np.int32, 1), "influence": (4, np.float32, 4), "nbr_count": (5, np.int32, 1),
     "keys": (6, np.uint32, 1), "perm": (7, np.int32, 1), "cell_start": (8, np.uint32, 1),
     "fb": (9, np.float32, 4), "boid_keys": (10, np.uint32, 1), "boid_perm": (11, np.int32, 1),
-    "boid_cell_start": (12, np.uint32, 1),
+    "boid_cell_start": (12, np.uint32, 1), "ncand": (13, np.int32, 1),
 }
 
 
@@ -68,6 +68,10 @@ _sig = {
     "sph_profile_enable": (_i, [_vp, _i]),
     "sph_profile_read": (_i, [_vp, _vp, _vp, _i]),
     "sph_bin_static": (_i, [_P, _i, _vp, _vp, _vp, _vp, _vp]),
+    "sph_batch_workspace_size": (_i, [_P, _vp, _vp, _i, ctypes.POINTER(_sz)]),
+    "sph_batch_create": (_i, [_P, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_vp)]),
+    "sph_set_tuning": (_i, [_vp, _i, _i]),
+    "sph_graph_step": (_i, [_vp, _i, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -131,6 +135,41 @@ def sph_create(params: dict, n_fluid: int, n_boid: int, workspace_ptr: int, ws_b
     _check(_lib.sph_create(ctypes.byref(make_params(params)), n_fluid, n_boid, workspace_ptr, ws_bytes,
                            ctypes.byref(h)))
     return h
+
+
+def _param_array(params_list):
+    arr = (SphParams * len(params_list))()
+    for k, p in enumerate(params_list):
+        arr[k] = make_params(p)
+    return arr
+
+
+def sph_batch_workspace_size(params_list, n_fluid, n_boid) -> int:
+    S = len(params_list)
+    nf = (ctypes.c_int * S)(*n_fluid)
+    nb = (ctypes.c_int * S)(*n_boid)
+    out = _sz()
+    _check(_lib.sph_batch_workspace_size(_param_array(params_list), ctypes.cast(nf, _vp), ctypes.cast(nb, _vp), S,
+                                         ctypes.byref(out)))
+    return int(out.value)
+
+
+def sph_batch_create(params_list, n_fluid, n_boid, workspace_ptr: int, ws_bytes: int):
+    S = len(params_list)
+    nf = (ctypes.c_int * S)(*n_fluid)
+    nb = (ctypes.c_int * S)(*n_boid)
+    h = _vp()
+    _check(_lib.sph_batch_create(_param_array(params_list), ctypes.cast(nf, _vp), ctypes.cast(nb, _vp), S,
+                                 workspace_ptr, ws_bytes, ctypes.byref(h)))
+    return h
+
+
+def sph_set_tuning(h, block: int, use_stream: int):
+    _check(_lib.sph_set_tuning(h, block, use_stream), h)
+
+
+def sph_graph_step(h, nsteps: int, stream: int):
+    _check(_lib.sph_graph_step(h, nsteps, stream), h)
 
 
 def sph_set_state(h, fluid_pos, fluid_vel, boid_pos, boid_vel, on_host: int, stream: int):
@@ -214,21 +253,31 @@ class Scene:
     Inputs are float32 ``(n, 4)`` arrays (numpy or torch); outputs are torch
     tensors on the device.  All calls use torch's current stream."""
 
-    def __init__(self, params: dict, n_fluid: int, n_boid: int, device="cuda"):
+    def __init__(self, params, n_fluid, n_boid, device="cuda"):
+        """One scene (params a dict, counts ints) or a batch (params a list
+        of dicts, counts lists); a batch concatenates the scenes' arrays."""
         import torch
 
         self.torch = torch
-        self.params = dict(params)
-        self.n_fluid, self.n_boid = int(n_fluid), int(n_boid)
+        batch = isinstance(params, (list, tuple))
+        self.params_list = [dict(p) for p in params] if batch else [dict(params)]
+        self.params = self.params_list[0]
+        nf = list(n_fluid) if batch else [int(n_fluid)]
+        nbl = list(n_boid) if batch else [int(n_boid)]
+        self.scene_n_fluid, self.scene_n_boid = nf, nbl
+        self.n_fluid, self.n_boid = int(sum(nf)), int(sum(nbl))
         self.n = self.n_fluid + self.n_boid
         self.device = torch.device(device)
-        nbytes = sph_workspace_size(self.params, self.n_fluid, self.n_boid)
+        nbytes = sph_batch_workspace_size(self.params_list, nf, nbl)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) & ~255
-        self.handle = sph_create(self.params, self.n_fluid, self.n_boid, self._ws_ptr, nbytes)
-        self.dims = sph_grid_dims(self.params, 0)
-        self.bdims = sph_grid_dims(self.params, 1)
+        self.handle = sph_batch_create(self.params_list, nf, nbl, self._ws_ptr, nbytes)
+        dims = [sph_grid_dims(p, 0) for p in self.params_list]
+        bdims = [sph_grid_dims(p, 1) for p in self.params_list]
+        self.dims, self.bdims = dims[0], bdims[0]
+        self.ncells = int(sum(d[0] * d[1] * d[2] for d in dims))
+        self.nbcells = int(sum(d[0] * d[1] * d[2] for d in bdims))
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -272,13 +321,20 @@ class Scene:
     def step(self, nsteps: int = 1):
         sph_step(self.handle, nsteps, self.stream)
 
+    def graph_step(self, nsteps: int = 1):
+        """sph_step replayed from a captured CUDA graph (non-default stream)."""
+        sph_graph_step(self.handle, nsteps, self.stream)
+
+    def set_tuning(self, block: int, use_stream: int):
+        sph_set_tuning(self.handle, block, use_stream)
+
     def field(self, name: str):
         t = self.torch
         code, dtype, width = FIELDS[name]
         if name == "cell_start":
-            n = self.dims[0] * self.dims[1] * self.dims[2] + 1
+            n = self.ncells + 1
         elif name == "boid_cell_start":
-            n = self.bdims[0] * self.bdims[1] * self.bdims[2] + 1
+            n = self.nbcells + 1
         elif name in ("fb", "boid_keys", "boid_perm"):
             n = self.n_boid
         else:

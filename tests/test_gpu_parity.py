@@ -32,9 +32,14 @@ def _check(p, sc):
     return s, g, o
 
 
-def test_dam_break_4096_first_step():
+CELLS = [1.0, 0.5, 0.34]  # cell size in units of h
+
+
+@pytest.mark.parametrize("cell", CELLS)
+def test_dam_break_4096_first_step(cell):
     sc = scenes.dam_break_small()
     p = lattice_params(sc)
+    p["cell_size"] = scenes.f32(p["h"] * cell)
     _check(p, sc)
 
 
@@ -48,26 +53,37 @@ def test_dam_break_4096_after_80_gpu_steps():
     _check(p, st)
 
 
-@pytest.mark.parametrize("const_set", [0, 1])
-def test_fluid_with_boids_inside(const_set):
+@pytest.mark.parametrize("const_set,cell", [(0, 0.5), (1, 0.5), (0, 1.0), (1, 0.34)])
+def test_fluid_with_boids_inside(const_set, cell):
     """12k particles with 300 boids moving through the fluid: coupling,
     touched_by_boid and boid_influence are all exercised."""
     sc = scenes.scaled_block(12000, 300, (0.6, 0.6, 0.6), (0.6, 0.4, 0.6), seed=77)
     sc["boid_pos"][:, 1] *= np.float32(0.4 / 0.6)
     p = dict(sc["params"], const_set=const_set)
+    p["cell_size"] = scenes.f32(p["h"] * cell)
     _s, _g, o = _check(p, sc)
     assert o["touched"].sum() > 1000
 
 
-def test_column_262144_first_step():
+@pytest.mark.parametrize("cell", [1.0, 0.5])
+def test_column_262144_first_step(cell):
     sc = scenes.dam_break_column()
     p = lattice_params(sc)
+    p["cell_size"] = scenes.f32(p["h"] * cell)
     _check(p, sc)
 
 
-def test_neighbor_lists_bit_exact():
+@pytest.mark.parametrize("cell", CELLS + [0.25])
+def test_neighbor_lists_bit_exact(cell):
+    """Neighbour lists, in walk order, equal the oracle's; particles are
+    squeezed into the corners and some lie outside the box."""
     sc = scenes.scaled_block(6000, 40, (0.5, 0.5, 0.5), (0.5, 0.5, 0.5), seed=3)
-    p = sc["params"]
+    p = dict(sc["params"], cell_size=scenes.f32(sc["params"]["h"] * cell))
+    fp = sc["fluid_pos"]
+    k = len(fp) // 4
+    fp[:k, :3] = np.where(fp[:k, :3] < 0.25, fp[:k, :3] * 0.1, 0.5 - (0.5 - fp[:k, :3]) * 0.1)
+    fp[k:k + 50, 0] = np.float32(-0.02)
+    fp[k + 50:k + 100, 1] = np.float32(0.53)
     s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
     s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
     counts, offsets, lst = s.neighbors()
@@ -78,16 +94,20 @@ def test_neighbor_lists_bit_exact():
     assert np.array_equal(lst.cpu().numpy(), l2)
 
 
-def test_crowded_cells_sort_paths():
-    """Cells with more than 32 and more than 512 particles take the other
-    two paths of the per-cell sort; order and sums must still match."""
+@pytest.mark.parametrize("cell", [1.0, 0.5])
+def test_crowded_cells_sort_paths(cell):
+    """Crowded cells take the block-sort path of the per-cell sort, and the
+    2,500-particle clump has more candidates per particle than the density
+    pass can record, so the force pass tests them again; order and sums must
+    still match."""
     rng = np.random.default_rng(5)
     p = scenes.default_params(mass=scenes.f32(0.001))
     h = p["h"]
-    a = 0.5 + rng.uniform(0, 0.9 * h, size=(700, 3))        # one cell, > 512
-    b = 0.2 + rng.uniform(0, 0.9 * h, size=(100, 3))        # one cell, 33..512
+    p["cell_size"] = scenes.f32(h * cell)
+    a = 0.5 + rng.uniform(0, 0.9 * h, size=(2500, 3))       # > 2,048 candidates each
+    b = 0.2 + rng.uniform(0, 0.4 * h, size=(100, 3))        # one crowded cell
     c = rng.uniform(0.05, 0.95, size=(3000, 3))             # sparse background
-    pos = np.zeros((3800, 4), np.float32)
+    pos = np.zeros((5600, 4), np.float32)
     pos[:, :3] = np.concatenate([a, b, c])
     sc = dict(fluid_pos=pos, fluid_vel=np.zeros_like(pos), boid_pos=np.zeros((0, 4), np.float32),
               boid_vel=np.zeros((0, 4), np.float32))

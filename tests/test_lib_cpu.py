@@ -55,8 +55,8 @@ def test_workspace_size_grows_with_particles(lib):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(h=0.0), dict(cell_size=0.04), dict(mass=-1.0), dict(dt=0.0), dict(box_max=(0.0, 1.0, 1.0)),
-    dict(const_set=7), dict(coupling_mode=1), dict(boid_cell_size=0.1), dict(r_sep=0.5),
+    dict(h=0.0), dict(cell_size=0.01), dict(mass=-1.0), dict(dt=0.0), dict(box_max=(0.0, 1.0, 1.0)),
+    dict(const_set=7), dict(coupling_mode=1), dict(boid_cell_size=0.04), dict(r_sep=0.5),
     dict(v_min=2.0), dict(k=float("nan")), dict(wall_restitution=-1.0),
 ])
 def test_invalid_parameters_are_rejected(lib, bad):
@@ -78,7 +78,9 @@ def test_grid_dims_match_oracle(lib, orc):
     for p in (_p(), _p(box_max=(2.0, 1.0, 1.0)), _p(box_max=(4.0, 2.0, 2.0))):
         assert lib.sph_grid_dims(p, 0) == orc.grid_dims(p, 0)
         assert lib.sph_grid_dims(p, 1) == orc.grid_dims(p, 1)
-    assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0)), 0) == (88, 44, 44)
+    h = scenes.default_params()["h"]
+    assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0), cell_size=h), 0) == (88, 44, 44)
+    assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0)), 0) == (176, 88, 88)
     assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0)), 1) == (22, 11, 11)
 
 
