@@ -59,6 +59,7 @@ extern "C" {
 /* Bits of the sticky device error word (sph_status). */
 #define SPH_DEV_NONFINITE 1u  /* a density, position or velocity became NaN/Inf  */
 #define SPH_DEV_CLAMPED   2u  /* a position lay outside the grid and was clamped */
+#define SPH_DEV_TIMEOUT   4u  /* a bounded wait inside a kernel gave up          */
 
 /* Fields that sph_get_fields can return (one per call). */
 #define SPH_FIELD_RHO         0  /* float[n_tot]   density, by particle id                 */
@@ -271,6 +272,57 @@ int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds);
 
 /* Free the host-side handle (the workspace stays the caller's). */
 void sph_destroy(sph_handle* h);
+
+/*
+ * Boid-force surrogate (not in the paper): an MLP from a boid's local flow
+ * features to the fluid force F_b of the SPH coupling.  Rows of x are
+ * SPH_MLP_IN BF16 features (256 stencil features, 3 boid-velocity features,
+ * zero padding); y rows are SPH_MLP_OUT FP32 outputs (0..2: F_b / F_scale,
+ * 3: error head, log10 of the expected relative error; the rest unused).
+ * Layers 272 -> 256 -> 256 -> 256 -> 16 with exact-erf GELU between them.
+ * Parameters are one FP32 vector of SPH_MLP_PARAMS floats in the order
+ * W1 [256][272], b1, W2 [256][256], b2, W3, b3, W4 [16][256], b4.  Every
+ * matrix product runs on the tensor cores (BF16 operands, FP32 accumulate);
+ * training is Adam on FP32 master weights.  A handle owns a caller-given
+ * workspace sized for batches of up to max_batch rows (a multiple of 128);
+ * every batch B must be a positive multiple of 128 and <= max_batch.
+ */
+#define SPH_MLP_IN      272
+#define SPH_MLP_HIDDEN  256
+#define SPH_MLP_OUT     16
+#define SPH_MLP_PARAMS  205584
+typedef struct sph_mlp sph_mlp;
+int sph_mlp_workspace_size(int max_batch, size_t* bytes);
+int sph_mlp_create(int max_batch, void* workspace, size_t ws_bytes, sph_mlp** out);
+void sph_mlp_destroy(sph_mlp* m);
+/* Load parameters (device FP32 vector) and reset the Adam moments. */
+int sph_mlp_set_params(sph_mlp* m, const float* params, void* stream);
+int sph_mlp_get_params(sph_mlp* m, float* params, void* stream);
+/* y[B][16] = MLP(x[B][272]) (device buffers; x 16-byte aligned). */
+int sph_mlp_forward(sph_mlp* m, const void* x_bf16, int B, float* y, void* stream);
+/* Parameter gradients of sum(dy * y) for an upstream gradient dy[B][16]
+ * (FP32, device), written to grads (SPH_MLP_PARAMS FP32, device). */
+int sph_mlp_gradients(sph_mlp* m, const void* x_bf16, const float* dy, int B, float* grads, void* stream);
+/* One Adam step on a batch: targets t[B][4] (0..2 force / F_scale, 3 error
+ * target).  phase 0: force loss mean 1/2 |y[0:3] - t[0:3]|^2, every
+ * parameter except the error head (row 3 of W4, b4[3]); phase 1: error loss
+ * mean 1/2 (y[3] - t[3])^2, the error head only.  *loss_out (device, may be
+ * NULL) receives the batch loss. */
+int sph_mlp_train_step(sph_mlp* m, const void* x_bf16, const float* target, int B, int phase, float lr,
+                       float* loss_out, void* stream);
+/* Sticky device error word of the MLP kernels (SPH_DEV_TIMEOUT); syncs. */
+int sph_mlp_status(sph_mlp* m, unsigned* bits, void* stream);
+long long sph_mlp_launch_count(sph_mlp* m);
+/*
+ * Test hook of the tensor-core GEMM: for BF16 row-major A[M][K] (leading
+ * dimension lda) and B[N][K] (ldb), both 16-byte aligned with leading
+ * dimensions multiples of 8, writes the FP32 partial products of `splits`
+ * K-ranges to C[split][M][N] (C holds splits * M * N floats; their sum is
+ * A B^T; the actual number of splits is min(splits, ceil(K / 64)) rounded
+ * so that no range is empty).  err: a device word for SPH_DEV_TIMEOUT.
+ */
+int sph_debug_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int splits, float* C,
+                   unsigned* err, void* stream);
 
 /*
  * Allocation-free binning.  The paper has no counterpart to this entry point;

@@ -1,0 +1,755 @@
+// sph_mlp.cu -- the boid-force surrogate: a 272 -> 256 -> 256 -> 256 -> 16
+// MLP (exact-erf GELU) whose inference and training GEMMs run on the
+// tensor cores (tcgen05.mma kind::f16: BF16 operands staged by TMA, FP32
+// accumulators in tensor memory), with Adam on FP32 master weights.
+//
+// The surrogate is not in the paper; it predicts the fluid force the SPH
+// coupling of section "Boid Motion and Agent Fluid Interaction" puts on a
+// boid (F_b in v_b += sph_factor dt F_b) from the flow around the boid.
+//
+// Layout: a layer's weight W is [out][in] (K-major for the B operand of the
+// forward GEMM) with a transposed BF16 copy W^T [in][out] for the backward
+// GEMM; activations are [batch][features] with transposed copies
+// [features][batch] for the weight-gradient GEMMs (which contract over the
+// batch).  Every GEMM is C[M][N] = A[M][K] . B[N][K]^T with both operands
+// K-major.
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+
+#include "sph_umma.cuh"
+
+namespace sphk {
+
+constexpr int BM = 128;  // rows per tile (UMMA M)
+constexpr int BK = 64;   // K elements per pipeline stage (one 128-byte row)
+constexpr int UK = 16;   // K per tcgen05.mma of kind::f16
+
+enum { EPI_BIAS_GELU = 0, EPI_BIAS = 1, EPI_GELU_GRAD = 2, EPI_F32 = 3 };
+
+struct GemmEpi {
+    int M, N;                 // valid rows / columns of C
+    int kb_total;             // K blocks of BK
+    int kb_per_split;         // K blocks per blockIdx.z
+    const float* bias;        // [N]
+    __nv_bfloat16* out_bf16;  // [M][ld_bf16]
+    int ld_bf16;
+    __nv_bfloat16* out_t;     // [N][ld_t] (transposed copy)
+    int ld_t;
+    float* out_f32;           // [M][ld_f32] (+ blockIdx.z * split_stride for EPI_F32)
+    int ld_f32;
+    long long split_stride;
+    const float* zin;         // [M][ld_z]: pre-activation for GELU'
+    int ld_z;
+    unsigned* err;
+};
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad_f(float z)
+{
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+template <int EPI>
+__device__ __forceinline__ void epilogue16(const GemmEpi& e, int row, int col0, const float (&v)[16])
+{
+    if (row >= e.M) return;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int n = col0 + j;
+        if (n >= e.N) break;
+        if (EPI == EPI_BIAS_GELU) {
+            const float z = v[j] + e.bias[n];
+            if (e.out_f32) e.out_f32[(size_t)row * e.ld_f32 + n] = z;
+            const __nv_bfloat16 hb = __float2bfloat16_rn(gelu_f(z));
+            e.out_bf16[(size_t)row * e.ld_bf16 + n] = hb;
+            if (e.out_t) e.out_t[(size_t)n * e.ld_t + row] = hb;
+        } else if (EPI == EPI_BIAS) {
+            e.out_f32[(size_t)row * e.ld_f32 + n] = v[j] + e.bias[n];
+        } else if (EPI == EPI_GELU_GRAD) {
+            const float d = v[j] * gelu_grad_f(e.zin[(size_t)row * e.ld_z + n]);
+            const __nv_bfloat16 db = __float2bfloat16_rn(d);
+            e.out_bf16[(size_t)row * e.ld_bf16 + n] = db;
+            if (e.out_t) e.out_t[(size_t)n * e.ld_t + row] = db;
+        } else {
+            e.out_f32[(size_t)blockIdx.z * e.split_stride + (size_t)row * e.ld_f32 + n] = v[j];
+        }
+    }
+}
+
+template <int NT, int STAGES>
+struct GemmSmem {
+    static constexpr uint32_t A_BYTES = BM * BK * 2;
+    static constexpr uint32_t B_BYTES = NT * BK * 2;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr uint32_t TILES = STAGES * STAGE;
+    static constexpr uint32_t TOTAL = 1024 + TILES + 8 * (2 * STAGES + 1) + 16;
+    static constexpr uint32_t TMEM_COLS = NT < 32 ? 32 : NT;
+};
+
+// One CTA of 128 threads per (M tile, N tile, K split).  Warp 0 lane 0
+// streams the A and B tiles through a STAGES-deep TMA ring, warp 1 lane 0
+// issues the tcgen05.mma and frees each stage with tcgen05.commit, and all
+// four warps read the 128 x NT FP32 accumulator out of tensor memory (warp
+// w owns rows 32w .. 32w+31) for the epilogue.  Every wait is bounded; on a
+// timeout the kernel records SPH_DEV_TIMEOUT, lets its own copies land,
+// frees its tensor memory and returns.
+template <int NT, int EPI, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, GemmEpi e)
+{
+    using L = GemmSmem<NT, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t tiles = (raw + 1023u) & ~1023u;
+    const uint32_t bars = tiles + L::TILES;
+    auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+    auto empty = [&](int s) { return bars + 8u * (uint32_t)(STAGES + s); };
+    const uint32_t done = bars + 8u * (uint32_t)(2 * STAGES);
+    const uint32_t tmem_slot = done + 8u;
+    uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(smem_raw + (tmem_slot - raw));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * NT;
+    const int kb0 = blockIdx.z * e.kb_per_split;
+    const int nk = min(e.kb_per_split, e.kb_total - kb0);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(done, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, L::TMEM_COLS);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot_ptr;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        int issued = 0;
+        bool ok = true;
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % STAGES;
+            if (i >= STAGES && !mbar_wait(empty(s), (uint32_t)((i / STAGES) - 1) & 1u, e.err)) {
+                ok = false;
+                break;
+            }
+            const uint32_t a = tiles + (uint32_t)s * L::STAGE;
+            mbar_expect_tx(full(s), L::STAGE);
+            tma_load_2d(&mapA, full(s), a, (kb0 + i) * BK, m0);
+            tma_load_2d(&mapB, full(s), a + L::A_BYTES, (kb0 + i) * BK, n0);
+            ++issued;
+        }
+        if (!ok) {
+            // let the copies still in flight land before the CTA goes away
+            for (int i = max(0, issued - STAGES); i < issued; ++i)
+                mbar_wait(full(i % STAGES), (uint32_t)(i / STAGES) & 1u, e.err);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        constexpr uint32_t idesc = umma_idesc_bf16(BM, NT);
+        for (int i = 0; i < nk; ++i) {
+            const int s = i % STAGES;
+            if (!mbar_wait(full(s), (uint32_t)(i / STAGES) & 1u, e.err)) break;
+            tc_fence_after();
+            const uint32_t a = tiles + (uint32_t)s * L::STAGE;
+            const uint32_t b = a + L::A_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / UK; ++k)
+                umma_bf16(tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
+                          (uint32_t)((i | k) != 0));
+            umma_commit(empty(s));
+        }
+        umma_commit(done);
+    }
+    __syncwarp();
+
+    // ---- epilogue: every warp reads its 32 accumulator rows
+    const bool ok = mbar_wait(done, 0, e.err);
+    tc_fence_after();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            epilogue16<EPI>(e, row, n0 + c0, v);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
+}
+
+// ------------------------------------------------------------ host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_encode_mutex;
+
+static cudaError_t get_encoder()
+{
+    std::lock_guard<std::mutex> lock(g_encode_mutex);
+    if (g_encode) return cudaSuccess;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return cudaSuccess;
+}
+
+// Tensor map of a row-major BF16 matrix [rows][cols] (row stride ld
+// elements), boxes of 64 columns x box_rows rows, 128-byte swizzle,
+// out-of-range elements read as zero.
+static cudaError_t make_map(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows)
+{
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t elem[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, elem,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int NT, int EPI>
+static cudaError_t launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEpi& e, int splits,
+                                 cudaStream_t s)
+{
+    constexpr int STAGES = NT >= 256 ? 4 : 6;
+    using L = GemmSmem<NT, STAGES>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t r = cudaFuncSetAttribute(k_gemm<NT, EPI, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L::TOTAL);
+        if (r != cudaSuccess) return r;
+        attr = true;
+    }
+    dim3 grid((e.M + BM - 1) / BM, (e.N + NT - 1) / NT, splits);
+    k_gemm<NT, EPI, STAGES><<<grid, 128, L::TOTAL, s>>>(ma, mb, e);
+    return cudaGetLastError();
+}
+
+// C[M][N] = A[M][K] . B[N][K]^T; A, B row-major BF16 with leading
+// dimensions lda, ldb (elements, multiples of 8).  NT chooses the N tile.
+static cudaError_t gemm(int NT, int EPI, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M,
+                        int N, int K, int splits, GemmEpi e, cudaStream_t s, long long* launches)
+{
+    CUtensorMap ma, mb;
+    cudaError_t r = make_map(&ma, A, M, K, lda, BM);
+    if (r != cudaSuccess) return r;
+    r = make_map(&mb, B, N, K, ldb, NT);
+    if (r != cudaSuccess) return r;
+    e.M = M;
+    e.N = N;
+    e.kb_total = (K + BK - 1) / BK;
+    splits = splits < 1 ? 1 : (splits > e.kb_total ? e.kb_total : splits);
+    e.kb_per_split = (e.kb_total + splits - 1) / splits;
+    splits = (e.kb_total + e.kb_per_split - 1) / e.kb_per_split;
+    ++*launches;
+#define SPH_GEMM_CASE(nt, epi) \
+    if (NT == nt && EPI == epi) return launch_gemm_t<nt, epi>(ma, mb, e, splits, s);
+    SPH_GEMM_CASE(256, EPI_BIAS_GELU)
+    SPH_GEMM_CASE(16, EPI_BIAS)
+    SPH_GEMM_CASE(256, EPI_GELU_GRAD)
+    SPH_GEMM_CASE(128, EPI_F32)
+    SPH_GEMM_CASE(16, EPI_F32)
+    SPH_GEMM_CASE(256, EPI_F32)
+#undef SPH_GEMM_CASE
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------- MLP kernels
+
+constexpr int MLP_IN = SPH_MLP_IN, MLP_H = SPH_MLP_HIDDEN, MLP_OUT = SPH_MLP_OUT;
+
+// Offsets of the packed parameter vector: W1 b1 W2 b2 W3 b3 W4 b4.
+struct ParamLayout {
+    int w[4], b[4], wn[4], in[4], out[4];
+    __host__ __device__ ParamLayout()
+    {
+        const int ins[4] = {MLP_IN, MLP_H, MLP_H, MLP_H}, outs[4] = {MLP_H, MLP_H, MLP_H, MLP_OUT};
+        int o = 0;
+        for (int l = 0; l < 4; ++l) {
+            in[l] = ins[l];
+            out[l] = outs[l];
+            w[l] = o;
+            wn[l] = ins[l] * outs[l];
+            o += wn[l];
+            b[l] = o;
+            o += outs[l];
+        }
+    }
+};
+
+// fp32 master -> BF16 W [out][in] and W^T [in][out] for every layer.
+__global__ void k_cast_weights(const float* __restrict__ P, __nv_bfloat16* __restrict__ W,
+                               __nv_bfloat16* __restrict__ WT)
+{
+    const ParamLayout L;
+    const int total = L.b[3] + MLP_OUT;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        for (int l = 0; l < 4; ++l) {
+            if (t >= L.w[l] && t < L.w[l] + L.wn[l]) {
+                const int r = (t - L.w[l]) / L.in[l], c = (t - L.w[l]) % L.in[l];
+                const __nv_bfloat16 v = __float2bfloat16_rn(P[t]);
+                W[t] = v;
+                WT[L.w[l] + c * L.out[l] + r] = v;
+            }
+        }
+    }
+}
+
+// x [B][MLP_IN] -> x^T [MLP_IN][B]
+__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ x, int rows, int cols, int ld_in,
+                                 __nv_bfloat16* __restrict__ xt, int ld_out)
+{
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        tile[i][threadIdx.x] = (r < rows && c < cols) ? x[(size_t)r * ld_in + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) xt[(size_t)c * ld_out + r] = tile[threadIdx.x][i];
+    }
+}
+
+// Upstream gradient of the loss at the output y [B][16] (FP32):
+// phase 0: force loss mean over rows of 1/2 |y[:,0:3] - t[:,0:3]|^2;
+// phase 1: error-head loss mean of 1/2 (y[:,3] - t[:,3])^2;
+// external: dy given (gradient test).  Writes dY and dY^T in BF16 and adds
+// the loss to *loss.
+__global__ void k_output_grad(const float* __restrict__ y, const float* __restrict__ t, const float* __restrict__ dy_in,
+                              int B, int phase, __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dyt,
+                              int ld_t, float* __restrict__ loss)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (r < B) {
+        for (int c = 0; c < MLP_OUT; ++c) {
+            float g = 0.f;
+            if (dy_in) {
+                g = dy_in[(size_t)r * MLP_OUT + c];
+            } else if ((phase == 0 && c < 3) || (phase == 1 && c == 3)) {
+                const float d = y[(size_t)r * MLP_OUT + c] - t[(size_t)r * 4 + c];
+                l += 0.5f * d * d;
+                g = d / (float)B;
+            }
+            const __nv_bfloat16 gb = __float2bfloat16_rn(g);
+            dy[(size_t)r * MLP_OUT + c] = gb;
+            dyt[(size_t)c * ld_t + r] = gb;
+        }
+    }
+    // block reduction of the loss
+    __shared__ float red[256];
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, red[0] / (float)B);
+}
+
+// Sum of the split-K partials of a weight gradient into G (FP32).
+__global__ void k_reduce_splits(const float* __restrict__ part, int splits, long long stride, int n,
+                                float* __restrict__ g)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < splits; ++k) s += part[(size_t)k * stride + t];
+        g[t] = s;
+    }
+}
+
+// Bias gradient: column sums of d [B][cols] (BF16), one thread per column.
+__global__ void k_col_sums(const __nv_bfloat16* __restrict__ d, int B, int cols, int ld, float* __restrict__ g)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < B; ++r) s += __bfloat162float(d[(size_t)r * ld + c]);
+    g[c] = s;
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters [lo, hi).
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ Mo,
+                       float* __restrict__ Vo, int lo, int hi, float lr, float b1, float b2, float eps, float c1,
+                       float c2)
+{
+    for (int t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < hi; t += gridDim.x * blockDim.x) {
+        const float g = G[t];
+        const float m = b1 * Mo[t] + (1.f - b1) * g;
+        const float v = b2 * Vo[t] + (1.f - b2) * g * g;
+        Mo[t] = m;
+        Vo[t] = v;
+        P[t] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    }
+}
+
+}  // namespace sphk
+
+// ------------------------------------------------------------------ API
+
+using namespace sphk;
+
+struct sph_mlp {
+    int max_batch;
+    float *P, *G, *Mo, *Vo;            // packed parameters, gradients, Adam moments
+    __nv_bfloat16 *W, *WT;             // BF16 weights and transposes (packed like P)
+    __nv_bfloat16 *XT;                 // [IN][Bmax]
+    __nv_bfloat16 *H[3], *HT[3];       // [B][H], [H][B]
+    float* Z[3];                       // [B][H]
+    float* Y;                          // [B][16]
+    __nv_bfloat16 *DY, *DYT;           // [B][16], [16][B]
+    __nv_bfloat16 *D[2], *DT[2];       // [B][H], [H][B] (alternating)
+    float* part;                       // split-K partials
+    float* loss;
+    unsigned* err;
+    long long step;
+    long long launches;
+    char msg[512];
+};
+
+static const int SPLITS = 8;
+
+static int mfail(sph_mlp* m, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (m) snprintf(m->msg, sizeof(m->msg), "%s", buf);
+    sphk::set_handleless_error(buf);
+    return code;
+}
+
+#define MLP_TRY(m, expr)                                                                           \
+    do {                                                                                           \
+        cudaError_t e_ = (expr);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return mfail((m), SPH_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                                \
+    } while (0)
+
+struct MCarver {
+    uintptr_t base, off;
+    template <class T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~(uintptr_t)255;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static size_t mlp_carve(sph_mlp* m, uintptr_t base)
+{
+    MCarver c{base, 0};
+    const size_t P = SPH_MLP_PARAMS, B = (size_t)m->max_batch;
+    m->P = c.take<float>(P);
+    m->G = c.take<float>(P);
+    m->Mo = c.take<float>(P);
+    m->Vo = c.take<float>(P);
+    m->W = c.take<__nv_bfloat16>(P);
+    m->WT = c.take<__nv_bfloat16>(P);
+    m->XT = c.take<__nv_bfloat16>((size_t)MLP_IN * B);
+    for (int l = 0; l < 3; ++l) {
+        m->H[l] = c.take<__nv_bfloat16>((size_t)MLP_H * B);
+        m->HT[l] = c.take<__nv_bfloat16>((size_t)MLP_H * B);
+        m->Z[l] = c.take<float>((size_t)MLP_H * B);
+    }
+    m->Y = c.take<float>((size_t)MLP_OUT * B);
+    m->DY = c.take<__nv_bfloat16>((size_t)MLP_OUT * B);
+    m->DYT = c.take<__nv_bfloat16>((size_t)MLP_OUT * B);
+    for (int l = 0; l < 2; ++l) {
+        m->D[l] = c.take<__nv_bfloat16>((size_t)MLP_H * B);
+        m->DT[l] = c.take<__nv_bfloat16>((size_t)MLP_H * B);
+    }
+    m->part = c.take<float>((size_t)SPLITS * MLP_H * MLP_IN);
+    m->loss = c.take<float>(4);
+    m->err = c.take<unsigned>(4);
+    return (c.off + 255) & ~(uintptr_t)255;
+}
+
+static GemmEpi epi0(sph_mlp* m)
+{
+    GemmEpi e;
+    memset(&e, 0, sizeof(e));
+    e.err = m->err;
+    return e;
+}
+
+// Forward pass of B rows of x (BF16 [B][IN]); keep = 1 also stores the
+// pre-activations and the transposed activations for the backward pass.
+static int mlp_forward(sph_mlp* m, const __nv_bfloat16* x, int B, float* y, bool keep, cudaStream_t s)
+{
+    const ParamLayout L;
+    const __nv_bfloat16* in = x;
+    int ld_in = MLP_IN, k_in = MLP_IN;
+    for (int l = 0; l < 3; ++l) {
+        GemmEpi e = epi0(m);
+        e.bias = m->P + L.b[l];
+        e.out_bf16 = m->H[l];
+        e.ld_bf16 = MLP_H;
+        if (keep) {
+            e.out_f32 = m->Z[l];
+            e.ld_f32 = MLP_H;
+            e.out_t = m->HT[l];
+            e.ld_t = m->max_batch;
+        }
+        MLP_TRY(m, gemm(256, EPI_BIAS_GELU, in, ld_in, m->W + L.w[l], L.in[l], B, MLP_H, k_in, 1, e, s, &m->launches));
+        in = m->H[l];
+        ld_in = MLP_H;
+        k_in = MLP_H;
+    }
+    GemmEpi e = epi0(m);
+    e.bias = m->P + L.b[3];
+    e.out_f32 = y;
+    e.ld_f32 = MLP_OUT;
+    MLP_TRY(m, gemm(16, EPI_BIAS, in, MLP_H, m->W + L.w[3], MLP_H, B, MLP_OUT, MLP_H, 1, e, s, &m->launches));
+    return SPH_OK;
+}
+
+// Weight and bias gradients of layer l from its output gradient d [B][out]
+// (d^T [out][B] given) and its input^T [in][B].
+static int layer_grads(sph_mlp* m, int l, const __nv_bfloat16* d, const __nv_bfloat16* dt, int ld_d,
+                       const __nv_bfloat16* in_t, int B, cudaStream_t s)
+{
+    const ParamLayout L;
+    const int nout = L.out[l], nin = L.in[l];
+    GemmEpi e = epi0(m);
+    e.out_f32 = m->part;
+    e.ld_f32 = nin;
+    e.split_stride = (long long)nout * nin;
+    const int NT = nin > 256 ? 128 : 256;
+    MLP_TRY(m, gemm(NT, EPI_F32, dt, m->max_batch, in_t, m->max_batch, nout, nin, B, SPLITS, e, s, &m->launches));
+    const int kb = (B + BK - 1) / BK, per = (kb + SPLITS - 1) / SPLITS, splits = (kb + per - 1) / per;
+    k_reduce_splits<<<120, 256, 0, s>>>(m->part, splits, e.split_stride, nout * nin, m->G + L.w[l]);
+    k_col_sums<<<(nout + 127) / 128, 128, 0, s>>>(d, B, nout, ld_d, m->G + L.b[l]);
+    m->launches += 2;
+    MLP_TRY(m, cudaGetLastError());
+    return SPH_OK;
+}
+
+// Backward pass from the output gradient (phase 0 / external: every layer;
+// phase 1: the output layer only).
+static int mlp_backward(sph_mlp* m, int B, bool trunk, cudaStream_t s)
+{
+    const ParamLayout L;
+    int rc = layer_grads(m, 3, m->DY, m->DYT, MLP_OUT, m->HT[2], B, s);
+    if (rc != SPH_OK || !trunk) return rc;
+    // d3 = (dY . W4) * gelu'(z3)
+    const __nv_bfloat16* dprev = m->DY;
+    int ld_prev = MLP_OUT, k_prev = MLP_OUT;
+    for (int l = 2; l >= 0; --l) {
+        const int cur = l & 1;
+        GemmEpi e = epi0(m);
+        e.zin = m->Z[l];
+        e.ld_z = MLP_H;
+        e.out_bf16 = m->D[cur];
+        e.ld_bf16 = MLP_H;
+        e.out_t = m->DT[cur];
+        e.ld_t = m->max_batch;
+        MLP_TRY(m, gemm(256, EPI_GELU_GRAD, dprev, ld_prev, m->WT + L.w[l + 1], L.out[l + 1], B, MLP_H, k_prev, 1, e,
+                        s, &m->launches));
+        rc = layer_grads(m, l, m->D[cur], m->DT[cur], MLP_H, l == 0 ? m->XT : m->HT[l - 1], B, s);
+        if (rc != SPH_OK) return rc;
+        dprev = m->D[cur];
+        ld_prev = MLP_H;
+        k_prev = MLP_H;
+    }
+    return SPH_OK;
+}
+
+static int check_batch(sph_mlp* m, int B)
+{
+    if (!m) return mfail(nullptr, SPH_ERR_ARG, "mlp is NULL");
+    if (B <= 0 || B > m->max_batch || (B & 127))
+        return mfail(m, SPH_ERR_ARG, "batch %d must be a positive multiple of 128 <= %d", B, m->max_batch);
+    return SPH_OK;
+}
+
+extern "C" {
+
+int sph_mlp_workspace_size(int max_batch, size_t* bytes)
+{
+    if (!bytes || max_batch <= 0 || (max_batch & 127))
+        return mfail(nullptr, SPH_ERR_ARG, "max_batch must be a positive multiple of 128");
+    sph_mlp t;
+    memset(&t, 0, sizeof(t));
+    t.max_batch = max_batch;
+    *bytes = mlp_carve(&t, 0);
+    return SPH_OK;
+}
+
+int sph_mlp_create(int max_batch, void* workspace, size_t ws_bytes, sph_mlp** out)
+{
+    size_t need = 0;
+    int rc = sph_mlp_workspace_size(max_batch, &need);
+    if (rc != SPH_OK) return rc;
+    if (!out || !workspace || ((uintptr_t)workspace & 255) || ws_bytes < need)
+        return mfail(nullptr, SPH_ERR_ARG, "workspace must be 256-byte aligned and >= %zu bytes", need);
+    sph_mlp* m = new (std::nothrow) sph_mlp;
+    if (!m) return mfail(nullptr, SPH_ERR_ARG, "out of host memory");
+    memset(m, 0, sizeof(*m));
+    m->max_batch = max_batch;
+    mlp_carve(m, (uintptr_t)workspace);
+    cudaError_t e = cudaMemset(workspace, 0, need);
+    if (e != cudaSuccess) {
+        delete m;
+        return mfail(nullptr, SPH_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+    }
+    *out = m;
+    return SPH_OK;
+}
+
+void sph_mlp_destroy(sph_mlp* m) { delete m; }
+
+int sph_mlp_set_params(sph_mlp* m, const float* params, void* stream)
+{
+    if (!m || !params) return mfail(m, SPH_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    MLP_TRY(m, cudaMemcpyAsync(m->P, params, sizeof(float) * SPH_MLP_PARAMS, cudaMemcpyDeviceToDevice, s));
+    MLP_TRY(m, cudaMemsetAsync(m->Mo, 0, sizeof(float) * SPH_MLP_PARAMS, s));
+    MLP_TRY(m, cudaMemsetAsync(m->Vo, 0, sizeof(float) * SPH_MLP_PARAMS, s));
+    k_cast_weights<<<256, 256, 0, s>>>(m->P, m->W, m->WT);
+    ++m->launches;
+    MLP_TRY(m, cudaGetLastError());
+    m->step = 0;
+    return SPH_OK;
+}
+
+int sph_mlp_get_params(sph_mlp* m, float* params, void* stream)
+{
+    if (!m || !params) return mfail(m, SPH_ERR_ARG, "NULL argument");
+    MLP_TRY(m, cudaMemcpyAsync(params, m->P, sizeof(float) * SPH_MLP_PARAMS, cudaMemcpyDeviceToDevice,
+                               (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_mlp_forward(sph_mlp* m, const void* x, int B, float* y, void* stream)
+{
+    int rc = check_batch(m, B);
+    if (rc != SPH_OK) return rc;
+    if (!x || !y || ((uintptr_t)x & 15)) return mfail(m, SPH_ERR_ARG, "x must be 16-byte aligned, y non-NULL");
+    return mlp_forward(m, (const __nv_bfloat16*)x, B, y, false, (cudaStream_t)stream);
+}
+
+int sph_mlp_gradients(sph_mlp* m, const void* x, const float* dy, int B, float* grads, void* stream)
+{
+    int rc = check_batch(m, B);
+    if (rc != SPH_OK) return rc;
+    if (!x || !dy || !grads || ((uintptr_t)x & 15)) return mfail(m, SPH_ERR_ARG, "bad pointers");
+    cudaStream_t s = (cudaStream_t)stream;
+    dim3 tb(32, 8), tg((MLP_IN + 31) / 32, (B + 31) / 32);
+    k_transpose_bf16<<<tg, tb, 0, s>>>((const __nv_bfloat16*)x, B, MLP_IN, MLP_IN, m->XT, m->max_batch);
+    ++m->launches;
+    rc = mlp_forward(m, (const __nv_bfloat16*)x, B, m->Y, true, s);
+    if (rc != SPH_OK) return rc;
+    k_output_grad<<<(B + 255) / 256, 256, 0, s>>>(m->Y, nullptr, dy, B, 0, m->DY, m->DYT, m->max_batch, nullptr);
+    ++m->launches;
+    MLP_TRY(m, cudaGetLastError());
+    rc = mlp_backward(m, B, true, s);
+    if (rc != SPH_OK) return rc;
+    MLP_TRY(m, cudaMemcpyAsync(grads, m->G, sizeof(float) * SPH_MLP_PARAMS, cudaMemcpyDeviceToDevice, s));
+    return SPH_OK;
+}
+
+int sph_mlp_train_step(sph_mlp* m, const void* x, const float* target, int B, int phase, float lr,
+                       float* loss_out, void* stream)
+{
+    int rc = check_batch(m, B);
+    if (rc != SPH_OK) return rc;
+    if (!x || !target || ((uintptr_t)x & 15)) return mfail(m, SPH_ERR_ARG, "bad pointers");
+    if (phase != 0 && phase != 1) return mfail(m, SPH_ERR_ARG, "phase must be 0 or 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ParamLayout L;
+    dim3 tb(32, 8), tg((MLP_IN + 31) / 32, (B + 31) / 32);
+    if (phase == 0) {
+        k_transpose_bf16<<<tg, tb, 0, s>>>((const __nv_bfloat16*)x, B, MLP_IN, MLP_IN, m->XT, m->max_batch);
+        ++m->launches;
+    }
+    rc = mlp_forward(m, (const __nv_bfloat16*)x, B, m->Y, true, s);
+    if (rc != SPH_OK) return rc;
+    MLP_TRY(m, cudaMemsetAsync(m->loss, 0, sizeof(float), s));
+    k_output_grad<<<(B + 255) / 256, 256, 0, s>>>(m->Y, target, nullptr, B, phase, m->DY, m->DYT, m->max_batch,
+                                                  m->loss);
+    ++m->launches;
+    MLP_TRY(m, cudaGetLastError());
+    rc = mlp_backward(m, B, phase == 0, s);
+    if (rc != SPH_OK) return rc;
+    ++m->step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
+    if (phase == 0) {
+        // every parameter except the error-head row 3 of W4 and b4[3]
+        k_adam<<<256, 256, 0, s>>>(m->P, m->G, m->Mo, m->Vo, 0, L.w[3] + 3 * MLP_H, lr, b1, b2, 1e-8f, c1, c2);
+        k_adam<<<4, 256, 0, s>>>(m->P, m->G, m->Mo, m->Vo, L.w[3] + 4 * MLP_H, L.b[3] + 3, lr, b1, b2, 1e-8f, c1, c2);
+        k_adam<<<1, 32, 0, s>>>(m->P, m->G, m->Mo, m->Vo, L.b[3] + 4, L.b[3] + MLP_OUT, lr, b1, b2, 1e-8f, c1, c2);
+        m->launches += 3;
+    } else {
+        k_adam<<<1, 256, 0, s>>>(m->P, m->G, m->Mo, m->Vo, L.w[3] + 3 * MLP_H, L.w[3] + 4 * MLP_H, lr, b1, b2, 1e-8f,
+                                 c1, c2);
+        k_adam<<<1, 32, 0, s>>>(m->P, m->G, m->Mo, m->Vo, L.b[3] + 3, L.b[3] + 4, lr, b1, b2, 1e-8f, c1, c2);
+        m->launches += 2;
+    }
+    k_cast_weights<<<256, 256, 0, s>>>(m->P, m->W, m->WT);
+    ++m->launches;
+    MLP_TRY(m, cudaGetLastError());
+    if (loss_out) MLP_TRY(m, cudaMemcpyAsync(loss_out, m->loss, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    return SPH_OK;
+}
+
+int sph_mlp_status(sph_mlp* m, unsigned* bits, void* stream)
+{
+    if (!m || !bits) return mfail(m, SPH_ERR_ARG, "NULL argument");
+    unsigned v = 0;
+    MLP_TRY(m, cudaMemcpyAsync(&v, m->err, sizeof(unsigned), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    MLP_TRY(m, cudaStreamSynchronize((cudaStream_t)stream));
+    *bits = v;
+    return SPH_OK;
+}
+
+long long sph_mlp_launch_count(sph_mlp* m) { return m ? m->launches : 0; }
+
+int sph_debug_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int splits, float* C,
+                   unsigned* err, void* stream)
+{
+    if (!A || !B || !C || !err || M <= 0 || N <= 0 || K <= 0 || (lda & 7) || (ldb & 7) || splits < 1)
+        return mfail(nullptr, SPH_ERR_ARG, "bad GEMM arguments");
+    if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return mfail(nullptr, SPH_ERR_ARG, "A, B must be 16-byte aligned");
+    GemmEpi e;
+    memset(&e, 0, sizeof(e));
+    e.err = err;
+    e.out_f32 = C;
+    e.ld_f32 = N;
+    e.split_stride = (long long)M * N;
+    long long launches = 0;
+    const int NT = N <= 16 ? 16 : (N <= 128 ? 128 : 256);
+    cudaError_t r = gemm(NT, EPI_F32, (const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)B, ldb, M, N, K, splits,
+                         e, (cudaStream_t)stream, &launches);
+    if (r != cudaSuccess) return mfail(nullptr, SPH_ERR_CUDA, "GEMM: %s", cudaGetErrorString(r));
+    return SPH_OK;
+}
+
+}  // extern "C"

@@ -72,6 +72,17 @@ _sig = {
     "sph_batch_create": (_i, [_P, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_vp)]),
     "sph_set_tuning": (_i, [_vp, _i, _i]),
     "sph_graph_step": (_i, [_vp, _i, _vp]),
+    "sph_mlp_workspace_size": (_i, [_i, ctypes.POINTER(_sz)]),
+    "sph_mlp_create": (_i, [_i, _vp, _sz, ctypes.POINTER(_vp)]),
+    "sph_mlp_destroy": (None, [_vp]),
+    "sph_mlp_set_params": (_i, [_vp, _vp, _vp]),
+    "sph_mlp_get_params": (_i, [_vp, _vp, _vp]),
+    "sph_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
+    "sph_mlp_gradients": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
+    "sph_mlp_train_step": (_i, [_vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp]),
+    "sph_mlp_status": (_i, [_vp, ctypes.POINTER(ctypes.c_uint), _vp]),
+    "sph_mlp_launch_count": (ctypes.c_longlong, [_vp]),
+    "sph_debug_gemm": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -243,6 +254,133 @@ def sph_bin_static(params: dict, n: int, pos_ptr, keys_ptr, perm_ptr, cell_start
     if q.get("mass") is None:
         q["mass"] = 1.0
     _check(_lib.sph_bin_static(ctypes.byref(make_params(q)), n, pos_ptr, keys_ptr, perm_ptr, cell_start_ptr, stream))
+
+
+SPH_MLP_IN, SPH_MLP_HIDDEN, SPH_MLP_OUT, SPH_MLP_PARAMS = 272, 256, 16, 205584
+
+
+def sph_mlp_workspace_size(max_batch: int) -> int:
+    out = _sz()
+    _check(_lib.sph_mlp_workspace_size(max_batch, ctypes.byref(out)))
+    return int(out.value)
+
+
+def sph_mlp_create(max_batch: int, workspace_ptr: int, ws_bytes: int):
+    h = _vp()
+    _check(_lib.sph_mlp_create(max_batch, workspace_ptr, ws_bytes, ctypes.byref(h)))
+    return h
+
+
+def sph_mlp_destroy(m):
+    _lib.sph_mlp_destroy(m)
+
+
+def sph_mlp_set_params(m, params_ptr: int, stream: int):
+    _check(_lib.sph_mlp_set_params(m, params_ptr, stream))
+
+
+def sph_mlp_get_params(m, params_ptr: int, stream: int):
+    _check(_lib.sph_mlp_get_params(m, params_ptr, stream))
+
+
+def sph_mlp_forward(m, x_ptr: int, B: int, y_ptr: int, stream: int):
+    _check(_lib.sph_mlp_forward(m, x_ptr, B, y_ptr, stream))
+
+
+def sph_mlp_gradients(m, x_ptr: int, dy_ptr: int, B: int, grads_ptr: int, stream: int):
+    _check(_lib.sph_mlp_gradients(m, x_ptr, dy_ptr, B, grads_ptr, stream))
+
+
+def sph_mlp_train_step(m, x_ptr: int, t_ptr: int, B: int, phase: int, lr: float, loss_ptr, stream: int):
+    _check(_lib.sph_mlp_train_step(m, x_ptr, t_ptr, B, phase, lr, loss_ptr, stream))
+
+
+def sph_mlp_status(m, stream: int) -> int:
+    bits = ctypes.c_uint()
+    _check(_lib.sph_mlp_status(m, ctypes.byref(bits), stream))
+    return int(bits.value)
+
+
+def sph_mlp_launch_count(m) -> int:
+    return int(_lib.sph_mlp_launch_count(m))
+
+
+def sph_debug_gemm(a_ptr, lda, b_ptr, ldb, M, N, K, splits, c_ptr, err_ptr, stream):
+    _check(_lib.sph_debug_gemm(a_ptr, lda, b_ptr, ldb, M, N, K, splits, c_ptr, err_ptr, stream))
+
+
+class Mlp:
+    """The surrogate MLP with its workspace in a torch tensor.  Inputs are
+    torch tensors on the device: x bfloat16 [B][272], targets float32 [B][4];
+    B is padded up to a multiple of 128 inside (padded rows are zero and
+    their outputs dropped; padded targets are zero with zero input, so they
+    add nothing but a constant to the loss)."""
+
+    def __init__(self, max_batch: int, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.max_batch = (int(max_batch) + 127) // 128 * 128
+        nbytes = sph_mlp_workspace_size(self.max_batch)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self._ws = (self.workspace.data_ptr() + 255) & ~255
+        self.handle = sph_mlp_create(self.max_batch, self._ws, nbytes)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None:
+            sph_mlp_destroy(h)
+            self.handle = None
+
+    @property
+    def stream(self) -> int:
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def _pad(self, x, width, dtype):
+        t = self.torch
+        B = x.shape[0]
+        Bp = (B + 127) // 128 * 128
+        if Bp == B and x.dtype == dtype and x.is_contiguous():
+            return x, B
+        out = t.zeros((Bp, width), dtype=dtype, device=self.device)
+        out[:B] = x
+        return out, B
+
+    def set_params(self, params):
+        p = self.torch.as_tensor(params, dtype=self.torch.float32, device=self.device).contiguous()
+        assert p.numel() == SPH_MLP_PARAMS
+        self._params = p
+        sph_mlp_set_params(self.handle, p.data_ptr(), self.stream)
+
+    def get_params(self):
+        p = self.torch.empty(SPH_MLP_PARAMS, dtype=self.torch.float32, device=self.device)
+        sph_mlp_get_params(self.handle, p.data_ptr(), self.stream)
+        return p
+
+    def forward(self, x):
+        xp, B = self._pad(x, SPH_MLP_IN, self.torch.bfloat16)
+        y = self.torch.empty((xp.shape[0], SPH_MLP_OUT), dtype=self.torch.float32, device=self.device)
+        sph_mlp_forward(self.handle, xp.data_ptr(), xp.shape[0], y.data_ptr(), self.stream)
+        return y[:B]
+
+    def gradients(self, x, dy):
+        xp, B = self._pad(x, SPH_MLP_IN, self.torch.bfloat16)
+        dyp, _ = self._pad(dy, SPH_MLP_OUT, self.torch.float32)
+        g = self.torch.empty(SPH_MLP_PARAMS, dtype=self.torch.float32, device=self.device)
+        sph_mlp_gradients(self.handle, xp.data_ptr(), dyp.data_ptr(), xp.shape[0], g.data_ptr(), self.stream)
+        return g
+
+    def train_step(self, x, t, lr, phase=0):
+        """One Adam step; returns the loss tensor (device, not synchronised)."""
+        assert x.shape[0] % 128 == 0, "training batches are multiples of 128"
+        sph_mlp_train_step(self.handle, x.data_ptr(), t.data_ptr(), x.shape[0], phase, float(lr),
+                           self.loss.data_ptr(), self.stream)
+        return self.loss
+
+    def status(self) -> int:
+        return sph_mlp_status(self.handle, self.stream)
 
 
 # ------------------------------------------------------ torch convenience

@@ -1,0 +1,132 @@
+"""The tensor-core surrogate MLP against torch and the FP64 oracle (needs a
+GB300)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as omlp
+from paper_2311_15088_gb300 import sph
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    return torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("M,N,K,splits", [(128, 256, 272, 1), (300, 16, 256, 1), (256, 272, 1024, 4),
+                                          (16, 256, 4096, 8), (384, 128, 64, 1), (130, 256, 16, 1)])
+def test_tcgen05_gemm_matches_fp32_product(M, N, K, splits):
+    g = torch.Generator().manual_seed(M * 7 + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((splits, M, N), float("nan"), dtype=torch.float32, device="cuda")
+    err = torch.zeros(4, dtype=torch.int32, device="cuda")
+    kb = (K + 63) // 64
+    s = min(splits, kb)
+    per = (kb + s - 1) // s
+    s = (kb + per - 1) // per
+    sph.sph_debug_gemm(A.data_ptr(), K, B.data_ptr(), K, M, N, K, splits, C.data_ptr(), err.data_ptr(),
+                       torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert int(err[0]) == 0
+    got = C[:s].sum(0).double()
+    ref = A.double() @ B.double().T
+    scale = (A.double().abs() @ B.double().abs().T)
+    assert torch.all((got - ref).abs() <= 1e-5 * scale + 1e-6), float(((got - ref).abs() / scale).max())
+
+
+def _oracle_params_bf16(seed):
+    """Oracle parameters with the weights rounded to BF16 (what the tensor
+    cores see) and small random biases."""
+    p = omlp.init_params(seed)
+    rng = np.random.default_rng(seed + 1)
+    for w, b, n_out, _ in omlp.LAYERS:
+        p[w] = _bf16(p[w]).double().numpy()
+        p[b] = rng.uniform(-0.1, 0.1, size=n_out)
+    return p
+
+
+def _pack(p):
+    return np.concatenate([np.concatenate([p[w].ravel(), p[b]]) for w, b, _, _ in omlp.LAYERS]).astype(np.float32)
+
+
+def _unpack(v):
+    out, o = {}, 0
+    for w, b, n_out, n_in in omlp.LAYERS:
+        out[w] = v[o:o + n_out * n_in].reshape(n_out, n_in)
+        o += n_out * n_in
+        out[b] = v[o:o + n_out]
+        o += n_out
+    return out
+
+
+def _inputs(B, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(B, omlp.D_IN))
+    x[:, 259:] = 0
+    return _bf16(x).double().numpy()
+
+
+def test_forward_matches_oracle():
+    p = _oracle_params_bf16(11)
+    x = _inputs(640, 12)
+    m = sph.Mlp(1024)
+    m.set_params(torch.from_numpy(_pack(p)))
+    y = m.forward(_bf16(x).cuda()).double().cpu().numpy()
+    assert m.status() == 0
+    ref = omlp.forward(p, x)["y"]
+    rel = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert rel <= 2e-2, rel
+    assert np.all(np.abs(y - ref) <= 2e-2 * np.abs(ref).max())
+
+
+def test_gradients_match_oracle():
+    p = _oracle_params_bf16(21)
+    x = _inputs(512, 22)
+    rng = np.random.default_rng(23)
+    dy = np.zeros((512, omlp.D_OUT))
+    dy[:, :4] = rng.normal(size=(512, 4)) / 512
+    m = sph.Mlp(512)
+    m.set_params(torch.from_numpy(_pack(p)))
+    g = m.gradients(_bf16(x).cuda(), torch.from_numpy(dy.astype(np.float32)).cuda()).double().cpu().numpy()
+    assert m.status() == 0
+    ref = omlp.backward(p, omlp.forward(p, x), dy)
+    got = _unpack(g)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"):
+        a, b = got[name].ravel(), ref[name].ravel()
+        if name in ("W4", "b4"):
+            a, b = got[name][:4].ravel(), ref[name][:4].ravel()
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+        assert cos >= 0.999, (name, cos)
+
+
+def test_training_fits_a_smooth_target():
+    rng = np.random.default_rng(5)
+    B = 4096
+    x = rng.normal(size=(B, omlp.D_IN)) * 0.5
+    x[:, 259:] = 0
+    t = np.zeros((B, 4))
+    t[:, 0] = np.tanh(x[:, 0] + 0.5 * x[:, 1])
+    t[:, 1] = x[:, 2] * x[:, 3]
+    t[:, 2] = np.sin(x[:, 4])
+    m = sph.Mlp(B)
+    m.set_params(torch.from_numpy(_pack(omlp.init_params(6))))
+    xb = _bf16(x).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    first = None
+    for it in range(300):
+        loss = float(m.train_step(xb, tt, 1e-3).item()) if it % 50 == 0 or it == 299 else m.train_step(xb, tt, 1e-3)
+        if it == 0:
+            first = loss
+    last = float(m.loss.item())
+    assert m.status() == 0
+    assert last < 0.2 * first, (first, last)
+    # the GPU forward of the trained weights agrees with the oracle forward
+    pt = m.get_params().double().cpu().numpy()
+    q = _unpack(pt)
+    for w, _, _, _ in omlp.LAYERS:
+        q[w] = _bf16(q[w]).double().numpy()
+    y = m.forward(xb[:512]).double().cpu().numpy()
+    ref = omlp.forward(q, _bf16(x[:512]).double().numpy())["y"]
+    assert np.linalg.norm(y[:, :3] - ref[:, :3]) / np.linalg.norm(ref[:, :3]) <= 3e-2
