@@ -77,6 +77,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=30, help="timed steps of the batched-scenes leg")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -286,6 +287,64 @@ def run_batched(a, dev, flush):
     }
 
 
+# ----------------------------------------------------------- surrogate
+
+def run_surrogate(a, dev):
+    """Boid-force queries: the surrogate (features + tensor-core MLP), the
+    surrogate with its exact fallback at the calibrated 5 % aggregate error,
+    and the exact force computed only where it is needed, on 65,536 queries
+    (64 states x 1,024 boids of held-out 262,144-particle column runs).  The
+    network is trained first (untimed) on 16 runs x 64 steps of the same
+    workload with other seeds."""
+    import torch
+
+    from paper_2311_15088_gb300 import surrogate
+    from paper_2311_15088_gb300.sph import (SPH_BOID_EXACT, SPH_BOID_EXACT_LOCAL, SPH_BOID_SURROGATE,
+                                            SPH_BOID_SURROGATE_FALLBACK, Scene)
+
+    mk = lambda sd: scenes.dam_break_column(seed_offset=100 + sd)
+    mlp, info = surrogate.build_and_train(mk, list(range(16)), [16, 17], steps=64)
+    sc = mk(40)
+    p = _params(sc)
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    s.set_surrogate(mlp, info["f_scale"], info["threshold"])
+    modes = {"exact_full": SPH_BOID_EXACT, "exact_local": SPH_BOID_EXACT_LOCAL, "surrogate": SPH_BOID_SURROGATE,
+             "surrogate_fallback": SPH_BOID_SURROGATE_FALLBACK}
+    ms = {k: 0.0 for k in modes}
+    got = {k: [] for k in modes}
+    fall = []
+    for _ in range(a.warmup):
+        for mode in modes.values():
+            s.boid_forces(mode)
+    n_states = 64
+    for _ in range(n_states):
+        for name, mode in modes.items():
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f = s.boid_forces(mode)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms[name] += e0.elapsed_time(e1)
+            got[name].append(f[:, :3].clone())
+            if name == "surrogate_fallback":
+                fall.append(f[:, 3].clone())
+        s.step(1)
+    q = n_states * s.n_boid
+    F = torch.cat(got["exact_local"])
+    out = {"workload": "65,536 boid-force queries: 64 states x 1,024 boids of a 262,144-particle column run",
+           "training": info, "queries": q}
+    for name in modes:
+        out[name] = {"qps": q / (ms[name] / 1e3), "ms_per_state": ms[name] / n_states,
+                     "aggregate_error": surrogate.aggregate_error(torch.cat(got[name]), F)}
+    out["surrogate_fallback"]["fallback_fraction"] = float(torch.cat(fall).mean().item())
+    out["exact_local_equals_exact_full"] = bool(torch.equal(F, torch.cat(got["exact_full"])))
+    out["speedup_surrogate_vs_exact_local"] = out["surrogate"]["qps"] / out["exact_local"]["qps"]
+    out["speedup_at_5pct_vs_exact_local"] = out["surrogate_fallback"]["qps"] / out["exact_local"]["qps"]
+    return out
+
+
 # ---------------------------------------------------------------- arms
 
 def run_reference(a):
@@ -450,6 +509,7 @@ def run_ours(a):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
 
     batched = None if a.no_batch else run_batched(a, dev, flush)
+    sur = None if a.no_surrogate else run_surrogate(a, dev)
 
     if rank == 0:
         line = {
@@ -464,6 +524,7 @@ def run_ours(a):
                        "candidates_per_particle": cand / n_all},
             "roofline": roofline, "hbm": hbm, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "device_status": status, "batched": batched,
+            "surrogate": sur,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
         }
         print(json.dumps(line), flush=True)

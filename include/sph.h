@@ -76,6 +76,7 @@ extern "C" {
 #define SPH_FIELD_BOID_PERM  11  /* int[n_boid]    boid id at each sorted boid slot         */
 #define SPH_FIELD_BOID_CELL_START 12 /* uint[nbcells+1] first sorted boid slot per cell    */
 #define SPH_FIELD_NCAND      13  /* int[n_tot]     candidates the density pass tested, by id */
+#define SPH_FIELD_FALLBACK   14  /* int[n_boid]    1 where the last surrogate call used the exact path */
 
 /*
  * Parameters of a scene.  Paper notation: h smoothing length, rho0 rest
@@ -203,14 +204,48 @@ int sph_step(sph_handle* h, int nsteps, void* stream);
 int sph_graph_step(sph_handle* h, int nsteps, void* stream);
 
 /*
- * Fluid force on every boid for the CURRENT state (mode 0 = exact SPH
- * coupling): F_b = (1/rho_b) sum_j f_bj over fluid neighbours j of the
- * boid's attached particle (section "Boid Motion and Agent Fluid
- * Interaction").  Writes n_boid float4 to out_f4 (device).  Does not
- * change the state.  Errors: SPH_ERR_ARG (mode != 0, NULL out),
- * SPH_ERR_STATE, SPH_ERR_CUDA.
+ * Fluid force on every boid for the CURRENT state, written as n_boid float4
+ * to out_f4 (device, 16-byte aligned); the state is not changed.  Modes:
+ *   SPH_BOID_EXACT: F_b = (1/rho_b) sum_j f_bj over the fluid neighbours j of
+ *     the boid's attached particle (section "Boid Motion and Agent Fluid
+ *     Interaction"), from a density pass over every particle; w = 0.
+ *   SPH_BOID_EXACT_LOCAL: the same forces, bit for bit, computing densities
+ *     only for the attached particles and their fluid neighbours; w = 0.
+ *   SPH_BOID_SURROGATE: the attached surrogate network (sph_set_surrogate)
+ *     on the boids' stencil features (sph_features): F_b = y[0:3] * f_scale,
+ *     w = 0.
+ *   SPH_BOID_SURROGATE_FALLBACK: the surrogate, except for the boids whose
+ *     error head y[3] exceeds log_err_max (or whose output is not finite):
+ *     those get the exact-local force and w = 1.
+ * Errors: SPH_ERR_ARG (mode, out), SPH_ERR_STATE (no state, or no surrogate
+ * for the surrogate modes), SPH_ERR_CUDA.
  */
+#define SPH_BOID_EXACT              0
+#define SPH_BOID_SURROGATE          1
+#define SPH_BOID_SURROGATE_FALLBACK 2
+#define SPH_BOID_EXACT_LOCAL        3
 int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream);
+
+/*
+ * Stencil features of every boid for the CURRENT state (the surrogate's
+ * input): x_out holds n_boid rows of SPH_MLP_IN BF16 (device, 16-byte
+ * aligned).  Row b: the 4 x 4 x 4 cells of the particle grid from
+ * c0 = floor((p_b - box_min) / cell_size - 1.5) per axis; cell q = (iz * 4 +
+ * iy) * 4 + ix gives columns 4q .. 4q+3 = (fluid particles in the cell *
+ * mass / (cell_size^3 rho0), their mean velocity); columns 256 .. 258 are
+ * the boid's velocity; the rest zero.  Errors: SPH_ERR_ARG, SPH_ERR_STATE,
+ * SPH_ERR_CUDA.
+ */
+int sph_features(sph_handle* h, void* x_out, void* stream);
+
+/*
+ * Attach a surrogate network (NULL detaches) for the surrogate modes of
+ * sph_boid_forces: forces are the network's outputs 0..2 times f_scale;
+ * boids whose error-head output exceeds log_err_max take the exact path in
+ * SPH_BOID_SURROGATE_FALLBACK.  The network must stay alive while attached.
+ */
+typedef struct sph_mlp sph_mlp;
+int sph_set_surrogate(sph_handle* h, sph_mlp* m, float f_scale, float log_err_max);
 
 /*
  * Copy one field of the most recent step (SPH_FIELD_*) to `out` (device,
@@ -291,7 +326,6 @@ void sph_destroy(sph_handle* h);
 #define SPH_MLP_HIDDEN  256
 #define SPH_MLP_OUT     16
 #define SPH_MLP_PARAMS  205584
-typedef struct sph_mlp sph_mlp;
 int sph_mlp_workspace_size(int max_batch, size_t* bytes);
 int sph_mlp_create(int max_batch, void* workspace, size_t ws_bytes, sph_mlp** out);
 void sph_mlp_destroy(sph_mlp* m);

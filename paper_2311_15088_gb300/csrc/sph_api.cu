@@ -48,6 +48,14 @@ struct sph_handle {
     unsigned* bbig_count;
     float4* fb;
     unsigned* err;
+    // surrogate: features, network output, exact-path masks
+    void* feat;               // BF16 [nb_pad][SPH_MLP_IN]
+    float* yout;              // [nb_pad][SPH_MLP_OUT]
+    unsigned char* need;      // per sorted slot
+    int* bflag;               // per boid
+    int nb_pad;
+    sph_mlp* mlp;
+    float f_scale, log_err_max;
     bool has_state, keys_ready, has_step;
     long long launches;
     cudaStream_t last_stream;
@@ -281,6 +289,11 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->bbig_count = cv.take<unsigned>(1);
     h->fb = cv.take<float4>(nb);
     h->err = cv.take<unsigned>(4);
+    h->nb_pad = nb ? (int)((nb + 127) / 128 * 128) : 0;
+    h->feat = cv.take<unsigned short>((size_t)h->nb_pad * SPH_MLP_IN);
+    h->yout = cv.take<float>((size_t)h->nb_pad * SPH_MLP_OUT);
+    h->need = cv.take<unsigned char>(n);
+    h->bflag = cv.take<int>(nb);
     return (size_t)((cv.off + 255) & ~(uintptr_t)255);
 }
 
@@ -686,9 +699,6 @@ int sph_get_state(sph_handle* h, float* fluid_pos4, float* fluid_vel4, float* bo
 // Keys (if needed), scan, scatter and per-cell sort + gather of the state
 // into the sorted scratch arrays.  consume = true zeroes the counts for the
 // next step's keys.
-// Keys (if needed), scan, scatter and per-cell sort + gather of the state
-// into the sorted scratch arrays.  consume = true zeroes the counts for the
-// next step's keys.
 static int bin_state(sph_handle* h, cudaStream_t s, bool consume)
 {
     if (!h->keys_ready) {
@@ -722,12 +732,12 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
     int rc = bin_state(h, s, true);
     if (rc != SPH_OK) return rc;
     prof_begin(h, SPH_KIND_DENSITY, s);
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand, h->err,
-                               s, &h->launches));
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand, nullptr,
+                               h->err, s, &h->launches));
     prof_end(h, s);
     prof_begin(h, SPH_KIND_FORCES, s);
     CUDA_TRY(h, launch_forces(0, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                              h->acc, h->touched, h->infl, h->fb, h->pos, h->vel, h->key, h->rank, h->count, h->err,
+                              nullptr, h->acc, h->touched, h->infl, h->fb, h->pos, h->vel, h->key, h->rank, h->count, h->err,
                               s, &h->launches));
     prof_end(h, s);
     if (h->n_boid > 0) {
@@ -817,23 +827,87 @@ int sph_graph_step(sph_handle* h, int nsteps, void* stream)
     return SPH_OK;
 }
 
-int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
+int sph_set_surrogate(sph_handle* h, sph_mlp* m, float f_scale, float log_err_max)
 {
     if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
-    if (mode != 0) return fail(h, SPH_ERR_ARG, "unsupported mode %d", mode);
-    if (h->n_boid && (!out_f4 || !aligned16(out_f4))) return fail(h, SPH_ERR_ARG, "out must be 16-byte aligned");
+    if (m && !(isfinite(f_scale) && f_scale > 0.0f)) return fail(h, SPH_ERR_ARG, "f_scale must be > 0");
+    h->mlp = m;
+    h->f_scale = f_scale;
+    h->log_err_max = log_err_max;
+    return SPH_OK;
+}
+
+int sph_features(sph_handle* h, void* x_out, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
     if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    if (h->n_boid && (!x_out || !aligned16(x_out))) return fail(h, SPH_ERR_ARG, "x_out must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
     if (h->n_boid == 0) return SPH_OK;
     int rc = bin_state(h, s, false);
     if (rc != SPH_OK) return rc;
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand,
+    CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, x_out, s, &h->launches));
+    h->has_step = false;
+    return SPH_OK;
+}
+
+// Exact fluid force on the boids flagged in bmask (NULL: every boid),
+// computing densities only where those forces need them.
+static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_t s)
+{
+    CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
+    CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, bmask, h->need, s, &h->launches));
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand, h->need,
                                h->err, s, &h->launches));
     CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                              nullptr, nullptr, nullptr, (float4*)out_f4, nullptr, nullptr, nullptr, nullptr,
-                              nullptr, h->err, s, &h->launches));
+                              bmask, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, h->err, s, &h->launches));
+    return SPH_OK;
+}
+
+int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (mode < SPH_BOID_EXACT || mode > SPH_BOID_EXACT_LOCAL) return fail(h, SPH_ERR_ARG, "unsupported mode %d", mode);
+    if (h->n_boid && (!out_f4 || !aligned16(out_f4))) return fail(h, SPH_ERR_ARG, "out must be 16-byte aligned");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    if ((mode == SPH_BOID_SURROGATE || mode == SPH_BOID_SURROGATE_FALLBACK) && !h->mlp)
+        return fail(h, SPH_ERR_STATE, "no surrogate attached (sph_set_surrogate)");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    if (h->n_boid == 0) return SPH_OK;
+    int rc = bin_state(h, s, false);
+    if (rc != SPH_OK) return rc;
+    float4* out = (float4*)out_f4;
     h->has_step = false;
+    if (mode == SPH_BOID_EXACT) {
+        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand,
+                                   nullptr, h->err, s, &h->launches));
+        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+                                  nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  h->err, s, &h->launches));
+        return SPH_OK;
+    }
+    if (mode == SPH_BOID_EXACT_LOCAL) {
+        // every boid flagged: bflag = 1
+        CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
+        CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, nullptr, h->need, s, &h->launches));
+        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand,
+                                   h->need, h->err, s, &h->launches));
+        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+                                  nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  h->err, s, &h->launches));
+        return SPH_OK;
+    }
+    // surrogate: features -> network -> forces (+ exact path for flagged boids)
+    CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, h->feat, s,
+                                &h->launches));
+    rc = sph_mlp_forward(h->mlp, h->feat, h->nb_pad, h->yout, stream);
+    if (rc != SPH_OK) return fail(h, rc, "surrogate forward: %s", sph_last_error(nullptr));
+    CUDA_TRY(h, launch_surrogate_out(h->yout, h->n_boid, h->f_scale, h->log_err_max, out, h->bflag, h->err + 1, s,
+                                     &h->launches));
+    if (mode == SPH_BOID_SURROGATE_FALLBACK) return exact_local(h, h->bflag, out, s);
     return SPH_OK;
 }
 
@@ -856,7 +930,8 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
 {
     if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
     if (!out) return fail(h, SPH_ERR_ARG, "out is NULL");
-    if (!h->has_step) return fail(h, SPH_ERR_STATE, "no step since the state was loaded or staged");
+    if (!h->has_step && field != SPH_FIELD_FALLBACK)
+        return fail(h, SPH_ERR_STATE, "no step since the state was loaded or staged");
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
     const int n = h->n, nb = h->n_boid;
@@ -887,6 +962,10 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
     case SPH_FIELD_NBR_COUNT:
         if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->nbr, n, (int*)dst);
         bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_FALLBACK:
+        bytes = (size_t)nb * 4;
+        if (nb) CUDA_TRY(h, cudaMemcpyAsync(dst, h->bflag, bytes, cudaMemcpyDeviceToDevice, s));
         break;
     case SPH_FIELD_NCAND:
         if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->ncand, n, (int*)dst);
@@ -928,7 +1007,9 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
     default:
         return fail(h, SPH_ERR_ARG, "unknown field %d", field);
     }
-    if (field != SPH_FIELD_FB && field != SPH_FIELD_KEYS && field != SPH_FIELD_BOID_KEYS) ++h->launches;
+    if (field != SPH_FIELD_FB && field != SPH_FIELD_FALLBACK && field != SPH_FIELD_KEYS &&
+        field != SPH_FIELD_BOID_KEYS)
+        ++h->launches;
     if (field == SPH_FIELD_KEYS || field == SPH_FIELD_BOID_KEYS) ++h->launches;
     CUDA_TRY(h, cudaGetLastError());
     if (on_host) {

@@ -244,14 +244,18 @@ struct Tuning {
 
 // Density, neighbour counts and the candidate bit stream (bits: NBR_WORDS
 // words per particle, word-interleaved; ncand: candidates per particle).
+// need (per sorted slot, may be NULL = every particle) restricts the pass to
+// the particles whose density is asked for.
 cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, int* nbr, unsigned* bits, int* ncand, unsigned* err, cudaStream_t s,
-                           long long* launches);
+                           float* rho, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
+                           unsigned* err, cudaStream_t s, long long* launches);
 // mode 0: full step (every particle; fluid integrated into pos_next/vel_next,
-// next keys emitted); mode 1: only the attached particles' F_b.
+// next keys emitted); mode 1: only the attached particles' F_b (bmask, per
+// boid, may be NULL = every boid; with a mask fb.w = 1 marks what was
+// written).
 cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
-                          const Tuning& t, float4* acc, int* touched, float4* infl, float4* fb,
+                          const Tuning& t, const int* bmask, float4* acc, int* touched, float4* infl, float4* fb,
                           float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,
                           unsigned* err, cudaStream_t s, long long* launches);
 cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const Scenes& sc, int* counts,
@@ -264,6 +268,14 @@ cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const 
                               float4* pos_next, float4* vel_next, const int* slot_of_boid,
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches);
+
+// Surrogate inputs and outputs (sph_features.cu).
+cudaError_t launch_features(const float4* pos, const float4* vel, const unsigned* start, const float4* bpos,
+                            const float4* bvel, const Scenes& sc, void* x, cudaStream_t s, long long* launches);
+cudaError_t launch_mark_needed(const float4* pos, const unsigned* start, const Scenes& sc, const int* bmask,
+                               unsigned char* need, cudaStream_t s, long long* launches);
+cudaError_t launch_surrogate_out(const float* y, int nb, float f_scale, float log_err_max, float4* out, int* flag,
+                                 unsigned* nflag, cudaStream_t s, long long* launches);
 
 // Set the message that sph_last_error(NULL) returns on this thread.
 void set_handleless_error(const char* msg);

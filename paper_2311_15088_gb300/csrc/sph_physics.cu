@@ -32,10 +32,12 @@ template <bool STREAM>
 __global__ void __launch_bounds__(512)
 k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
           float* __restrict__ rho, int* __restrict__ nbr, unsigned* __restrict__ bits,
-          int* __restrict__ ncand, unsigned* __restrict__ err)
+          int* __restrict__ ncand, const unsigned char* __restrict__ need,
+          unsigned* __restrict__ err)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sc.n_all) return;
+    if (need && !need[i]) return;  // density of this particle not asked for
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
     const float h2 = c.h2;
     const int nb_all = sc.nb_all, n_all = sc.n_all;
@@ -78,15 +80,15 @@ k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Sc
 }
 
 cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, int* nbr, unsigned* bits, int* ncand, unsigned* err, cudaStream_t s,
-                           long long* launches)
+                           float* rho, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
+                           unsigned* err, cudaStream_t s, long long* launches)
 {
     if (sc.n_all <= 0) return cudaSuccess;
     const int blocks = (sc.n_all + t.block - 1) / t.block;
     if (t.use_stream)
-        k_density<true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, err);
+        k_density<true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, need, err);
     else
-        k_density<false><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, err);
+        k_density<false><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, need, err);
     ++*launches;
     return cudaGetLastError();
 }
@@ -99,7 +101,8 @@ template <int MODE>
 __global__ void __launch_bounds__(512)
 k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ rho,
          const unsigned* __restrict__ start, const unsigned* __restrict__ bits, const int* __restrict__ ncand,
-         Scenes sc, int use_stream, float4* __restrict__ acc, int* __restrict__ touched,
+         Scenes sc, int use_stream, const int* __restrict__ bmask, float4* __restrict__ acc,
+         int* __restrict__ touched,
          float4* __restrict__ infl, float4* __restrict__ fb, float4* __restrict__ pos_next,
          float4* __restrict__ vel_next, unsigned* __restrict__ key, unsigned* __restrict__ rank,
          unsigned* __restrict__ count, unsigned* __restrict__ err)
@@ -113,7 +116,7 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     const int id_i = id_of(pi);
     const bool att_i = id_i < nb_all;
     // MODE 1 computes only the attached particles (threads of the others idle)
-    const bool work = active && (MODE == 0 || att_i);
+    const bool work = active && (MODE == 0 || (att_i && (!bmask || bmask[id_i])));
     const unsigned* cstart = start + c.c_base;
 
     float ax = 0.f, ay = 0.f, az = 0.f;
@@ -205,7 +208,7 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     az *= inv_rho;
 
     if (MODE == 1) {
-        if (work) fb[id_i] = make_float4(ax, ay, az, 0.0f);
+        if (work) fb[id_i] = make_float4(ax, ay, az, bmask ? 1.0f : 0.0f);
         return;
     }
 
@@ -256,17 +259,17 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
 
 cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
-                          const Tuning& t, float4* acc, int* touched, float4* infl, float4* fb,
+                          const Tuning& t, const int* bmask, float4* acc, int* touched, float4* infl, float4* fb,
                           float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,
                           unsigned* err, cudaStream_t s, long long* launches)
 {
     if (sc.n_all <= 0) return cudaSuccess;
     const int blocks = (sc.n_all + t.block - 1) / t.block;
     if (mode == 0)
-        k_forces<0><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, acc, touched,
+        k_forces<0><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
                                                infl, fb, pos_next, vel_next, key, rank, count, err);
     else
-        k_forces<1><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, acc, touched,
+        k_forces<1><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
                                                infl, fb, pos_next, vel_next, key, rank, count, err);
     ++*launches;
     return cudaGetLastError();

@@ -23,14 +23,15 @@ _lib = ctypes.CDLL(_LIB_PATH)
 SPH_OK, SPH_ERR_ARG, SPH_ERR_CUDA, SPH_ERR_OVERFLOW, SPH_ERR_TIMEOUT, SPH_ERR_STATE = range(6)
 SPH_MULLER3D, SPH_PAPER_LITERAL = 0, 1
 SPH_COUPLE_FORCE = 0
-SPH_DEV_NONFINITE, SPH_DEV_CLAMPED = 1, 2
+SPH_DEV_NONFINITE, SPH_DEV_CLAMPED, SPH_DEV_TIMEOUT = 1, 2, 4
+SPH_BOID_EXACT, SPH_BOID_SURROGATE, SPH_BOID_SURROGATE_FALLBACK, SPH_BOID_EXACT_LOCAL = 0, 1, 2, 3
 
 FIELDS = {
     "rho": (0, np.float32, 1), "pressure": (1, np.float32, 1), "acc": (2, np.float32, 4),
     "touched": (3, np.int32, 1), "influence": (4, np.float32, 4), "nbr_count": (5, np.int32, 1),
     "keys": (6, np.uint32, 1), "perm": (7, np.int32, 1), "cell_start": (8, np.uint32, 1),
     "fb": (9, np.float32, 4), "boid_keys": (10, np.uint32, 1), "boid_perm": (11, np.int32, 1),
-    "boid_cell_start": (12, np.uint32, 1), "ncand": (13, np.int32, 1),
+    "boid_cell_start": (12, np.uint32, 1), "ncand": (13, np.int32, 1), "fallback": (14, np.int32, 1),
 }
 
 
@@ -83,6 +84,8 @@ _sig = {
     "sph_mlp_status": (_i, [_vp, ctypes.POINTER(ctypes.c_uint), _vp]),
     "sph_mlp_launch_count": (ctypes.c_longlong, [_vp]),
     "sph_debug_gemm": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "sph_features": (_i, [_vp, _vp, _vp]),
+    "sph_set_surrogate": (_i, [_vp, _vp, ctypes.c_float, ctypes.c_float]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -197,6 +200,14 @@ def sph_step(h, nsteps: int, stream: int):
 
 def sph_boid_forces(h, mode: int, out_ptr: int, stream: int):
     _check(_lib.sph_boid_forces(h, mode, out_ptr, stream), h)
+
+
+def sph_features(h, x_ptr, stream: int):
+    _check(_lib.sph_features(h, x_ptr, stream), h)
+
+
+def sph_set_surrogate(h, mlp_handle, f_scale: float, log_err_max: float):
+    _check(_lib.sph_set_surrogate(h, mlp_handle, float(f_scale), float(log_err_max)), h)
 
 
 def sph_get_fields(h, field: int, out_ptr: int, on_host: int, stream: int):
@@ -473,7 +484,7 @@ class Scene:
             n = self.ncells + 1
         elif name == "boid_cell_start":
             n = self.nbcells + 1
-        elif name in ("fb", "boid_keys", "boid_perm"):
+        elif name in ("fb", "boid_keys", "boid_perm", "fallback"):
             n = self.n_boid
         else:
             n = self.n
@@ -483,11 +494,23 @@ class Scene:
             sph_get_fields(self.handle, code, out.data_ptr(), 0, self.stream)
         return out
 
-    def boid_forces(self):
+    def boid_forces(self, mode: int = 0):
+        """F_b of every boid for the current state (SPH_BOID_* mode)."""
         t = self.torch
         out = t.empty((self.n_boid, 4), dtype=t.float32, device=self.device)
-        sph_boid_forces(self.handle, 0, out.data_ptr() if out.numel() else None, self.stream)
+        sph_boid_forces(self.handle, mode, out.data_ptr() if out.numel() else None, self.stream)
         return out
+
+    def features(self):
+        """Stencil features of every boid (BF16 [n_boid][272])."""
+        t = self.torch
+        x = t.empty((self.n_boid, SPH_MLP_IN), dtype=t.bfloat16, device=self.device)
+        sph_features(self.handle, x.data_ptr() if x.numel() else None, self.stream)
+        return x
+
+    def set_surrogate(self, mlp, f_scale: float, log_err_max: float):
+        self._mlp = mlp
+        sph_set_surrogate(self.handle, mlp.handle if mlp is not None else None, f_scale, log_err_max)
 
     def neighbors(self, lists: bool = True):
         t = self.torch

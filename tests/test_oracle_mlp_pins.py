@@ -49,3 +49,33 @@ def test_first_adam_step_closed_form():
     # bias-corrected moments equal g and g^2 after one step
     assert np.allclose(w1, w - lr * g / (np.abs(g) + 1e-8))
     assert math.isclose(m[0], 0.1 * 0.3) and math.isclose(v[1], 0.001 * 16.0)
+
+
+def test_stencil_features_by_hand():
+    """A boid at the centre of cell (8, 8, 8) of a grid of h/2 cells: its
+    stencil starts at cell 7 per axis (floor(8.5 - 1.5)); fluid particles
+    placed in stencil cells (0,0,0) and (3,1,2) and one outside."""
+    from oracle.features import stencil_features
+    from paper_2311_15088_gb300 import scenes
+
+    p = scenes.default_params(mass=0.01, cell_size=0.25, box_max=(4.0, 4.0, 4.0))
+    d = 0.25
+    boid = np.array([[8.5 * d, 8.5 * d, 8.5 * d, 0]], np.float32)
+    bvel = np.array([[0.1, -0.2, 0.3, 0]], np.float32)
+    pts = [[7.5 * d, 7.5 * d, 7.5 * d], [7.2 * d, 7.9 * d, 7.1 * d],   # cell (7,7,7): stencil (0,0,0)
+           [10.5 * d, 8.5 * d, 9.5 * d],                              # cell (10,8,9): stencil (3,1,2)
+           [12.5 * d, 8.5 * d, 8.5 * d]]                              # outside the stencil
+    vel = [[1, 0, 0], [0, 2, 0], [0, 0, 3], [5, 5, 5]]
+    fp = np.zeros((4, 4), np.float32)
+    fp[:, :3] = pts
+    fv = np.zeros((4, 4), np.float32)
+    fv[:, :3] = vel
+    x = stencil_features(p, fp, fv, boid, bvel)
+    scale = p["mass"] / (d ** 3 * 1000.0)
+    q0 = 0
+    q1 = (2 * 4 + 1) * 4 + 3
+    assert x[0, 4 * q0] == 2 * scale and np.allclose(x[0, 4 * q0 + 1:4 * q0 + 4], [0.5, 1.0, 0.0])
+    assert x[0, 4 * q1] == scale and np.allclose(x[0, 4 * q1 + 1:4 * q1 + 4], [0, 0, 3])
+    others = np.delete(np.arange(64), [q0, q1])
+    assert np.all(x[0, 4 * others] == 0)
+    assert np.allclose(x[0, 256:259], [0.1, -0.2, 0.3]) and np.all(x[0, 259:] == 0)
