@@ -25,6 +25,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -46,12 +47,17 @@ SETTLE = 200
 # FP32 peak of the ALU-bound passes: 152 SMs x 128 FP32 lanes x 2 flops (FMA)
 # x 2070 MHz (maximum SM clock).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# Work per particle-step: a candidate test is 3 sub + 1 mul + 2 fma = 8
-# flops; an accepted density pair 4 flops; a force pair 30 flops.  The
-# density pass tests every candidate of the walk (its count is read back
-# from the library); the force pass visits only the neighbours it recorded,
-# except for particles whose candidate stream exceeded the stored capacity.
-FLOP_CAND, FLOP_DENS_PAIR, FLOP_FORCE_PAIR = 8, 4, 30
+# Algorithmic work per particle-step, as the method defines it: each pass
+# tests the candidates of the 27-cell stencil of cell size h, C = 27 n h^3
+# per particle (n the number density), i.e. C = N * 27 / (4 pi / 3) with N
+# = (4 pi / 3) n h^3 the neighbour count; a candidate test is 9 flops (3 sub,
+# 3 mul / fma, compare), a density pair 5 flops, a force pair 35 flops.
+# "executed" counts instead the candidates the pruned walk actually tests
+# (read back from the library): every candidate in the density pass, and in
+# the force pass every candidate again, or only the overflowing particles'
+# when the candidate-bit stream is on.
+FLOP_CAND, FLOP_DENS_PAIR, FLOP_FORCE_PAIR = 9, 5, 35
+STENCIL_CAND_PER_NBR = 27.0 / (4.0 * math.pi / 3.0)
 STREAM_CAPACITY = 64 * 32  # candidate bits stored per particle
 # Compulsory bytes per particle of each pass (float4 pos/vel, float rho ...):
 BYTES = {"scatter": 12, "sort": 68, "density": 24, "forces": 112}
@@ -78,6 +84,8 @@ def _args():
     ap.add_argument("--batch-steps", type=int, default=30, help="timed steps of the batched-scenes leg")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--settle", type=int, default=None,
+                    help="settling steps of the large tank before the boids are released (default 200)")
     return ap.parse_args()
 
 
@@ -389,6 +397,9 @@ def run_ours(a):
 
         dist.init_process_group("nccl", device_id=dev)
     sc, desc, settle = _workload(a.workload)
+    if a.settle is not None and settle:
+        settle = a.settle
+        desc = desc.replace(f"settled {SETTLE} steps", f"settled {settle} steps")
     p = _params(sc)
     nf, nb = len(sc["fluid_pos"]), len(sc["boid_pos"])
     z = np.zeros((0, 4), np.float32)
@@ -419,11 +430,17 @@ def run_ours(a):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     launches0 = s.launches
+    # the work of a step grows as the fluid compresses: sample the candidate
+    # and neighbour counts between timed steps (outside the step events)
+    every = max(1, a.steps // 20)
+    works = []
     for k in range(a.steps):
         flush.zero_()
         ev0[k].record()
         s.step(1)
         ev1[k].record()
+        if k % every == every - 1:
+            works.append(_work_snapshot(s))
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -442,15 +459,19 @@ def run_ours(a):
     status = s.status()
 
     # ---- roofline of the dominant pass and the HBM view of the step
-    cand = 0.5 * (work0["candidates"] + work1["candidates"])
-    pairs = 0.5 * (work0["pairs"] + work1["pairs"])
-    over = 0.5 * (work0["overflow_candidates"] + work1["overflow_candidates"])
+    works = works or [work0, work1]
+    cand = statistics.mean(w["candidates"] for w in works)
+    pairs = statistics.mean(w["pairs"] for w in works)
+    over = statistics.mean(w["overflow_candidates"] for w in works)
     n_all = nf + nb
     passes = {k: {"ms_per_step": ms / max(cnt, 1), "launch_groups": cnt} for k, (ms, cnt) in prof.items() if cnt}
     f_ms = passes["forces"]["ms_per_step"]
     d_ms = passes["density"]["ms_per_step"]
-    force_flops = FLOP_CAND * over + FLOP_FORCE_PAIR * pairs
-    dens_flops = FLOP_CAND * cand + FLOP_DENS_PAIR * (pairs + n_all)
+    stencil = STENCIL_CAND_PER_NBR * pairs
+    force_flops = FLOP_CAND * stencil + FLOP_FORCE_PAIR * pairs
+    dens_flops = FLOP_CAND * stencil + FLOP_DENS_PAIR * (pairs + n_all)
+    force_exec = FLOP_CAND * (over if s.tuning[1] else cand) + FLOP_FORCE_PAIR * pairs
+    dens_exec = FLOP_CAND * cand + FLOP_DENS_PAIR * (pairs + n_all)
     achieved = force_flops / (f_ms * 1e-3) / 1e12
     src = os.path.join(ROOT, "paper_2311_15088_gb300", "csrc", "sph_physics.cu")
     traffic = None
@@ -476,8 +497,13 @@ def run_ours(a):
         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
         "flops_per_launch": force_flops,
+        "flops_definition": "27-cell stencil at cell size h: 9 flops x 27/(4pi/3) x neighbours + 35 x neighbours",
+        "executed": {"flops_per_launch": force_exec, "achieved": force_exec / (f_ms * 1e-3) / 1e12,
+                     "frac": force_exec / (f_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                     "candidates_per_particle": cand / n_all},
         "density_pass": {"achieved": dens_flops / (d_ms * 1e-3) / 1e12,
-                         "frac": dens_flops / (d_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
+                         "frac": dens_flops / (d_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "executed_frac": dens_exec / (d_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
     }
     hbm = {"algorithmic_bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (ms_per_step * 1e-3) / 1e9,
            "peak_GBps": hbm_peak, "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak,
@@ -519,8 +545,10 @@ def run_ours(a):
             "config": {"workload": desc, "fluid_particles": nf, "boids": nb, "settle_steps": settle,
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "neighbours_mean": 0.5 * (work0["nbr_mean"] + work1["nbr_mean"]),
-                       "neighbours_max": max(work0["nbr_max"], work1["nbr_max"]),
+                       "cell_size_over_h": float(np.float32(p["cell_size"]) / np.float32(p["h"])),
+                       "tuning": {"block": s.tuning[0], "use_stream": s.tuning[1]},
+                       "neighbours_mean": statistics.mean(w["nbr_mean"] for w in works),
+                       "neighbours_max": max(w["nbr_max"] for w in works),
                        "candidates_per_particle": cand / n_all},
             "roofline": roofline, "hbm": hbm, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "device_status": status, "batched": batched,

@@ -33,6 +33,7 @@ struct sph_handle {
     int* big_list;
     unsigned* big_count;
     float* rho;
+    float2* ab;  // (m / rho, p) per sorted slot
     int* nbr;
     unsigned* bits;
     int* ncand;
@@ -268,6 +269,7 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->big_list = cv.take<int>(C);
     h->big_count = cv.take<unsigned>(1);
     h->rho = cv.take<float>(n);
+    h->ab = cv.take<float2>(n);
     h->nbr = cv.take<int>(n);
     h->bits = cv.take<unsigned>(n * (size_t)NBR_WORDS);
     h->ncand = cv.take<int>(n);
@@ -732,11 +734,11 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
     int rc = bin_state(h, s, true);
     if (rc != SPH_OK) return rc;
     prof_begin(h, SPH_KIND_DENSITY, s);
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand, nullptr,
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, nullptr,
                                h->err, s, &h->launches));
     prof_end(h, s);
     prof_begin(h, SPH_KIND_FORCES, s);
-    CUDA_TRY(h, launch_forces(0, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+    CUDA_TRY(h, launch_forces(0, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
                               nullptr, h->acc, h->touched, h->infl, h->fb, h->pos, h->vel, h->key, h->rank, h->count, h->err,
                               s, &h->launches));
     prof_end(h, s);
@@ -858,9 +860,9 @@ static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_
 {
     CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
     CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, bmask, h->need, s, &h->launches));
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand, h->need,
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, h->need,
                                h->err, s, &h->launches));
-    CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+    CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
                               bmask, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr,
                               nullptr, nullptr, h->err, s, &h->launches));
     return SPH_OK;
@@ -882,9 +884,9 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
     float4* out = (float4*)out_f4;
     h->has_step = false;
     if (mode == SPH_BOID_EXACT) {
-        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand,
+        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
                                    nullptr, h->err, s, &h->launches));
-        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
                                   nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
                                   h->err, s, &h->launches));
         return SPH_OK;
@@ -893,9 +895,9 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
         // every boid flagged: bflag = 1
         CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
         CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, nullptr, h->need, s, &h->launches));
-        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->nbr, h->bits, h->ncand,
+        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
                                    h->need, h->err, s, &h->launches));
-        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
                                   nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
                                   h->err, s, &h->launches));
         return SPH_OK;

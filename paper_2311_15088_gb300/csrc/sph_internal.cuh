@@ -186,7 +186,9 @@ struct RowWalk {
             const int yy = y++;
             const float ryz = rz - axis_gap2(py, yy, g.dim[1], g.minf[1], wb);
             if (!(ryz > 0.0f)) continue;
-            const float xr = sqrtf(ryz) + wb.margin;
+            // x half-width of the row: ryz * rsqrt(ryz) is within 3e-7 of
+            // sqrt(ryz) relatively, far inside margin (>= 1e-5 d, d >= h/4)
+            const float xr = fmaf(ryz, rsqrtf(ryz), wb.margin);
             bool cl = false;
             const int x0 = cell_coord(px - xr, g.minf[0], g.inv_d, g.dim[0], &cl);
             const int x1 = cell_coord(px + xr, g.minf[0], g.inv_d, g.dim[0], &cl);
@@ -247,13 +249,13 @@ struct Tuning {
 // need (per sorted slot, may be NULL = every particle) restricts the pass to
 // the particles whose density is asked for.
 cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
+                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
                            unsigned* err, cudaStream_t s, long long* launches);
 // mode 0: full step (every particle; fluid integrated into pos_next/vel_next,
 // next keys emitted); mode 1: only the attached particles' F_b (bmask, per
 // boid, may be NULL = every boid; with a mask fb.w = 1 marks what was
 // written).
-cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho,
+cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
                           const Tuning& t, const int* bmask, float4* acc, int* touched, float4* infl, float4* fb,
                           float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,

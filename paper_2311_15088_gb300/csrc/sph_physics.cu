@@ -28,12 +28,19 @@ namespace sphk {
 // bits[(k / 32) * n + i].  The force pass then visits only those slots.
 // Particles with more than NBR_WORDS * 32 candidates keep no stream
 // (ncand > capacity) and the force pass tests their candidates again.
+//
+// Besides rho_i it stores ab[i] = (m / rho_i, k (rho_i - rho0)): the two
+// per-particle factors of the pair force, so that the force pass divides
+// once per particle instead of once per pair (same float32 values).
+//
+// A fluid particle has no excluded pairs, so its loop counts every hit and
+// subtracts the self pair (always visited: r2 = 0) at the end; the sums
+// take the same terms in the same order as the attached particles' loop.
 template <bool STREAM>
 __global__ void __launch_bounds__(512)
 k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
-          float* __restrict__ rho, int* __restrict__ nbr, unsigned* __restrict__ bits,
-          int* __restrict__ ncand, const unsigned char* __restrict__ need,
-          unsigned* __restrict__ err)
+          float* __restrict__ rho, float2* __restrict__ ab, int* __restrict__ nbr, unsigned* __restrict__ bits,
+          int* __restrict__ ncand, const unsigned char* __restrict__ need, unsigned* __restrict__ err)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= sc.n_all) return;
@@ -49,46 +56,74 @@ k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Sc
     int nc = 0;
     RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
     unsigned s0, s1;
-    while (walk.next(s0, s1)) {
-        for (unsigned j = s0; j < s1; ++j) {
-            const float4 pj = __ldg(pos + j);
+    if (!STREAM && !att_i) {
+        auto take = [&](const float4& pj) {
             const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
-            const bool hit = r2 < h2;
-            const bool att_pair = att_i && id_of(pj) < nb_all;
-            if (hit && !(att_pair && j != (unsigned)i)) {
+            if (r2 < h2) {
                 const float t = h2 - r2;
                 sum = fmaf(t * t, t, sum);
-                cnt += j != (unsigned)i;
+                ++cnt;
             }
-            if (STREAM) {
-                word |= (unsigned)(hit && r2 != 0.0f && !att_pair) << (nc & 31);
-                if (((nc + 1) & 31) == 0) {
-                    const int w = nc >> 5;
-                    if (w < NBR_WORDS) bits[(size_t)w * n_all + i] = word;
-                    word = 0;
-                }
+        };
+        while (walk.next(s0, s1)) {
+            nc += (int)(s1 - s0);
+            // four candidate loads in flight per iteration, taken in order
+            const float4* p = pos + s0;
+            const float4* e = pos + s1;
+            for (; p + 4 <= e; p += 4) {
+                const float4 a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2), a3 = __ldg(p + 3);
+                take(a0);
+                take(a1);
+                take(a2);
+                take(a3);
             }
-            ++nc;
+            for (; p < e; ++p) take(__ldg(p));
         }
+        --cnt;  // the particle itself
+    } else {
+        while (walk.next(s0, s1)) {
+            for (unsigned j = s0; j < s1; ++j) {
+                const float4 pj = __ldg(pos + j);
+                const float r2 =
+                    pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+                const bool hit = r2 < h2;
+                const bool att_pair = att_i && id_of(pj) < nb_all;
+                if (hit && !(att_pair && j != (unsigned)i)) {
+                    const float t = h2 - r2;
+                    sum = fmaf(t * t, t, sum);
+                    cnt += j != (unsigned)i;
+                }
+                if (STREAM) {
+                    word |= (unsigned)(hit && r2 != 0.0f && !att_pair) << (nc & 31);
+                    if (((nc + 1) & 31) == 0) {
+                        const int w = nc >> 5;
+                        if (w < NBR_WORDS) bits[(size_t)w * n_all + i] = word;
+                        word = 0;
+                    }
+                }
+                ++nc;
+            }
+        }
+        if (STREAM && (nc & 31) != 0 && (nc >> 5) < NBR_WORDS) bits[(size_t)(nc >> 5) * n_all + i] = word;
     }
-    if (STREAM && (nc & 31) != 0 && (nc >> 5) < NBR_WORDS) bits[(size_t)(nc >> 5) * n_all + i] = word;
     ncand[i] = nc;
-    float r = c.mC6 * sum;
+    const float r = c.mC6 * sum;
     rho[i] = r;
+    ab[i] = make_float2(c.mass / r, c.k * (r - c.rho0));
     nbr[i] = cnt;
     if (!isfinite(r)) atomicOr(err, SPH_DEV_NONFINITE);
 }
 
 cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
+                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
                            unsigned* err, cudaStream_t s, long long* launches)
 {
     if (sc.n_all <= 0) return cudaSuccess;
     const int blocks = (sc.n_all + t.block - 1) / t.block;
     if (t.use_stream)
-        k_density<true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, need, err);
+        k_density<true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, need, err);
     else
-        k_density<false><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, nbr, bits, ncand, need, err);
+        k_density<false><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, need, err);
     ++*launches;
     return cudaGetLastError();
 }
@@ -100,7 +135,7 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const Scene
 template <int MODE>
 __global__ void __launch_bounds__(512)
 k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ rho,
-         const unsigned* __restrict__ start, const unsigned* __restrict__ bits, const int* __restrict__ ncand,
+         const float2* __restrict__ ab, const unsigned* __restrict__ start, const unsigned* __restrict__ bits, const int* __restrict__ ncand,
          Scenes sc, int use_stream, const int* __restrict__ bmask, float4* __restrict__ acc,
          int* __restrict__ touched,
          float4* __restrict__ infl, float4* __restrict__ fb, float4* __restrict__ pos_next,
@@ -127,7 +162,8 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     if (work) {
         const float4 vi = __ldg(vel + i);
         rho_i = __ldg(rho + i);
-        const float p_i = c.k * (rho_i - c.rho0);
+        const float p_i = __ldg(ab + i).y;
+        const float half_cp_h = c.half_cp_h, cv_mu = c.cv_mu, inv_h = c.inv_h;
         // one neighbour j (0 < r2 < h2, not two attached particles)
         auto pair = [&](unsigned j) {
             const float4 pj = __ldg(pos + j);
@@ -136,16 +172,16 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
             const float dz_ = __fsub_rn(pj.z, pi.z);
             const float r2 = pair_r2(dx, dy_, dz_);
             const float4 vj = __ldg(vel + j);
-            const float rho_j = __ldg(rho + j);
-            const float p_j = c.k * (rho_j - c.rho0);
+            const float2 abj = __ldg(ab + j);  // (m / rho_j, p_j)
+            const float p_j = abj.y;
             const float rinv = rsqrtf(r2);
-            const float q = r2 * rinv * c.inv_h;
+            const float q = r2 * rinv * inv_h;
             const float omq = 1.0f - q;
-            const float m_rho_j = c.mass / rho_j;
+            const float m_rho_j = abj.x;
             // pressure: C_p (p_i+p_j)/2 (1-q)^2 / q along r_ij = -(dx,dy,dz)
-            const float sp = -m_rho_j * c.half_cp_h * (p_i + p_j) * omq * omq * rinv;
+            const float sp = -m_rho_j * half_cp_h * (p_i + p_j) * omq * omq * rinv;
             // viscosity: -C_v mu (1-q) (v_i - v_j)
-            const float sv = -m_rho_j * c.cv_mu * omq;
+            const float sv = -m_rho_j * cv_mu * omq;
             const float fx = fmaf(sp, dx, sv * (vi.x - vj.x));
             const float fy = fmaf(sp, dy_, sv * (vi.y - vj.y));
             const float fz = fmaf(sp, dz_, sv * (vi.z - vj.z));
@@ -190,14 +226,26 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
             // no stored stream: test every candidate again (same order)
             RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
             unsigned s0, s1;
+            // test a chunk of up to 32 candidates into a bit mask, then run
+            // the pair code over the set bits: the warp executes the pair
+            // code max(hits) times per chunk instead of once per candidate
+            const float h2 = c.h2;
             while (walk.next(s0, s1)) {
-                for (unsigned j = s0; j < s1; ++j) {
-                    const float4 pj = __ldg(pos + j);
-                    const float r2 =
-                        pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
-                    if (!(r2 < c.h2) || r2 == 0.0f) continue;
-                    if (att_i && id_of(pj) < nb_all) continue;
-                    pair(j);
+                for (unsigned base = s0; base < s1; base += 32) {
+                    const unsigned len = min(32u, s1 - base);
+                    unsigned m = 0;
+                    for (unsigned k = 0; k < len; ++k) {
+                        const float4 pj = __ldg(pos + base + k);
+                        const float r2 =
+                            pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+                        const bool take = r2 < h2 && r2 != 0.0f && !(att_i && id_of(pj) < nb_all);
+                        m |= (unsigned)take << k;
+                    }
+                    while (m) {
+                        const int t = __ffs(m) - 1;
+                        m &= m - 1u;
+                        pair(base + (unsigned)t);
+                    }
                 }
             }
         }
@@ -257,7 +305,7 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     if (__any_sync(FULL, clamped) && (threadIdx.x & 31) == 0) atomicOr(err, SPH_DEV_CLAMPED);
 }
 
-cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho,
+cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
                           const Tuning& t, const int* bmask, float4* acc, int* touched, float4* infl, float4* fb,
                           float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,
@@ -266,10 +314,10 @@ cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const 
     if (sc.n_all <= 0) return cudaSuccess;
     const int blocks = (sc.n_all + t.block - 1) / t.block;
     if (mode == 0)
-        k_forces<0><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
+        k_forces<0><<<blocks, t.block, 0, s>>>(pos, vel, rho, ab, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
                                                infl, fb, pos_next, vel_next, key, rank, count, err);
     else
-        k_forces<1><<<blocks, t.block, 0, s>>>(pos, vel, rho, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
+        k_forces<1><<<blocks, t.block, 0, s>>>(pos, vel, rho, ab, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
                                                infl, fb, pos_next, vel_next, key, rank, count, err);
     ++*launches;
     return cudaGetLastError();

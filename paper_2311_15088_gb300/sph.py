@@ -427,6 +427,7 @@ class Scene:
         self.dims, self.bdims = dims[0], bdims[0]
         self.ncells = int(sum(d[0] * d[1] * d[2] for d in dims))
         self.nbcells = int(sum(d[0] * d[1] * d[2] for d in bdims))
+        self.tuning = (256, 0)  # the library's default (block, use_stream)
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -476,6 +477,7 @@ class Scene:
 
     def set_tuning(self, block: int, use_stream: int):
         sph_set_tuning(self.handle, block, use_stream)
+        self.tuning = (int(block), int(use_stream))
 
     def field(self, name: str):
         t = self.torch

@@ -218,3 +218,16 @@ def test_large_tank_settled_step_full_size():
     s2.step(20)
     st = _state_of(s2, p)
     _check(p, st)
+
+
+@pytest.mark.parametrize("cell", [1.0, 0.5, 0.25])
+def test_candidate_counts_cover_neighbours(cell):
+    """Every neighbour is a candidate the walk visited (the particle itself
+    too), so ncand >= nbr_count + 1 for every particle."""
+    sc = scenes.dam_break_column(n_side=32, n_boid=64)
+    p = lattice_params(sc)
+    p["cell_size"] = scenes.f32(p["h"] * cell)
+    s = run_gpu(p, sc, steps=3)
+    nc = s.field("ncand").cpu().numpy().astype(np.int64)
+    nbr = s.field("nbr_count").cpu().numpy().astype(np.int64)
+    assert np.all(nc >= nbr + 1)
