@@ -350,7 +350,8 @@ long long sph_mlp_launch_count(sph_mlp* m);
 /*
  * Test hook of the tensor-core GEMM: for BF16 row-major A[M][K] (leading
  * dimension lda) and B[N][K] (ldb), both 16-byte aligned with leading
- * dimensions multiples of 8, writes the FP32 partial products of `splits`
+ * dimensions multiples of 8, N a multiple of 4 and C 16-byte aligned
+ * (SPH_ERR_ARG otherwise), writes the FP32 partial products of `splits`
  * K-ranges to C[split][M][N] (C holds splits * M * N floats; their sum is
  * A B^T; the actual number of splits is min(splits, ceil(K / 64)) rounded
  * so that no range is empty).  err: a device word for SPH_DEV_TIMEOUT.

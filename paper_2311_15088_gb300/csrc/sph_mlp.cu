@@ -56,30 +56,104 @@ __device__ __forceinline__ float gelu_grad_f(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-template <int EPI>
-__device__ __forceinline__ void epilogue16(const GemmEpi& e, int row, int col0, const float (&v)[16])
+// Epilogue, in column chunks of EC (32, or NT when NT < 32), through shared
+// memory so that every global store is a coalesced row segment:
+//   1. each thread (one accumulator row) loads EC columns from TMEM and
+//      writes them, plus the bias where the epilogue adds one, to the FP32
+//      staging tile F[128][EC + 4];
+//   2. the CTA walks F with 4 consecutive columns per thread (EC / 4
+//      threads per row): GELU / GELU' (reading the pre-activation as a
+//      coalesced float4), BF16 casts and row stores; the BF16 values of the
+//      transposed copy go to T[EC][128 + 8];
+//   3. the CTA writes T as rows of the transposed output.
+template <int NT>
+struct EpiShape {
+    static constexpr int EC = NT < 32 ? NT : 32;   // columns per chunk
+    static constexpr int FLD = EC + 4;               // F row stride (floats)
+    static constexpr int TLD = BM + 8;               // T row stride (BF16)
+    static constexpr uint32_t BYTES = BM * FLD * 4 + EC * TLD * 2;
+};
+
+template <int NT, int EPI>
+__device__ __forceinline__ void gemm_epilogue(const GemmEpi& e, uint32_t tmem, int m0, int n0, uint8_t* stage)
 {
-    if (row >= e.M) return;
+    using S = EpiShape<NT>;
+    constexpr int EC = S::EC, FLD = S::FLD, TLD = S::TLD;
+    float* F = reinterpret_cast<float*>(stage);
+    __nv_bfloat16* T = reinterpret_cast<__nv_bfloat16*>(stage + BM * FLD * 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r_own = warp * 32 + lane;
+    const bool has_t = (EPI == EPI_BIAS_GELU || EPI == EPI_GELU_GRAD) && e.out_t != nullptr;
+    constexpr int TPR = EC / 4;          // threads per row in phase 2
+    constexpr int RPP = 128 / TPR;       // rows per pass of the CTA
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += EC) {
+        // ---- 1: TMEM -> F (row per thread)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int n = col0 + j;
-        if (n >= e.N) break;
-        if (EPI == EPI_BIAS_GELU) {
-            const float z = v[j] + e.bias[n];
-            if (e.out_f32) e.out_f32[(size_t)row * e.ld_f32 + n] = z;
-            const __nv_bfloat16 hb = __float2bfloat16_rn(gelu_f(z));
-            e.out_bf16[(size_t)row * e.ld_bf16 + n] = hb;
-            if (e.out_t) e.out_t[(size_t)n * e.ld_t + row] = hb;
-        } else if (EPI == EPI_BIAS) {
-            e.out_f32[(size_t)row * e.ld_f32 + n] = v[j] + e.bias[n];
-        } else if (EPI == EPI_GELU_GRAD) {
-            const float d = v[j] * gelu_grad_f(e.zin[(size_t)row * e.ld_z + n]);
-            const __nv_bfloat16 db = __float2bfloat16_rn(d);
-            e.out_bf16[(size_t)row * e.ld_bf16 + n] = db;
-            if (e.out_t) e.out_t[(size_t)n * e.ld_t + row] = db;
-        } else {
-            e.out_f32[(size_t)blockIdx.z * e.split_stride + (size_t)row * e.ld_f32 + n] = v[j];
+        for (int h = 0; h < EC; h += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + h), v);
+            if (EPI == EPI_BIAS_GELU || EPI == EPI_BIAS) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + h + j;
+                    v[j] += n < e.N ? __ldg(e.bias + n) : 0.0f;
+                }
+            }
+            // float4 stores: the 8 lanes of one store phase hit 32 distinct banks
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4*>(F + r_own * FLD + h + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
         }
+        __syncthreads();
+        // ---- 2: coalesced row segments
+        const int cq = (threadIdx.x % TPR) * 4;
+        const int n = n0 + c0 + cq;
+#pragma unroll 1
+        for (int r = threadIdx.x / TPR; r < BM; r += RPP) {
+            const int row = m0 + r;
+            const float4 x = *reinterpret_cast<const float4*>(F + r * FLD + cq);
+            if (row >= e.M || n >= e.N) continue;
+            if (EPI == EPI_F32) {
+                *reinterpret_cast<float4*>(e.out_f32 + (size_t)blockIdx.z * e.split_stride + (size_t)row * e.ld_f32 + n) = x;
+            } else if (EPI == EPI_BIAS) {
+                *reinterpret_cast<float4*>(e.out_f32 + (size_t)row * e.ld_f32 + n) = x;
+            } else {
+                float4 o;
+                if (EPI == EPI_BIAS_GELU) {
+                    if (e.out_f32) *reinterpret_cast<float4*>(e.out_f32 + (size_t)row * e.ld_f32 + n) = x;
+                    o = make_float4(gelu_f(x.x), gelu_f(x.y), gelu_f(x.z), gelu_f(x.w));
+                } else {  // EPI_GELU_GRAD
+                    const float4 z = __ldg(reinterpret_cast<const float4*>(e.zin + (size_t)row * e.ld_z + n));
+                    o = make_float4(x.x * gelu_grad_f(z.x), x.y * gelu_grad_f(z.y), x.z * gelu_grad_f(z.z),
+                                    x.w * gelu_grad_f(z.w));
+                }
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(o.x, o.y), hi = __floats2bfloat162_rn(o.z, o.w);
+                uint2 pk;
+                pk.x = *reinterpret_cast<const unsigned*>(&lo);
+                pk.y = *reinterpret_cast<const unsigned*>(&hi);
+                *reinterpret_cast<uint2*>(e.out_bf16 + (size_t)row * e.ld_bf16 + n) = pk;
+                if (has_t) {
+                    T[(cq + 0) * TLD + r] = lo.x;
+                    T[(cq + 1) * TLD + r] = lo.y;
+                    T[(cq + 2) * TLD + r] = hi.x;
+                    T[(cq + 3) * TLD + r] = hi.y;
+                }
+            }
+        }
+        if (has_t) {
+            __syncthreads();
+            // ---- 3: transposed rows out_t[n][m0 .. m0+127], 8 BF16 per store
+#pragma unroll 1
+            for (int t = threadIdx.x; t < EC * (BM / 8); t += 128) {
+                const int c = t / (BM / 8), r8 = (t % (BM / 8)) * 8;
+                const int nn = n0 + c0 + c, row = m0 + r8;
+                if (nn < e.N && row < e.M)
+                    *reinterpret_cast<uint4*>(e.out_t + (size_t)nn * e.ld_t + row) =
+                        *reinterpret_cast<const uint4*>(T + c * TLD + r8);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -88,7 +162,7 @@ struct GemmSmem {
     static constexpr uint32_t A_BYTES = BM * BK * 2;
     static constexpr uint32_t B_BYTES = NT * BK * 2;
     static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
-    static constexpr uint32_t TILES = STAGES * STAGE;
+    static constexpr uint32_t TILES = STAGES * STAGE > EpiShape<NT>::BYTES ? STAGES * STAGE : EpiShape<NT>::BYTES;
     static constexpr uint32_t TOTAL = 1024 + TILES + 8 * (2 * STAGES + 1) + 16;
     static constexpr uint32_t TMEM_COLS = NT < 32 ? 32 : NT;
 };
@@ -174,18 +248,12 @@ k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtenso
     }
     __syncwarp();
 
-    // ---- epilogue: every warp reads its 32 accumulator rows
+    // ---- epilogue (the stage buffers are idle once every MMA completed)
     const bool ok = mbar_wait(done, 0, e.err);
     tc_fence_after();
-    if (ok) {
-        const int row = m0 + warp * 32 + lane;
-#pragma unroll 1
-        for (int c0 = 0; c0 < NT; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            epilogue16<EPI>(e, row, n0 + c0, v);
-        }
-    }
+    // the CTA agrees on ok, so that the barriers inside are reached by all
+    if (__syncthreads_and(ok ? 1 : 0))
+        gemm_epilogue<NT, EPI>(e, tmem, m0, n0, smem_raw + (tiles - raw));
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, L::TMEM_COLS);
@@ -263,9 +331,9 @@ static cudaError_t gemm(int NT, int EPI, const __nv_bfloat16* A, int lda, const 
     ++*launches;
 #define SPH_GEMM_CASE(nt, epi) \
     if (NT == nt && EPI == epi) return launch_gemm_t<nt, epi>(ma, mb, e, splits, s);
-    SPH_GEMM_CASE(256, EPI_BIAS_GELU)
+    SPH_GEMM_CASE(128, EPI_BIAS_GELU)
     SPH_GEMM_CASE(16, EPI_BIAS)
-    SPH_GEMM_CASE(256, EPI_GELU_GRAD)
+    SPH_GEMM_CASE(128, EPI_GELU_GRAD)
     SPH_GEMM_CASE(128, EPI_F32)
     SPH_GEMM_CASE(16, EPI_F32)
     SPH_GEMM_CASE(256, EPI_F32)
@@ -517,7 +585,7 @@ static int mlp_forward(sph_mlp* m, const __nv_bfloat16* x, int B, float* y, bool
             e.out_t = m->HT[l];
             e.ld_t = m->max_batch;
         }
-        MLP_TRY(m, gemm(256, EPI_BIAS_GELU, in, ld_in, m->W + L.w[l], L.in[l], B, MLP_H, k_in, 1, e, s, &m->launches));
+        MLP_TRY(m, gemm(128, EPI_BIAS_GELU, in, ld_in, m->W + L.w[l], L.in[l], B, MLP_H, k_in, 1, e, s, &m->launches));
         in = m->H[l];
         ld_in = MLP_H;
         k_in = MLP_H;
@@ -570,7 +638,7 @@ static int mlp_backward(sph_mlp* m, int B, bool trunk, cudaStream_t s)
         e.ld_bf16 = MLP_H;
         e.out_t = m->DT[cur];
         e.ld_t = m->max_batch;
-        MLP_TRY(m, gemm(256, EPI_GELU_GRAD, dprev, ld_prev, m->WT + L.w[l + 1], L.out[l + 1], B, MLP_H, k_prev, 1, e,
+        MLP_TRY(m, gemm(128, EPI_GELU_GRAD, dprev, ld_prev, m->WT + L.w[l + 1], L.out[l + 1], B, MLP_H, k_prev, 1, e,
                         s, &m->launches));
         rc = layer_grads(m, l, m->D[cur], m->DT[cur], MLP_H, l == 0 ? m->XT : m->HT[l - 1], B, s);
         if (rc != SPH_OK) return rc;
@@ -735,9 +803,10 @@ long long sph_mlp_launch_count(sph_mlp* m) { return m ? m->launches : 0; }
 int sph_debug_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int splits, float* C,
                    unsigned* err, void* stream)
 {
-    if (!A || !B || !C || !err || M <= 0 || N <= 0 || K <= 0 || (lda & 7) || (ldb & 7) || splits < 1)
+    if (!A || !B || !C || !err || M <= 0 || N <= 0 || K <= 0 || (lda & 7) || (ldb & 7) || (N & 3) || splits < 1)
         return mfail(nullptr, SPH_ERR_ARG, "bad GEMM arguments");
-    if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return mfail(nullptr, SPH_ERR_ARG, "A, B must be 16-byte aligned");
+    if (((uintptr_t)A & 15) || ((uintptr_t)B & 15) || ((uintptr_t)C & 15))
+        return mfail(nullptr, SPH_ERR_ARG, "A, B, C must be 16-byte aligned");
     GemmEpi e;
     memset(&e, 0, sizeof(e));
     e.err = err;
