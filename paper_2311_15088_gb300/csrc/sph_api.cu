@@ -209,6 +209,7 @@ static void make_const(const sph_params* p, int n_fluid, int n_boid, StepConst* 
     }
     c->half_cp_h = (float)(0.5 * cp * h);
     c->cv_mu = (float)(cv * (double)p->mu);
+    c->h = p->h;
     c->inv_h = (float)(1.0 / h);
     c->mass = p->mass;
     c->k = p->k;

@@ -54,7 +54,7 @@ struct StepConst {
     float mC6;          // m * 315 / (64 pi h^9): poly6 prefactor times mass
     float half_cp_h;    // C_p h / 2: pressure pair prefactor (times 1/r)
     float cv_mu;        // C_v mu: viscosity pair prefactor
-    float inv_h, mass, k, rho0, dt;
+    float h, inv_h, mass, k, rho0, dt;  // inv_h = fl(1 / h) (double quotient rounded)
     float grav[3];      // gravity
     float box_min[3], box_max[3];
     float restitution;

@@ -26,6 +26,12 @@ from . import scenes
 from .sph import SPH_BOID_EXACT_LOCAL, SPH_BOID_SURROGATE, SPH_BOID_SURROGATE_FALLBACK, Mlp, Scene
 
 REL_FLOOR = 0.05  # per-query relative error is taken against max(|F|, 0.05 F_scale)
+# Feature columns beyond the 256 stencil features and the boid velocity:
+# the boid's offset from the stencil centre (259 .. 261) and its own
+# density and kernel moments (262 .. 269); zeroing them gives the
+# stencil-only network for ablations.
+EXTRA_COLS = slice(259, 272)
+MOMENT_COLS = slice(262, 272)
 
 
 def _params(sc):
@@ -181,19 +187,31 @@ def evaluate(mlp: Mlp, X, F, f_scale: float, threshold: float) -> dict:
     }
 
 
-def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=30, batch=8192, lr=2e-3,
-                    device="cuda", target=0.05, seed=0, head_epochs=10):
+def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=60, batch=8192, lr=2e-3,
+                    device="cuda", target=0.05, seed=0, head_epochs=10, zero_cols=None, pairs=None,
+                    return_pairs=False):
     """Log training pairs (one run of ``steps`` steps per training seed of
     make_scene) and held-out pairs (validation seeds), train the network,
     fit the error head and calibrate the fallback threshold for an
-    aggregate error <= target.  Returns (mlp, info)."""
+    aggregate error <= target.  ``zero_cols`` (a slice) blanks feature
+    columns in every pair (an ablation; such a network is for Python-side
+    evaluation only, since the library's features fill them).  ``pairs``
+    reuses logged (X, F, Xv, Fv).  Returns (mlp, info), plus the pairs when
+    ``return_pairs``."""
     import time
 
     import torch
 
     t0 = time.perf_counter()
-    X, F = log_runs(make_scene, train_seeds, steps, device=device)
-    Xv, Fv = log_runs(make_scene, val_seeds, steps, device=device)
+    if pairs is None:
+        X, F = log_runs(make_scene, train_seeds, steps, device=device)
+        Xv, Fv = log_runs(make_scene, val_seeds, steps, device=device)
+    else:
+        X, F, Xv, Fv = pairs
+    if zero_cols is not None:
+        X, Xv = X.clone(), Xv.clone()
+        X[:, zero_cols] = 0
+        Xv[:, zero_cols] = 0
     torch.cuda.synchronize()
     t_log = time.perf_counter() - t0
     fs = f_scale_of(F)
@@ -210,6 +228,8 @@ def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=30, bat
             "threshold": thr, "val_fallback_fraction": frac, "val_aggregate_error": err,
             "train_aggregate_error": aggregate_error(predict(mlp, X[:262144], fs)[0], F[:262144]),
             "seconds_logging": t_log, "seconds_training": t_train, "status": mlp.status()}
+    if return_pairs:
+        return mlp, info, (X, F, Xv, Fv)
     return mlp, info
 
 

@@ -52,30 +52,59 @@ def test_first_adam_step_closed_form():
 
 
 def test_stencil_features_by_hand():
-    """A boid at the centre of cell (8, 8, 8) of a grid of h/2 cells: its
-    stencil starts at cell 7 per axis (floor(8.5 - 1.5)); fluid particles
-    placed in stencil cells (0,0,0) and (3,1,2) and one outside."""
+    """h = 0.25: a boid at cell coordinate 8.5 of the feature grid (cells of
+    size h) has its stencil start at cell 7 per axis (floor(8.5 - 1.5)) and
+    sits 0.5 cells below the stencil's centre; fluid particles placed in
+    stencil cells (0,0,0), (3,1,2) and (2,1,1) and one outside; only the
+    last lies within h of the boid (r = h/2, q = 1/2)."""
     from oracle.features import stencil_features
     from paper_2311_15088_gb300 import scenes
 
-    p = scenes.default_params(mass=0.01, cell_size=0.25, box_max=(4.0, 4.0, 4.0))
-    d = 0.25
-    boid = np.array([[8.5 * d, 8.5 * d, 8.5 * d, 0]], np.float32)
+    h = 0.25
+    p = scenes.default_params(mass=0.01, h=h, cell_size=h / 2, box_max=(4.0, 4.0, 4.0))
+    boid = np.array([[8.5 * h, 8.5 * h, 8.5 * h, 0]], np.float32)
     bvel = np.array([[0.1, -0.2, 0.3, 0]], np.float32)
-    pts = [[7.5 * d, 7.5 * d, 7.5 * d], [7.2 * d, 7.9 * d, 7.1 * d],   # cell (7,7,7): stencil (0,0,0)
-           [10.5 * d, 8.5 * d, 9.5 * d],                              # cell (10,8,9): stencil (3,1,2)
-           [12.5 * d, 8.5 * d, 8.5 * d]]                              # outside the stencil
-    vel = [[1, 0, 0], [0, 2, 0], [0, 0, 3], [5, 5, 5]]
-    fp = np.zeros((4, 4), np.float32)
+    pts = [[7.5 * h, 7.5 * h, 7.5 * h], [7.2 * h, 7.9 * h, 7.1 * h],   # cell (7,7,7): stencil (0,0,0)
+           [10.5 * h, 8.5 * h, 9.5 * h],                              # cell (10,8,9): stencil (3,1,2)
+           [12.5 * h, 8.5 * h, 8.5 * h],                              # outside the stencil
+           [9.0 * h, 8.5 * h, 8.5 * h]]                               # cell (9,8,8): stencil (2,1,1)
+    vel = [[1, 0, 0], [0, 2, 0], [0, 0, 3], [5, 5, 5], [0, 0, 1]]
+    fp = np.zeros((5, 4), np.float32)
     fp[:, :3] = pts
-    fv = np.zeros((4, 4), np.float32)
+    fv = np.zeros((5, 4), np.float32)
     fv[:, :3] = vel
     x = stencil_features(p, fp, fv, boid, bvel)
-    scale = p["mass"] / (d ** 3 * 1000.0)
-    q0 = 0
-    q1 = (2 * 4 + 1) * 4 + 3
-    assert x[0, 4 * q0] == 2 * scale and np.allclose(x[0, 4 * q0 + 1:4 * q0 + 4], [0.5, 1.0, 0.0])
-    assert x[0, 4 * q1] == scale and np.allclose(x[0, 4 * q1 + 1:4 * q1 + 4], [0, 0, 3])
-    others = np.delete(np.arange(64), [q0, q1])
+    unit = p["mass"] / (h ** 3 * 1000.0)
+    q0, q1, q2 = 0, (2 * 4 + 1) * 4 + 3, (1 * 4 + 1) * 4 + 2
+    assert math.isclose(x[0, 4 * q0], 2 * unit) and np.allclose(x[0, 4 * q0 + 1:4 * q0 + 4], [0.5, 1.0, 0.0])
+    assert math.isclose(x[0, 4 * q1], unit) and np.allclose(x[0, 4 * q1 + 1:4 * q1 + 4], [0, 0, 3])
+    assert math.isclose(x[0, 4 * q2], unit) and np.allclose(x[0, 4 * q2 + 1:4 * q2 + 4], [0, 0, 1])
+    others = np.delete(np.arange(64), [q0, q1, q2])
     assert np.all(x[0, 4 * others] == 0)
-    assert np.allclose(x[0, 256:259], [0.1, -0.2, 0.3]) and np.all(x[0, 259:] == 0)
+    assert np.allclose(x[0, 256:259], [0.1, -0.2, 0.3]) and np.all(x[0, 270:] == 0)
+    assert np.all(x[0, 259:262] == -0.5)
+    # moments: the one neighbour at r = h/2 has weight 1 - q = 1/2
+    kn = p["mass"] / (1000.0 * h ** 3)
+    c6 = p["mass"] * 315.0 / (64.0 * math.pi * h ** 9)
+    assert math.isclose(x[0, 262], c6 * h ** 6 * (1.0 + 0.75 ** 3) / 1000.0, rel_tol=1e-6)
+    assert math.isclose(x[0, 263], 0.5 * kn, rel_tol=1e-6)
+    assert np.allclose(x[0, 264:267], 0.5 * kn * np.array([-0.1, 0.2, 0.7]), rtol=1e-6)
+    assert np.allclose(x[0, 267:270], 0.25 * kn * np.array([-1.0, 0.0, 0.0]), rtol=1e-6, atol=1e-12)
+
+
+def test_stencil_offset_moves_with_the_boid():
+    """The offset column follows the boid across a cell: at cell coordinate
+    9.25 the stencil starts at 7 (floor(7.75)) and the offset is +0.25; at
+    9.5 the stencil starts at 8 and the offset is -0.5."""
+    from oracle.features import stencil_features
+    from paper_2311_15088_gb300 import scenes
+
+    h = 0.25
+    p = scenes.default_params(mass=0.01, h=h, cell_size=h / 2, box_max=(4.0, 4.0, 4.0))
+    boid = np.array([[9.25 * h, 9.5 * h, 8.0 * h, 0], [0.1 * h, 0.6 * h, 2.0 * h, 0]], np.float32)
+    z = np.zeros((0, 4), np.float32)
+    x = stencil_features(p, z, z, boid, np.zeros_like(boid))
+    assert np.allclose(x[0, 259:262], [0.25, -0.5, 0.0])
+    # near the minimum wall the stencil starts outside the grid (c0 = -2)
+    assert np.allclose(x[1, 259:262], [0.1, 0.6 - 1.0, 0.0], atol=1e-6)
+    assert np.all(x[:, :256] == 0)
