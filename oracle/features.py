@@ -23,7 +23,8 @@ Row b of the features (272 columns), for boid b at p_b with velocity v_b:
 j runs over the fluid particles with r_j = |x_j - p_b| < h (float64 here),
 q_j = r_j / h.  Counts and sums in float64.  ``with_scale=True`` also
 returns, per feature, the magnitude its float32 evaluation rounds against
-(the same sums of absolute values for the moments, |feature| elsewhere).
+(the same sums or means of absolute values for the velocity means and the
+moments, |feature| elsewhere).
 """
 from __future__ import annotations
 
@@ -59,6 +60,7 @@ def stencil_features(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, with_sca
         q = rel[inside, 0] + 4 * (rel[inside, 1] + 4 * rel[inside, 2])
         cnt = np.bincount(q, minlength=64).astype(np.float64)
         vs = np.stack([np.bincount(q, weights=fv[inside, a], minlength=64) for a in range(3)], 1)
+        vabs = np.stack([np.bincount(q, weights=np.abs(fv[inside, a]), minlength=64) for a in range(3)], 1)
         x[b, 0:256:4] = cnt * dens_unit
         safe = np.maximum(cnt, 1.0)
         for a in range(3):
@@ -80,6 +82,8 @@ def stencil_features(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, with_sca
         unit[pos_r] = -dn[pos_r] / rn[pos_r, None]
         x[b, 267:270] = kn * ((w ** 2)[:, None] * unit).sum(0)
         scale[b] = np.abs(x[b])
+        for a in range(3):
+            scale[b, 1 + a:256:4] = np.where(cnt > 0, vabs[:, a] / safe, 0.0)
         scale[b, 264:267] = kn * (w[:, None] * np.abs(dv)).sum(0)
         scale[b, 267:270] = kn * (w ** 2).sum()
     return (x, scale) if with_scale else x

@@ -52,7 +52,9 @@ struct sph_handle {
     // surrogate: features, network output, exact-path masks
     void* feat;               // BF16 [nb_pad][SPH_MLP_IN]
     float* yout;              // [nb_pad][SPH_MLP_OUT]
-    unsigned char* need;      // per sorted slot
+    unsigned char* need;
+    int* need_list;     // compacted slots whose density a boid force needs
+    unsigned* need_len;      // per sorted slot
     int* bflag;               // per boid
     int nb_pad;
     sph_mlp* mlp;
@@ -296,6 +298,8 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->feat = cv.take<unsigned short>((size_t)h->nb_pad * SPH_MLP_IN);
     h->yout = cv.take<float>((size_t)h->nb_pad * SPH_MLP_OUT);
     h->need = cv.take<unsigned char>(n);
+    h->need_list = cv.take<int>(n);
+    h->need_len = cv.take<unsigned>(1);
     h->bflag = cv.take<int>(nb);
     return (size_t)((cv.off + 255) & ~(uintptr_t)255);
 }
@@ -736,12 +740,12 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
     if (rc != SPH_OK) return rc;
     prof_begin(h, SPH_KIND_DENSITY, s);
     CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, nullptr,
-                               h->err, s, &h->launches));
+                               nullptr, h->err, s, &h->launches));
     prof_end(h, s);
     prof_begin(h, SPH_KIND_FORCES, s);
-    CUDA_TRY(h, launch_forces(0, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                              nullptr, h->acc, h->touched, h->infl, h->fb, h->pos, h->vel, h->key, h->rank, h->count, h->err,
-                              s, &h->launches));
+    CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+                              true, h->slot_of_boid, nullptr, h->fb, h->acc, h->touched, h->infl, h->pos, h->vel,
+                              h->key, h->rank, h->count, h->err, s, &h->launches));
     prof_end(h, s);
     if (h->n_boid > 0) {
         prof_begin(h, SPH_KIND_BOID_BIN, s);
@@ -857,14 +861,18 @@ int sph_features(sph_handle* h, void* x_out, void* stream)
 
 // Exact fluid force on the boids flagged in bmask (NULL: every boid),
 // computing densities only where those forces need them.
+// F_b of the boids in bmask (NULL: all) from the densities of only the
+// particles they need: mark them, compact their slots into a list, run the
+// density pass over the list and the force pass over the boids.
 static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_t s)
 {
     CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
-    CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, bmask, h->need, s, &h->launches));
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, h->need,
-                               h->err, s, &h->launches));
-    CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                              bmask, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr,
+    CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, h->slot_of_boid, bmask, h->need, s, &h->launches));
+    CUDA_TRY(h, launch_compact_needed(h->need, h->n, h->need_list, h->need_len, s, &h->launches));
+    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
+                               h->need_list, h->need_len, h->err, s, &h->launches));
+    CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+                              false, h->slot_of_boid, bmask, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                               nullptr, nullptr, h->err, s, &h->launches));
     return SPH_OK;
 }
@@ -886,23 +894,13 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
     h->has_step = false;
     if (mode == SPH_BOID_EXACT) {
         CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
-                                   nullptr, h->err, s, &h->launches));
-        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                                  nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                  h->err, s, &h->launches));
+                                   nullptr, nullptr, h->err, s, &h->launches));
+        CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+                                  false, h->slot_of_boid, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  nullptr, nullptr, nullptr, h->err, s, &h->launches));
         return SPH_OK;
     }
-    if (mode == SPH_BOID_EXACT_LOCAL) {
-        // every boid flagged: bflag = 1
-        CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
-        CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, nullptr, h->need, s, &h->launches));
-        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
-                                   h->need, h->err, s, &h->launches));
-        CUDA_TRY(h, launch_forces(1, h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                                  nullptr, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                  h->err, s, &h->launches));
-        return SPH_OK;
-    }
+    if (mode == SPH_BOID_EXACT_LOCAL) return exact_local(h, nullptr, out, s);
     // surrogate: features -> network -> forces (+ exact path for flagged boids)
     CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, h->feat, s,
                                 &h->launches));

@@ -24,28 +24,36 @@
 // floor((x - m) * inv_h) in float32 (inv_h = fl(1 / h)), like the grid's
 // own cell function.
 //
-// One block of FT threads per boid sweeps the particle-grid rows under the
-// stencil's box (one cell of margin) once: counts and velocity sums go to
-// shared bins by integer atomics (velocities in 2^-32 fixed point, so the
-// sums do not depend on the order), the kernel moments to per-thread sums
-// reduced in a fixed order.
 #include <cuda_bf16.h>
 
 #include "sph_internal.cuh"
 
 namespace sphk {
 
-constexpr int FT = 128;
-constexpr double FIX = 4294967296.0;  // 2^32
+// One block of FT = 256 threads per boid, every sum in a fixed order:
+//   1. the rows (y, z) of particle-grid cells under the stencil's box (one
+//      cell of margin) get their slot ranges loaded in parallel, and a block
+//      scan of their lengths numbers the box's particles 0 .. total-1;
+//   2. thread t takes particles t, t + FT, ...: a particle of a stencil
+//      cell adds 1 and its velocity in 2^-16 fixed point to the cell's
+//      shared integer sums (integer sums do not depend on the order; they
+//      hold while a cell's mean speed stays below 2^15 / count m/s, beyond
+//      any flow of these scenes), and a particle within h of the boid adds
+//      its kernel moments to the thread's own sums;
+//   3. the moments are reduced by a butterfly in each warp, then warp by warp.
+constexpr int FT = 256;
+constexpr int FROWS = 512;  // rows of the box (d >= h/4: at most 19 x 19 with margins)
+constexpr float VFIX = 65536.0f;
 
 __global__ void __launch_bounds__(FT)
 k_features(const float4* __restrict__ pos, const float4* __restrict__ vel, const unsigned* __restrict__ start,
            const float4* __restrict__ bpos, const float4* __restrict__ bvel, Scenes sc,
            __nv_bfloat16* __restrict__ x)
 {
-    __shared__ int cnt[64];
-    __shared__ unsigned long long vsum[64][3];
-    __shared__ float red[FT / 32][10];
+    __shared__ unsigned row_s0[FROWS];
+    __shared__ unsigned row_pre[FROWS + 1];
+    __shared__ int cnt[64], vsum[64][3];
+    __shared__ float red[FT / 32][8];
     const int b = blockIdx.x;
     const int tid = threadIdx.x;
     const StepConst& c = sc.c[scene_of(sc.bbase, sc.S, (unsigned)b)];
@@ -64,93 +72,125 @@ k_features(const float4* __restrict__ pos, const float4* __restrict__ vel, const
         lo[a] = (int)fmaxf(floorf(e0) - 1.0f, 0.0f);
         hi[a] = (int)fminf(floorf(e1) + 1.0f, (float)(c.g.dim[a] - 1));
     }
+    const int ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1;
+    int nrows = (lo[0] <= hi[0] && ny > 0 && nz > 0) ? ny * nz : 0;
+    nrows = nrows < FROWS ? nrows : FROWS;  // a box this large only arises for far-off boids
+    const unsigned* cstart = start + c.c_base;
+    // ---- 1: row ranges and their prefix sums
+    for (int r = tid; r < FROWS; r += FT) {
+        unsigned len = 0;
+        if (r < nrows) {
+            const int y = lo[1] + r % ny, z = lo[2] + r / ny;
+            const unsigned rk = (unsigned)c.g.dim[0] * ((unsigned)y + (unsigned)c.g.dim[1] * (unsigned)z);
+            const unsigned s0 = __ldg(cstart + rk + lo[0]);
+            row_s0[r] = s0;
+            len = __ldg(cstart + rk + hi[0] + 1) - s0;
+        }
+        row_pre[r + 1] = len;
+    }
+    if (tid == 0) row_pre[0] = 0;
     if (tid < 64) {
         cnt[tid] = 0;
-        vsum[tid][0] = vsum[tid][1] = vsum[tid][2] = 0ull;
+        vsum[tid][0] = vsum[tid][1] = vsum[tid][2] = 0;
     }
     __syncthreads();
+    if (tid < 32) {  // inclusive scan of row_pre[1 .. FROWS] by one warp
+        unsigned carry = 0;
+        for (int base = 1; base <= FROWS; base += 32) {
+            unsigned v = row_pre[base + tid];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned u = __shfl_up_sync(FULL, v, o);
+                if (tid >= o) v += u;
+            }
+            row_pre[base + tid] = v + carry;
+            carry += __shfl_sync(FULL, v, 31);
+        }
+    }
+    __syncthreads();
+    const unsigned total = row_pre[nrows];
     const float h2 = c.h2;
-    float m[10] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // poly6, S0, S1 (3), S2 (3)
-    const unsigned* cstart = start + c.c_base;
-    for (int z = lo[2]; z <= hi[2]; ++z) {
-        for (int y = lo[1]; y <= hi[1]; ++y) {
-            if (lo[0] > hi[0]) continue;
-            const unsigned row = (unsigned)c.g.dim[0] * ((unsigned)y + (unsigned)c.g.dim[1] * (unsigned)z);
-            const unsigned s0 = __ldg(cstart + row + lo[0]), s1 = __ldg(cstart + row + hi[0] + 1);
-            for (unsigned j = s0 + tid; j < s1; j += FT) {
-                const float4 pj = __ldg(pos + j);
-                if (id_of(pj) < sc.nb_all) continue;  // fluid particles only
-                const float fx = floorf(__fmul_rn(__fsub_rn(pj.x, c.g.minf[0]), c.inv_h)) - c0[0];
-                const float fy = floorf(__fmul_rn(__fsub_rn(pj.y, c.g.minf[1]), c.inv_h)) - c0[1];
-                const float fz = floorf(__fmul_rn(__fsub_rn(pj.z, c.g.minf[2]), c.inv_h)) - c0[2];
-                const bool in = fx >= 0.f && fx < 4.f && fy >= 0.f && fy < 4.f && fz >= 0.f && fz < 4.f;
-                const float dx = __fsub_rn(pj.x, pb.x), dy = __fsub_rn(pj.y, pb.y), dz = __fsub_rn(pj.z, pb.z);
-                const float r2 = pair_r2(dx, dy, dz);
-                const bool near = r2 < h2;
-                if (!in && !near) continue;
-                const float4 vj = __ldg(vel + j);
-                if (in) {
-                    const int q = (int)fx + 4 * ((int)fy + 4 * (int)fz);
-                    atomicAdd(&cnt[q], 1);
-                    atomicAdd(&vsum[q][0], (unsigned long long)__double2ll_rn((double)vj.x * FIX));
-                    atomicAdd(&vsum[q][1], (unsigned long long)__double2ll_rn((double)vj.y * FIX));
-                    atomicAdd(&vsum[q][2], (unsigned long long)__double2ll_rn((double)vj.z * FIX));
-                }
-                if (near) {
-                    const float u = h2 - r2;
-                    m[0] += u * u * u;
-                    const float r = sqrtf(r2);
-                    const float w = 1.0f - r * c.inv_h;
-                    m[1] += w;
-                    m[2] += w * (vj.x - vb.x);
-                    m[3] += w * (vj.y - vb.y);
-                    m[4] += w * (vj.z - vb.z);
-                    if (r2 > 0.0f) {
-                        const float s = -w * w / r;  // (x_b - x_j) / r = -d / r
-                        m[5] += s * dx;
-                        m[6] += s * dy;
-                        m[7] += s * dz;
-                    }
-                }
+    float mo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // poly6, S0, S1 (3), S2 (3)
+    // ---- 2: every particle of the box once
+    for (unsigned g = tid; g < total; g += FT) {
+        int lo_r = 0, hi_r = nrows;  // row r with row_pre[r] <= g < row_pre[r + 1]
+        while (hi_r - lo_r > 1) {
+            const int mid = (lo_r + hi_r) >> 1;
+            if (row_pre[mid] <= g) lo_r = mid;
+            else hi_r = mid;
+        }
+        const unsigned j = row_s0[lo_r] + (g - row_pre[lo_r]);
+        const float4 pj = __ldg(pos + j);
+        if (id_of(pj) < sc.nb_all) continue;  // fluid particles only
+        const float fx = floorf(__fmul_rn(__fsub_rn(pj.x, c.g.minf[0]), c.inv_h)) - c0[0];
+        const float fy = floorf(__fmul_rn(__fsub_rn(pj.y, c.g.minf[1]), c.inv_h)) - c0[1];
+        const float fz = floorf(__fmul_rn(__fsub_rn(pj.z, c.g.minf[2]), c.inv_h)) - c0[2];
+        const bool in = fx >= 0.f && fx < 4.f && fy >= 0.f && fy < 4.f && fz >= 0.f && fz < 4.f;
+        const float dx = __fsub_rn(pj.x, pb.x), dy = __fsub_rn(pj.y, pb.y), dz = __fsub_rn(pj.z, pb.z);
+        const float r2 = pair_r2(dx, dy, dz);
+        const bool near = r2 < h2;
+        if (!in && !near) continue;
+        const float4 vj = __ldg(vel + j);
+        if (in) {
+            const int q = (int)fx + 4 * ((int)fy + 4 * (int)fz);
+            atomicAdd(&cnt[q], 1);
+            atomicAdd(&vsum[q][0], __float2int_rn(vj.x * VFIX));
+            atomicAdd(&vsum[q][1], __float2int_rn(vj.y * VFIX));
+            atomicAdd(&vsum[q][2], __float2int_rn(vj.z * VFIX));
+        }
+        if (near) {
+            const float u = h2 - r2;
+            mo[0] += u * u * u;
+            const float rr = sqrtf(r2);
+            const float w = 1.0f - rr * c.inv_h;
+            mo[1] += w;
+            mo[2] += w * (vj.x - vb.x);
+            mo[3] += w * (vj.y - vb.y);
+            mo[4] += w * (vj.z - vb.z);
+            if (r2 > 0.0f) {
+                const float sdir = -w * w / rr;  // (x_b - x_j) / r = -d / r
+                mo[5] += sdir * dx;
+                mo[6] += sdir * dy;
+                mo[7] += sdir * dz;
             }
         }
     }
-    // fixed-order reduction of the moments: warp butterflies, then warps in order
+    // ---- 3: moments
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(FULL, m[k], o);
+        for (int o = 16; o > 0; o >>= 1) mo[k] += __shfl_xor_sync(FULL, mo[k], o);
     }
     if ((tid & 31) == 0) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) red[tid >> 5][k] = m[k];
+        for (int k = 0; k < 8; ++k) red[tid >> 5][k] = mo[k];
     }
     __syncthreads();
     __nv_bfloat16* row = x + (size_t)b * SPH_MLP_IN;
     if (tid < 64) {
         const int n = cnt[tid];
         const float dens = (float)n * (c.mass / (c.h * c.h * c.h * c.rho0));
-        const double inv = n ? 1.0 / ((double)n * FIX) : 0.0;
+        const float inv = n ? 1.0f / ((float)n * VFIX) : 0.0f;
         row[4 * tid + 0] = __float2bfloat16_rn(dens);
-        row[4 * tid + 1] = __float2bfloat16_rn((float)((double)(long long)vsum[tid][0] * inv));
-        row[4 * tid + 2] = __float2bfloat16_rn((float)((double)(long long)vsum[tid][1] * inv));
-        row[4 * tid + 3] = __float2bfloat16_rn((float)((double)(long long)vsum[tid][2] * inv));
+        row[4 * tid + 1] = __float2bfloat16_rn((float)vsum[tid][0] * inv);
+        row[4 * tid + 2] = __float2bfloat16_rn((float)vsum[tid][1] * inv);
+        row[4 * tid + 3] = __float2bfloat16_rn((float)vsum[tid][2] * inv);
     } else if (tid < 64 + (SPH_MLP_IN - 256)) {
-        const int k = tid - 64;
+        const int m = tid - 64;
         float tot[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int k = 0; k < 8; ++k) {
             float acc = 0.0f;
-            for (int w = 0; w < FT / 32; ++w) acc += red[w][i];
-            tot[i] = acc;
+            for (int w = 0; w < FT / 32; ++w) acc += red[w][k];
+            tot[k] = acc;
         }
         const float kn = c.mass / (c.rho0 * c.h * c.h * c.h);
         float v = 0.0f;
-        if (k < 3) v = k == 0 ? vb.x : (k == 1 ? vb.y : vb.z);
-        else if (k < 6) v = centre_off[k - 3];
-        else if (k == 6) v = c.mC6 * (tot[0] + h2 * h2 * h2) / c.rho0;
-        else if (k < 14) v = kn * tot[k - 6];
-        row[256 + k] = __float2bfloat16_rn(v);
+        if (m < 3) v = m == 0 ? vb.x : (m == 1 ? vb.y : vb.z);
+        else if (m < 6) v = centre_off[m - 3];
+        else if (m == 6) v = c.mC6 * (tot[0] + h2 * h2 * h2) / c.rho0;
+        else if (m < 14) v = kn * tot[m - 6];
+        row[256 + m] = __float2bfloat16_rn(v);
     }
 }
 
@@ -163,25 +203,27 @@ cudaError_t launch_features(const float4* pos, const float4* vel, const unsigned
     return cudaGetLastError();
 }
 
-// For every attached particle whose boid is flagged (bmask NULL = all):
-// need[slot] = 1 for the particle and for each fluid neighbour (their
-// densities enter the boid's force).
-__global__ void __launch_bounds__(256)
+// For every flagged boid (bmask NULL = all): need[slot] = 1 for its attached
+// particle and for each fluid neighbour (their densities enter the boid's
+// force).  One warp per boid, the lanes striding over each row of the walk.
+constexpr int MARK_WARPS = 8;
+
+__global__ void __launch_bounds__(MARK_WARPS * 32)
 k_mark_needed(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
-              const int* __restrict__ bmask, unsigned char* __restrict__ need)
+              const int* __restrict__ slot_of_boid, const int* __restrict__ bmask, unsigned char* __restrict__ need)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sc.n_all) return;
+    const int b = blockIdx.x * MARK_WARPS + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= sc.nb_all || (bmask && !bmask[b])) return;  // uniform per warp
+    const int i = slot_of_boid[b];
+    if (lane == 0) need[i] = 1;
     const float4 pi = pos[i];
-    const int id = id_of(pi);
-    if (id >= sc.nb_all || (bmask && !bmask[id])) return;
-    need[i] = 1;
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
-    RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+    RowWalkT<true> walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
     unsigned s0, s1;
     while (walk.next(s0, s1)) {
-        for (unsigned j = s0; j < s1; ++j) {
-            const float4 pj = pos[j];
+        for (unsigned j = s0 + lane; j < s1; j += 32) {
+            const float4 pj = __ldg(pos + j);
             if (id_of(pj) < sc.nb_all) continue;
             const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
             if (r2 < c.h2) need[j] = 1;
@@ -189,11 +231,37 @@ k_mark_needed(const float4* __restrict__ pos, const unsigned* __restrict__ start
     }
 }
 
-cudaError_t launch_mark_needed(const float4* pos, const unsigned* start, const Scenes& sc, const int* bmask,
-                               unsigned char* need, cudaStream_t s, long long* launches)
+cudaError_t launch_mark_needed(const float4* pos, const unsigned* start, const Scenes& sc, const int* slot_of_boid,
+                               const int* bmask, unsigned char* need, cudaStream_t s, long long* launches)
 {
-    if (sc.n_all <= 0) return cudaSuccess;
-    k_mark_needed<<<(sc.n_all + 255) / 256, 256, 0, s>>>(pos, start, sc, bmask, need);
+    if (sc.nb_all <= 0) return cudaSuccess;
+    k_mark_needed<<<(sc.nb_all + MARK_WARPS - 1) / MARK_WARPS, MARK_WARPS * 32, 0, s>>>(pos, start, sc, slot_of_boid,
+                                                                                          bmask, need);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// Stream compaction of the marked slots: one atomic per warp.
+__global__ void __launch_bounds__(256)
+k_compact_needed(const unsigned char* __restrict__ need, int n, int* __restrict__ list, unsigned* __restrict__ len)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool take = i < n && need[i];
+    const unsigned ballot = __ballot_sync(FULL, take);
+    if (!ballot) return;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(len, (unsigned)__popc(ballot));
+    base = __shfl_sync(FULL, base, 0);
+    if (take) list[base + __popc(ballot & ((1u << lane) - 1u))] = i;
+}
+
+cudaError_t launch_compact_needed(const unsigned char* need, int n, int* list, unsigned* len, cudaStream_t s,
+                                  long long* launches)
+{
+    cudaError_t e = cudaMemsetAsync(len, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    k_compact_needed<<<(n + 255) / 256, 256, 0, s>>>(need, n, list, len);
     ++*launches;
     return cudaGetLastError();
 }

@@ -150,16 +150,21 @@ __device__ __forceinline__ float axis_gap2(float v, int c, int dim, float mn, co
 // reach).  Rows and x-ranges are pruned per query with bounds that are
 // conservative for the float32 predicate, so the visited set always holds
 // every neighbour.  Usage: RowWalk w(...); while (w.next(s0, s1)) {...}
-// yields each non-empty row [s0, s1).
-struct RowWalk {
+// yields the rows [s0, s1).  With AHEAD the slot bounds of the following
+// row are loaded one row early (rows may then be empty): the same rows in
+// the same order, for kernels whose few walks leave load latency exposed.
+template <bool AHEAD = false>
+struct RowWalkT {
     const GridDesc& g;
     const WalkBounds& wb;
     const unsigned* __restrict__ start;
     float px, py, pz, rz;
     int z, z1, y, y0, y1;
+    unsigned n0, n1;  // AHEAD: the row loaded ahead
+    bool ahead;
 
-    __device__ __forceinline__ RowWalk(const GridDesc& g_, const WalkBounds& w_, const unsigned* __restrict__ st,
-                                       float x_, float y_, float z_)
+    __device__ __forceinline__ RowWalkT(const GridDesc& g_, const WalkBounds& w_, const unsigned* __restrict__ st,
+                                        float x_, float y_, float z_)
         : g(g_), wb(w_), start(st), px(x_), py(y_), pz(z_), rz(0.0f)
     {
         bool cl = false;
@@ -168,10 +173,13 @@ struct RowWalk {
         y0 = cell_coord(py - wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
         y1 = cell_coord(py + wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
         z = z0 - 1;
-        y = y1 + 1;  // forces the first next() to open row z0
+        y = y1 + 1;  // forces the first step to open row z0
+        if (AHEAD) ahead = advance(n0, n1, false);
     }
 
-    __device__ __forceinline__ bool next(unsigned& s0, unsigned& s1)
+    // The next row the sphere reaches: its bounds; with skip_empty, the next
+    // non-empty one.
+    __device__ __forceinline__ bool advance(unsigned& s0, unsigned& s1, bool skip_empty)
     {
         for (;;) {
             if (y > y1) {
@@ -195,10 +203,21 @@ struct RowWalk {
             const unsigned rowk = (unsigned)g.dim[0] * ((unsigned)yy + (unsigned)g.dim[1] * (unsigned)z);
             s0 = __ldg(start + rowk + x0);
             s1 = __ldg(start + rowk + x1 + 1);
-            if (s0 < s1) return true;
+            if (!skip_empty || s0 < s1) return true;
         }
     }
+
+    __device__ __forceinline__ bool next(unsigned& s0, unsigned& s1)
+    {
+        if (!AHEAD) return advance(s0, s1, true);
+        if (!ahead) return false;
+        s0 = n0;
+        s1 = n1;
+        ahead = advance(n0, n1, false);
+        return true;
+    }
 };
+using RowWalk = RowWalkT<false>;
 
 // ---------------------------------------------------------------- launchers
 
@@ -246,20 +265,22 @@ struct Tuning {
 
 // Density, neighbour counts and the candidate bit stream (bits: NBR_WORDS
 // words per particle, word-interleaved; ncand: candidates per particle).
-// need (per sorted slot, may be NULL = every particle) restricts the pass to
-// the particles whose density is asked for.
+// list (may be NULL = every particle) restricts the pass to the sorted
+// slots list[0 .. *list_len) (device memory, built on the device).
 cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
-                           unsigned* err, cudaStream_t s, long long* launches);
-// mode 0: full step (every particle; fluid integrated into pos_next/vel_next,
-// next keys emitted); mode 1: only the attached particles' F_b (bmask, per
-// boid, may be NULL = every boid; with a mask fb.w = 1 marks what was
-// written).
-cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho, const float2* ab,
+                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const int* list,
+                           const unsigned* list_len, unsigned* err, cudaStream_t s, long long* launches);
+// The step's force pass: F_b of every boid (bmask NULL) or of the boids with
+// bmask[b] != 0 (their fb.w = 1), a warp per boid, also stored to acc at the
+// attached slot when acc is given; with fluid = true also every fluid
+// particle, integrated into pos_next/vel_next with the next keys emitted
+// (attached particles get touched = 0, influence = 0).  One launch.
+cudaError_t launch_forces(const float4* pos, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
-                          const Tuning& t, const int* bmask, float4* acc, int* touched, float4* infl, float4* fb,
-                          float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,
-                          unsigned* err, cudaStream_t s, long long* launches);
+                          const Tuning& t, bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
+                          float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
+                          unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
+                          long long* launches);
 cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const Scenes& sc, int* counts,
                                  const long long* offsets, int* list, cudaStream_t s, long long* launches);
 
@@ -274,8 +295,12 @@ cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const 
 // Surrogate inputs and outputs (sph_features.cu).
 cudaError_t launch_features(const float4* pos, const float4* vel, const unsigned* start, const float4* bpos,
                             const float4* bvel, const Scenes& sc, void* x, cudaStream_t s, long long* launches);
-cudaError_t launch_mark_needed(const float4* pos, const unsigned* start, const Scenes& sc, const int* bmask,
-                               unsigned char* need, cudaStream_t s, long long* launches);
+cudaError_t launch_mark_needed(const float4* pos, const unsigned* start, const Scenes& sc, const int* slot_of_boid,
+                               const int* bmask, unsigned char* need, cudaStream_t s, long long* launches);
+// list[0 .. *len) = the slots with need[slot] != 0 (order unspecified); *len
+// is reset first.
+cudaError_t launch_compact_needed(const unsigned char* need, int n, int* list, unsigned* len, cudaStream_t s,
+                                  long long* launches);
 cudaError_t launch_surrogate_out(const float* y, int nb, float f_scale, float log_err_max, float4* out, int* flag,
                                  unsigned* nflag, cudaStream_t s, long long* launches);
 

@@ -36,15 +36,12 @@ namespace sphk {
 // A fluid particle has no excluded pairs, so its loop counts every hit and
 // subtracts the self pair (always visited: r2 = 0) at the end; the sums
 // take the same terms in the same order as the attached particles' loop.
-template <bool STREAM>
-__global__ void __launch_bounds__(512)
-k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
-          float* __restrict__ rho, float2* __restrict__ ab, int* __restrict__ nbr, unsigned* __restrict__ bits,
-          int* __restrict__ ncand, const unsigned char* __restrict__ need, unsigned* __restrict__ err)
+template <bool STREAM, bool AHEAD>
+__device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos, const unsigned* __restrict__ start,
+                                           const Scenes& sc, float* __restrict__ rho, float2* __restrict__ ab,
+                                           int* __restrict__ nbr, unsigned* __restrict__ bits,
+                                           int* __restrict__ ncand, unsigned* __restrict__ err)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sc.n_all) return;
-    if (need && !need[i]) return;  // density of this particle not asked for
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
     const float h2 = c.h2;
     const int nb_all = sc.nb_all, n_all = sc.n_all;
@@ -54,7 +51,7 @@ k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Sc
     int cnt = 0;
     unsigned word = 0;
     int nc = 0;
-    RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+    RowWalkT<AHEAD> walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
     unsigned s0, s1;
     if (!STREAM && !att_i) {
         auto take = [&](const float4& pj) {
@@ -114,16 +111,43 @@ k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Sc
     if (!isfinite(r)) atomicOr(err, SPH_DEV_NONFINITE);
 }
 
+// Every particle (thread i = slot i), or only the slots of a list whose
+// length the device holds (grid-stride loop; the list is built on the
+// device, so the launch does not wait for its length).
+template <bool STREAM, bool LIST>
+__global__ void __launch_bounds__(512)
+k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
+          float* __restrict__ rho, float2* __restrict__ ab, int* __restrict__ nbr, unsigned* __restrict__ bits,
+          int* __restrict__ ncand, const int* __restrict__ list, const unsigned* __restrict__ list_len,
+          unsigned* __restrict__ err)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!LIST) {
+        if (t < sc.n_all) density_at<STREAM, false>(t, pos, start, sc, rho, ab, nbr, bits, ncand, err);
+        return;
+    }
+    const int len = (int)min(*list_len, (unsigned)sc.n_all);
+    for (int k = t; k < len; k += gridDim.x * blockDim.x)
+        density_at<STREAM, false>(list[k], pos, start, sc, rho, ab, nbr, bits, ncand, err);
+}
+
 cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const unsigned char* need,
-                           unsigned* err, cudaStream_t s, long long* launches)
+                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const int* list,
+                           const unsigned* list_len, unsigned* err, cudaStream_t s, long long* launches)
 {
     if (sc.n_all <= 0) return cudaSuccess;
-    const int blocks = (sc.n_all + t.block - 1) / t.block;
-    if (t.use_stream)
-        k_density<true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, need, err);
-    else
-        k_density<false><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, need, err);
+    const int all = (sc.n_all + t.block - 1) / t.block;
+    if (list) {
+        const int blocks = all < 152 * 8 ? all : 152 * 8;
+        if (t.use_stream)
+            k_density<true, true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, list, list_len, err);
+        else
+            k_density<false, true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, list, list_len, err);
+    } else if (t.use_stream) {
+        k_density<true, false><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, nullptr, nullptr, err);
+    } else {
+        k_density<false, false><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, nullptr, nullptr, err);
+    }
     ++*launches;
     return cudaGetLastError();
 }
@@ -132,26 +156,111 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const Scene
 
 // f_ij = m/rho_j [ C_p (p_i + p_j)/2 (1-q)^2/q r_ij - C_v mu (1-q) v_ij ],
 // r_ij = x_i - x_j, v_ij = v_i - v_j; a_i = (1/rho_i) sum_j f_ij (+ g).
-template <int MODE>
+// d = x_j - x_i (float32), r2 its squared norm, ab_j = (m / rho_j, p_j).
+struct PairTerms {
+    float4 pi, vi;
+    float p_i, half_cp_h, cv_mu, inv_h;
+
+    __device__ __forceinline__ void add(float dx, float dy, float dz, float r2, const float4& vj, float2 abj,
+                                        float& fx, float& fy, float& fz) const
+    {
+        const float rinv = rsqrtf(r2);
+        const float q = r2 * rinv * inv_h;
+        const float omq = 1.0f - q;
+        const float m_rho_j = abj.x;
+        // pressure: C_p (p_i+p_j)/2 (1-q)^2 / q along r_ij = -(dx,dy,dz)
+        const float sp = -m_rho_j * half_cp_h * (p_i + abj.y) * omq * omq * rinv;
+        // viscosity: -C_v mu (1-q) (v_i - v_j)
+        const float sv = -m_rho_j * cv_mu * omq;
+        fx = fmaf(sp, dx, sv * (vi.x - vj.x));
+        fy = fmaf(sp, dy, sv * (vi.y - vj.y));
+        fz = fmaf(sp, dz, sv * (vi.z - vj.z));
+    }
+};
+
+// F_b of boid b (section "Boids and Fluid Interaction"): the acceleration
+// of its attached particle from the fluid particles within h.  One warp per
+// boid: the lanes stride over each row of the particle's walk, each keeps
+// its own sum, and a butterfly adds the 32 sums (a fixed order).
+__device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __restrict__ pos,
+                                             const float4* __restrict__ vel, const float* __restrict__ rho,
+                                             const float2* __restrict__ ab, const unsigned* __restrict__ start,
+                                             const Scenes& sc, const int* __restrict__ slot_of_boid,
+                                             const int* __restrict__ bmask, float4* __restrict__ fb,
+                                             float4* __restrict__ acc)
+{
+    const int i = slot_of_boid[b];
+    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+    const int nb_all = sc.nb_all;
+    PairTerms T;
+    T.pi = pos[i];
+    T.vi = vel[i];
+    T.p_i = ab[i].y;
+    T.half_cp_h = c.half_cp_h;
+    T.cv_mu = c.cv_mu;
+    T.inv_h = c.inv_h;
+    const float h2 = c.h2;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    RowWalkT<true> walk(c.g, c.wg, start + c.c_base, T.pi.x, T.pi.y, T.pi.z);
+    unsigned s0, s1;
+    while (walk.next(s0, s1)) {
+        for (unsigned j = s0 + lane; j < s1; j += 32) {
+            const float4 pj = __ldg(pos + j);
+            const float dx = __fsub_rn(pj.x, T.pi.x), dy = __fsub_rn(pj.y, T.pi.y), dz = __fsub_rn(pj.z, T.pi.z);
+            const float r2 = pair_r2(dx, dy, dz);
+            if (r2 < h2 && r2 != 0.0f && id_of(pj) >= nb_all) {
+                float fx, fy, fz;
+                T.add(dx, dy, dz, r2, __ldg(vel + j), __ldg(ab + j), fx, fy, fz);
+                ax += fx;
+                ay += fy;
+                az += fz;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(FULL, ax, o);
+        ay += __shfl_xor_sync(FULL, ay, o);
+        az += __shfl_xor_sync(FULL, az, o);
+    }
+    if (lane == 0) {
+        const float inv_rho = 1.0f / rho[i];
+        const float4 f = make_float4(ax * inv_rho, ay * inv_rho, az * inv_rho, 0.0f);
+        fb[b] = make_float4(f.x, f.y, f.z, bmask ? 1.0f : 0.0f);
+        if (acc) acc[i] = f;
+    }
+}
+
+// The step's force pass.  The first boid_blocks blocks compute F_b, a warp
+// per boid (boid_fb_warp; F_b also goes to acc at the attached slot); they
+// come first in the grid so that these latency-bound warps run alongside
+// the fluid blocks.  The remaining blocks (fluid_blocks of them, possibly
+// none) take a particle per thread: pair forces with touched_by_boid and
+// boid_influence, gravity, Euler-Cromer integration, damped walls and the
+// next step's cell keys; attached particles only record touched = 0 and
+// influence = 0 (attached pairs are excluded).
 __global__ void __launch_bounds__(512)
 k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ rho,
-         const float2* __restrict__ ab, const unsigned* __restrict__ start, const unsigned* __restrict__ bits, const int* __restrict__ ncand,
-         Scenes sc, int use_stream, const int* __restrict__ bmask, float4* __restrict__ acc,
-         int* __restrict__ touched,
-         float4* __restrict__ infl, float4* __restrict__ fb, float4* __restrict__ pos_next,
-         float4* __restrict__ vel_next, unsigned* __restrict__ key, unsigned* __restrict__ rank,
-         unsigned* __restrict__ count, unsigned* __restrict__ err)
+         const float2* __restrict__ ab, const unsigned* __restrict__ start, const unsigned* __restrict__ bits,
+         const int* __restrict__ ncand, Scenes sc, int use_stream, int boid_blocks,
+         const int* __restrict__ slot_of_boid, const int* __restrict__ bmask, float4* __restrict__ fb,
+         float4* __restrict__ acc, int* __restrict__ touched, float4* __restrict__ infl,
+         float4* __restrict__ pos_next, float4* __restrict__ vel_next, unsigned* __restrict__ key,
+         unsigned* __restrict__ rank, unsigned* __restrict__ count, unsigned* __restrict__ err)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int)blockIdx.x < boid_blocks) {
+        const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (b < sc.nb_all && !(bmask && !bmask[b]))  // uniform per warp
+            boid_fb_warp(b, threadIdx.x & 31, pos, vel, rho, ab, start, sc, slot_of_boid, bmask, fb, acc);
+        return;
+    }
+    const int i = (blockIdx.x - boid_blocks) * blockDim.x + threadIdx.x;
     const bool active = i < sc.n_all;
     const int ii = active ? i : 0;
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)ii)];
     const int nb_all = sc.nb_all;
     const float4 pi = pos[ii];
-    const int id_i = id_of(pi);
-    const bool att_i = id_i < nb_all;
-    // MODE 1 computes only the attached particles (threads of the others idle)
-    const bool work = active && (MODE == 0 || (att_i && (!bmask || bmask[id_i])));
+    const bool fluid = active && id_of(pi) >= nb_all;
     const unsigned* cstart = start + c.c_base;
 
     float ax = 0.f, ay = 0.f, az = 0.f;
@@ -159,48 +268,37 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     int touch = 0;
     float rho_i = 1.0f;
     bool clamped = false;
-    if (work) {
-        const float4 vi = __ldg(vel + i);
+    if (fluid) {
+        PairTerms T;
+        T.pi = pi;
+        T.vi = __ldg(vel + i);
         rho_i = __ldg(rho + i);
-        const float p_i = __ldg(ab + i).y;
-        const float half_cp_h = c.half_cp_h, cv_mu = c.cv_mu, inv_h = c.inv_h;
-        // one neighbour j (0 < r2 < h2, not two attached particles)
+        T.p_i = __ldg(ab + i).y;
+        T.half_cp_h = c.half_cp_h;
+        T.cv_mu = c.cv_mu;
+        T.inv_h = c.inv_h;
+        // one neighbour j (0 < r2 < h2)
         auto pair = [&](unsigned j) {
             const float4 pj = __ldg(pos + j);
-            const float dx = __fsub_rn(pj.x, pi.x);
-            const float dy_ = __fsub_rn(pj.y, pi.y);
-            const float dz_ = __fsub_rn(pj.z, pi.z);
-            const float r2 = pair_r2(dx, dy_, dz_);
-            const float4 vj = __ldg(vel + j);
-            const float2 abj = __ldg(ab + j);  // (m / rho_j, p_j)
-            const float p_j = abj.y;
-            const float rinv = rsqrtf(r2);
-            const float q = r2 * rinv * inv_h;
-            const float omq = 1.0f - q;
-            const float m_rho_j = abj.x;
-            // pressure: C_p (p_i+p_j)/2 (1-q)^2 / q along r_ij = -(dx,dy,dz)
-            const float sp = -m_rho_j * half_cp_h * (p_i + p_j) * omq * omq * rinv;
-            // viscosity: -C_v mu (1-q) (v_i - v_j)
-            const float sv = -m_rho_j * cv_mu * omq;
-            const float fx = fmaf(sp, dx, sv * (vi.x - vj.x));
-            const float fy = fmaf(sp, dy_, sv * (vi.y - vj.y));
-            const float fz = fmaf(sp, dz_, sv * (vi.z - vj.z));
+            const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
+            float fx, fy, fz;
+            T.add(dx, dy, dz, pair_r2(dx, dy, dz), __ldg(vel + j), __ldg(ab + j), fx, fy, fz);
             ax += fx;
             ay += fy;
             az += fz;
-            if (MODE == 0 && id_of(pj) < nb_all) {
+            if (id_of(pj) < nb_all) {
                 ++touch;
                 bx += fx;
                 by += fy;
                 bz += fz;
             }
         };
+        RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
+        unsigned s0, s1;
         if (use_stream && ncand[i] <= NBR_WORDS * 32) {
             // decode the density pass's candidate bits, row by row
             int bitpos = 0, wcur = -1;
             unsigned wv = 0;
-            RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
-            unsigned s0, s1;
             while (walk.next(s0, s1)) {
                 unsigned j = s0;
                 while (j < s1) {
@@ -223,9 +321,6 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
                 }
             }
         } else {
-            // no stored stream: test every candidate again (same order)
-            RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
-            unsigned s0, s1;
             // test a chunk of up to 32 candidates into a bit mask, then run
             // the pair code over the set bits: the warp executes the pair
             // code max(hits) times per chunk instead of once per candidate
@@ -238,8 +333,7 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
                         const float4 pj = __ldg(pos + base + k);
                         const float r2 =
                             pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
-                        const bool take = r2 < h2 && r2 != 0.0f && !(att_i && id_of(pj) < nb_all);
-                        m |= (unsigned)take << k;
+                        m |= (unsigned)(r2 < h2 && r2 != 0.0f) << k;
                     }
                     while (m) {
                         const int t = __ffs(m) - 1;
@@ -255,28 +349,16 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     ay *= inv_rho;
     az *= inv_rho;
 
-    if (MODE == 1) {
-        if (work) fb[id_i] = make_float4(ax, ay, az, bmask ? 1.0f : 0.0f);
-        return;
-    }
-
-    // ---- MODE 0: record, integrate, emit the next step's keys
-    bool fluid = active && !att_i;
     unsigned k_next = 0;
     if (active) {
-        if (att_i) {
-            fb[id_i] = make_float4(ax, ay, az, 0.0f);
-            acc[i] = make_float4(ax, ay, az, 0.0f);
-        } else {
-            ax += c.grav[0];
-            ay += c.grav[1];
-            az += c.grav[2];
-            acc[i] = make_float4(ax, ay, az, 0.0f);
-        }
         touched[i] = touch;
         infl[i] = make_float4(bx * inv_rho, by * inv_rho, bz * inv_rho, 0.0f);
     }
     if (fluid) {
+        ax += c.grav[0];
+        ay += c.grav[1];
+        az += c.grav[2];
+        acc[i] = make_float4(ax, ay, az, 0.0f);
         const float4 vi = __ldg(vel + i);
         float v[3] = {fmaf(ax, c.dt, vi.x), fmaf(ay, c.dt, vi.y), fmaf(az, c.dt, vi.z)};
         float x[3] = {fmaf(v[0], c.dt, pi.x), fmaf(v[1], c.dt, pi.y), fmaf(v[2], c.dt, pi.z)};
@@ -305,20 +387,20 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     if (__any_sync(FULL, clamped) && (threadIdx.x & 31) == 0) atomicOr(err, SPH_DEV_CLAMPED);
 }
 
-cudaError_t launch_forces(int mode, const float4* pos, const float4* vel, const float* rho, const float2* ab,
+cudaError_t launch_forces(const float4* pos, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
-                          const Tuning& t, const int* bmask, float4* acc, int* touched, float4* infl, float4* fb,
-                          float4* pos_next, float4* vel_next, unsigned* key, unsigned* rank, unsigned* count,
-                          unsigned* err, cudaStream_t s, long long* launches)
+                          const Tuning& t, bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
+                          float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
+                          unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
+                          long long* launches)
 {
-    if (sc.n_all <= 0) return cudaSuccess;
-    const int blocks = (sc.n_all + t.block - 1) / t.block;
-    if (mode == 0)
-        k_forces<0><<<blocks, t.block, 0, s>>>(pos, vel, rho, ab, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
-                                               infl, fb, pos_next, vel_next, key, rank, count, err);
-    else
-        k_forces<1><<<blocks, t.block, 0, s>>>(pos, vel, rho, ab, start, bits, ncand, sc, t.use_stream, bmask, acc, touched,
-                                               infl, fb, pos_next, vel_next, key, rank, count, err);
+    const int warps = t.block / 32;
+    const int boid_blocks = (sc.nb_all + warps - 1) / warps;
+    const int fluid_blocks = fluid ? (sc.n_all + t.block - 1) / t.block : 0;
+    if (boid_blocks + fluid_blocks == 0) return cudaSuccess;
+    k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(pos, vel, rho, ab, start, bits, ncand, sc, t.use_stream,
+                                                            boid_blocks, slot_of_boid, bmask, fb, acc, touched, infl,
+                                                            pos_next, vel_next, key, rank, count, err);
     ++*launches;
     return cudaGetLastError();
 }
