@@ -65,7 +65,8 @@ BYTES_PER_CELL_SCAN = 12
 
 # DRAM traffic of the force pass from one ncu capture (bytes per launch) and
 # the sha256 of the kernel source it was taken on; null once the source moved.
-FORCES_TRAFFIC = None  # {"bytes": ..., "source_sha256": ...}
+FORCES_TRAFFIC = {"bytes": 99560960 + 115067392, "source_sha256": "c9132a0abaa407e7f58b8200e0da60a3bcbf34e3cfd35b715d65b94c97389ca9",
+                  "capture": "ncu, 2,097,152-particle tank released unsettled (bench.py --settle 0)"}
 
 
 def _args():
@@ -84,6 +85,9 @@ def _args():
     ap.add_argument("--batch-steps", type=int, default=30, help="timed steps of the batched-scenes leg")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--mlp-throughput", action="store_true",
+                    help="only time the surrogate network's forward pass on 65,536 queries (features of "
+                         "the 262,144-particle column's 1,024 boids, tiled), untrained weights")
     ap.add_argument("--settle", type=int, default=None,
                     help="settling steps of the large tank before the boids are released (default 200)")
     return ap.parse_args()
@@ -353,6 +357,40 @@ def run_surrogate(a, dev):
     return out
 
 
+def run_mlp_throughput(a):
+    """Forward passes of the surrogate network on 65,536 feature rows (the
+    1,024 boid rows of a column state, tiled 64 times): queries per second
+    and the tensor rate of the four layers, per CUDA events."""
+    import torch
+
+    from paper_2311_15088_gb300 import surrogate
+    from paper_2311_15088_gb300.sph import Mlp, Scene
+
+    sc = scenes.dam_break_column(seed_offset=140)
+    p = _params(sc)
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    s.step(3)
+    X = s.features().repeat(64, 1).contiguous()
+    m = Mlp(X.shape[0])
+    m.set_params(torch.from_numpy(surrogate.init_params(0)))
+    for _ in range(max(a.warmup, 3)):
+        m.forward(X)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        m.forward(X)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    flops = 2.0 * X.shape[0] * (272 * 256 + 256 * 256 * 2 + 256 * 16)
+    print(json.dumps({"metric": "surrogate MLP forward, queries/s", "value": X.shape[0] / (ms * 1e-3),
+                      "unit": "queries/s", "ms_per_batch": ms, "batch": int(X.shape[0]), "steps": a.steps,
+                      "tflops": flops / (ms * 1e-3) / 1e12, "status": m.status()}), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- arms
 
 def run_reference(a):
@@ -565,6 +603,8 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.mlp_throughput:
+        return run_mlp_throughput(a)
     return run_ours(a)
 
 

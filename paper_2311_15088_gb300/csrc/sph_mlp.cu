@@ -175,7 +175,7 @@ struct GemmSmem {
 // timeout the kernel records SPH_DEV_TIMEOUT, lets its own copies land,
 // frees its tensor memory and returns.
 template <int NT, int EPI, int STAGES>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
 k_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, GemmEpi e)
 {
     using L = GemmSmem<NT, STAGES>;
@@ -298,7 +298,10 @@ template <int NT, int EPI>
 static cudaError_t launch_gemm_t(const CUtensorMap& ma, const CUtensorMap& mb, const GemmEpi& e, int splits,
                                  cudaStream_t s)
 {
-    constexpr int STAGES = NT >= 256 ? 4 : 6;
+    // 128-wide tiles with a short K (the layers): 3 stages (96 KB) so that two
+    // CTAs share an SM and one's epilogue overlaps the other's main loop;
+    // the weight-gradient products (long K over the batch) keep a deeper ring
+    constexpr int STAGES = NT >= 256 ? 4 : (NT >= 128 ? (EPI == EPI_F32 ? 6 : 3) : 6);
     using L = GemmSmem<NT, STAGES>;
     static bool attr = false;
     if (!attr) {
