@@ -85,6 +85,9 @@ def _args():
     ap.add_argument("--batch-steps", type=int, default=30, help="timed steps of the batched-scenes leg")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--neighbor-lists", action="store_true",
+                    help="build neighbour lists every step (pair buffer of 3x the pairs after warm-up) "
+                         "and read them in the force pass instead of testing candidates")
     ap.add_argument("--mlp-throughput", action="store_true",
                     help="only time the surrogate network's forward pass on 65,536 queries (features of "
                          "the 262,144-particle column's 1,024 boids, tiled), untrained weights")
@@ -184,6 +187,38 @@ def _work_snapshot(s):
 
 def _source_sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+# ------------------------------------------------------- neighbour search
+
+def _neighbor_search(s, dev):
+    """Neighbour counts of the current state by the exact walk and by the
+    fixed-capacity hash grid (buckets of twice the most crowded cell of the
+    previous binning, and of 16 entries): times (binning included, CUDA
+    events) and the fraction of neighbour pairs the 16-entry buckets lose."""
+    import torch
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1), out
+
+    s.step(1)  # (the end-to-end leg's host downloads staged through the step's scratch)
+    occupancy = int(torch.diff(s.field("cell_start").to(torch.int64)).max().item())  # of that step's binning
+    ms_walk, (exact, _, _) = timed(lambda: s.neighbors(lists=False))
+    ms_full, (full, dropped_full) = timed(lambda: s.bucket_neighbors(2 * occupancy))
+    ms_16, (c16, dropped) = timed(lambda: s.bucket_neighbors(16))
+    pairs = float(exact.to(torch.float64).sum().item())
+    return {"walk_ms": ms_walk, "bucket_ms": ms_full, "bucket_capacity": 2 * occupancy,
+            "bucket_dropped_particles": int(dropped_full.item()),
+            "bucket_equals_walk": bool(torch.equal(full, exact)),
+            "bucket16_ms": ms_16, "bucket16_dropped_particles": int(dropped.item()),
+            "bucket16_lost_pair_fraction": 1.0 - float(c16.to(torch.float64).sum().item()) / max(pairs, 1.0)}
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -457,6 +492,8 @@ def run_ours(a):
         s.step(1)
     torch.cuda.synchronize(dev)
     work0 = _work_snapshot(s)
+    if a.neighbor_lists:
+        s.set_neighbor_lists(3 * work0["pairs"])
     start_state = [t.clone() for t in s.get_state()]  # the e2e leg restarts from here
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -572,6 +609,7 @@ def run_ours(a):
                                                             min_seconds=a.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
 
+    nsearch = _neighbor_search(s, dev)
     batched = None if a.no_batch else run_batched(a, dev, flush)
     sur = None if a.no_surrogate else run_surrogate(a, dev)
 
@@ -585,11 +623,13 @@ def run_ours(a):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "cell_size_over_h": float(np.float32(p["cell_size"]) / np.float32(p["h"])),
                        "tuning": {"block": s.tuning[0], "use_stream": s.tuning[1]},
+                       "force_pass_neighbours": "pair lists" if a.neighbor_lists else "walk",
                        "neighbours_mean": statistics.mean(w["nbr_mean"] for w in works),
                        "neighbours_max": max(w["nbr_max"] for w in works),
                        "candidates_per_particle": cand / n_all},
             "roofline": roofline, "hbm": hbm, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "device_status": status, "batched": batched,
+            "gpu_launches": launches, "clocks": clk, "device_status": status, "neighbor_search": nsearch,
+            "batched": batched,
             "surrogate": sur,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
         }

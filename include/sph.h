@@ -60,6 +60,7 @@ extern "C" {
 #define SPH_DEV_NONFINITE 1u  /* a density, position or velocity became NaN/Inf  */
 #define SPH_DEV_CLAMPED   2u  /* a position lay outside the grid and was clamped */
 #define SPH_DEV_TIMEOUT   4u  /* a bounded wait inside a kernel gave up          */
+#define SPH_DEV_LIST_OVERFLOW 8u /* a neighbour list did not fit the pair buffer  */
 
 /* Fields that sph_get_fields can return (one per call). */
 #define SPH_FIELD_RHO         0  /* float[n_tot]   density, by particle id                 */
@@ -256,6 +257,22 @@ int sph_set_surrogate(sph_handle* h, sph_mlp* m, float f_scale, float log_err_ma
 int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* stream);
 
 /*
+ * The fixed-capacity hash grid of section "Neighborhood Search", as an
+ * ablation of the exact search: every particle appends its index to its
+ * cell's bucket through an atomic counter, a bucket keeps at most
+ * `capacity` indices and drops the rest, and each particle counts its
+ * neighbours (the exclusions of sph_debug_neighbors) over the cells within
+ * ceil(h / cell_size) of its own.  counts: device int per particle id
+ * (n_fluid + n_boid); *dropped (device, 8-byte aligned): the particles the
+ * buckets lost; scratch: device, 4-byte aligned, at least
+ * ncells * (1 + capacity) * 4 bytes.  Equal to sph_debug_neighbors' counts
+ * when no cell holds more than `capacity` particles; test hook, not part of
+ * the step.  Errors: SPH_ERR_ARG, SPH_ERR_STATE, SPH_ERR_CUDA.
+ */
+int sph_debug_bucket_neighbors(sph_handle* h, void* scratch, size_t bytes, int capacity, int* counts,
+                               unsigned long long* dropped, void* stream);
+
+/*
  * Test hook: bin the CURRENT state and write every particle's neighbour
  * list, N(i) = { j != i : not both attached, r_ij^2 < h^2 } with the float32
  * predicate, in the order the 27-cell walk visits them (cells dz, dy, dx
@@ -301,9 +318,28 @@ long long sph_launch_count(sph_handle* h);
 #define SPH_KIND_FORCES     5
 #define SPH_KIND_BOID_BIN   6
 #define SPH_KIND_BOID_RULES 7
-#define SPH_NUM_KINDS       8
+#define SPH_KIND_LISTS      8  /* neighbour lists: offsets scan + fill (when set) */
+#define SPH_NUM_KINDS       9
 int sph_profile_enable(sph_handle* h, int max_passes);
 int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds);
+
+/*
+ * Neighbour lists, an alternative to testing candidates in the force pass
+ * (the list-building neighbour search of section "Neighborhood Search";
+ * an ablation of the walk).  With a pair buffer set, every sph_step scans
+ * the density pass's neighbour counts into per-particle offsets, writes
+ * each particle's neighbours (fluid particles: every particle within h but
+ * itself; attached particles: the fluid ones), in walk order, into the
+ * buffer, and the force pass reads a fluid particle's list instead of
+ * testing its candidates: results are bit-identical to the walk.
+ * pair_buffer: device memory, 4-byte aligned, bytes / 4 entries (one per
+ * ordered neighbour pair, i.e. the sum of the neighbour counts is needed).
+ * A particle whose list would end beyond the buffer tests its candidates as
+ * without lists and sets SPH_DEV_LIST_OVERFLOW.  NULL (or bytes < 4) turns
+ * the lists off (the default).  The buffer stays the caller's and must
+ * outlive its use.  Errors: SPH_ERR_ARG.
+ */
+int sph_set_neighbor_lists(sph_handle* h, void* pair_buffer, size_t bytes);
 
 /* Free the host-side handle (the workspace stays the caller's). */
 void sph_destroy(sph_handle* h);

@@ -54,7 +54,11 @@ struct sph_handle {
     float* yout;              // [nb_pad][SPH_MLP_OUT]
     unsigned char* need;
     int* need_list;     // compacted slots whose density a boid force needs
-    unsigned* need_len;      // per sorted slot
+    unsigned* need_len;
+    unsigned* noff;        // neighbour-list offsets (n + 1) and scan partials
+    unsigned* noff_part;
+    unsigned* list;        // the caller's pair buffer (NULL: no lists)
+    size_t list_cap;      // per sorted slot
     int* bflag;               // per boid
     int nb_pad;
     sph_mlp* mlp;
@@ -300,6 +304,8 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->need = cv.take<unsigned char>(n);
     h->need_list = cv.take<int>(n);
     h->need_len = cv.take<unsigned>(1);
+    h->noff = cv.take<unsigned>(n + 1);
+    h->noff_part = cv.take<unsigned>((size_t)scan_parts((int)n) + 1);
     h->bflag = cv.take<int>(nb);
     return (size_t)((cv.off + 255) & ~(uintptr_t)255);
 }
@@ -565,6 +571,24 @@ static void prof_free(sph_handle* h)
     h->prof_cap = h->prof_n = 0;
 }
 
+int sph_set_neighbor_lists(sph_handle* h, void* pair_buffer, size_t bytes)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (pair_buffer && ((uintptr_t)pair_buffer & 3)) return fail(h, SPH_ERR_ARG, "pair buffer must be 4-byte aligned");
+    if (!pair_buffer || bytes < 4) {
+        h->list = nullptr;
+        h->list_cap = 0;
+    } else {
+        h->list = (unsigned*)pair_buffer;
+        h->list_cap = bytes / 4;
+    }
+    if (h->graph) {  // the captured step no longer matches
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return SPH_OK;
+}
+
 void sph_destroy(sph_handle* h)
 {
     if (!h) return;
@@ -742,10 +766,18 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
     CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, nullptr,
                                nullptr, h->err, s, &h->launches));
     prof_end(h, s);
+    if (h->list) {
+        prof_begin(h, SPH_KIND_LISTS, s);
+        CUDA_TRY(h, launch_scan((const unsigned*)h->nbr, h->n, h->noff_part, h->noff, s, &h->launches));
+        CUDA_TRY(h, launch_fill_lists(h->pos_s, h->cell_start, h->sc, h->noff, h->list, h->list_cap, h->err, s,
+                                      &h->launches));
+        prof_end(h, s);
+    }
     prof_begin(h, SPH_KIND_FORCES, s);
     CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                              true, h->slot_of_boid, nullptr, h->fb, h->acc, h->touched, h->infl, h->pos, h->vel,
-                              h->key, h->rank, h->count, h->err, s, &h->launches));
+                              h->list, h->noff, h->list_cap, true, h->slot_of_boid, nullptr, h->fb, h->acc,
+                              h->touched, h->infl, h->pos, h->vel, h->key, h->rank, h->count, h->err, s,
+                              &h->launches));
     prof_end(h, s);
     if (h->n_boid > 0) {
         prof_begin(h, SPH_KIND_BOID_BIN, s);
@@ -872,7 +904,7 @@ static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_
     CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
                                h->need_list, h->need_len, h->err, s, &h->launches));
     CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                              false, h->slot_of_boid, bmask, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, 0, false, h->slot_of_boid, bmask, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                               nullptr, nullptr, h->err, s, &h->launches));
     return SPH_OK;
 }
@@ -896,7 +928,7 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
         CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
                                    nullptr, nullptr, h->err, s, &h->launches));
         CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                                  false, h->slot_of_boid, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  nullptr, nullptr, 0, false, h->slot_of_boid, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
                                   nullptr, nullptr, nullptr, h->err, s, &h->launches));
         return SPH_OK;
     }
@@ -909,6 +941,26 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
     CUDA_TRY(h, launch_surrogate_out(h->yout, h->n_boid, h->f_scale, h->log_err_max, out, h->bflag, h->err + 1, s,
                                      &h->launches));
     if (mode == SPH_BOID_SURROGATE_FALLBACK) return exact_local(h, h->bflag, out, s);
+    return SPH_OK;
+}
+
+int sph_debug_bucket_neighbors(sph_handle* h, void* scratch, size_t bytes, int capacity, int* counts,
+                               unsigned long long* dropped, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (!scratch || !counts || !dropped || capacity < 1) return fail(h, SPH_ERR_ARG, "bad arguments");
+    if (((uintptr_t)scratch & 3) || ((uintptr_t)dropped & 7)) return fail(h, SPH_ERR_ARG, "misaligned buffers");
+    const size_t need = (size_t)h->ncells * (1 + (size_t)capacity) * sizeof(unsigned);
+    if (bytes < need) return fail(h, SPH_ERR_ARG, "scratch too small: %zu < %zu bytes", bytes, need);
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    int rc = bin_state(h, s, false);
+    if (rc != SPH_OK) return rc;
+    unsigned* tracker = (unsigned*)scratch;
+    CUDA_TRY(h, launch_bucket_neighbors(h->pos_s, h->cell_start, h->sc, tracker, (int)h->ncells, tracker + h->ncells,
+                                        capacity, counts, dropped, s, &h->launches));
+    h->has_step = false;
     return SPH_OK;
 }
 

@@ -277,10 +277,22 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const Scene
 // (attached particles get touched = 0, influence = 0).  One launch.
 cudaError_t launch_forces(const float4* pos, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
-                          const Tuning& t, bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
+                          const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
+                          bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
                           float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
                           unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
                           long long* launches);
+// Neighbour lists of every particle at off[i] (exclusive scan of the
+// density pass's counts), in walk order; lists ending beyond cap are
+// skipped and flagged SPH_DEV_LIST_OVERFLOW.
+cudaError_t launch_fill_lists(const float4* pos, const unsigned* start, const Scenes& sc, const unsigned* off,
+                              unsigned* list, size_t cap, unsigned* err, cudaStream_t s, long long* launches);
+// The lossy fixed-capacity hash grid (ablation): neighbour counts per slot
+// through buckets of cap entries per cell; *dropped = entries lost.
+// tracker: ncells counters; buckets: ncells * cap entries.
+cudaError_t launch_bucket_neighbors(const float4* pos, const unsigned* start, const Scenes& sc, unsigned* tracker,
+                                    int ncells, unsigned* buckets, int cap, int* counts, unsigned long long* dropped,
+                                    cudaStream_t s, long long* launches);
 cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const Scenes& sc, int* counts,
                                  const long long* offsets, int* list, cudaStream_t s, long long* launches);
 

@@ -242,7 +242,8 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
 __global__ void __launch_bounds__(512)
 k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ rho,
          const float2* __restrict__ ab, const unsigned* __restrict__ start, const unsigned* __restrict__ bits,
-         const int* __restrict__ ncand, Scenes sc, int use_stream, int boid_blocks,
+         const int* __restrict__ ncand, Scenes sc, int use_stream, const unsigned* __restrict__ list,
+         const unsigned* __restrict__ list_off, unsigned list_cap, int boid_blocks,
          const int* __restrict__ slot_of_boid, const int* __restrict__ bmask, float4* __restrict__ fb,
          float4* __restrict__ acc, int* __restrict__ touched, float4* __restrict__ infl,
          float4* __restrict__ pos_next, float4* __restrict__ vel_next, unsigned* __restrict__ key,
@@ -295,7 +296,19 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
         };
         RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
         unsigned s0, s1;
-        if (use_stream && ncand[i] <= NBR_WORDS * 32) {
+        unsigned o0 = 0, o1 = 0;
+        if (list) {
+            o0 = __ldg(list_off + i);
+            o1 = __ldg(list_off + i + 1);
+        }
+        if (list && o1 <= list_cap) {
+            // the neighbour list, in walk order (coincident particles skipped)
+            for (unsigned k = o0; k < o1; ++k) {
+                const unsigned j = __ldg(list + k);
+                const float4 pj = __ldg(pos + j);
+                if (pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z)) != 0.0f) pair(j);
+            }
+        } else if (use_stream && ncand[i] <= NBR_WORDS * 32) {
             // decode the density pass's candidate bits, row by row
             int bitpos = 0, wcur = -1;
             unsigned wv = 0;
@@ -389,19 +402,149 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
 
 cudaError_t launch_forces(const float4* pos, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
-                          const Tuning& t, bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
+                          const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
+                          bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
                           float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
                           unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
                           long long* launches)
 {
+    const unsigned cap = list_cap > 0xffffffffu ? 0xffffffffu : (unsigned)list_cap;
     const int warps = t.block / 32;
     const int boid_blocks = (sc.nb_all + warps - 1) / warps;
     const int fluid_blocks = fluid ? (sc.n_all + t.block - 1) / t.block : 0;
     if (boid_blocks + fluid_blocks == 0) return cudaSuccess;
     k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(pos, vel, rho, ab, start, bits, ncand, sc, t.use_stream,
-                                                            boid_blocks, slot_of_boid, bmask, fb, acc, touched, infl,
-                                                            pos_next, vel_next, key, rank, count, err);
+                                                            list, list_off, cap, boid_blocks, slot_of_boid, bmask,
+                                                            fb, acc, touched, infl, pos_next, vel_next, key, rank,
+                                                            count, err);
     ++*launches;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- pair lists
+
+// list[off[i] ..] = the neighbours of particle i in walk order: every j != i
+// with r2 < h2, except attached j for attached i (the density pass counted
+// exactly these: off is the exclusive scan of its counts).  A list that
+// would end beyond cap is not written (the force pass walks instead).
+__global__ void __launch_bounds__(256)
+k_fill_lists(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
+             const unsigned* __restrict__ off, unsigned* __restrict__ list, size_t cap, unsigned* __restrict__ err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < sc.n_all;
+    bool over = false;
+    if (active) {
+        const unsigned o0 = off[i], o1 = off[i + 1];
+        over = o1 > cap;
+        if (!over && o1 > o0) {
+            const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+            const int nb_all = sc.nb_all;
+            const float4 pi = pos[i];
+            const bool att_i = id_of(pi) < nb_all;
+            unsigned k = o0;
+            RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+            unsigned s0, s1;
+            while (walk.next(s0, s1)) {
+                for (unsigned j = s0; j < s1; ++j) {
+                    if (j == (unsigned)i) continue;
+                    const float4 pj = __ldg(pos + j);
+                    if (att_i && id_of(pj) < nb_all) continue;
+                    const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+                    if (r2 < c.h2 && k < o1) list[k++] = j;
+                }
+            }
+        }
+    }
+    if (__any_sync(FULL, over) && (threadIdx.x & 31) == 0) atomicOr(err, SPH_DEV_LIST_OVERFLOW);
+}
+
+cudaError_t launch_fill_lists(const float4* pos, const unsigned* start, const Scenes& sc, const unsigned* off,
+                              unsigned* list, size_t cap, unsigned* err, cudaStream_t s, long long* launches)
+{
+    if (sc.n_all <= 0) return cudaSuccess;
+    k_fill_lists<<<(sc.n_all + 255) / 256, 256, 0, s>>>(pos, start, sc, off, list, cap, err);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------- fixed-capacity hash grid
+
+// The hash grid of section "Neighborhood Search": every particle appends
+// its index to its cell's bucket through an atomic per-cell counter; a
+// bucket holds at most cap indices and the particles beyond are dropped
+// (the grid is lossy where cells are crowded).  Slots of the sorted state;
+// the order inside a bucket is the order of the atomics.
+__global__ void __launch_bounds__(256)
+k_bucket_insert(const float4* __restrict__ pos, Scenes sc, unsigned* __restrict__ tracker,
+                unsigned* __restrict__ buckets, int cap)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n_all) return;
+    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+    const float4 p = pos[i];
+    bool cl = false;
+    const unsigned key = (unsigned)c.c_base + cell_key(c.g, p.x, p.y, p.z, &cl);
+    const unsigned slot = atomicAdd(tracker + key, 1u);
+    if (slot < (unsigned)cap) buckets[(size_t)key * cap + slot] = (unsigned)i;
+}
+
+// Neighbour count of every particle (by id) through the buckets: the cells within
+// ceil(h / d) of its own (the 27 cells at d = h), min(count, cap) entries
+// each, the predicate and exclusions of the density pass (j != i, no pair
+// of attached particles).  dropped += the entries the buckets lost.
+__global__ void __launch_bounds__(256)
+k_bucket_count(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
+               const unsigned* __restrict__ tracker, const unsigned* __restrict__ buckets, int cap,
+               int* __restrict__ counts, unsigned long long* __restrict__ dropped)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n_all) return;
+    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+    const float4 pi = pos[i];
+    const bool att_i = id_of(pi) < sc.nb_all;
+    bool cl = false;
+    const int cx = cell_coord(pi.x, c.g.minf[0], c.g.inv_d, c.g.dim[0], &cl);
+    const int cy = cell_coord(pi.y, c.g.minf[1], c.g.inv_d, c.g.dim[1], &cl);
+    const int cz = cell_coord(pi.z, c.g.minf[2], c.g.inv_d, c.g.dim[2], &cl);
+    const int R = (int)ceilf(c.h * c.g.inv_d);
+    int n = 0;
+    for (int z = max(cz - R, 0); z <= min(cz + R, c.g.dim[2] - 1); ++z)
+        for (int y = max(cy - R, 0); y <= min(cy + R, c.g.dim[1] - 1); ++y)
+            for (int x = max(cx - R, 0); x <= min(cx + R, c.g.dim[0] - 1); ++x) {
+                const unsigned key = (unsigned)c.c_base + (unsigned)x +
+                                     (unsigned)c.g.dim[0] * ((unsigned)y + (unsigned)c.g.dim[1] * (unsigned)z);
+                const unsigned m = min(__ldg(tracker + key), (unsigned)cap);
+                for (unsigned k = 0; k < m; ++k) {
+                    const unsigned j = __ldg(buckets + (size_t)key * cap + k);
+                    if (j == (unsigned)i) continue;
+                    const float4 pj = __ldg(pos + j);
+                    if (att_i && id_of(pj) < sc.nb_all) continue;
+                    if (pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z)) < c.h2) ++n;
+                }
+            }
+    counts[id_of(pi)] = n;
+    // the first slot of each cell (sorted order) reports what the cell lost
+    const unsigned own = (unsigned)c.c_base + (unsigned)cx +
+                         (unsigned)c.g.dim[0] * ((unsigned)cy + (unsigned)c.g.dim[1] * (unsigned)cz);
+    const unsigned t = tracker[own];
+    if (t > (unsigned)cap && (unsigned)i == __ldg(start + own))
+        atomicAdd(dropped, (unsigned long long)(t - (unsigned)cap));
+}
+
+cudaError_t launch_bucket_neighbors(const float4* pos, const unsigned* start, const Scenes& sc, unsigned* tracker,
+                                    int ncells,
+                                    unsigned* buckets, int cap, int* counts, unsigned long long* dropped,
+                                    cudaStream_t s, long long* launches)
+{
+    if (sc.n_all <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(tracker, 0, (size_t)ncells * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dropped, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (sc.n_all + 255) / 256;
+    k_bucket_insert<<<blocks, 256, 0, s>>>(pos, sc, tracker, buckets, cap);
+    k_bucket_count<<<blocks, 256, 0, s>>>(pos, start, sc, tracker, buckets, cap, counts, dropped);
+    *launches += 2;
     return cudaGetLastError();
 }
 

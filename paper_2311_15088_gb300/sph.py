@@ -72,6 +72,8 @@ _sig = {
     "sph_batch_workspace_size": (_i, [_P, _vp, _vp, _i, ctypes.POINTER(_sz)]),
     "sph_batch_create": (_i, [_P, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_vp)]),
     "sph_set_tuning": (_i, [_vp, _i, _i]),
+    "sph_set_neighbor_lists": (_i, [_vp, _vp, ctypes.c_size_t]),
+    "sph_debug_bucket_neighbors": (_i, [_vp, _vp, ctypes.c_size_t, _i, _vp, _vp, _vp]),
     "sph_graph_step": (_i, [_vp, _i, _vp]),
     "sph_mlp_workspace_size": (_i, [_i, ctypes.POINTER(_sz)]),
     "sph_mlp_create": (_i, [_i, _vp, _sz, ctypes.POINTER(_vp)]),
@@ -182,6 +184,14 @@ def sph_set_tuning(h, block: int, use_stream: int):
     _check(_lib.sph_set_tuning(h, block, use_stream), h)
 
 
+def sph_set_neighbor_lists(h, pair_buffer_ptr, nbytes: int):
+    _check(_lib.sph_set_neighbor_lists(h, pair_buffer_ptr, nbytes), h)
+
+
+def sph_debug_bucket_neighbors(h, scratch_ptr, nbytes: int, capacity: int, counts_ptr, dropped_ptr, stream: int):
+    _check(_lib.sph_debug_bucket_neighbors(h, scratch_ptr, nbytes, capacity, counts_ptr, dropped_ptr, stream), h)
+
+
 def sph_graph_step(h, nsteps: int, stream: int):
     _check(_lib.sph_graph_step(h, nsteps, stream), h)
 
@@ -240,7 +250,7 @@ def sph_destroy(h):
     _lib.sph_destroy(h)
 
 
-KINDS = ("keys", "scan", "scatter", "sort", "density", "forces", "boid_bin", "boid_rules")
+KINDS = ("keys", "scan", "scatter", "sort", "density", "forces", "boid_bin", "boid_rules", "lists")
 
 
 def sph_profile_enable(h, max_passes: int):
@@ -474,6 +484,27 @@ class Scene:
     def graph_step(self, nsteps: int = 1):
         """sph_step replayed from a captured CUDA graph (non-default stream)."""
         sph_graph_step(self.handle, nsteps, self.stream)
+
+    def set_neighbor_lists(self, max_pairs: int):
+        """Keep a device pair buffer of max_pairs entries and build neighbour
+        lists every step (0 turns them off)."""
+        if max_pairs > 0:
+            self.pair_buffer = self.torch.empty(int(max_pairs), dtype=self.torch.int32, device=self.device)
+            sph_set_neighbor_lists(self.handle, self.pair_buffer.data_ptr(), 4 * int(max_pairs))
+        else:
+            sph_set_neighbor_lists(self.handle, None, 0)
+            self.pair_buffer = None
+
+    def bucket_neighbors(self, capacity: int):
+        """Neighbour counts by particle id through the lossy fixed-capacity
+        hash grid, and the number of particles its buckets dropped."""
+        t = self.torch
+        scratch = t.empty(self.ncells * (1 + capacity), dtype=t.int32, device=self.device)
+        counts = t.empty(self.n, dtype=t.int32, device=self.device)
+        dropped = t.zeros(1, dtype=t.int64, device=self.device)
+        sph_debug_bucket_neighbors(self.handle, scratch.data_ptr(), 4 * scratch.numel(), capacity,
+                                   counts.data_ptr(), dropped.data_ptr(), self.stream)
+        return counts, dropped
 
     def set_tuning(self, block: int, use_stream: int):
         sph_set_tuning(self.handle, block, use_stream)

@@ -187,13 +187,14 @@ def evaluate(mlp: Mlp, X, F, f_scale: float, threshold: float) -> dict:
     }
 
 
-def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=60, batch=8192, lr=2e-3,
-                    device="cuda", target=0.05, seed=0, head_epochs=10, zero_cols=None, pairs=None,
+def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=120, batch=2048, lr=1e-3,
+                    device="cuda", target=0.045, seed=0, head_epochs=10, zero_cols=None, pairs=None,
                     return_pairs=False):
     """Log training pairs (one run of ``steps`` steps per training seed of
     make_scene) and held-out pairs (validation seeds), train the network,
     fit the error head and calibrate the fallback threshold for an
-    aggregate error <= target.  ``zero_cols`` (a slice) blanks feature
+    aggregate error <= target on the validation pairs (4.5 % by default: a
+    margin under the 5 % goal for queries the calibration has not seen).  ``zero_cols`` (a slice) blanks feature
     columns in every pair (an ablation; such a network is for Python-side
     evaluation only, since the library's features fill them).  ``pairs``
     reuses logged (X, F, Xv, Fv).  Returns (mlp, info), plus the pairs when

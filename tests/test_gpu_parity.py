@@ -231,3 +231,51 @@ def test_candidate_counts_cover_neighbours(cell):
     nc = s.field("ncand").cpu().numpy().astype(np.int64)
     nbr = s.field("nbr_count").cpu().numpy().astype(np.int64)
     assert np.all(nc >= nbr + 1)
+
+
+@pytest.mark.parametrize("cap", ["ample", "tiny"])
+def test_neighbor_lists_bitwise_equal_to_walk(cap):
+    """With pair lists the force pass reads each particle's neighbours from
+    its list (walk order) instead of testing candidates: 20 steps give the
+    walk's bits.  A pair buffer too small for the lists makes the particles
+    that do not fit walk instead, flagged SPH_DEV_LIST_OVERFLOW (8)."""
+    sc = scenes.scaled_block(12000, 300, (0.6, 0.6, 0.6), (0.6, 0.4, 0.6), seed=77)
+    sc["boid_pos"][:, 1] *= np.float32(0.4 / 0.6)
+    p = sc["params"]
+    a = run_gpu(p, sc, steps=20)
+    b = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    b.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    b.step(1)
+    pairs = int(b.field("nbr_count").cpu().numpy().astype(np.int64).sum())
+    b.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    b.set_neighbor_lists(3 * pairs if cap == "ample" else pairs // 3)
+    b.step(20)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert torch.equal(x, y)
+    assert torch.equal(a.field("acc"), b.field("acc"))
+    overflow = b.status() & 8
+    assert (overflow == 0) if cap == "ample" else (overflow != 0)
+
+
+@pytest.mark.parametrize("cell", [1.0, 0.5])
+def test_bucket_grid_ablation(cell):
+    """The paper's fixed-capacity hash grid: with buckets as large as the
+    most crowded cell its neighbour counts are the exact ones; with smaller
+    buckets it drops particles and never finds more neighbours than exist."""
+    sc = scenes.scaled_block(12000, 300, (0.6, 0.6, 0.6), (0.6, 0.4, 0.6), seed=77)
+    sc["boid_pos"][:, 1] *= np.float32(0.4 / 0.6)
+    p = dict(sc["params"], cell_size=scenes.f32(sc["params"]["h"] * cell))
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    exact, _, _ = s.neighbors()
+    exact = exact.cpu().numpy()
+    s.step(1)
+    occupancy = int(np.diff(s.field("cell_start").cpu().numpy().astype(np.int64)).max())
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    counts, dropped = s.bucket_neighbors(occupancy)
+    assert np.array_equal(counts.cpu().numpy(), exact) and int(dropped.item()) == 0
+    small = max(1, occupancy // 3)
+    counts, dropped = s.bucket_neighbors(small)
+    c = counts.cpu().numpy()
+    assert int(dropped.item()) > 0
+    assert np.all(c <= exact) and c.sum() < exact.sum()
