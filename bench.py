@@ -336,13 +336,57 @@ def run_batched(a, dev, flush):
 
 # ----------------------------------------------------------- surrogate
 
-def run_surrogate(a, dev):
+def _time_modes(s, modes, n_states, warmup):
+    """Per mode: summed ms of sph_boid_forces over n_states states (one
+    step between states), the forces and the fallback flags."""
+    import torch
+
+    ms = {k: 0.0 for k in modes}
+    got = {k: [] for k in modes}
+    fall = []
+    for _ in range(warmup):
+        for mode in modes.values():
+            s.boid_forces(mode)
+    for _ in range(n_states):
+        for name, mode in modes.items():
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f = s.boid_forces(mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms[name] += e0.elapsed_time(e1)
+            got[name].append(f[:, :3].clone())
+            if name == "surrogate_fallback":
+                fall.append(f[:, 3].clone())
+        s.step(1)
+    return ms, got, fall
+
+
+def _mode_report(surrogate, ms, got, fall, q, n_states):
+    import torch
+
+    F = torch.cat(got["exact_local"])
+    out = {}
+    for name in ms:
+        out[name] = {"qps": q / (ms[name] / 1e3), "ms_per_state": ms[name] / n_states,
+                     "aggregate_error": surrogate.aggregate_error(torch.cat(got[name]), F)}
+    out["surrogate_fallback"]["fallback_fraction"] = float(torch.cat(fall).mean().item())
+    out["exact_local_equals_exact_full"] = bool(torch.equal(F, torch.cat(got["exact_full"])))
+    out["speedup_surrogate_vs_exact_full"] = out["surrogate"]["qps"] / out["exact_full"]["qps"]
+    out["speedup_at_5pct_vs_exact_full"] = out["surrogate_fallback"]["qps"] / out["exact_full"]["qps"]
+    return out
+
+
+def run_surrogate(a, dev, big=None):
     """Boid-force queries: the surrogate (features + tensor-core MLP), the
     surrogate with its exact fallback at the calibrated 5 % aggregate error,
     and the exact force computed only where it is needed, on 65,536 queries
-    (64 states x 1,024 boids of held-out 262,144-particle column runs).  The
-    network is trained first (untimed) on 16 runs x 64 steps of the same
-    workload with other seeds."""
+    (64 states x 1,024 boids of held-out 262,144-particle column runs), and
+    on the settled large tank ``big`` (4 states x 16,384 boids, a shift from
+    the training distribution).  The network is trained first (untimed) on
+    16 runs x 64 steps of the column with other seeds.  Each per-state time
+    includes the state's binning, which every mode needs."""
     import torch
 
     from paper_2311_15088_gb300 import surrogate
@@ -358,37 +402,20 @@ def run_surrogate(a, dev):
     s.set_surrogate(mlp, info["f_scale"], info["threshold"])
     modes = {"exact_full": SPH_BOID_EXACT, "exact_local": SPH_BOID_EXACT_LOCAL, "surrogate": SPH_BOID_SURROGATE,
              "surrogate_fallback": SPH_BOID_SURROGATE_FALLBACK}
-    ms = {k: 0.0 for k in modes}
-    got = {k: [] for k in modes}
-    fall = []
-    for _ in range(a.warmup):
-        for mode in modes.values():
-            s.boid_forces(mode)
     n_states = 64
-    for _ in range(n_states):
-        for name, mode in modes.items():
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            f = s.boid_forces(mode)
-            e1.record()
-            torch.cuda.synchronize(dev)
-            ms[name] += e0.elapsed_time(e1)
-            got[name].append(f[:, :3].clone())
-            if name == "surrogate_fallback":
-                fall.append(f[:, 3].clone())
-        s.step(1)
-    q = n_states * s.n_boid
-    F = torch.cat(got["exact_local"])
+    ms, got, fall = _time_modes(s, modes, n_states, a.warmup)
     out = {"workload": "65,536 boid-force queries: 64 states x 1,024 boids of a 262,144-particle column run",
-           "training": info, "queries": q}
-    for name in modes:
-        out[name] = {"qps": q / (ms[name] / 1e3), "ms_per_state": ms[name] / n_states,
-                     "aggregate_error": surrogate.aggregate_error(torch.cat(got[name]), F)}
-    out["surrogate_fallback"]["fallback_fraction"] = float(torch.cat(fall).mean().item())
-    out["exact_local_equals_exact_full"] = bool(torch.equal(F, torch.cat(got["exact_full"])))
-    out["speedup_surrogate_vs_exact_local"] = out["surrogate"]["qps"] / out["exact_local"]["qps"]
-    out["speedup_at_5pct_vs_exact_local"] = out["surrogate_fallback"]["qps"] / out["exact_local"]["qps"]
+           "training": info, "queries": n_states * s.n_boid}
+    out.update(_mode_report(surrogate, ms, got, fall, n_states * s.n_boid, n_states))
+    if big is not None:
+        # distribution shift: the settled 2M-particle tank and its 16,384 boids
+        big.set_surrogate(mlp, info["f_scale"], info["threshold"])
+        nb = 4
+        ms, got, fall = _time_modes(big, modes, nb, 1)
+        out["large_tank"] = {"workload": f"{nb * big.n_boid:,} queries: {nb} states x {big.n_boid:,} boids of the "
+                                         "settled 2,097,152-particle tank (trained on the column: a shift)",
+                             "queries": nb * big.n_boid}
+        out["large_tank"].update(_mode_report(surrogate, ms, got, fall, nb * big.n_boid, nb))
     return out
 
 
@@ -611,7 +638,7 @@ def run_ours(a):
 
     nsearch = _neighbor_search(s, dev)
     batched = None if a.no_batch else run_batched(a, dev, flush)
-    sur = None if a.no_surrogate else run_surrogate(a, dev)
+    sur = None if a.no_surrogate else run_surrogate(a, dev, big=s)
 
     if rank == 0:
         line = {
