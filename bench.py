@@ -118,6 +118,22 @@ def _params(sc):
     return p
 
 
+def _max_over_ranks(t: float, world: int, dev) -> float:
+    """The slowest rank's timed seconds (every rank gets it)."""
+    if world <= 1:
+        return t
+    import torch
+
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def _job_value(n_fluid: int, steps: int, world: int, seconds: float) -> float:
+    """Whole-job particle-steps/s: every rank steps its own replica."""
+    return n_fluid * steps * world / seconds
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -551,12 +567,8 @@ def run_ours(a):
     prof = sph.sph_profile_read(s.handle)
     sph.sph_profile_enable(s.handle, 0)
     step_ms = [e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]
-    t = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
-    value = nf * a.steps * world / t
+    t = _max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    value = _job_value(nf, a.steps, world, t)
     work1 = _work_snapshot(s)
     status = s.status()
 
