@@ -205,7 +205,8 @@ cudaError_t launch_features(const float4* pos, const float4* vel, const unsigned
 
 // For every flagged boid (bmask NULL = all): need[slot] = 1 for its attached
 // particle and for each fluid neighbour (their densities enter the boid's
-// force).  One warp per boid, the lanes striding over each row of the walk.
+// force).  One warp per boid: the lanes fetch the walk's rows together
+// (WarpRows) and take the candidates by flat index.
 constexpr int MARK_WARPS = 8;
 
 __global__ void __launch_bounds__(MARK_WARPS * 32)
@@ -219,10 +220,14 @@ k_mark_needed(const float4* __restrict__ pos, const unsigned* __restrict__ start
     if (lane == 0) need[i] = 1;
     const float4 pi = pos[i];
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
-    RowWalkT<true> walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
-    unsigned s0, s1;
-    while (walk.next(s0, s1)) {
-        for (unsigned j = s0 + lane; j < s1; j += 32) {
+    WarpRows rows(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+    for (int bt = 0; 32 * bt < rows.nrows; ++bt) {
+        rows.batch(bt);
+        const unsigned total = rows.flatten();
+        for (unsigned k0 = 0; k0 < total; k0 += 32) {
+            const unsigned k = k0 + (unsigned)lane;
+            const unsigned j = rows.slot(k < total ? k : total - 1);
+            if (k >= total) continue;
             const float4 pj = __ldg(pos + j);
             if (id_of(pj) < sc.nb_all) continue;
             const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));

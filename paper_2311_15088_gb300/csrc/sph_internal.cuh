@@ -150,21 +150,16 @@ __device__ __forceinline__ float axis_gap2(float v, int c, int dim, float mn, co
 // reach).  Rows and x-ranges are pruned per query with bounds that are
 // conservative for the float32 predicate, so the visited set always holds
 // every neighbour.  Usage: RowWalk w(...); while (w.next(s0, s1)) {...}
-// yields the rows [s0, s1).  With AHEAD the slot bounds of the following
-// row are loaded one row early (rows may then be empty): the same rows in
-// the same order, for kernels whose few walks leave load latency exposed.
-template <bool AHEAD = false>
-struct RowWalkT {
+// yields each non-empty row [s0, s1).
+struct RowWalk {
     const GridDesc& g;
     const WalkBounds& wb;
     const unsigned* __restrict__ start;
     float px, py, pz, rz;
     int z, z1, y, y0, y1;
-    unsigned n0, n1;  // AHEAD: the row loaded ahead
-    bool ahead;
 
-    __device__ __forceinline__ RowWalkT(const GridDesc& g_, const WalkBounds& w_, const unsigned* __restrict__ st,
-                                        float x_, float y_, float z_)
+    __device__ __forceinline__ RowWalk(const GridDesc& g_, const WalkBounds& w_, const unsigned* __restrict__ st,
+                                       float x_, float y_, float z_)
         : g(g_), wb(w_), start(st), px(x_), py(y_), pz(z_), rz(0.0f)
     {
         bool cl = false;
@@ -173,13 +168,10 @@ struct RowWalkT {
         y0 = cell_coord(py - wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
         y1 = cell_coord(py + wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
         z = z0 - 1;
-        y = y1 + 1;  // forces the first step to open row z0
-        if (AHEAD) ahead = advance(n0, n1, false);
+        y = y1 + 1;  // forces the first next() to open row z0
     }
 
-    // The next row the sphere reaches: its bounds; with skip_empty, the next
-    // non-empty one.
-    __device__ __forceinline__ bool advance(unsigned& s0, unsigned& s1, bool skip_empty)
+    __device__ __forceinline__ bool next(unsigned& s0, unsigned& s1)
     {
         for (;;) {
             if (y > y1) {
@@ -203,21 +195,97 @@ struct RowWalkT {
             const unsigned rowk = (unsigned)g.dim[0] * ((unsigned)yy + (unsigned)g.dim[1] * (unsigned)z);
             s0 = __ldg(start + rowk + x0);
             s1 = __ldg(start + rowk + x1 + 1);
-            if (!skip_empty || s0 < s1) return true;
+            if (s0 < s1) return true;
         }
     }
+};
 
-    __device__ __forceinline__ bool next(unsigned& s0, unsigned& s1)
+// The rows of RowWalk's walk of (px, py, pz), fetched by the 32 lanes of a
+// warp at once: row r of the (y, z) box (z-major, the walk's order) goes to
+// lane r % 32 of batch r / 32, which applies the walk's pruning and loads
+// the row's slot bounds (a pruned row gets an empty range).  row(k) then
+// hands every lane the bounds of row k of the current batch.  Every lane of
+// the warp must take part (the query point is the same for all).
+struct WarpRows {
+    const GridDesc& g;
+    const WalkBounds& wb;
+    const unsigned* __restrict__ start;
+    float px, py, pz;
+    int z0, y0, ny, nrows;
+    unsigned s0, s1;  // this lane's row of the current batch
+
+    __device__ __forceinline__ WarpRows(const GridDesc& g_, const WalkBounds& w_, const unsigned* __restrict__ st,
+                                        float x_, float y_, float z_)
+        : g(g_), wb(w_), start(st), px(x_), py(y_), pz(z_)
     {
-        if (!AHEAD) return advance(s0, s1, true);
-        if (!ahead) return false;
-        s0 = n0;
-        s1 = n1;
-        ahead = advance(n0, n1, false);
-        return true;
+        bool cl = false;
+        z0 = cell_coord(pz - wb.reach, g.minf[2], g.inv_d, g.dim[2], &cl);
+        const int z1 = cell_coord(pz + wb.reach, g.minf[2], g.inv_d, g.dim[2], &cl);
+        y0 = cell_coord(py - wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
+        const int y1 = cell_coord(py + wb.reach, g.minf[1], g.inv_d, g.dim[1], &cl);
+        ny = y1 - y0 + 1;
+        nrows = ny * (z1 - z0 + 1);
+    }
+
+    // Load batch b (rows 32 b .. 32 b + 31); returns the rows in it.
+    __device__ __forceinline__ int batch(int b)
+    {
+        const int r = 32 * b + (int)(threadIdx.x & 31);
+        s0 = s1 = 0;
+        if (r < nrows) {
+            const int z = z0 + r / ny, yy = y0 + r % ny;
+            const float rz = wb.reach2 - axis_gap2(pz, z, g.dim[2], g.minf[2], wb);
+            const float ryz = rz - axis_gap2(py, yy, g.dim[1], g.minf[1], wb);
+            if (rz > 0.0f && ryz > 0.0f) {
+                const float xr = fmaf(ryz, rsqrtf(ryz), wb.margin);
+                bool cl = false;
+                const int x0 = cell_coord(px - xr, g.minf[0], g.inv_d, g.dim[0], &cl);
+                const int x1 = cell_coord(px + xr, g.minf[0], g.inv_d, g.dim[0], &cl);
+                const unsigned rowk = (unsigned)g.dim[0] * ((unsigned)yy + (unsigned)g.dim[1] * (unsigned)z);
+                s0 = __ldg(start + rowk + x0);
+                s1 = __ldg(start + rowk + x1 + 1);
+            }
+        }
+        const int left = nrows - 32 * b;
+        return left < 32 ? left : 32;
+    }
+
+    __device__ __forceinline__ void row(int k, unsigned& r0, unsigned& r1) const
+    {
+        r0 = __shfl_sync(0xffffffffu, s0, k);
+        r1 = __shfl_sync(0xffffffffu, s1, k);
+    }
+
+    // After batch(): number the batch's candidates 0 .. total-1 in walk order
+    // (rows in order, slots ascending) so that the lanes can take them by
+    // flat index.  Returns total.
+    unsigned pre;  // this lane's row: first flat index
+    __device__ __forceinline__ unsigned flatten()
+    {
+        const unsigned lane = threadIdx.x & 31;
+        const unsigned len = s1 - s0;
+        unsigned inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (unsigned)o) inc += u;
+        }
+        pre = inc - len;
+        return __shfl_sync(0xffffffffu, inc, 31);
+    }
+
+    // Slot of flat index k (k < total), for every lane (each its own k).
+    __device__ __forceinline__ unsigned slot(unsigned k) const
+    {
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {  // the last row whose first index <= k
+            const unsigned p = __shfl_sync(0xffffffffu, pre, lo + step);
+            if (p <= k) lo += step;
+        }
+        return __shfl_sync(0xffffffffu, s0, lo) + (k - __shfl_sync(0xffffffffu, pre, lo));
     }
 };
-using RowWalk = RowWalkT<false>;
 
 // ---------------------------------------------------------------- launchers
 

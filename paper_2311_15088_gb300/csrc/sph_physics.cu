@@ -36,7 +36,7 @@ namespace sphk {
 // A fluid particle has no excluded pairs, so its loop counts every hit and
 // subtracts the self pair (always visited: r2 = 0) at the end; the sums
 // take the same terms in the same order as the attached particles' loop.
-template <bool STREAM, bool AHEAD>
+template <bool STREAM>
 __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos, const unsigned* __restrict__ start,
                                            const Scenes& sc, float* __restrict__ rho, float2* __restrict__ ab,
                                            int* __restrict__ nbr, unsigned* __restrict__ bits,
@@ -51,7 +51,7 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
     int cnt = 0;
     unsigned word = 0;
     int nc = 0;
-    RowWalkT<AHEAD> walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+    RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
     unsigned s0, s1;
     if (!STREAM && !att_i) {
         auto take = [&](const float4& pj) {
@@ -111,24 +111,77 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
     if (!isfinite(r)) atomicOr(err, SPH_DEV_NONFINITE);
 }
 
-// Every particle (thread i = slot i), or only the slots of a list whose
-// length the device holds (grid-stride loop; the list is built on the
-// device, so the launch does not wait for its length).
-template <bool STREAM, bool LIST>
+// Every particle (thread i = slot i).
+template <bool STREAM>
 __global__ void __launch_bounds__(512)
 k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
           float* __restrict__ rho, float2* __restrict__ ab, int* __restrict__ nbr, unsigned* __restrict__ bits,
-          int* __restrict__ ncand, const int* __restrict__ list, const unsigned* __restrict__ list_len,
-          unsigned* __restrict__ err)
+          int* __restrict__ ncand, unsigned* __restrict__ err)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!LIST) {
-        if (t < sc.n_all) density_at<STREAM, false>(t, pos, start, sc, rho, ab, nbr, bits, ncand, err);
-        return;
-    }
+    if (t < sc.n_all) density_at<STREAM>(t, pos, start, sc, rho, ab, nbr, bits, ncand, err);
+}
+
+// Only the slots of a list whose length the device holds (the list is built
+// on the device; warps stride over it): a warp per particle, the lanes fetch
+// the walk's rows together and test a row's candidates side by side, then
+// the hits are added in slot order by the same fused multiply-adds as the
+// one-thread pass (the lanes pass the terms by shuffles), so the density is
+// bit for bit the full pass's.  Kept for few particles (the exact-local
+// path), where the one-thread walk leaves its latency exposed.
+__global__ void __launch_bounds__(256)
+k_density_list(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
+               float* __restrict__ rho, float2* __restrict__ ab, int* __restrict__ nbr, int* __restrict__ ncand,
+               const int* __restrict__ list, const unsigned* __restrict__ list_len, unsigned* __restrict__ err)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
     const int len = (int)min(*list_len, (unsigned)sc.n_all);
-    for (int k = t; k < len; k += gridDim.x * blockDim.x)
-        density_at<STREAM, false>(list[k], pos, start, sc, rho, ab, nbr, bits, ncand, err);
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < len; w += nw) {
+        const int i = list[w];
+        const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+        const float h2 = c.h2;
+        const int nb_all = sc.nb_all;
+        const float4 pi = pos[i];
+        const bool att_i = id_of(pi) < nb_all;
+        float sum = 0.0f;
+        int cnt = 0, nc = 0;
+        WarpRows rows(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
+        for (int bt = 0; 32 * bt < rows.nrows; ++bt) {
+            rows.batch(bt);
+            const unsigned total = rows.flatten();
+            nc += (int)total;
+            for (unsigned k0 = 0; k0 < total; k0 += 32) {
+                const unsigned k = k0 + (unsigned)lane;
+                const unsigned j = rows.slot(k < total ? k : total - 1);
+                bool hit = false, self = false;
+                float t = 0.0f;
+                if (k < total) {
+                    const float4 pj = __ldg(pos + j);
+                    const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+                    self = j == (unsigned)i;
+                    hit = r2 < h2 && !(att_i && !self && id_of(pj) < nb_all);
+                    t = h2 - r2;
+                }
+                unsigned m = __ballot_sync(FULL, hit);
+                cnt += __popc(m & ~__ballot_sync(FULL, self));
+                while (m) {  // the hits in walk order, one fused multiply-add each
+                    const int q = __ffs(m) - 1;
+                    m &= m - 1u;
+                    const float v = __shfl_sync(FULL, t, q);
+                    sum = fmaf(v * v, v, sum);
+                }
+            }
+        }
+        if (lane == 0) {
+            ncand[i] = nc;
+            const float r = c.mC6 * sum;
+            rho[i] = r;
+            ab[i] = make_float2(c.mass / r, c.k * (r - c.rho0));
+            nbr[i] = cnt;
+            if (!isfinite(r)) atomicOr(err, SPH_DEV_NONFINITE);
+        }
+    }
 }
 
 cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
@@ -138,15 +191,12 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const Scene
     if (sc.n_all <= 0) return cudaSuccess;
     const int all = (sc.n_all + t.block - 1) / t.block;
     if (list) {
-        const int blocks = all < 152 * 8 ? all : 152 * 8;
-        if (t.use_stream)
-            k_density<true, true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, list, list_len, err);
-        else
-            k_density<false, true><<<blocks, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, list, list_len, err);
+        const int blocks = (sc.n_all + 7) / 8 < 152 * 16 ? (sc.n_all + 7) / 8 : 152 * 16;  // 8 warps each
+        k_density_list<<<blocks, 256, 0, s>>>(pos, start, sc, rho, ab, nbr, ncand, list, list_len, err);
     } else if (t.use_stream) {
-        k_density<true, false><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, nullptr, nullptr, err);
+        k_density<true><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, err);
     } else {
-        k_density<false, false><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, nullptr, nullptr, err);
+        k_density<false><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, err);
     }
     ++*launches;
     return cudaGetLastError();
@@ -180,8 +230,10 @@ struct PairTerms {
 
 // F_b of boid b (section "Boids and Fluid Interaction"): the acceleration
 // of its attached particle from the fluid particles within h.  One warp per
-// boid: the lanes stride over each row of the particle's walk, each keeps
-// its own sum, and a butterfly adds the 32 sums (a fixed order).
+// boid: the lanes fetch the walk's rows together (WarpRows) and take its
+// candidates by flat index (lane l: candidates l, l + 32, ... in walk
+// order), each keeping its own sum, and a butterfly adds the 32 sums (a
+// fixed order).
 __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __restrict__ pos,
                                              const float4* __restrict__ vel, const float* __restrict__ rho,
                                              const float2* __restrict__ ab, const unsigned* __restrict__ start,
@@ -201,10 +253,14 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
     T.inv_h = c.inv_h;
     const float h2 = c.h2;
     float ax = 0.f, ay = 0.f, az = 0.f;
-    RowWalkT<true> walk(c.g, c.wg, start + c.c_base, T.pi.x, T.pi.y, T.pi.z);
-    unsigned s0, s1;
-    while (walk.next(s0, s1)) {
-        for (unsigned j = s0 + lane; j < s1; j += 32) {
+    WarpRows rows(c.g, c.wg, start + c.c_base, T.pi.x, T.pi.y, T.pi.z);
+    for (int bt = 0; 32 * bt < rows.nrows; ++bt) {
+        rows.batch(bt);
+        const unsigned total = rows.flatten();
+        for (unsigned k0 = 0; k0 < total; k0 += 32) {
+            const unsigned k = k0 + (unsigned)lane;
+            const unsigned j = rows.slot(k < total ? k : total - 1);
+            if (k >= total) continue;
             const float4 pj = __ldg(pos + j);
             const float dx = __fsub_rn(pj.x, T.pi.x), dy = __fsub_rn(pj.y, T.pi.y), dz = __fsub_rn(pj.z, T.pi.z);
             const float r2 = pair_r2(dx, dy, dz);
