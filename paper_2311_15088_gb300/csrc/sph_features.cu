@@ -34,7 +34,8 @@ namespace sphk {
 //   1. the rows (y, z) of particle-grid cells under the stencil's box (one
 //      cell of margin) get their slot ranges loaded in parallel, and a block
 //      scan of their lengths numbers the box's particles 0 .. total-1;
-//   2. thread t takes particles t, t + FT, ...: a particle of a stencil
+//   2. thread t takes particles t, t + FT, ... (four at a time, their loads
+//      issued together): a particle of a stencil
 //      cell adds 1 and its velocity in 2^-16 fixed point to the cell's
 //      shared integer sums (integer sums do not depend on the order; they
 //      hold while a cell's mean speed stays below 2^15 / count m/s, beyond
@@ -76,8 +77,9 @@ k_features(const float4* __restrict__ pos, const float4* __restrict__ vel, const
     int nrows = (lo[0] <= hi[0] && ny > 0 && nz > 0) ? ny * nz : 0;
     nrows = nrows < FROWS ? nrows : FROWS;  // a box this large only arises for far-off boids
     const unsigned* cstart = start + c.c_base;
-    // ---- 1: row ranges and their prefix sums
-    for (int r = tid; r < FROWS; r += FT) {
+    // ---- 1: row ranges and their prefix sums (rows past nrows count 0)
+    const int nscan = (nrows + 31) & ~31;
+    for (int r = tid; r < nscan; r += FT) {
         unsigned len = 0;
         if (r < nrows) {
             const int y = lo[1] + r % ny, z = lo[2] + r / ny;
@@ -96,7 +98,7 @@ k_features(const float4* __restrict__ pos, const float4* __restrict__ vel, const
     __syncthreads();
     if (tid < 32) {  // inclusive scan of row_pre[1 .. FROWS] by one warp
         unsigned carry = 0;
-        for (int base = 1; base <= FROWS; base += 32) {
+        for (int base = 1; base <= nscan; base += 32) {
             unsigned v = row_pre[base + tid];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -111,47 +113,66 @@ k_features(const float4* __restrict__ pos, const float4* __restrict__ vel, const
     const unsigned total = row_pre[nrows];
     const float h2 = c.h2;
     float mo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // poly6, S0, S1 (3), S2 (3)
-    // ---- 2: every particle of the box once
-    for (unsigned g = tid; g < total; g += FT) {
-        int lo_r = 0, hi_r = nrows;  // row r with row_pre[r] <= g < row_pre[r + 1]
-        while (hi_r - lo_r > 1) {
-            const int mid = (lo_r + hi_r) >> 1;
-            if (row_pre[mid] <= g) lo_r = mid;
-            else hi_r = mid;
+    // ---- 2: every particle of the box once, four per thread at a time (the
+    // positions and velocities of the four are loaded before any is used)
+    constexpr int U = 4;
+    for (unsigned g0 = tid; g0 < total; g0 += FT * U) {
+        unsigned js[U];
+        float4 ps[U], vs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned g = g0 + (unsigned)(u * FT);
+            js[u] = 0xffffffffu;
+            if (g < total) {
+                int lo_r = 0, hi_r = nrows;  // row r with row_pre[r] <= g < row_pre[r + 1]
+                while (hi_r - lo_r > 1) {
+                    const int mid = (lo_r + hi_r) >> 1;
+                    if (row_pre[mid] <= g) lo_r = mid;
+                    else hi_r = mid;
+                }
+                js[u] = row_s0[lo_r] + (g - row_pre[lo_r]);
+            }
         }
-        const unsigned j = row_s0[lo_r] + (g - row_pre[lo_r]);
-        const float4 pj = __ldg(pos + j);
-        if (id_of(pj) < sc.nb_all) continue;  // fluid particles only
-        const float fx = floorf(__fmul_rn(__fsub_rn(pj.x, c.g.minf[0]), c.inv_h)) - c0[0];
-        const float fy = floorf(__fmul_rn(__fsub_rn(pj.y, c.g.minf[1]), c.inv_h)) - c0[1];
-        const float fz = floorf(__fmul_rn(__fsub_rn(pj.z, c.g.minf[2]), c.inv_h)) - c0[2];
-        const bool in = fx >= 0.f && fx < 4.f && fy >= 0.f && fy < 4.f && fz >= 0.f && fz < 4.f;
-        const float dx = __fsub_rn(pj.x, pb.x), dy = __fsub_rn(pj.y, pb.y), dz = __fsub_rn(pj.z, pb.z);
-        const float r2 = pair_r2(dx, dy, dz);
-        const bool near = r2 < h2;
-        if (!in && !near) continue;
-        const float4 vj = __ldg(vel + j);
-        if (in) {
-            const int q = (int)fx + 4 * ((int)fy + 4 * (int)fz);
-            atomicAdd(&cnt[q], 1);
-            atomicAdd(&vsum[q][0], __float2int_rn(vj.x * VFIX));
-            atomicAdd(&vsum[q][1], __float2int_rn(vj.y * VFIX));
-            atomicAdd(&vsum[q][2], __float2int_rn(vj.z * VFIX));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (js[u] != 0xffffffffu) {
+                ps[u] = __ldg(pos + js[u]);
+                vs[u] = __ldg(vel + js[u]);
+            }
         }
-        if (near) {
-            const float u = h2 - r2;
-            mo[0] += u * u * u;
-            const float rr = sqrtf(r2);
-            const float w = 1.0f - rr * c.inv_h;
-            mo[1] += w;
-            mo[2] += w * (vj.x - vb.x);
-            mo[3] += w * (vj.y - vb.y);
-            mo[4] += w * (vj.z - vb.z);
-            if (r2 > 0.0f) {
-                const float sdir = -w * w / rr;  // (x_b - x_j) / r = -d / r
-                mo[5] += sdir * dx;
-                mo[6] += sdir * dy;
-                mo[7] += sdir * dz;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (js[u] == 0xffffffffu) continue;
+            const float4 pj = ps[u], vj = vs[u];
+            if (id_of(pj) < sc.nb_all) continue;  // fluid particles only
+            const float fx = floorf(__fmul_rn(__fsub_rn(pj.x, c.g.minf[0]), c.inv_h)) - c0[0];
+            const float fy = floorf(__fmul_rn(__fsub_rn(pj.y, c.g.minf[1]), c.inv_h)) - c0[1];
+            const float fz = floorf(__fmul_rn(__fsub_rn(pj.z, c.g.minf[2]), c.inv_h)) - c0[2];
+            const bool in = fx >= 0.f && fx < 4.f && fy >= 0.f && fy < 4.f && fz >= 0.f && fz < 4.f;
+            if (in) {
+                const int q = (int)fx + 4 * ((int)fy + 4 * (int)fz);
+                atomicAdd(&cnt[q], 1);
+                atomicAdd(&vsum[q][0], __float2int_rn(vj.x * VFIX));
+                atomicAdd(&vsum[q][1], __float2int_rn(vj.y * VFIX));
+                atomicAdd(&vsum[q][2], __float2int_rn(vj.z * VFIX));
+            }
+            const float dx = __fsub_rn(pj.x, pb.x), dy = __fsub_rn(pj.y, pb.y), dz = __fsub_rn(pj.z, pb.z);
+            const float r2 = pair_r2(dx, dy, dz);
+            if (r2 < h2) {
+                const float u2 = h2 - r2;
+                mo[0] += u2 * u2 * u2;
+                const float rr = sqrtf(r2);
+                const float w = 1.0f - rr * c.inv_h;
+                mo[1] += w;
+                mo[2] += w * (vj.x - vb.x);
+                mo[3] += w * (vj.y - vb.y);
+                mo[4] += w * (vj.z - vb.z);
+                if (r2 > 0.0f) {
+                    const float sdir = -w * w / rr;  // (x_b - x_j) / r = -d / r
+                    mo[5] += sdir * dx;
+                    mo[6] += sdir * dy;
+                    mo[7] += sdir * dz;
+                }
             }
         }
     }

@@ -475,6 +475,186 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
     }
 }
 
+// ------------------------------------------------------------- fused forward
+
+// The forward pass of one 128-row tile in one CTA (inference): the input
+// tile and the hidden activations stay in shared memory in the layout the
+// tensor cores read (K-major, 64-column tiles of 128-byte rows with the
+// 128-byte swizzle that TMA writes), the 128 x 256 FP32 accumulator in
+// tensor memory, and the 17 weight tiles of the four layers stream through
+// a two-stage TMA ring.  Warp 8 loads, warp 9 issues the MMAs, warps 0 .. 7
+// are the epilogue (warp w reads tensor-memory lanes 32 (w % 4) .. and
+// columns 128 (w / 4) .. of the accumulator): bias, GELU, BF16, written
+// straight into the next layer's operand tile; the last layer's 16 columns
+// go to y with their bias.  Same K order and epilogue arithmetic as the
+// per-layer GEMMs, so the same outputs.  Every wait is bounded.
+namespace fused {
+constexpr int KB_IN = (MLP_IN + BK - 1) / BK;   // 5 K tiles of the input
+constexpr int KB_H = MLP_H / BK;                // 4 K tiles of a hidden layer
+constexpr uint32_t A_TILE = BM * BK * 2;        // 16 KB: 128 rows x 64 BF16
+constexpr uint32_t W_TILE = MLP_H * BK * 2;     // 32 KB: 256 rows x 64 BF16
+constexpr uint32_t BUF_A = 0;                   // input, then layer-2 output
+constexpr uint32_t BUF_B = BUF_A + KB_IN * A_TILE;  // layer-1 and layer-3 outputs
+constexpr uint32_t RING = BUF_B + KB_H * A_TILE;
+constexpr int STAGES = 2;
+constexpr uint32_t BARS = RING + STAGES * W_TILE;
+// barriers: x_full, full[2], empty[2], acc_full, act_ready; then the TMEM slot
+constexpr uint32_t TOTAL = 1024 + BARS + 8 * 8 + 16;
+constexpr int THREADS = 320;
+constexpr int EPI_THREADS = 256;
+constexpr int TILES = KB_IN + 2 * KB_H + KB_H;  // 17 weight tiles
+}  // namespace fused
+
+// byte offset of element (r, c) in a K-major 64-column tile with 128-byte swizzle
+__device__ __forceinline__ uint32_t sw128_offset(int r, int c)
+{
+    return (uint32_t)(r * 128 + ((((c * 2) >> 4) ^ (r & 7)) << 4) + ((c * 2) & 15));
+}
+
+__global__ void __launch_bounds__(fused::THREADS, 1)
+k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapW0,
+            const __grid_constant__ CUtensorMap mapW1, const __grid_constant__ CUtensorMap mapW2,
+            const __grid_constant__ CUtensorMap mapW3, const float* __restrict__ P, int B, float* __restrict__ y,
+            unsigned* __restrict__ err)
+{
+    using namespace fused;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (base - raw);
+    const uint32_t bars = base + BARS;
+    const uint32_t x_full = bars, acc_full = bars + 40, act_ready = bars + 48;
+    auto full = [&](int s) { return bars + 8u + 8u * (uint32_t)s; };
+    auto empty = [&](int s) { return bars + 24u + 8u * (uint32_t)s; };
+    const uint32_t tmem_slot = bars + 64;
+    uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(gbase + BARS + 64);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    const ParamLayout L;
+
+    if (threadIdx.x == 0) {
+        mbar_init(x_full, 1);
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(act_ready, EPI_THREADS);
+        mbar_fence_init();
+    }
+    if (warp == 8) tmem_alloc(tmem_slot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot_ptr;
+
+    if (warp == 8) {
+        if (lane == 0) {
+            // ---- loads: the input tile, then the 17 weight tiles in order
+            mbar_expect_tx(x_full, KB_IN * A_TILE);
+            for (int kb = 0; kb < KB_IN; ++kb) tma_load_2d(&mapX, x_full, base + BUF_A + kb * A_TILE, kb * BK, m0);
+            int issued = 0;
+            bool ok = true;
+            for (int g = 0; g < TILES && ok; ++g) {
+                const int s = g % STAGES;
+                if (g >= STAGES && !mbar_wait(empty(s), (uint32_t)((g / STAGES) - 1) & 1u, err)) {
+                    ok = false;
+                    break;
+                }
+                const int layer = g < KB_IN ? 0 : 1 + (g - KB_IN) / KB_H;
+                const int kb = g < KB_IN ? g : (g - KB_IN) % KB_H;
+                const CUtensorMap* map = layer == 0 ? &mapW0 : layer == 1 ? &mapW1 : layer == 2 ? &mapW2 : &mapW3;
+                const uint32_t bytes = layer == 3 ? MLP_OUT * BK * 2 : W_TILE;
+                mbar_expect_tx(full(s), bytes);
+                tma_load_2d(map, full(s), base + RING + s * W_TILE, kb * BK, 0);
+                ++issued;
+            }
+            if (!ok)  // let the copies in flight land before the CTA goes away
+                for (int g = (issued > STAGES ? issued - STAGES : 0); g < issued; ++g)
+                    mbar_wait(full(g % STAGES), (uint32_t)(g / STAGES) & 1u, err);
+            mbar_wait(x_full, 0, err);
+        }
+    } else if (warp == 9) {
+        if (lane == 0) {
+            // ---- MMA issue: layer by layer, each after its operand is ready
+            bool ok = mbar_wait(x_full, 0, err);
+            int g = 0;
+            for (int layer = 0; layer < 4 && ok; ++layer) {
+                if (layer > 0) ok = mbar_wait(act_ready, (uint32_t)(layer - 1) & 1u, err);
+                tc_fence_after();
+                const uint32_t a_buf = base + ((layer & 1) ? BUF_B : BUF_A);
+                const int nkb = layer == 0 ? KB_IN : KB_H;
+                const uint32_t idesc = umma_idesc_bf16(BM, layer == 3 ? MLP_OUT : MLP_H);
+                for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (!mbar_wait(full(s), (uint32_t)(g / STAGES) & 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = a_buf + kb * A_TILE;
+                    const uint32_t b = base + RING + s * W_TILE;
+#pragma unroll
+                    for (int k = 0; k < BK / UK; ++k)
+                        umma_bf16(tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
+                                  (uint32_t)((kb | k) != 0));
+                    umma_commit(empty(s));
+                }
+                umma_commit(acc_full);
+            }
+            if (!ok) umma_commit(acc_full);  // so that the epilogue does not wait for nothing
+        }
+    } else {
+        // ---- epilogue warps 0 .. 7
+        const int q = warp & 3, half = warp >> 2;
+        const int r = q * 32 + lane;  // tile row of this thread
+        const int row = m0 + r;
+        for (int layer = 0; layer < 4; ++layer) {
+            const bool ok = mbar_wait(acc_full, (uint32_t)layer & 1u, err);
+            tc_fence_after();
+            if (!ok) break;
+            const float* bias = P + L.b[layer];
+            if (layer < 3) {
+                uint8_t* out = gbase + ((layer & 1) ? BUF_A : BUF_B);  // layer 0 -> B, 1 -> A, 2 -> B
+#pragma unroll 1
+                for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                    uint32_t pk[8];
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(v[j] + __ldg(bias + c0 + j)),
+                                                                      gelu_f(v[j + 1] + __ldg(bias + c0 + j + 1)));
+                        pk[j >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
+                    }
+                    // columns c0 .. c0+15: K tile c0 / 64, two 16-byte chunks
+                    uint8_t* tile = out + (c0 / BK) * A_TILE;
+                    const int cc = c0 % BK;
+                    *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tc_fence_before();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(act_ready) : "memory");
+            } else if (half == 0) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16), v);
+                if (row < B) {
+                    float4* o = reinterpret_cast<float4*>(y + (size_t)row * MLP_OUT);
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        o[j / 4] = make_float4(v[j] + __ldg(bias + j), v[j + 1] + __ldg(bias + j + 1),
+                                               v[j + 2] + __ldg(bias + j + 2), v[j + 3] + __ldg(bias + j + 3));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 8) tmem_dealloc(tmem, 256);
+}
+
 }  // namespace sphk
 
 // ------------------------------------------------------------------ API
@@ -601,6 +781,26 @@ static int mlp_forward(sph_mlp* m, const __nv_bfloat16* x, int B, float* y, bool
     return SPH_OK;
 }
 
+// Inference: the four layers in one launch (k_mlp_fused), 128 rows per CTA.
+static int mlp_forward_fused(sph_mlp* m, const __nv_bfloat16* x, int B, float* y, cudaStream_t s)
+{
+    const ParamLayout L;
+    CUtensorMap mx, mw[4];
+    MLP_TRY(m, make_map(&mx, x, B, MLP_IN, MLP_IN, BM));
+    for (int l = 0; l < 4; ++l)
+        MLP_TRY(m, make_map(&mw[l], m->W + L.w[l], L.out[l], L.in[l], L.in[l], L.out[l]));
+    static bool attr = false;
+    if (!attr) {
+        MLP_TRY(m, cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused::TOTAL));
+        attr = true;
+    }
+    k_mlp_fused<<<(B + BM - 1) / BM, fused::THREADS, fused::TOTAL, s>>>(mx, mw[0], mw[1], mw[2], mw[3], m->P, B, y,
+                                                                        m->err);
+    ++m->launches;
+    MLP_TRY(m, cudaGetLastError());
+    return SPH_OK;
+}
+
 // Weight and bias gradients of layer l from its output gradient d [B][out]
 // (d^T [out][B] given) and its input^T [in][B].
 static int layer_grads(sph_mlp* m, int l, const __nv_bfloat16* d, const __nv_bfloat16* dt, int ld_d,
@@ -722,8 +922,9 @@ int sph_mlp_forward(sph_mlp* m, const void* x, int B, float* y, void* stream)
 {
     int rc = check_batch(m, B);
     if (rc != SPH_OK) return rc;
-    if (!x || !y || ((uintptr_t)x & 15)) return mfail(m, SPH_ERR_ARG, "x must be 16-byte aligned, y non-NULL");
-    return mlp_forward(m, (const __nv_bfloat16*)x, B, y, false, (cudaStream_t)stream);
+    if (!x || !y || ((uintptr_t)x & 15) || ((uintptr_t)y & 15))
+        return mfail(m, SPH_ERR_ARG, "x and y must be 16-byte aligned");
+    return mlp_forward_fused(m, (const __nv_bfloat16*)x, B, y, (cudaStream_t)stream);
 }
 
 int sph_mlp_gradients(sph_mlp* m, const void* x, const float* dy, int B, float* grads, void* stream)
