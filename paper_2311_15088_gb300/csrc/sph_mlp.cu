@@ -482,9 +482,9 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 // tensor cores read (K-major, 64-column tiles of 128-byte rows with the
 // 128-byte swizzle that TMA writes), the 128 x 256 FP32 accumulator in
 // tensor memory, and the 17 weight tiles of the four layers stream through
-// a two-stage TMA ring.  Warp 8 loads, warp 9 issues the MMAs, warps 0 .. 7
-// are the epilogue (warp w reads tensor-memory lanes 32 (w % 4) .. and
-// columns 128 (w / 4) .. of the accumulator): bias, GELU, BF16, written
+// a two-stage TMA ring.  Warp 16 loads, warp 17 issues the MMAs, warps
+// 0 .. 15 are the epilogue (warp w reads tensor-memory lanes 32 (w % 4) ..
+// and columns 64 (w / 4) .. of the accumulator): bias, GELU, BF16, written
 // straight into the next layer's operand tile; the last layer's 16 columns
 // go to y with their bias.  Same K order and epilogue arithmetic as the
 // per-layer GEMMs, so the same outputs.  Every wait is bounded.
@@ -500,8 +500,11 @@ constexpr int STAGES = 2;
 constexpr uint32_t BARS = RING + STAGES * W_TILE;
 // barriers: x_full, full[2], empty[2], acc_full, act_ready; then the TMEM slot
 constexpr uint32_t TOTAL = 1024 + BARS + 8 * 8 + 16;
-constexpr int THREADS = 320;
-constexpr int EPI_THREADS = 256;
+constexpr int EPI_WARPS = 16;
+constexpr int LOAD_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
+constexpr int THREADS = 32 * (EPI_WARPS + 2);
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int EPI_COLS = MLP_H / (EPI_WARPS / 4);  // accumulator columns per epilogue warp
 constexpr int TILES = KB_IN + 2 * KB_H + KB_H;  // 17 weight tiles
 }  // namespace fused
 
@@ -543,13 +546,13 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
         mbar_init(act_ready, EPI_THREADS);
         mbar_fence_init();
     }
-    if (warp == 8) tmem_alloc(tmem_slot, 256);
+    if (warp == LOAD_WARP) tmem_alloc(tmem_slot, 256);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot_ptr;
 
-    if (warp == 8) {
+    if (warp == LOAD_WARP) {
         if (lane == 0) {
             // ---- loads: the input tile, then the 17 weight tiles in order
             mbar_expect_tx(x_full, KB_IN * A_TILE);
@@ -575,7 +578,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
                     mbar_wait(full(g % STAGES), (uint32_t)(g / STAGES) & 1u, err);
             mbar_wait(x_full, 0, err);
         }
-    } else if (warp == 9) {
+    } else if (warp == MMA_WARP) {
         if (lane == 0) {
             // ---- MMA issue: layer by layer, each after its operand is ready
             bool ok = mbar_wait(x_full, 0, err);
@@ -606,8 +609,8 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
             if (!ok) umma_commit(acc_full);  // so that the epilogue does not wait for nothing
         }
     } else {
-        // ---- epilogue warps 0 .. 7
-        const int q = warp & 3, half = warp >> 2;
+        // ---- epilogue warps
+        const int q = warp & 3, part = warp >> 2;
         const int r = q * 32 + lane;  // tile row of this thread
         const int row = m0 + r;
         for (int layer = 0; layer < 4; ++layer) {
@@ -618,7 +621,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
             if (layer < 3) {
                 uint8_t* out = gbase + ((layer & 1) ? BUF_A : BUF_B);  // layer 0 -> B, 1 -> A, 2 -> B
 #pragma unroll 1
-                for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+                for (int c0 = part * EPI_COLS; c0 < part * EPI_COLS + EPI_COLS; c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                     uint32_t pk[8];
@@ -637,7 +640,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc_fence_before();
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(act_ready) : "memory");
-            } else if (half == 0) {
+            } else if (part == 0) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16), v);
                 if (row < B) {
@@ -652,7 +655,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 8) tmem_dealloc(tmem, 256);
+    if (warp == LOAD_WARP) tmem_dealloc(tmem, 256);
 }
 
 }  // namespace sphk
