@@ -349,6 +349,10 @@ class Mlp:
         self.handle = sph_mlp_create(self.max_batch, self._ws, nbytes)
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
 
+    @property
+    def launches(self) -> int:
+        return sph_mlp_launch_count(self.handle)
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None:
