@@ -352,29 +352,42 @@ def run_batched(a, dev, flush):
 
 # ----------------------------------------------------------- surrogate
 
-def _time_modes(s, modes, n_states, warmup):
+HEAD_ONLY = "surrogate_fallback_head_only"
+
+
+def _time_modes(s, modes, n_states, warmup, bounds=None):
     """Per mode: summed ms of sph_boid_forces over n_states states (one
-    step between states), the forces and the fallback flags."""
+    step between states), the forces and the fallback flags.  The mode
+    named HEAD_ONLY runs the fallback with the input-range check off."""
     import torch
 
     ms = {k: 0.0 for k in modes}
     got = {k: [] for k in modes}
-    fall = []
+    fall = {k: [] for k in modes if k.startswith("surrogate_fallback")}
+
+    def call(name, mode):
+        if name == HEAD_ONLY:
+            s.set_surrogate_bounds(None)
+        f = s.boid_forces(mode)
+        if name == HEAD_ONLY:
+            s.set_surrogate_bounds(bounds)
+        return f
+
     for _ in range(warmup):
-        for mode in modes.values():
-            s.boid_forces(mode)
+        for name, mode in modes.items():
+            call(name, mode)
     for _ in range(n_states):
         for name, mode in modes.items():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            f = s.boid_forces(mode)
+            f = call(name, mode)
             e1.record()
             torch.cuda.synchronize()
             ms[name] += e0.elapsed_time(e1)
             got[name].append(f[:, :3].clone())
-            if name == "surrogate_fallback":
-                fall.append(f[:, 3].clone())
+            if name in fall:
+                fall[name].append(f[:, 3].clone())
         s.step(1)
     return ms, got, fall
 
@@ -387,7 +400,8 @@ def _mode_report(surrogate, ms, got, fall, q, n_states):
     for name in ms:
         out[name] = {"qps": q / (ms[name] / 1e3), "ms_per_state": ms[name] / n_states,
                      "aggregate_error": surrogate.aggregate_error(torch.cat(got[name]), F)}
-    out["surrogate_fallback"]["fallback_fraction"] = float(torch.cat(fall).mean().item())
+    for name, fl in fall.items():
+        out[name]["fallback_fraction"] = float(torch.cat(fl).mean().item())
     out["exact_local_equals_exact_full"] = bool(torch.equal(F, torch.cat(got["exact_full"])))
     out["speedup_surrogate_vs_exact_full"] = out["surrogate"]["qps"] / out["exact_full"]["qps"]
     out["speedup_at_5pct_vs_exact_full"] = out["surrogate_fallback"]["qps"] / out["exact_full"]["qps"]
@@ -415,19 +429,19 @@ def run_surrogate(a, dev, big=None):
     p = _params(sc)
     s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
     s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
-    s.set_surrogate(mlp, info["f_scale"], info["threshold"])
+    s.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
     modes = {"exact_full": SPH_BOID_EXACT, "exact_local": SPH_BOID_EXACT_LOCAL, "surrogate": SPH_BOID_SURROGATE,
-             "surrogate_fallback": SPH_BOID_SURROGATE_FALLBACK}
+             "surrogate_fallback": SPH_BOID_SURROGATE_FALLBACK, HEAD_ONLY: SPH_BOID_SURROGATE_FALLBACK}
     n_states = 64
-    ms, got, fall = _time_modes(s, modes, n_states, a.warmup)
+    ms, got, fall = _time_modes(s, modes, n_states, a.warmup, mlp.bounds)
     out = {"workload": "65,536 boid-force queries: 64 states x 1,024 boids of a 262,144-particle column run",
            "training": info, "queries": n_states * s.n_boid}
     out.update(_mode_report(surrogate, ms, got, fall, n_states * s.n_boid, n_states))
     if big is not None:
         # distribution shift: the settled 2M-particle tank and its 16,384 boids
-        big.set_surrogate(mlp, info["f_scale"], info["threshold"])
+        big.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
         nb = 4
-        ms, got, fall = _time_modes(big, modes, nb, 1)
+        ms, got, fall = _time_modes(big, modes, nb, 1, mlp.bounds)
         out["large_tank"] = {"workload": f"{nb * big.n_boid:,} queries: {nb} states x {big.n_boid:,} boids of the "
                                          "settled 2,097,152-particle tank (trained on the column: a shift)",
                              "queries": nb * big.n_boid}

@@ -230,11 +230,16 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream);
 /*
  * Stencil features of every boid for the CURRENT state (the surrogate's
  * input): x_out holds n_boid rows of SPH_MLP_IN BF16 (device, 16-byte
- * aligned).  Row b: the 4 x 4 x 4 cells of the particle grid from
- * c0 = floor((p_b - box_min) / cell_size - 1.5) per axis; cell q = (iz * 4 +
- * iy) * 4 + ix gives columns 4q .. 4q+3 = (fluid particles in the cell *
- * mass / (cell_size^3 rho0), their mean velocity); columns 256 .. 258 are
- * the boid's velocity; the rest zero.  Errors: SPH_ERR_ARG, SPH_ERR_STATE,
+ * aligned).  Row b: the 4 x 4 x 4 cells of size h of a grid anchored at
+ * box_min, from c0 = floor((p_b - box_min) / h - 1.5) per axis; cell
+ * q = (iz * 4 + iy) * 4 + ix gives columns 4q .. 4q+3 = (fluid particles in
+ * the cell * mass / (h^3 rho0), their mean velocity); columns 256 .. 258:
+ * the boid's velocity; 259 .. 261: its offset from the stencil's centre,
+ * (p_b - box_min) / h - c0 - 2; 262: the density of its attached particle
+ * / rho0; 263: S0 = m / (rho0 h^3) sum (1 - q); 264 .. 266: S1 = m / (rho0
+ * h^3) sum (1 - q) (v_j - v_b); 267 .. 269: S2 = m / (rho0 h^3) sum
+ * (1 - q)^2 (p_b - x_j) / r, over the fluid particles j within h
+ * (q = r / h); 270, 271: zero.  Errors: SPH_ERR_ARG, SPH_ERR_STATE,
  * SPH_ERR_CUDA.
  */
 int sph_features(sph_handle* h, void* x_out, void* stream);
@@ -247,6 +252,14 @@ int sph_features(sph_handle* h, void* x_out, void* stream);
  */
 typedef struct sph_mlp sph_mlp;
 int sph_set_surrogate(sph_handle* h, sph_mlp* m, float f_scale, float log_err_max);
+/*
+ * Input range of the surrogate (the gate's out-of-range check): with lo and
+ * hi set (device, SPH_MLP_IN floats each, the caller's; NULL turns the
+ * check off), a boid any of whose features lies outside [lo, hi] is flagged
+ * for the exact path like one whose error head is too high.  Errors:
+ * SPH_ERR_ARG (only one of lo, hi given).
+ */
+int sph_set_surrogate_bounds(sph_handle* h, const float* lo, const float* hi);
 
 /*
  * Copy one field of the most recent step (SPH_FIELD_*) to `out` (device,

@@ -63,6 +63,7 @@ struct sph_handle {
     int nb_pad;
     sph_mlp* mlp;
     float f_scale, log_err_max;
+    const float *feat_lo, *feat_hi;  // the caller's input range (NULL: no check)
     bool has_state, keys_ready, has_step;
     long long launches;
     cudaStream_t last_stream;
@@ -876,6 +877,15 @@ int sph_set_surrogate(sph_handle* h, sph_mlp* m, float f_scale, float log_err_ma
     return SPH_OK;
 }
 
+int sph_set_surrogate_bounds(sph_handle* h, const float* lo, const float* hi)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if ((lo == nullptr) != (hi == nullptr)) return fail(h, SPH_ERR_ARG, "give both lo and hi, or neither");
+    h->feat_lo = lo;
+    h->feat_hi = hi;
+    return SPH_OK;
+}
+
 int sph_features(sph_handle* h, void* x_out, void* stream)
 {
     if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
@@ -938,8 +948,8 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
                                 &h->launches));
     rc = sph_mlp_forward(h->mlp, h->feat, h->nb_pad, h->yout, stream);
     if (rc != SPH_OK) return fail(h, rc, "surrogate forward: %s", sph_last_error(nullptr));
-    CUDA_TRY(h, launch_surrogate_out(h->yout, h->n_boid, h->f_scale, h->log_err_max, out, h->bflag, h->err + 1, s,
-                                     &h->launches));
+    CUDA_TRY(h, launch_surrogate_out(h->yout, h->feat, h->feat_lo, h->feat_hi, h->n_boid, h->f_scale, h->log_err_max,
+                                     out, h->bflag, h->err + 1, s, &h->launches));
     if (mode == SPH_BOID_SURROGATE_FALLBACK) return exact_local(h, h->bflag, out, s);
     return SPH_OK;
 }

@@ -294,26 +294,54 @@ cudaError_t launch_compact_needed(const unsigned char* need, int n, int* list, u
 
 // Network output y [nb][16] -> forces: F_b = y[0:3] * f_scale, w = 0; the
 // boid is flagged for the exact path (flag = 1) where the error head
-// y[3] (log10 of the expected relative error) exceeds log_err_max or the
-// output is not finite.
-__global__ void k_surrogate_out(const float* __restrict__ y, int nb, float f_scale, float log_err_max,
-                                float4* __restrict__ out, int* __restrict__ flag, unsigned* __restrict__ nflag)
+// y[3] (log10 of the expected relative error) exceeds log_err_max, the
+// output is not finite, or (lo, hi given) a feature lies outside [lo, hi].
+// A warp per boid: the lanes test the row's 34 chunks of 8 BF16 features.
+constexpr int SO_THREADS = 256;
+
+__global__ void __launch_bounds__(SO_THREADS) k_surrogate_out(
+    const float* __restrict__ y, const __nv_bfloat16* __restrict__ x, const float* __restrict__ lo,
+    const float* __restrict__ hi, int nb, float f_scale, float log_err_max, float4* __restrict__ out,
+    int* __restrict__ flag, unsigned* __restrict__ nflag)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+    const int b = (int)(((size_t)blockIdx.x * SO_THREADS + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;  // the whole warp
+    bool oob = false;
+    if (lo) {
+        static_assert(SPH_MLP_IN % 8 == 0, "rows are whole 16-byte chunks");
+        const uint4* row = reinterpret_cast<const uint4*>(x + (size_t)b * SPH_MLP_IN);
+        for (int c = lane; c < SPH_MLP_IN / 8; c += 32) {
+            const uint4 v = __ldg(row + c);
+            const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                // BF16 -> FP32 is the high half of the word
+                const float a = __uint_as_float(w[j] << 16), e = __uint_as_float(w[j] & 0xffff0000u);
+                const int k = c * 8 + 2 * j;
+                oob |= !(a >= __ldg(lo + k) && a <= __ldg(hi + k));
+                oob |= !(e >= __ldg(lo + k + 1) && e <= __ldg(hi + k + 1));
+            }
+        }
+        oob = __any_sync(0xffffffffu, oob);
+    }
+    if (lane != 0) return;
     const float* r = y + (size_t)b * SPH_MLP_OUT;
     const float fx = r[0] * f_scale, fy = r[1] * f_scale, fz = r[2] * f_scale;
-    const bool bad = !(r[3] <= log_err_max) || !isfinite(fx) || !isfinite(fy) || !isfinite(fz);
+    const bool bad = oob || !(r[3] <= log_err_max) || !isfinite(fx) || !isfinite(fy) || !isfinite(fz);
     out[b] = make_float4(fx, fy, fz, 0.0f);
     flag[b] = bad ? 1 : 0;
     if (bad && nflag) atomicAdd(nflag, 1u);
 }
 
-cudaError_t launch_surrogate_out(const float* y, int nb, float f_scale, float log_err_max, float4* out, int* flag,
-                                 unsigned* nflag, cudaStream_t s, long long* launches)
+cudaError_t launch_surrogate_out(const float* y, const void* x, const float* lo, const float* hi, int nb,
+                                 float f_scale, float log_err_max, float4* out, int* flag, unsigned* nflag,
+                                 cudaStream_t s, long long* launches)
 {
     if (nb <= 0) return cudaSuccess;
-    k_surrogate_out<<<(nb + 255) / 256, 256, 0, s>>>(y, nb, f_scale, log_err_max, out, flag, nflag);
+    const int per_block = SO_THREADS / 32;
+    k_surrogate_out<<<(nb + per_block - 1) / per_block, SO_THREADS, 0, s>>>(
+        y, (const __nv_bfloat16*)x, lo, hi, nb, f_scale, log_err_max, out, flag, nflag);
     ++*launches;
     return cudaGetLastError();
 }

@@ -381,8 +381,9 @@ cudaError_t launch_mark_needed(const float4* pos, const unsigned* start, const S
 // is reset first.
 cudaError_t launch_compact_needed(const unsigned char* need, int n, int* list, unsigned* len, cudaStream_t s,
                                   long long* launches);
-cudaError_t launch_surrogate_out(const float* y, int nb, float f_scale, float log_err_max, float4* out, int* flag,
-                                 unsigned* nflag, cudaStream_t s, long long* launches);
+cudaError_t launch_surrogate_out(const float* y, const void* x, const float* lo, const float* hi, int nb,
+                                 float f_scale, float log_err_max, float4* out, int* flag, unsigned* nflag,
+                                 cudaStream_t s, long long* launches);
 
 // Set the message that sph_last_error(NULL) returns on this thread.
 void set_handleless_error(const char* msg);

@@ -88,6 +88,7 @@ _sig = {
     "sph_debug_gemm": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
     "sph_features": (_i, [_vp, _vp, _vp]),
     "sph_set_surrogate": (_i, [_vp, _vp, ctypes.c_float, ctypes.c_float]),
+    "sph_set_surrogate_bounds": (_i, [_vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _fn = getattr(_lib, _name)
@@ -218,6 +219,10 @@ def sph_features(h, x_ptr, stream: int):
 
 def sph_set_surrogate(h, mlp_handle, f_scale: float, log_err_max: float):
     _check(_lib.sph_set_surrogate(h, mlp_handle, float(f_scale), float(log_err_max)), h)
+
+
+def sph_set_surrogate_bounds(h, lo, hi):
+    _check(_lib.sph_set_surrogate_bounds(h, lo, hi), h)
 
 
 def sph_get_fields(h, field: int, out_ptr: int, on_host: int, stream: int):
@@ -545,9 +550,24 @@ class Scene:
         sph_features(self.handle, x.data_ptr() if x.numel() else None, self.stream)
         return x
 
-    def set_surrogate(self, mlp, f_scale: float, log_err_max: float):
+    def set_surrogate(self, mlp, f_scale: float, log_err_max: float, bounds=None):
+        """Attach the surrogate network; bounds = (lo, hi), SPH_MLP_IN floats
+        each, turns on the gate's input-range check (None: off)."""
         self._mlp = mlp
         sph_set_surrogate(self.handle, mlp.handle if mlp is not None else None, f_scale, log_err_max)
+        self.set_surrogate_bounds(bounds)
+
+    def set_surrogate_bounds(self, bounds):
+        t = self.torch
+        if bounds is None:
+            self._bounds = None
+            sph_set_surrogate_bounds(self.handle, None, None)
+            return
+        lo, hi = (t.as_tensor(v, dtype=t.float32).to(self.device).contiguous() for v in bounds)
+        if lo.numel() != SPH_MLP_IN or hi.numel() != SPH_MLP_IN:
+            raise ValueError(f"bounds need {SPH_MLP_IN} floats each")
+        self._bounds = (lo, hi)  # the library keeps the pointers
+        sph_set_surrogate_bounds(self.handle, lo.data_ptr(), hi.data_ptr())
 
     def neighbors(self, lists: bool = True):
         t = self.torch

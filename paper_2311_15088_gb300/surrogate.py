@@ -12,7 +12,8 @@ MLP forward / backward / Adam); this module only schedules them:
    |F_pred - F| / max(|F|, 0.05 F_scale).
 4. ``calibrate``: the largest error-head threshold whose fallback keeps the
    aggregate error ||F_used - F||_2 / ||F||_2 of the held-out pairs at or
-   below the target (5 %).
+   below the target (5 %); queries with a feature outside the training
+   range (widened by a margin, ``input_bounds``) always fall back.
 5. ``evaluate``: that aggregate error, the per-query relative errors and the
    fallback fraction on fresh queries.
 """
@@ -144,35 +145,67 @@ def aggregate_error(F_used, F) -> float:
     return float((F_used - F).double().norm() / F.double().norm().clamp_min(1e-30))
 
 
-def calibrate(mlp: Mlp, Xv, Fv, f_scale: float, target: float = 0.05):
+BOUND_MARGIN = 0.1
+
+
+def input_bounds(X, margin: float = BOUND_MARGIN):
+    """The gate's input range: per feature, the [min, max] of the training
+    inputs X widened by ``margin`` times its width on both sides (FP32,
+    SPH_MLP_IN values each)."""
+    x = X.float()
+    lo, hi = x.min(0).values, x.max(0).values
+    w = (hi - lo) * margin
+    return (lo - w).contiguous(), (hi + w).contiguous()
+
+
+def out_of_range(X, bounds):
+    """Queries with a feature outside ``bounds`` (None: no query)."""
+    import torch
+
+    if bounds is None:
+        return torch.zeros(X.shape[0], dtype=torch.bool, device=X.device)
+    lo, hi = bounds
+    x = X.float()
+    return ((x < lo) | (x > hi)).any(1)
+
+
+def calibrate(mlp: Mlp, Xv, Fv, f_scale: float, target: float = 0.05, bounds=None):
     """Largest threshold t on the error head (queries with head > t fall
-    back to the exact force) keeping the aggregate error <= target.
-    Returns (t, fallback fraction, aggregate error) on the held-out set."""
+    back to the exact force; so do those out of ``bounds``) keeping the
+    aggregate error <= target.  Returns (t, fallback fraction, aggregate
+    error) on the held-out set."""
     import torch
 
     Fp, head = predict(mlp, Xv, f_scale)
-    order = torch.argsort(head, descending=True)
+    forced = out_of_range(Xv, bounds)
+    nf = int(forced.sum().item())
+    # out-of-range queries fall back whatever t is: order them first
+    order = torch.argsort(torch.where(forced, torch.full_like(head, float("inf")), head), descending=True)
     # fall back on the k queries with the largest head, k = 0 .. N
     d2 = (Fp - Fv).double().pow(2).sum(1)[order]
     total = Fv.double().pow(2).sum()
     remaining = d2.sum() - torch.cat([torch.zeros(1, dtype=torch.float64, device=d2.device), torch.cumsum(d2, 0)])
     err = (remaining.clamp_min(0) / total).sqrt()
     ok = torch.nonzero(err <= target)
-    k = int(ok[0].item()) if len(ok) else len(d2)
+    k = max(int(ok[0].item()) if len(ok) else len(d2), nf)
     hs = head[order]
-    t = float(hs[k - 1].item()) - 1e-6 if k > 0 else float(hs[0].item()) + 1.0
-    if k < len(hs):
-        t = float(0.5 * (hs[k - 1] + hs[k]).item()) if k > 0 else float(hs[0].item()) + 1e-3
+    if k >= len(hs):
+        t = float(head.min().item()) - 1e-3
+    elif k > nf:
+        t = float(0.5 * (hs[k - 1] + hs[k]).item())
+    else:
+        t = float(hs[k].item()) + 1e-3  # no query in range falls back
     return t, k / len(hs), float(err[k].item())
 
 
-def evaluate(mlp: Mlp, X, F, f_scale: float, threshold: float) -> dict:
+def evaluate(mlp: Mlp, X, F, f_scale: float, threshold: float, bounds=None) -> dict:
     """Aggregate and per-query errors of the surrogate alone and with the
-    fallback at ``threshold`` on queries (X, F)."""
+    fallback at ``threshold`` (and out of ``bounds``) on queries (X, F)."""
     import torch
 
     Fp, head = predict(mlp, X, f_scale)
-    fall = head > threshold
+    oor = out_of_range(X, bounds)
+    fall = (head > threshold) | oor
     used = torch.where(fall[:, None], F, Fp)
     r = rel_errors(Fp, F, f_scale).cpu().numpy()
     return {
@@ -182,6 +215,7 @@ def evaluate(mlp: Mlp, X, F, f_scale: float, threshold: float) -> dict:
         "aggregate_error_zero_predictor": 1.0,
         "aggregate_error_mean_predictor": aggregate_error(F.mean(0, keepdim=True).expand_as(F), F),
         "fallback_fraction": float(fall.float().mean().item()),
+        "out_of_range_fraction": float(oor.float().mean().item()),
         "rel_error_median": float(np.median(r)),
         "rel_error_p90": float(np.percentile(r, 90)),
     }
@@ -189,7 +223,7 @@ def evaluate(mlp: Mlp, X, F, f_scale: float, threshold: float) -> dict:
 
 def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=120, batch=2048, lr=1e-3,
                     device="cuda", target=0.045, seed=0, head_epochs=10, zero_cols=None, pairs=None,
-                    return_pairs=False):
+                    return_pairs=False, bound_margin=BOUND_MARGIN):
     """Log training pairs (one run of ``steps`` steps per training seed of
     make_scene) and held-out pairs (validation seeds), train the network,
     fit the error head and calibrate the fallback threshold for an
@@ -197,8 +231,10 @@ def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=120, ba
     margin under the 5 % goal for queries the calibration has not seen).  ``zero_cols`` (a slice) blanks feature
     columns in every pair (an ablation; such a network is for Python-side
     evaluation only, since the library's features fill them).  ``pairs``
-    reuses logged (X, F, Xv, Fv).  Returns (mlp, info), plus the pairs when
-    ``return_pairs``."""
+    reuses logged (X, F, Xv, Fv).  The gate's input range is the training
+    range widened by ``bound_margin`` (None: no range check); it is
+    ``mlp.bounds``, for Scene.set_surrogate.  Returns (mlp, info), plus the
+    pairs when ``return_pairs``."""
     import time
 
     import torch
@@ -223,8 +259,11 @@ def build_and_train(make_scene, train_seeds, val_seeds, steps=64, epochs=120, ba
     fit_error_head(mlp, Xv, Fv, fs, epochs=head_epochs, batch=batch)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    thr, frac, err = calibrate(mlp, Xv, Fv, fs, target)
-    info = {"train_pairs": int(X.shape[0]), "val_pairs": int(Xv.shape[0]), "f_scale": fs,
+    mlp.bounds = input_bounds(X, bound_margin) if bound_margin is not None else None
+    thr, frac, err = calibrate(mlp, Xv, Fv, fs, target, mlp.bounds)
+    info = {"bound_margin": bound_margin,
+            "val_out_of_range_fraction": float(out_of_range(Xv, mlp.bounds).float().mean().item()),
+            "train_pairs": int(X.shape[0]), "val_pairs": int(Xv.shape[0]), "f_scale": fs,
             "epochs": epochs, "batch": batch, "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
             "threshold": thr, "val_fallback_fraction": frac, "val_aggregate_error": err,
             "train_aggregate_error": aggregate_error(predict(mlp, X[:262144], fs)[0], F[:262144]),

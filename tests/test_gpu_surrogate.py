@@ -4,7 +4,7 @@ import pytest
 import torch
 
 from oracle.features import stencil_features
-from paper_2311_15088_gb300 import scenes, surrogate
+from paper_2311_15088_gb300 import scenes, sph, surrogate
 from paper_2311_15088_gb300.sph import (SPH_BOID_EXACT, SPH_BOID_EXACT_LOCAL, SPH_BOID_SURROGATE,
                                         SPH_BOID_SURROGATE_FALLBACK, Mlp, Scene)
 
@@ -69,6 +69,34 @@ def test_fallback_takes_exact_forces_for_flagged_boids():
     assert 0 < int(flag.sum()) < len(flag)
     assert torch.equal(mixed[flag, :3], exact[flag, :3]) and torch.all(mixed[flag, 3] == 1)
     assert torch.equal(mixed[~flag, :3], sur[~flag, :3]) and torch.all(mixed[~flag, 3] == 0)
+
+
+def test_fallback_flags_features_out_of_range():
+    sc = _boids_in_fluid()
+    s = _scene(sc)
+    m = Mlp(512)
+    m.set_params(torch.from_numpy(surrogate.init_params(5)))
+    exact = s.boid_forces(SPH_BOID_EXACT)
+    x = s.features().float()
+    lo, hi = x.min(0).values.clone(), x.max(0).values.clone()
+    s.set_surrogate(m, 3.0, 1e9, (lo, hi))      # the boids' own range: none out
+    s.boid_forces(SPH_BOID_SURROGATE_FALLBACK)
+    assert int(s.field("fallback").sum()) == 0
+    # the density column capped at its median, a velocity column floored
+    hi[262] = torch.median(x[:, 262])
+    lo[257] = torch.median(x[:, 257])
+    s.set_surrogate_bounds((lo, hi))
+    mixed = s.boid_forces(SPH_BOID_SURROGATE_FALLBACK)
+    flag = s.field("fallback").bool()
+    expect = (x[:, 262] > hi[262]) | (x[:, 257] < lo[257])
+    assert torch.equal(flag, expect) and 0 < int(flag.sum()) < len(flag)
+    assert torch.equal(mixed[flag, :3], exact[flag, :3])
+    assert torch.equal(flag, surrogate.out_of_range(s.features(), (lo, hi)))
+    s.set_surrogate_bounds(None)
+    s.boid_forces(SPH_BOID_SURROGATE_FALLBACK)
+    assert int(s.field("fallback").sum()) == 0
+    with pytest.raises(RuntimeError):
+        sph.sph_set_surrogate_bounds(s.handle, lo.data_ptr(), None)
 
 
 def test_trained_surrogate_beats_no_network():
