@@ -76,7 +76,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("large", "column", "small"), default="large")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end leg (default: the K timed steps, from the same state)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="approximate CPU time of the oracle baseline sample")
     ap.add_argument("--reference-budget", type=float, default=150.0,
@@ -642,7 +643,7 @@ def run_ours(a):
     # and downloads the new state
     host = [t.cpu().pin_memory() for t in start_state]
     torch.cuda.synchronize(dev)
-    n_e2e = min(a.e2e_steps, a.steps)
+    n_e2e = a.steps if a.e2e_steps is None else min(a.e2e_steps, a.steps)
     t0 = time.perf_counter()
     for _ in range(n_e2e):
         s.set_state_host(*host)

@@ -27,6 +27,7 @@ struct sph_handle {
     int ncells, nbcells;      // totals over the scenes
     // state (storage order) and the sorted scratch copy
     float4 *pos, *vel, *pos_s, *vel_s;
+    float* soa;               // pos_s as three float arrays (x, y, z), soa_stride(n) each
     unsigned *key, *rank;
     int* tmp;
     unsigned *count, *cell_start, *scan_part;
@@ -268,6 +269,7 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->vel = cv.take<float4>(n);
     h->pos_s = cv.take<float4>(n);
     h->vel_s = cv.take<float4>(n);
+    h->soa = cv.take<float>(3 * soa_stride(n));
     h->key = cv.take<unsigned>(n);
     h->rank = cv.take<unsigned>(n);
     h->tmp = cv.take<int>(n > C ? n : C);
@@ -728,6 +730,12 @@ int sph_get_state(sph_handle* h, float* fluid_pos4, float* fluid_vel4, float* bo
     return SPH_OK;
 }
 
+static SoaPos soa_of(const sph_handle* h)
+{
+    const size_t st = soa_stride((size_t)h->n);
+    return SoaPos{h->soa, h->soa + st, h->soa + 2 * st};
+}
+
 // Keys (if needed), scan, scatter and per-cell sort + gather of the state
 // into the sorted scratch arrays.  consume = true zeroes the counts for the
 // next step's keys.
@@ -750,6 +758,7 @@ static int bin_state(sph_handle* h, cudaStream_t s, bool consume)
     CUDA_TRY(h, launch_cellsort_slots(h->cell_start, h->key, h->n, h->ncells, h->tmp, h->pos, h->vel, h->pos_s,
                                       h->vel_s, h->n_boid, h->slot_of_boid, h->big_list, h->big_count, s,
                                       &h->launches));
+    CUDA_TRY(h, launch_soa(h->pos_s, h->n, h->soa, s, &h->launches));
     prof_end(h, s);
     if (consume) {
         CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)h->ncells * sizeof(unsigned), s));
@@ -764,7 +773,7 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
     int rc = bin_state(h, s, true);
     if (rc != SPH_OK) return rc;
     prof_begin(h, SPH_KIND_DENSITY, s);
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, nullptr,
+    CUDA_TRY(h, launch_density(h->pos_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, nullptr,
                                nullptr, h->err, s, &h->launches));
     prof_end(h, s);
     if (h->list) {
@@ -775,7 +784,7 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
         prof_end(h, s);
     }
     prof_begin(h, SPH_KIND_FORCES, s);
-    CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+    CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
                               h->list, h->noff, h->list_cap, true, h->slot_of_boid, nullptr, h->fb, h->acc,
                               h->touched, h->infl, h->pos, h->vel, h->key, h->rank, h->count, h->err, s,
                               &h->launches));
@@ -911,9 +920,9 @@ static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_
     CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
     CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, h->slot_of_boid, bmask, h->need, s, &h->launches));
     CUDA_TRY(h, launch_compact_needed(h->need, h->n, h->need_list, h->need_len, s, &h->launches));
-    CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
+    CUDA_TRY(h, launch_density(h->pos_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
                                h->need_list, h->need_len, h->err, s, &h->launches));
-    CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+    CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
                               nullptr, nullptr, 0, false, h->slot_of_boid, bmask, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                               nullptr, nullptr, h->err, s, &h->launches));
     return SPH_OK;
@@ -935,9 +944,9 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
     float4* out = (float4*)out_f4;
     h->has_step = false;
     if (mode == SPH_BOID_EXACT) {
-        CUDA_TRY(h, launch_density(h->pos_s, h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
+        CUDA_TRY(h, launch_density(h->pos_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
                                    nullptr, nullptr, h->err, s, &h->launches));
-        CUDA_TRY(h, launch_forces(h->pos_s, h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+        CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
                                   nullptr, nullptr, 0, false, h->slot_of_boid, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
                                   nullptr, nullptr, nullptr, h->err, s, &h->launches));
         return SPH_OK;

@@ -324,6 +324,20 @@ cudaError_t launch_slot_keys(const unsigned* start, int ncells, unsigned* slot_k
 // Candidate bits the density pass keeps per particle for the force pass.
 constexpr int NBR_WORDS = 64;
 
+// The sorted positions once more as three float arrays (x, y, z of slot j
+// at x[j], y[j], z[j]; 8-byte aligned, so slots 2k, 2k + 1 load as one
+// float2 per axis): the candidate tests of the neighbour passes read two
+// candidates per load and test them with packed float32x2 arithmetic.
+struct SoaPos {
+    const float* __restrict__ x;
+    const float* __restrict__ y;
+    const float* __restrict__ z;
+};
+// Elements per axis of the SoA copy of n positions (even).
+__host__ __device__ inline size_t soa_stride(size_t n) { return (n + 1) & ~(size_t)1; }
+// soa[axis * soa_stride(n) + j] = pos[j].{x, y, z}
+cudaError_t launch_soa(const float4* pos, int n, float* soa, cudaStream_t s, long long* launches);
+
 // Launch shape of the neighbour passes (chosen by the autotuner; results do
 // not depend on it).
 struct Tuning {
@@ -335,7 +349,7 @@ struct Tuning {
 // words per particle, word-interleaved; ncand: candidates per particle).
 // list (may be NULL = every particle) restricts the pass to the sorted
 // slots list[0 .. *list_len) (device memory, built on the device).
-cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
+cudaError_t launch_density(const float4* pos, const SoaPos& xyz, const unsigned* start, const Scenes& sc, const Tuning& t,
                            float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const int* list,
                            const unsigned* list_len, unsigned* err, cudaStream_t s, long long* launches);
 // The step's force pass: F_b of every boid (bmask NULL) or of the boids with
@@ -343,7 +357,7 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const Scene
 // attached slot when acc is given; with fluid = true also every fluid
 // particle, integrated into pos_next/vel_next with the next keys emitted
 // (attached particles get touched = 0, influence = 0).  One launch.
-cudaError_t launch_forces(const float4* pos, const float4* vel, const float* rho, const float2* ab,
+cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
                           const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
                           bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,

@@ -37,7 +37,8 @@ namespace sphk {
 // subtracts the self pair (always visited: r2 = 0) at the end; the sums
 // take the same terms in the same order as the attached particles' loop.
 template <bool STREAM>
-__device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos, const unsigned* __restrict__ start,
+__device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos, const SoaPos& xyz,
+                                           const unsigned* __restrict__ start,
                                            const Scenes& sc, float* __restrict__ rho, float2* __restrict__ ab,
                                            int* __restrict__ nbr, unsigned* __restrict__ bits,
                                            int* __restrict__ ncand, unsigned* __restrict__ err)
@@ -54,6 +55,10 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
     RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
     unsigned s0, s1;
     if (!STREAM && !att_i) {
+        // candidates in slot order: an odd first slot alone, then slot
+        // pairs (2k, 2k + 1) from the SoA copy, tested side by side with
+        // packed float32x2 operations (each component rounded exactly as
+        // the scalar form), then an odd last slot alone
         auto take = [&](const float4& pj) {
             const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
             if (r2 < h2) {
@@ -62,19 +67,46 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
                 ++cnt;
             }
         };
+        // x_j - x_i as x_j + (-x_i) and h2 - r2 as fma(r2, -1, h2): the
+        // same roundings as the subtractions
+        const float2 nx2 = make_float2(-pi.x, -pi.x), ny2 = make_float2(-pi.y, -pi.y), nz2 = make_float2(-pi.z, -pi.z);
+        const float2 h22 = make_float2(h2, h2), m11 = make_float2(-1.0f, -1.0f);
+        auto take2 = [&](float2 X, float2 Y, float2 Z) {
+            const float2 dx = __fadd2_rn(X, nx2), dy = __fadd2_rn(Y, ny2), dz = __fadd2_rn(Z, nz2);
+            const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+            const float2 t = __ffma2_rn(r2, m11, h22);
+            const float2 tt = __fmul2_rn(t, t);
+            if (r2.x < h2) {
+                sum = fmaf(tt.x, t.x, sum);
+                ++cnt;
+            }
+            if (r2.y < h2) {
+                sum = fmaf(tt.y, t.y, sum);
+                ++cnt;
+            }
+        };
+        const float2* __restrict__ X2 = reinterpret_cast<const float2*>(xyz.x);
+        const float2* __restrict__ Y2 = reinterpret_cast<const float2*>(xyz.y);
+        const float2* __restrict__ Z2 = reinterpret_cast<const float2*>(xyz.z);
         while (walk.next(s0, s1)) {
             nc += (int)(s1 - s0);
-            // four candidate loads in flight per iteration, taken in order
-            const float4* p = pos + s0;
-            const float4* e = pos + s1;
-            for (; p + 4 <= e; p += 4) {
-                const float4 a0 = __ldg(p), a1 = __ldg(p + 1), a2 = __ldg(p + 2), a3 = __ldg(p + 3);
-                take(a0);
-                take(a1);
-                take(a2);
-                take(a3);
+            unsigned j = s0;
+            if (j & 1u) take(__ldg(pos + j++));
+            const unsigned e = s1 & ~1u;
+            // two slot pairs (four candidates) in flight per iteration
+            for (; j + 4 <= e; j += 4) {
+                const unsigned k = j >> 1;
+                const float2 xa = __ldg(X2 + k), ya = __ldg(Y2 + k), za = __ldg(Z2 + k);
+                const float2 xb = __ldg(X2 + k + 1), yb = __ldg(Y2 + k + 1), zb = __ldg(Z2 + k + 1);
+                take2(xa, ya, za);
+                take2(xb, yb, zb);
             }
-            for (; p < e; ++p) take(__ldg(p));
+            if (j < e) {
+                const unsigned k = j >> 1;
+                take2(__ldg(X2 + k), __ldg(Y2 + k), __ldg(Z2 + k));
+                j += 2;
+            }
+            if (j < s1) take(__ldg(pos + j));
         }
         --cnt;  // the particle itself
     } else {
@@ -113,13 +145,33 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
 
 // Every particle (thread i = slot i).
 template <bool STREAM>
-__global__ void __launch_bounds__(512)
-k_density(const float4* __restrict__ pos, const unsigned* __restrict__ start, Scenes sc,
+__global__ void __launch_bounds__(512, 3)
+k_density(const float4* __restrict__ pos, SoaPos xyz, const unsigned* __restrict__ start, Scenes sc,
           float* __restrict__ rho, float2* __restrict__ ab, int* __restrict__ nbr, unsigned* __restrict__ bits,
           int* __restrict__ ncand, unsigned* __restrict__ err)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < sc.n_all) density_at<STREAM>(t, pos, start, sc, rho, ab, nbr, bits, ncand, err);
+    if (t < sc.n_all) density_at<STREAM>(t, pos, xyz, start, sc, rho, ab, nbr, bits, ncand, err);
+}
+
+// soa[axis * stride + j] = pos[j].{x, y, z}
+__global__ void __launch_bounds__(256)
+k_soa(const float4* __restrict__ pos, int n, size_t stride, float* __restrict__ soa)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float4 p = pos[j];
+    soa[j] = p.x;
+    soa[stride + j] = p.y;
+    soa[2 * stride + j] = p.z;
+}
+
+cudaError_t launch_soa(const float4* pos, int n, float* soa, cudaStream_t s, long long* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_soa<<<(n + 255) / 256, 256, 0, s>>>(pos, n, soa_stride((size_t)n), soa);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 // Only the slots of a list whose length the device holds (the list is built
@@ -184,7 +236,7 @@ k_density_list(const float4* __restrict__ pos, const unsigned* __restrict__ star
     }
 }
 
-cudaError_t launch_density(const float4* pos, const unsigned* start, const Scenes& sc, const Tuning& t,
+cudaError_t launch_density(const float4* pos, const SoaPos& xyz, const unsigned* start, const Scenes& sc, const Tuning& t,
                            float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const int* list,
                            const unsigned* list_len, unsigned* err, cudaStream_t s, long long* launches)
 {
@@ -194,9 +246,9 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const Scene
         const int blocks = (sc.n_all + 7) / 8 < 152 * 16 ? (sc.n_all + 7) / 8 : 152 * 16;  // 8 warps each
         k_density_list<<<blocks, 256, 0, s>>>(pos, start, sc, rho, ab, nbr, ncand, list, list_len, err);
     } else if (t.use_stream) {
-        k_density<true><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, err);
+        k_density<true><<<all, t.block, 0, s>>>(pos, xyz, start, sc, rho, ab, nbr, bits, ncand, err);
     } else {
-        k_density<false><<<all, t.block, 0, s>>>(pos, start, sc, rho, ab, nbr, bits, ncand, err);
+        k_density<false><<<all, t.block, 0, s>>>(pos, xyz, start, sc, rho, ab, nbr, bits, ncand, err);
     }
     ++*launches;
     return cudaGetLastError();
@@ -206,27 +258,47 @@ cudaError_t launch_density(const float4* pos, const unsigned* start, const Scene
 
 // f_ij = m/rho_j [ C_p (p_i + p_j)/2 (1-q)^2/q r_ij - C_v mu (1-q) v_ij ],
 // r_ij = x_i - x_j, v_ij = v_i - v_j; a_i = (1/rho_i) sum_j f_ij (+ g).
-// d = x_j - x_i (float32), r2 its squared norm, ab_j = (m / rho_j, p_j).
+// d = x_j - x_i (float32; x and y packed), r2 its squared norm,
+// ab_j = (m / rho_j, p_j).  Every operation is rounded once, in the order
+// written (intrinsics, no contraction), and every caller (the force pass,
+// the boids' F_b, the list and stream variants) uses this one function,
+// so a pair contributes the same bits wherever it is summed.
 struct PairTerms {
     float4 pi, vi;
-    float p_i, half_cp_h, cv_mu, inv_h;
+    float p_i, n_hcp, n_cv, inv_h;  // n_hcp = -C_p h / 2, n_cv = -C_v mu
 
-    __device__ __forceinline__ void add(float dx, float dy, float dz, float r2, const float4& vj, float2 abj,
-                                        float& fx, float& fy, float& fz) const
+    __device__ __forceinline__ void set(const StepConst& c, const float4& pos_i, const float4& vel_i, float p)
+    {
+        pi = pos_i;
+        vi = vel_i;
+        p_i = p;
+        n_hcp = -c.half_cp_h;
+        n_cv = -c.cv_mu;
+        inv_h = c.inv_h;
+    }
+
+    __device__ __forceinline__ void add(float2 dxy, float dz, float r2, const float4& vj, float2 abj, float2& fxy,
+                                        float& fz) const
     {
         const float rinv = rsqrtf(r2);
-        const float q = r2 * rinv * inv_h;
-        const float omq = 1.0f - q;
-        const float m_rho_j = abj.x;
-        // pressure: C_p (p_i+p_j)/2 (1-q)^2 / q along r_ij = -(dx,dy,dz)
-        const float sp = -m_rho_j * half_cp_h * (p_i + abj.y) * omq * omq * rinv;
-        // viscosity: -C_v mu (1-q) (v_i - v_j)
-        const float sv = -m_rho_j * cv_mu * omq;
-        fx = fmaf(sp, dx, sv * (vi.x - vj.x));
-        fy = fmaf(sp, dy, sv * (vi.y - vj.y));
-        fz = fmaf(sp, dz, sv * (vi.z - vj.z));
+        const float omq = __fmaf_rn(-__fmul_rn(r2, rinv), inv_h, 1.0f);  // 1 - q
+        const float s = __fmul_rn(abj.x, omq);                          // m/rho_j (1 - q)
+        // pressure: -C_p h/2 (p_i + p_j) m/rho_j (1-q)^2 / r along d
+        const float sp = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(p_i, abj.y), n_hcp), __fmul_rn(s, omq)), rinv);
+        // viscosity: -C_v mu m/rho_j (1-q) (v_i - v_j)
+        const float sv = __fmul_rn(s, n_cv);
+        const float2 dv = __ffma2_rn(make_float2(vj.x, vj.y), make_float2(-1.0f, -1.0f), make_float2(vi.x, vi.y));
+        fxy = __ffma2_rn(make_float2(sp, sp), dxy, __fmul2_rn(make_float2(sv, sv), dv));
+        fz = __fmaf_rn(sp, dz, __fmul_rn(sv, __fsub_rn(vi.z, vj.z)));
     }
 };
+
+// x_j - x_i, y_j - y_i as one packed addition of (-x_i, -y_i): the same
+// roundings as the subtractions.
+__device__ __forceinline__ float2 dxy_of(const float4& pj, float2 nxy)
+{
+    return __fadd2_rn(make_float2(pj.x, pj.y), nxy);
+}
 
 // F_b of boid b (section "Boids and Fluid Interaction"): the acceleration
 // of its attached particle from the fluid particles within h.  One warp per
@@ -245,14 +317,11 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
     const int nb_all = sc.nb_all;
     PairTerms T;
-    T.pi = pos[i];
-    T.vi = vel[i];
-    T.p_i = ab[i].y;
-    T.half_cp_h = c.half_cp_h;
-    T.cv_mu = c.cv_mu;
-    T.inv_h = c.inv_h;
+    T.set(c, pos[i], vel[i], ab[i].y);
+    const float2 nxy = make_float2(-T.pi.x, -T.pi.y);
     const float h2 = c.h2;
-    float ax = 0.f, ay = 0.f, az = 0.f;
+    float2 axy = make_float2(0.f, 0.f);
+    float az = 0.f;
     WarpRows rows(c.g, c.wg, start + c.c_base, T.pi.x, T.pi.y, T.pi.z);
     for (int bt = 0; 32 * bt < rows.nrows; ++bt) {
         rows.batch(bt);
@@ -262,17 +331,19 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
             const unsigned j = rows.slot(k < total ? k : total - 1);
             if (k >= total) continue;
             const float4 pj = __ldg(pos + j);
-            const float dx = __fsub_rn(pj.x, T.pi.x), dy = __fsub_rn(pj.y, T.pi.y), dz = __fsub_rn(pj.z, T.pi.z);
-            const float r2 = pair_r2(dx, dy, dz);
+            const float2 dxy = dxy_of(pj, nxy);
+            const float dz = __fsub_rn(pj.z, T.pi.z);
+            const float r2 = pair_r2(dxy.x, dxy.y, dz);
             if (r2 < h2 && r2 != 0.0f && id_of(pj) >= nb_all) {
-                float fx, fy, fz;
-                T.add(dx, dy, dz, r2, __ldg(vel + j), __ldg(ab + j), fx, fy, fz);
-                ax += fx;
-                ay += fy;
-                az += fz;
+                float2 fxy;
+                float fz;
+                T.add(dxy, dz, r2, __ldg(vel + j), __ldg(ab + j), fxy, fz);
+                axy = __fadd2_rn(axy, fxy);
+                az = __fadd_rn(az, fz);
             }
         }
     }
+    float ax = axy.x, ay = axy.y;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ax += __shfl_xor_sync(FULL, ax, o);
@@ -296,7 +367,7 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
 // next step's cell keys; attached particles only record touched = 0 and
 // influence = 0 (attached pairs are excluded).
 __global__ void __launch_bounds__(512)
-k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ rho,
+k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ vel, const float* __restrict__ rho,
          const float2* __restrict__ ab, const unsigned* __restrict__ start, const unsigned* __restrict__ bits,
          const int* __restrict__ ncand, Scenes sc, int use_stream, const unsigned* __restrict__ list,
          const unsigned* __restrict__ list_off, unsigned list_cap, int boid_blocks,
@@ -320,34 +391,30 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     const bool fluid = active && id_of(pi) >= nb_all;
     const unsigned* cstart = start + c.c_base;
 
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    float bx = 0.f, by = 0.f, bz = 0.f;
+    float2 axy = make_float2(0.f, 0.f), bxy = make_float2(0.f, 0.f);
+    float az = 0.f, bz = 0.f;
     int touch = 0;
     float rho_i = 1.0f;
     bool clamped = false;
     if (fluid) {
         PairTerms T;
-        T.pi = pi;
-        T.vi = __ldg(vel + i);
+        T.set(c, pi, __ldg(vel + i), __ldg(ab + i).y);
         rho_i = __ldg(rho + i);
-        T.p_i = __ldg(ab + i).y;
-        T.half_cp_h = c.half_cp_h;
-        T.cv_mu = c.cv_mu;
-        T.inv_h = c.inv_h;
+        const float2 nxy = make_float2(-pi.x, -pi.y);
         // one neighbour j (0 < r2 < h2)
         auto pair = [&](unsigned j) {
             const float4 pj = __ldg(pos + j);
-            const float dx = __fsub_rn(pj.x, pi.x), dy = __fsub_rn(pj.y, pi.y), dz = __fsub_rn(pj.z, pi.z);
-            float fx, fy, fz;
-            T.add(dx, dy, dz, pair_r2(dx, dy, dz), __ldg(vel + j), __ldg(ab + j), fx, fy, fz);
-            ax += fx;
-            ay += fy;
-            az += fz;
+            const float2 dxy = dxy_of(pj, nxy);
+            const float dz = __fsub_rn(pj.z, pi.z);
+            float2 fxy;
+            float fz;
+            T.add(dxy, dz, pair_r2(dxy.x, dxy.y, dz), __ldg(vel + j), __ldg(ab + j), fxy, fz);
+            axy = __fadd2_rn(axy, fxy);
+            az = __fadd_rn(az, fz);
             if (id_of(pj) < nb_all) {
                 ++touch;
-                bx += fx;
-                by += fy;
-                bz += fz;
+                bxy = __fadd2_rn(bxy, fxy);
+                bz = __fadd_rn(bz, fz);
             }
         };
         RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
@@ -393,17 +460,42 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
             // test a chunk of up to 32 candidates into a bit mask, then run
             // the pair code over the set bits: the warp executes the pair
             // code max(hits) times per chunk instead of once per candidate
+            // (slot pairs from the SoA copy, as in the density pass)
             const float h2 = c.h2;
+            const float2 nx2 = make_float2(-pi.x, -pi.x), ny2 = make_float2(-pi.y, -pi.y),
+                         nz2 = make_float2(-pi.z, -pi.z);
+            const float2* __restrict__ X2 = reinterpret_cast<const float2*>(xyz.x);
+            const float2* __restrict__ Y2 = reinterpret_cast<const float2*>(xyz.y);
+            const float2* __restrict__ Z2 = reinterpret_cast<const float2*>(xyz.z);
+            auto test1 = [&](unsigned j) {
+                const float4 pj = __ldg(pos + j);
+                const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
+                return (unsigned)(r2 < h2 && r2 != 0.0f);
+            };
+            auto test2 = [&](float2 X, float2 Y, float2 Z) {
+                const float2 dx = __fadd2_rn(X, nx2), dy = __fadd2_rn(Y, ny2), dz = __fadd2_rn(Z, nz2);
+                const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+                return (unsigned)(r2.x < h2 && r2.x != 0.0f) | (unsigned)(r2.y < h2 && r2.y != 0.0f) << 1;
+            };
             while (walk.next(s0, s1)) {
                 for (unsigned base = s0; base < s1; base += 32) {
-                    const unsigned len = min(32u, s1 - base);
-                    unsigned m = 0;
-                    for (unsigned k = 0; k < len; ++k) {
-                        const float4 pj = __ldg(pos + base + k);
-                        const float r2 =
-                            pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
-                        m |= (unsigned)(r2 < h2 && r2 != 0.0f) << k;
+                    const unsigned e = min(base + 32u, s1);
+                    unsigned m = 0, j = base;
+                    if (j & 1u) m = test1(j++);
+                    const unsigned e2 = e & ~1u;
+                    for (; j + 4 <= e2; j += 4) {
+                        const unsigned k = j >> 1;
+                        const float2 xa = __ldg(X2 + k), ya = __ldg(Y2 + k), za = __ldg(Z2 + k);
+                        const float2 xb = __ldg(X2 + k + 1), yb = __ldg(Y2 + k + 1), zb = __ldg(Z2 + k + 1);
+                        m |= test2(xa, ya, za) << (j - base);
+                        m |= test2(xb, yb, zb) << (j + 2 - base);
                     }
+                    if (j < e2) {
+                        const unsigned k = j >> 1;
+                        m |= test2(__ldg(X2 + k), __ldg(Y2 + k), __ldg(Z2 + k)) << (j - base);
+                        j += 2;
+                    }
+                    if (j < e) m |= test1(j) << (j - base);
                     while (m) {
                         const int t = __ffs(m) - 1;
                         m &= m - 1u;
@@ -414,9 +506,9 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
         }
     }
     const float inv_rho = 1.0f / rho_i;
-    ax *= inv_rho;
-    ay *= inv_rho;
+    float ax = axy.x * inv_rho, ay = axy.y * inv_rho;
     az *= inv_rho;
+    const float bx = bxy.x, by = bxy.y;
 
     unsigned k_next = 0;
     if (active) {
@@ -456,7 +548,7 @@ k_forces(const float4* __restrict__ pos, const float4* __restrict__ vel, const f
     if (__any_sync(FULL, clamped) && (threadIdx.x & 31) == 0) atomicOr(err, SPH_DEV_CLAMPED);
 }
 
-cudaError_t launch_forces(const float4* pos, const float4* vel, const float* rho, const float2* ab,
+cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* vel, const float* rho, const float2* ab,
                           const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
                           const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
                           bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
@@ -469,7 +561,7 @@ cudaError_t launch_forces(const float4* pos, const float4* vel, const float* rho
     const int boid_blocks = (sc.nb_all + warps - 1) / warps;
     const int fluid_blocks = fluid ? (sc.n_all + t.block - 1) / t.block : 0;
     if (boid_blocks + fluid_blocks == 0) return cudaSuccess;
-    k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(pos, vel, rho, ab, start, bits, ncand, sc, t.use_stream,
+    k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(pos, xyz, vel, rho, ab, start, bits, ncand, sc, t.use_stream,
                                                             list, list_off, cap, boid_blocks, slot_of_boid, bmask,
                                                             fb, acc, touched, infl, pos_next, vel_next, key, rank,
                                                             count, err);
