@@ -397,6 +397,14 @@ int sph_mlp_train_step(sph_mlp* m, const void* x_bf16, const float* target, int 
 int sph_mlp_status(sph_mlp* m, unsigned* bits, void* stream);
 long long sph_mlp_launch_count(sph_mlp* m);
 /*
+ * Test hook of the activation the network's kernels use: out[i] = GELU(z[i])
+ * (grad = 0) or GELU'(z[i]) (grad = 1) for n floats in device memory, GELU
+ * the exact-erf form (z Phi(z)), erf evaluated by formula 7.1.26 of
+ * Abramowitz and Stegun (absolute error <= 1.5e-7 plus float32 rounding).
+ * Errors: SPH_ERR_ARG (NULL pointers, n < 0, grad not 0/1), SPH_ERR_CUDA.
+ */
+int sph_debug_gelu(const float* z, int n, int grad, float* out, void* stream);
+/*
  * Test hook of the tensor-core GEMM: for BF16 row-major A[M][K] (leading
  * dimension lda) and B[N][K] (ldb), both 16-byte aligned with leading
  * dimensions multiples of 8, N a multiple of 4 and C 16-byte aligned

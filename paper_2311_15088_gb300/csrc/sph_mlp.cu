@@ -49,11 +49,38 @@ struct GemmEpi {
     unsigned* err;
 };
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// erf by formula 7.1.26 of Abramowitz and Stegun, "Handbook of Mathematical
+// Functions": for x >= 0, erf x = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5))))
+// exp(-x^2) with t = 1 / (1 + p x), absolute error <= 1.5e-7; erf is odd.
+// Evaluated in float32 with the hardware reciprocal and exponential
+// approximations, which add a few 1e-7: far below the BF16 rounding of the
+// activations (2^-9 relative).  About half the instructions of the
+// library erff, and the GELU epilogue is what bounds the fused forward pass.
+__device__ __forceinline__ float erf_as(float x)
+{
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    poly *= t;
+    return copysignf(fmaf(-poly, __expf(-ax * ax), 1.0f), x);
+}
+
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative
+// Phi(z) + z phi(z), phi the standard normal density.
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
 
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+__global__ void k_debug_gelu(const float* __restrict__ z, int n, int grad, float* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = grad ? gelu_grad_f(z[i]) : gelu_f(z[i]);
 }
 
 // Epilogue, in column chunks of EC (32, or NT when NT < 32), through shared
@@ -1006,6 +1033,15 @@ int sph_mlp_status(sph_mlp* m, unsigned* bits, void* stream)
 }
 
 long long sph_mlp_launch_count(sph_mlp* m) { return m ? m->launches : 0; }
+
+int sph_debug_gelu(const float* z, int n, int grad, float* out, void* stream)
+{
+    if (!z || !out || n < 0 || (grad != 0 && grad != 1)) return mfail(nullptr, SPH_ERR_ARG, "bad GELU arguments");
+    if (n == 0) return SPH_OK;
+    k_debug_gelu<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(z, n, grad, out);
+    MLP_TRY(nullptr, cudaGetLastError());
+    return SPH_OK;
+}
 
 int sph_debug_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int splits, float* C,
                    unsigned* err, void* stream)

@@ -86,6 +86,7 @@ _sig = {
     "sph_mlp_status": (_i, [_vp, ctypes.POINTER(ctypes.c_uint), _vp]),
     "sph_mlp_launch_count": (ctypes.c_longlong, [_vp]),
     "sph_debug_gemm": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "sph_debug_gelu": (_i, [_vp, _i, _i, _vp, _vp]),
     "sph_features": (_i, [_vp, _vp, _vp]),
     "sph_set_surrogate": (_i, [_vp, _vp, ctypes.c_float, ctypes.c_float]),
     "sph_set_surrogate_bounds": (_i, [_vp, _vp, _vp]),
@@ -329,6 +330,10 @@ def sph_mlp_status(m, stream: int) -> int:
 
 def sph_mlp_launch_count(m) -> int:
     return int(_lib.sph_mlp_launch_count(m))
+
+
+def sph_debug_gelu(z_ptr, n: int, grad: int, out_ptr, stream):
+    _check(_lib.sph_debug_gelu(z_ptr, n, grad, out_ptr, stream))
 
 
 def sph_debug_gemm(a_ptr, lda, b_ptr, ldb, M, N, K, splits, c_ptr, err_ptr, stream):
