@@ -86,6 +86,7 @@ def _args():
     ap.add_argument("--batch-steps", type=int, default=30, help="timed steps of the batched-scenes leg")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-surface", action="store_true", help="skip the voxel density + marching cubes leg")
     ap.add_argument("--neighbor-lists", action="store_true",
                     help="build neighbour lists every step (pair buffer of 3x the pairs after warm-up) "
                          "and read them in the force pass instead of testing candidates")
@@ -236,6 +237,81 @@ def _neighbor_search(s, dev):
             "bucket_equals_walk": bool(torch.equal(full, exact)),
             "bucket16_ms": ms_16, "bucket16_dropped_particles": int(dropped.item()),
             "bucket16_lost_pair_fraction": 1.0 - float(c16.to(torch.float64).sum().item()) / max(pairs, 1.0)}
+
+
+# ------------------------------------------------------------ surface
+
+def _surface(s, dev, p, warmup=3, reps=10):
+    """Surface reconstruction of the current state (the paper's third stage):
+    voxel density on the corner grid over the box at spacing h/2 (R = h,
+    particle radius h/4), then marching cubes into a device triangle buffer;
+    CUDA-event times (mean of ``reps`` after ``warmup``), the voxel pass's
+    roofline against the FP32 ALU peak (9 flops per candidate tested, 20 per
+    neighbour) and the marching-cubes pass's against the HBM peak (corner
+    values read once, triangles written: compulsory bytes)."""
+    import torch
+
+    from paper_2311_15088_gb300 import sph
+
+    h = float(np.float32(p["h"]))
+    sp, R, r = float(np.float32(h * 0.5)), float(np.float32(h)), float(np.float32(h * 0.25))
+    origin, dims = sph.sph_voxel_grid(p, sp, R)
+    n = dims[0] * dims[1] * dims[2]
+    phi = torch.empty(n, dtype=torch.float32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ncubes = (dims[0] - 1) * (dims[1] - 1) * (dims[2] - 1)
+    ws_bytes = sph.sph_mc_workspace_size(dims)
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
+    ws_ptr = (ws.data_ptr() + 255) & ~255
+    cap = 4 << 20
+    tris = torch.empty((cap, 9), dtype=torch.float32, device=dev)
+    ntri = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def voxel():
+        sph.sph_voxel_density(s.handle, origin, dims, sp, R, r, phi.data_ptr(), cnt.data_ptr(), stream)
+
+    def mc():
+        sph.sph_marching_cubes(phi.data_ptr(), dims, origin, sp, 0.0, ws_ptr, ws_bytes, tris.data_ptr(), cap,
+                               ntri.data_ptr(), stream)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    ms_voxel = timed(voxel)  # includes the state's binning
+    ms_mc = timed(mc)
+    total = int(ntri.item())
+    nbrs = float(cnt.to(torch.float64).sum().item())
+    occupied = int((cnt > 0).sum().item())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    flops = FLOP_CAND * STENCIL_CAND_PER_NBR * nbrs + 20 * nbrs
+    mc_bytes = 4 * n + 36 * min(total, cap)
+    return {"workload": "voxel density + marching cubes of the tank after the timed steps",
+            "spacing": sp, "radius": R, "particle_radius": r, "corners": n, "cubes": ncubes,
+            "corners_with_neighbours": occupied, "mean_neighbours_per_occupied_corner": nbrs / max(occupied, 1),
+            "triangles": total, "voxel_ms": ms_voxel, "mc_ms": ms_mc,
+            "corners_per_s": n / (ms_voxel * 1e-3), "triangles_per_s": total / (ms_mc * 1e-3),
+            "voxel_roofline": {"bound": "alu", "achieved": flops / (ms_voxel * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                               "unit": "TFLOP/s", "frac": flops / (ms_voxel * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                               "definition": "27-cell stencil at cell size R: 9 flops x 27/(4pi/3) x neighbours "
+                                             "+ 20 x neighbours; time includes the binning"},
+            "mc_roofline": {"bound": "hbm", "achieved": mc_bytes / (ms_mc * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": mc_bytes / (ms_mc * 1e-3) / 1e9 / hbm,
+                            "definition": "4 B per corner read + 36 B per triangle written"}}
 
 
 # --------------------------------------------------------------- CPU oracle
@@ -664,6 +740,7 @@ def run_ours(a):
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
 
     nsearch = _neighbor_search(s, dev)
+    surface = None if a.no_surface else _surface(s, dev, p, a.warmup)
     batched = None if a.no_batch else run_batched(a, dev, flush)
     sur = None if a.no_surrogate else run_surrogate(a, dev, big=s)
 
@@ -685,6 +762,7 @@ def run_ours(a):
             "gpu_launches": launches, "clocks": clk, "device_status": status, "neighbor_search": nsearch,
             "batched": batched,
             "surrogate": sur,
+            "surface": surface,
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
         }
         print(json.dumps(line), flush=True)

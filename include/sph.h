@@ -416,6 +416,73 @@ int sph_debug_gelu(const float* z, int n, int grad, float* out, void* stream);
 int sph_debug_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int splits, float* C,
                    unsigned* err, void* stream);
 
+/* ------------------------------------------------------------ surface
+ * Surface reconstruction from the particles (NEXT row of the scope: the
+ * paper's third stage), headless: the triangles go to a device buffer.
+ *
+ * Voxel density (section "Voxel Density"): at every corner x of a grid,
+ * phi(x) = |x - xbar| - r with xbar = sum_i w_i x_i,
+ * w_i = k(|x - x_i| / R) / sum_j k(|x - x_j| / R), k(s) = (1 - s^2)^3, over
+ * the fluid particles with |x - x_i| < R (decided in float32 like the step's
+ * neighbour predicate, R for h; boid-attached particles are not fluid); r is
+ * the particle radius; a corner without neighbours gets phi = R.  Corner
+ * (ix, iy, iz) lies at fl(origin + fl(i * spacing)) per axis and is element
+ * ix + nx (iy + ny iz).
+ *
+ * sph_voxel_grid: the corner grid covering p's box with ceil(R / spacing) + 1
+ * corners beyond it on every side (those are farther than R from any
+ * particle in the box, so the surface closes inside the grid): origin[3],
+ * dims[3] (corners per axis).  Errors: SPH_ERR_ARG (spacing or radius not
+ * > 0, empty box), SPH_ERR_OVERFLOW (more than 2^31 - 1 corners).
+ *
+ * sph_voxel_density: phi (device float array of nx ny nz) and, if counts
+ * is not NULL, the neighbour count of every corner (device int array), for
+ * the state the handle holds, enqueued on `stream`.  Single-scene handles
+ * only.  Errors: SPH_ERR_ARG (NULL, misaligned (4 bytes) or bad sizes,
+ * batched handle), SPH_ERR_OVERFLOW (> 2^31 - 1 corners), SPH_ERR_STATE (no
+ * state), SPH_ERR_CUDA.  Like sph_features, it re-bins the state and
+ * invalidates the step's fields.
+ */
+int sph_voxel_grid(const sph_params* p, float spacing, float radius, float origin[3], int dims[3]);
+int sph_voxel_density(sph_handle* h, const float origin[3], const int dims[3], float spacing, float radius,
+                      float particle_radius, float* phi, int* counts, void* stream);
+/*
+ * Marching cubes (section "Marching Cubes") over a corner grid of float32
+ * values phi (device, nx ny nz, layout as above): cube (ix, iy, iz) has
+ * vertex v at corner (ix, iy, iz) + (0,0,0), (1,0,0), (1,1,0), (0,1,0),
+ * (0,0,1), (1,0,1), (1,1,1), (0,1,1) for v = 0..7 and edges (v0 v1),
+ * (v1 v2), (v2 v3), (v3 v0), (v4 v5), (v5 v6), (v6 v7), (v7 v4), (v0 v4),
+ * (v1 v5), (v2 v6), (v3 v7) (the numbering of the paper's worked example);
+ * its cube index has bit v set when phi at vertex v is below iso; a cut
+ * edge's vertex is p1 + (iso - v1) / (v2 - v1) (p2 - p1), p1 its endpoint of
+ * smaller coordinate.  The triangles of the generated table (sph_mc_tables)
+ * go to tris as 9 floats each (three vertices x, y, z), cubes in order of
+ * their index ix + (nx-1) (iy + (ny-1) iz), each cube's triangles in table
+ * order; triangles wind so that their right-hand normal points to the side
+ * below iso.  At most max_tris are written; *ntri (a device unsigned)
+ * receives the total, which may exceed max_tris.  workspace: device memory
+ * of sph_mc_workspace_size bytes, 256-byte aligned, owned by the caller.
+ * The first call on a device copies the tables to its constant memory
+ * (synchronously); make it before any stream capture.  Errors: SPH_ERR_ARG
+ * (NULL, misaligned, too small a workspace, spacing not > 0, iso not
+ * finite), SPH_ERR_OVERFLOW (more than 2^31 - 1 corners or (2^31 - 1) / 5
+ * cubes), SPH_ERR_CUDA.  Messages in sph_last_error(NULL).
+ */
+int sph_mc_workspace_size(const int dims[3], size_t* bytes);
+int sph_marching_cubes(const float* phi, const int dims[3], const float origin[3], float spacing, float iso,
+                       void* workspace, size_t ws_bytes, float* tris, long long max_tris, unsigned* ntri,
+                       void* stream);
+/*
+ * Host copies of the marching-cubes tables the library generates from the
+ * cube's numbering: edge_table[256] (bit e set when edge e is cut) and
+ * tri_table[256][16] (edge triples, -1 terminated; at most 5 triangles).
+ * A face with four cut edges is split around each of its corners below the
+ * isovalue (a rule of the face alone, so neighbouring cubes agree and the
+ * surface closes).  Either pointer may be NULL.  Errors: SPH_ERR_CUDA if
+ * the generator fails its own consistency checks.
+ */
+int sph_mc_tables(unsigned short* edge_table, signed char* tri_table);
+
 /*
  * Allocation-free binning.  The paper has no counterpart to this entry point;
  * it exists for callers that cannot allocate device memory: code that runs

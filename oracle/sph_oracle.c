@@ -605,3 +605,100 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
     free(x32); free(x); free(v); free(keys); free(perm); free(cs); free(rho); free(acc);
     return 0;
 }
+
+/* ------------------------------------------------------ voxel density */
+
+/* Voxel density (section "Voxel Density") at every corner of a grid:
+ *   phi(x) = |x - xbar| - rbar,  xbar = sum_i w_i x_i,  rbar = r,
+ *   w_i = k(|x - x_i| / R) / sum_j k(|x - x_j| / R),  k(s) = (1 - s^2)^3,
+ * over the n particles pos3 with |x - x_i| < R, the distance decided in
+ * float32 like the step's neighbour predicate (d = x_i - x per component,
+ * r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < fl(R * R)).  Corner
+ * (ix, iy, iz) is at fl(origin + fl(i * spacing)) per axis and has index
+ * ix + nx (iy + ny iz).  A corner without neighbours gets phi = R.  The
+ * candidates come from a plain grid of cell R over the particles' bounding
+ * box, two cells each way (a candidate list, not a result: the predicate
+ * decides).  Values in double.  Returns 0, or -1 on bad arguments. */
+int or_voxel_density(int n, const float *pos3, const float *origin, float spacing, const int *dims,
+                     float radius, float particle_radius, double *phi, int *count)
+{
+    if (n < 0 || !origin || !dims || !phi || spacing <= 0.0f || radius <= 0.0f) return -1;
+    const float R2 = radius * radius;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = 1e300;
+        hi[a] = -1e300;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (pos3[3 * i + a] < lo[a]) lo[a] = pos3[3 * i + a];
+            if (pos3[3 * i + a] > hi[a]) hi[a] = pos3[3 * i + a];
+        }
+    int gd[3] = {1, 1, 1};
+    if (n > 0)
+        for (int a = 0; a < 3; ++a) gd[a] = (int)floor((hi[a] - lo[a]) / radius) + 1;
+    long gcells = (long)gd[0] * gd[1] * gd[2];
+    int *gstart = (int *)calloc((size_t)gcells + 1, sizeof(int));
+    int *gidx = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    int *gcell = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = (int)floor((pos3[3 * i + a] - lo[a]) / radius);
+            if (c[a] < 0) c[a] = 0;
+            if (c[a] >= gd[a]) c[a] = gd[a] - 1;
+        }
+        gcell[i] = c[0] + gd[0] * (c[1] + gd[1] * c[2]);
+        gstart[gcell[i] + 1] += 1;
+    }
+    for (long c = 0; c < gcells; ++c) gstart[c + 1] += gstart[c];
+    int *cur = (int *)calloc((size_t)gcells, sizeof(int));
+    for (int i = 0; i < n; ++i) gidx[gstart[gcell[i]] + cur[gcell[i]]++] = i;
+    free(cur);
+    const long ncorner = (long)dims[0] * dims[1] * dims[2];
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long idx = 0; idx < ncorner; ++idx) {
+        const int ix = (int)(idx % dims[0]), iy = (int)((idx / dims[0]) % dims[1]),
+                  iz = (int)(idx / ((long)dims[0] * dims[1]));
+        float x[3];
+        x[0] = origin[0] + (float)ix * spacing;
+        x[1] = origin[1] + (float)iy * spacing;
+        x[2] = origin[2] + (float)iz * spacing;
+        int c[3];
+        for (int a = 0; a < 3; ++a) c[a] = (int)floor((x[a] - lo[a]) / radius);
+        double ksum = 0.0, kx[3] = {0, 0, 0};
+        int cnt = 0;
+        for (int z = c[2] - 2; z <= c[2] + 2; ++z)
+            for (int y = c[1] - 2; y <= c[1] + 2; ++y)
+                for (int xx = c[0] - 2; xx <= c[0] + 2; ++xx) {
+                    if (xx < 0 || y < 0 || z < 0 || xx >= gd[0] || y >= gd[1] || z >= gd[2]) continue;
+                    const long g = xx + (long)gd[0] * (y + (long)gd[1] * z);
+                    for (int k = gstart[g]; k < gstart[g + 1]; ++k) {
+                        const float *p = pos3 + 3 * gidx[k];
+                        if (!(r2_f32(x, p) < R2)) continue;
+                        double d2 = 0.0;
+                        for (int a = 0; a < 3; ++a) d2 += ((double)p[a] - x[a]) * ((double)p[a] - x[a]);
+                        const double s2 = d2 / ((double)radius * radius);
+                        const double w = (1.0 - s2) * (1.0 - s2) * (1.0 - s2);
+                        ksum += w;
+                        for (int a = 0; a < 3; ++a) kx[a] += w * p[a];
+                        ++cnt;
+                    }
+                }
+        if (count) count[idx] = cnt;
+        if (cnt == 0) {
+            phi[idx] = radius;
+            continue;
+        }
+        double dist2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            const double xb = kx[a] / ksum;
+            dist2 += (x[a] - xb) * (x[a] - xb);
+        }
+        phi[idx] = sqrt(dist2) - (double)particle_radius;
+    }
+    free(gstart);
+    free(gidx);
+    free(gcell);
+    return 0;
+}

@@ -1110,3 +1110,125 @@ int sph_clear_status(sph_handle* h, void* stream)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ surface
+
+int sph_voxel_grid(const sph_params* p, float spacing, float radius, float* origin, int* dims)
+{
+    if (!p || !origin || !dims) return fail(nullptr, SPH_ERR_ARG, "NULL argument");
+    if (!finite_pos(spacing) || !finite_pos(radius)) return fail(nullptr, SPH_ERR_ARG, "spacing and radius must be > 0");
+    const int pad = (int)ceilf(radius / spacing) + 1;
+    long long total = 1;
+    for (int a = 0; a < 3; ++a) {
+        const float ext = p->box_max[a] - p->box_min[a];
+        if (!(ext > 0.0f) || !isfinite(ext)) return fail(nullptr, SPH_ERR_ARG, "empty box");
+        const double n = floor((double)ext / spacing) + 1.0 + 2.0 * pad;
+        if (n > 2147483647.0) return fail(nullptr, SPH_ERR_OVERFLOW, "too many corners");
+        dims[a] = (int)n;
+        origin[a] = p->box_min[a] - (float)pad * spacing;
+        total *= dims[a];
+    }
+    if (total > 2147483647LL) return fail(nullptr, SPH_ERR_OVERFLOW, "more than 2^31 - 1 corners");
+    return SPH_OK;
+}
+
+int sph_voxel_density(sph_handle* h, const float* origin, const int* dims, float spacing, float radius,
+                      float particle_radius, float* phi, int* counts, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (h->S != 1) return fail(h, SPH_ERR_ARG, "voxel density needs a single-scene handle");
+    if (!origin || !dims || !phi) return fail(h, SPH_ERR_ARG, "NULL argument");
+    if (((uintptr_t)phi & 3) || ((uintptr_t)counts & 3)) return fail(h, SPH_ERR_ARG, "misaligned output");
+    if (!finite_pos(spacing) || !finite_pos(radius) || !(particle_radius >= 0.0f) || !isfinite(particle_radius))
+        return fail(h, SPH_ERR_ARG, "spacing, radius must be > 0, particle_radius >= 0");
+    long long total = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || !isfinite(origin[a])) return fail(h, SPH_ERR_ARG, "bad grid");
+        total *= dims[a];
+    }
+    if (total > 2147483647LL) return fail(h, SPH_ERR_OVERFLOW, "more than 2^31 - 1 corners");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    int rc = bin_state(h, s, false);
+    if (rc != SPH_OK) return rc;
+    VoxelConst v;
+    for (int a = 0; a < 3; ++a) {
+        v.dims[a] = dims[a];
+        v.origin[a] = origin[a];
+    }
+    v.spacing = spacing;
+    v.R = radius;
+    v.R2 = radius * radius;
+    v.invR2 = (float)(1.0 / (double)v.R2);
+    v.r = particle_radius;
+    v.wb = make_bounds(&h->params[0], v.R2, h->params[0].cell_size);
+    CUDA_TRY(h, launch_voxel_density(h->pos_s, h->cell_start, h->sc, v, phi, counts, s, &h->launches));
+    h->has_step = false;
+    return SPH_OK;
+}
+
+struct McLayout {
+    long long ncubes;
+    size_t cnt, off, part, total;
+};
+
+static int mc_layout(const int* dims, McLayout* L)
+{
+    if (!dims || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return SPH_ERR_ARG;
+    const long long n = (long long)(dims[0] - 1) * (dims[1] - 1) * (dims[2] - 1);
+    if ((long long)dims[0] * dims[1] * dims[2] > 2147483647LL || n > 2147483647LL / 5) return SPH_ERR_OVERFLOW;
+    L->ncubes = n;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    L->cnt = 0;
+    L->off = up((size_t)n * sizeof(unsigned));
+    L->part = L->off + up(((size_t)n + 1) * sizeof(unsigned));
+    L->total = L->part + up(((size_t)(n > 0 ? scan_parts((int)n) : 0) + 1) * sizeof(unsigned));
+    return SPH_OK;
+}
+
+int sph_mc_workspace_size(const int* dims, size_t* bytes)
+{
+    if (!bytes) return fail(nullptr, SPH_ERR_ARG, "NULL argument");
+    McLayout L;
+    const int rc = mc_layout(dims, &L);
+    if (rc != SPH_OK) return fail(nullptr, rc, "bad or too large corner grid");
+    *bytes = L.total;
+    return SPH_OK;
+}
+
+int sph_marching_cubes(const float* phi, const int* dims, const float* origin, float spacing, float iso,
+                       void* workspace, size_t ws_bytes, float* tris, long long max_tris, unsigned* ntri,
+                       void* stream)
+{
+    if (!phi || !origin || !workspace || !ntri || (max_tris > 0 && !tris) || max_tris < 0)
+        return fail(nullptr, SPH_ERR_ARG, "NULL argument or negative capacity");
+    if (((uintptr_t)phi & 3) || ((uintptr_t)workspace & 255) || ((uintptr_t)tris & 3) || ((uintptr_t)ntri & 3))
+        return fail(nullptr, SPH_ERR_ARG, "misaligned buffer (workspace: 256 bytes, others: 4)");
+    if (!finite_pos(spacing) || !isfinite(iso)) return fail(nullptr, SPH_ERR_ARG, "spacing must be > 0, iso finite");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(origin[a])) return fail(nullptr, SPH_ERR_ARG, "origin not finite");
+    McLayout L;
+    int rc = mc_layout(dims, &L);
+    if (rc != SPH_OK) return fail(nullptr, rc, "bad or too large corner grid");
+    if (ws_bytes < L.total) return fail(nullptr, SPH_ERR_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+    cudaError_t e = mc_upload_tables();
+    if (e != cudaSuccess) return fail(nullptr, SPH_ERR_CUDA, "marching-cubes tables: %s", cudaGetErrorString(e));
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t* w = (uint8_t*)workspace;
+    unsigned* off = (unsigned*)(w + L.off);
+    long long launches = 0;
+    e = launch_marching_cubes(phi, dims, origin, spacing, iso, (unsigned*)(w + L.cnt), off, (unsigned*)(w + L.part),
+                              tris, (unsigned long long)max_tris, s, &launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ntri, off + L.ncubes, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(nullptr, SPH_ERR_CUDA, "marching cubes: %s", cudaGetErrorString(e));
+    return SPH_OK;
+}
+
+int sph_mc_tables(unsigned short* edge_table, signed char* tri_table)
+{
+    if (mc_tables_host(edge_table, tri_table) != 0)
+        return fail(nullptr, SPH_ERR_CUDA, "marching-cubes table generator failed its checks");
+    return SPH_OK;
+}

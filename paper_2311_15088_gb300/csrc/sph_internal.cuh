@@ -399,6 +399,28 @@ cudaError_t launch_surrogate_out(const float* y, const void* x, const float* lo,
                                  float f_scale, float log_err_max, float4* out, int* flag, unsigned* nflag,
                                  cudaStream_t s, long long* launches);
 
+// Surface reconstruction (sph_surface.cu): the voxel density on a grid of
+// corners and marching cubes into a triangle buffer.
+struct VoxelConst {
+    int dims[3];        // corners per axis
+    float origin[3];    // corner (0, 0, 0)
+    float spacing;
+    float R, R2, invR2; // neighbourhood radius, fl(R R), fl(1 / R2)
+    float r;            // particle radius
+    WalkBounds wb;      // walk bounds of radius R on the particle grid
+};
+cudaError_t launch_voxel_density(const float4* pos, const unsigned* start, const Scenes& sc, const VoxelConst& v,
+                                 float* phi, int* count, cudaStream_t s, long long* launches);
+// Host copies of the generated marching-cubes tables (edge: 256 masks, tri:
+// 256 x 16, -1 terminated); -1 if the generator failed its own checks.
+int mc_tables_host(unsigned short* edge, signed char* tri);
+// Copy the tables to the current device's constant memory (once per device).
+cudaError_t mc_upload_tables();
+// cnt: ncubes counts, off: ncubes + 1 offsets, part: scan_parts(ncubes) + 1.
+cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const float origin[3], float spacing,
+                                  float iso, unsigned* cnt, unsigned* off, unsigned* part, float* tris,
+                                  unsigned long long cap, cudaStream_t s, long long* launches);
+
 // Set the message that sph_last_error(NULL) returns on this thread.
 void set_handleless_error(const char* msg);
 

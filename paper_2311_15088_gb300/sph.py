@@ -88,6 +88,12 @@ _sig = {
     "sph_debug_gemm": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
     "sph_debug_gelu": (_i, [_vp, _i, _i, _vp, _vp]),
     "sph_features": (_i, [_vp, _vp, _vp]),
+    "sph_voxel_grid": (_i, [_P, ctypes.c_float, ctypes.c_float, _vp, _vp]),
+    "sph_voxel_density": (_i, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp, _vp, _vp]),
+    "sph_mc_workspace_size": (_i, [_vp, ctypes.POINTER(_sz)]),
+    "sph_marching_cubes": (_i, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _sz, _vp, ctypes.c_longlong,
+                                _vp, _vp]),
+    "sph_mc_tables": (_i, [_vp, _vp]),
     "sph_set_surrogate": (_i, [_vp, _vp, ctypes.c_float, ctypes.c_float]),
     "sph_set_surrogate_bounds": (_i, [_vp, _vp, _vp]),
 }
@@ -332,6 +338,66 @@ def sph_mlp_launch_count(m) -> int:
     return int(_lib.sph_mlp_launch_count(m))
 
 
+def sph_voxel_grid(params: dict, spacing: float, radius: float):
+    """(origin (3 floats), dims (3 ints)) of the corner grid over the box."""
+    o = (ctypes.c_float * 3)()
+    d = (ctypes.c_int * 3)()
+    _check(_lib.sph_voxel_grid(ctypes.byref(make_params(params)), float(spacing), float(radius),
+                               ctypes.cast(o, _vp), ctypes.cast(d, _vp)))
+    return tuple(float(x) for x in o), tuple(int(x) for x in d)
+
+
+def sph_voxel_density(h, origin, dims, spacing: float, radius: float, particle_radius: float, phi_ptr,
+                      counts_ptr, stream):
+    o = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    d = (ctypes.c_int * 3)(*[int(x) for x in dims])
+    _check(_lib.sph_voxel_density(h, ctypes.cast(o, _vp), ctypes.cast(d, _vp), float(spacing), float(radius),
+                                  float(particle_radius), phi_ptr, counts_ptr, stream), h)
+
+
+def sph_mc_workspace_size(dims) -> int:
+    d = (ctypes.c_int * 3)(*[int(x) for x in dims])
+    out = _sz()
+    _check(_lib.sph_mc_workspace_size(ctypes.cast(d, _vp), ctypes.byref(out)))
+    return int(out.value)
+
+
+def sph_marching_cubes(phi_ptr, dims, origin, spacing: float, iso: float, ws_ptr, ws_bytes: int, tris_ptr,
+                       max_tris: int, ntri_ptr, stream):
+    d = (ctypes.c_int * 3)(*[int(x) for x in dims])
+    o = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    _check(_lib.sph_marching_cubes(phi_ptr, ctypes.cast(d, _vp), ctypes.cast(o, _vp), float(spacing), float(iso),
+                                   ws_ptr, ws_bytes, tris_ptr, int(max_tris), ntri_ptr, stream))
+
+
+def sph_mc_tables():
+    """(edge_table uint16 [256], tri_table int8 [256, 16]) as numpy arrays."""
+    e = np.zeros(256, np.uint16)
+    t = np.zeros((256, 16), np.int8)
+    _check(_lib.sph_mc_tables(e.ctypes.data_as(_vp), t.ctypes.data_as(_vp)))
+    return e, t
+
+
+def marching_cubes(phi, dims, origin, spacing: float, iso: float = 0.0, max_tris: int | None = None):
+    """Triangles of the iso-surface of a device float32 corner grid:
+    returns (tris, total), tris a (min(total, max_tris), 3, 3) float32
+    tensor on phi's device (default capacity: 5 per cube)."""
+    import torch
+
+    ncubes = max(0, (dims[0] - 1) * (dims[1] - 1) * (dims[2] - 1))
+    cap = 5 * ncubes if max_tris is None else int(max_tris)
+    ws_bytes = sph_mc_workspace_size(dims)
+    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=phi.device)
+    ws_ptr = (ws.data_ptr() + 255) & ~255
+    tris = torch.empty((max(cap, 1), 3, 3), dtype=torch.float32, device=phi.device)
+    ntri = torch.zeros(1, dtype=torch.int32, device=phi.device)
+    stream = torch.cuda.current_stream(phi.device).cuda_stream
+    sph_marching_cubes(phi.data_ptr(), dims, origin, spacing, iso, ws_ptr, ws_bytes, tris.data_ptr(), cap,
+                       ntri.data_ptr(), stream)
+    total = int(ntri.item()) & 0xFFFFFFFF
+    return tris[:min(total, cap)], total
+
+
 def sph_debug_gelu(z_ptr, n: int, grad: int, out_ptr, stream):
     _check(_lib.sph_debug_gelu(z_ptr, n, grad, out_ptr, stream))
 
@@ -547,6 +613,18 @@ class Scene:
         out = t.empty((self.n_boid, 4), dtype=t.float32, device=self.device)
         sph_boid_forces(self.handle, mode, out.data_ptr() if out.numel() else None, self.stream)
         return out
+
+    def voxel_density(self, spacing: float, radius: float, particle_radius: float, counts: bool = True):
+        """phi and neighbour counts on the corner grid over the box (sph_voxel_grid):
+        returns (phi (nz, ny, nx) float32, counts or None, origin, dims)."""
+        t = self.torch
+        origin, dims = sph_voxel_grid(self.params, spacing, radius)
+        n = dims[0] * dims[1] * dims[2]
+        phi = t.empty(n, dtype=t.float32, device=self.device)
+        cnt = t.empty(n, dtype=t.int32, device=self.device) if counts else None
+        sph_voxel_density(self.handle, origin, dims, spacing, radius, particle_radius, phi.data_ptr(),
+                          cnt.data_ptr() if counts else None, self.stream)
+        return phi, cnt, origin, dims
 
     def features(self):
         """Stencil features of every boid (BF16 [n_boid][272])."""

@@ -88,3 +88,20 @@ def test_grid_dims_match_oracle(lib, orc):
 def test_lattice_mass_matches_oracle(lib, orc, spacing):
     p = _p()
     assert lib.sph_lattice_mass(p, spacing) == pytest.approx(orc.lattice_mass(p, np.float32(spacing)), rel=1e-6)
+
+
+def test_library_mc_tables_equal_the_oracle_generator(lib):
+    """The library and the oracle each generate the marching-cubes tables
+    from the cube's numbering (two independent implementations of the same
+    rules); they must agree entry for entry, and the library's must hold
+    the paper's worked example (cube index 8: edges 2, 3, 11; triangle
+    3, 11, 2 up to rotation)."""
+    import numpy as np
+
+    from oracle import surface
+
+    e, t = lib.sph_mc_tables()
+    oe, ot = surface.tables()
+    assert np.array_equal(e.astype(np.int64), oe)
+    assert np.array_equal(t.astype(np.int64), ot)
+    assert e[8] == 0x80C and list(t[8][:4]) == [2, 3, 11, -1]
