@@ -78,6 +78,7 @@ extern "C" {
 #define SPH_FIELD_BOID_CELL_START 12 /* uint[nbcells+1] first sorted boid slot per cell    */
 #define SPH_FIELD_NCAND      13  /* int[n_tot]     candidates the density pass tested, by id */
 #define SPH_FIELD_FALLBACK   14  /* int[n_boid]    1 where the last surrogate call used the exact path */
+#define SPH_FIELD_OBSTACLE_GRID 15 /* float4[nbcells] mean obstacle normal (xyz) and count (w) per boid-grid cell */
 
 /*
  * Parameters of a scene.  Paper notation: h smoothing length, rho0 rest
@@ -415,6 +416,34 @@ int sph_debug_gelu(const float* z, int n, int grad, float* out, void* stream);
  */
 int sph_debug_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int splits, float* C,
                    unsigned* err, void* stream);
+
+/* ---------------------------------------------------------- obstacles
+ * Obstacle avoidance of the boids (section "Boid Motion and Agent Fluid
+ * Interaction": an obstacle grid holds the normals of the obstacles'
+ * meshes; a boid steers by the averaged normals of the obstacle cells
+ * within its visual range, those within its protection range weighted
+ * more).  Analytic obstacles stand in for the meshes: spheres (host array
+ * of n_sphere x (centre x, y, z, radius > 0)) and boxes (host array of
+ * n_box x (min x, y, z, max x, y, z)), at most SPH_MAX_OBSTACLES together.
+ * The obstacle grid has the boid grid's cells; an obstacle counts in a cell
+ * when its signed distance at the cell's centre fl(min + fl((i + 0.5) d))
+ * is within half a cell diagonal (fl(0.8660254 d)), and adds its outward
+ * unit normal at the surface point nearest the centre (inside a box: the
+ * normal of its nearest face); each cell keeps the mean and the count
+ * (SPH_FIELD_OBSTACLE_GRID).  Each step, after the fluid coupling and before
+ * the edge avoidance and the speed limit, a boid adds
+ * w_obst * (sum over the obstacle cells whose centre is within r_vis of
+ * it of w_c * mean normal_c) / (their number), w_c = near_factor within
+ * r_sep and 1 beyond (the float32 distance predicate of the boid pairs).
+ * n_sphere = n_box = 0 turns the term off.  Single-scene handles only; the
+ * call waits for its own copies on `stream`, so make it outside any stream
+ * capture.  Errors: SPH_ERR_ARG (bad counts, NULL arrays, a radius <= 0, a
+ * box with max < min, non-finite values, near_factor < 0, a batched
+ * handle), SPH_ERR_CUDA.
+ */
+#define SPH_MAX_OBSTACLES 256
+int sph_set_obstacles(sph_handle* h, const float* spheres, int n_sphere, const float* boxes, int n_box,
+                      float w_obst, float near_factor, void* stream);
 
 /* ------------------------------------------------------------ surface
  * Surface reconstruction from the particles (NEXT row of the scope: the

@@ -50,7 +50,31 @@ class OrParams(ctypes.Structure):
         ("sph_factor", ctypes.c_double), ("v_min", ctypes.c_double),
         ("v_max", ctypes.c_double), ("edge_turn", ctypes.c_double),
         ("boid_cell_size", ctypes.c_double), ("coupling_mode", ctypes.c_int),
+        ("obstacles", ctypes.c_void_p),
     ]
+
+
+class OrObstacles(ctypes.Structure):
+    _fields_ = [
+        ("n_sphere", ctypes.c_int), ("n_box", ctypes.c_int),
+        ("sphere", ctypes.c_void_p), ("box", ctypes.c_void_p),
+        ("w_obst", ctypes.c_double), ("near_factor", ctypes.c_double),
+    ]
+
+
+def make_obstacles(spheres=None, boxes=None, w_obst=0.05, near_factor=2.0):
+    """The oracle's obstacle struct; returns (struct, arrays it points to)."""
+    sph = np.ascontiguousarray(np.asarray(spheres if spheres is not None else np.zeros((0, 4)), np.float32)
+                               .reshape(-1, 4))
+    box = np.ascontiguousarray(np.asarray(boxes if boxes is not None else np.zeros((0, 6)), np.float32)
+                               .reshape(-1, 6))
+    o = OrObstacles()
+    o.n_sphere, o.n_box = len(sph), len(box)
+    o.sphere = sph.ctypes.data_as(ctypes.c_void_p) if len(sph) else None
+    o.box = box.ctypes.data_as(ctypes.c_void_p) if len(box) else None
+    o.w_obst = float(np.float32(w_obst))
+    o.near_factor = float(np.float32(near_factor))
+    return o, (sph, box)
 
 
 _P = ctypes.POINTER
@@ -184,12 +208,24 @@ def neighbors(p: dict, pos, n_att: int = 0, brute: bool = False, lists: bool = T
     return counts, offsets, lst
 
 
-def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel) -> dict:
+def obstacle_grid(p: dict, spheres=None, boxes=None) -> np.ndarray:
+    """The obstacle grid over the boid grid's cells: (ncells, 4) = mean
+    outward normal, count."""
+    bd = grid_dims(p, 1)
+    out = np.zeros((bd[0] * bd[1] * bd[2], 4))
+    o, keep = make_obstacles(spheres, boxes)
+    lib().or_obstacle_grid(ctypes.byref(make_params(p)), ctypes.byref(o), _ptr(out))
+    return out
+
+
+def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, obstacles=None) -> dict:
     """One oracle step; returns every output as numpy arrays.
 
     Per-particle arrays are indexed by particle id (ids < n_boid are the
     boid-attached particles), per-fluid arrays by fluid index, per-boid
-    arrays by boid index."""
+    arrays by boid index.  obstacles: None or a dict(spheres=(k, 4),
+    boxes=(k, 6), w_obst, near_factor) of analytic obstacles the boids
+    avoid."""
     fp, fv, bp, bv = (_xyz(a) for a in (fluid_pos, fluid_vel, boid_pos, boid_vel))
     nf, nb = fp.shape[0], bp.shape[0]
     n = nf + nb
@@ -211,8 +247,14 @@ def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel) -> dict:
     for name, arr in o.items():
         ctype = dict(OrOutputs._fields_)[name]
         setattr(outs, name, arr.ctypes.data_as(ctype))
-    rc = lib().or_step(ctypes.byref(make_params(p)), nf, nb, _ptr(fp), _ptr(fv), _ptr(bp), _ptr(bv),
+    par = make_params(p)
+    keep = None
+    if obstacles is not None:
+        ob, keep = make_obstacles(**obstacles)
+        par.obstacles = ctypes.cast(ctypes.pointer(ob), ctypes.c_void_p)
+    rc = lib().or_step(ctypes.byref(par), nf, nb, _ptr(fp), _ptr(fv), _ptr(bp), _ptr(bv),
                        ctypes.byref(outs))
+    del keep
     if rc != 0:
         raise ValueError(f"oracle step rejected the parameters (rc={rc})")
     return o

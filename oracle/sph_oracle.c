@@ -51,7 +51,15 @@
  *   - the order inside a cell is the particle id (stable counting sort);
  *   - walls: reflect the position about the wall and scale the normal
  *     velocity by -wall_restitution, then clamp;
- *   - boids read a start-of-step snapshot; rules apply in the listed order.
+ *   - boids read a start-of-step snapshot; rules apply in the listed order;
+ *   - obstacle avoidance (when obstacles are given): analytic spheres and
+ *     boxes stand in for the obstacle meshes; their normals fill an obstacle
+ *     grid over the boid grid's cells; a boid adds w_obst times the mean of
+ *     the normals of the obstacle cells within its visual range (weighted
+ *     near_factor within its protection range), after the fluid coupling
+ *     and before the edge avoidance and the speed limit;
+ *   - the voxel density and the corner grid of the surface stage: see
+ *     or_voxel_density and oracle/surface.py.
  */
 #include <math.h>
 #include <stdint.h>
@@ -71,7 +79,19 @@ typedef struct {
     double r_sep, r_vis, w_sep, w_align, w_coh, sph_factor, v_min, v_max, edge_turn;
     double boid_cell_size;
     int coupling_mode;      /* 0: force coupling (the only mode the oracle states) */
+    const void *obstacles;  /* const or_obstacles *, or NULL: no obstacle avoidance */
 } or_params;
+
+/* Analytic obstacles standing in for the paper's obstacle meshes (section
+ * "Boid Motion and Agent Fluid Interaction": the obstacle grid and obstacle
+ * avoidance). */
+typedef struct {
+    int n_sphere, n_box;
+    const float *sphere;    /* n_sphere x 4: centre x, y, z, radius */
+    const float *box;       /* n_box x 6: min corner, max corner */
+    double w_obst;          /* gain on the averaged normal */
+    double near_factor;     /* weight of cells in the protection range */
+} or_obstacles;
 
 /* Outputs of or_step.  Any pointer may be NULL.  Particle ids: 0..n_boid-1
  * are the boid-attached particles, n_boid.. are fluid particles. */
@@ -397,6 +417,103 @@ static void pair_force(const or_params *p, double cp, double cv,
                                   cv * p->mu * vmag * (1.0 - 0.5 * q));
 }
 
+/* ----------------------------------------------------- obstacle grid */
+
+/* Centre of boid-grid cell i along axis a: fl(min + fl(fl(i + 0.5) d)). */
+static float cell_centre(const or_params *p, int a, int i)
+{
+    const float d = (float)p->boid_cell_size;
+    return (float)p->box_min[a] + ((float)i + 0.5f) * d;
+}
+
+/* The obstacle grid (the boid grid's cells): every obstacle whose surface
+ * passes within half a cell diagonal of a cell's centre (|sdf| <= fl(0.8660254 d),
+ * the signed distance evaluated in float32 in a fixed order) adds its
+ * outward unit normal at the surface point nearest the centre; the cell
+ * keeps the mean of those normals and their count: out4[4 c + 0..2] = mean
+ * normal, out4[4 c + 3] = count.  Reading: spheres and boxes stand in for
+ * the paper's meshes, whose normals it attributes to grid cells. */
+int or_obstacle_grid(const or_params *p, const or_obstacles *ob, double *out4)
+{
+    or_grid g;
+    grid_make(&g, p->box_min, p->box_max, p->boid_cell_size);
+    const float half_diag = 0.866025403784f * (float)p->boid_cell_size;
+    for (long c = 0; c < g.ncells; ++c) {
+        const int ix = (int)(c % g.dim[0]), iy = (int)((c / g.dim[0]) % g.dim[1]),
+                  iz = (int)(c / ((long)g.dim[0] * g.dim[1]));
+        const float x[3] = {cell_centre(p, 0, ix), cell_centre(p, 1, iy), cell_centre(p, 2, iz)};
+        double sum[3] = {0, 0, 0};
+        int cnt = 0;
+        for (int k = 0; ob && k < ob->n_sphere; ++k) {
+            const float *S = ob->sphere + 4 * k;
+            const float d[3] = {x[0] - S[0], x[1] - S[1], x[2] - S[2]};
+            const float q2 = fmaf(d[2], d[2], fmaf(d[1], d[1], d[0] * d[0]));
+            const float dist = sqrtf(q2) - S[3];
+            if (!(fabsf(dist) <= half_diag) || !(q2 > 0.0f)) continue;
+            const double len = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+            for (int a = 0; a < 3; ++a) sum[a] += d[a] / len;
+            ++cnt;
+        }
+        for (int k = 0; ob && k < ob->n_box; ++k) {
+            const float *B = ob->box + 6 * k;
+            float q[3], m[3];
+            for (int a = 0; a < 3; ++a) {
+                q[a] = fmaxf(B[a] - x[a], x[a] - B[3 + a]);
+                m[a] = fmaxf(q[a], 0.0f);
+            }
+            const int outside = q[0] > 0.0f || q[1] > 0.0f || q[2] > 0.0f;
+            const float dist = outside ? sqrtf(fmaf(m[2], m[2], fmaf(m[1], m[1], m[0] * m[0])))
+                                       : fmaxf(q[0], fmaxf(q[1], q[2]));
+            if (!(fabsf(dist) <= half_diag)) continue;
+            double n[3] = {0, 0, 0};
+            if (outside) {
+                double len = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    n[a] = x[a] > B[3 + a] ? (double)m[a] : (x[a] < B[a] ? -(double)m[a] : 0.0);
+                    len += n[a] * n[a];
+                }
+                len = sqrt(len);
+                for (int a = 0; a < 3; ++a) n[a] /= len;
+            } else {
+                int ax = 0;  /* the nearest face: largest q, the lowest axis on ties */
+                for (int a = 1; a < 3; ++a)
+                    if (q[a] > q[ax]) ax = a;
+                n[ax] = (x[ax] - B[3 + ax] >= B[ax] - x[ax]) ? 1.0 : -1.0;
+            }
+            for (int a = 0; a < 3; ++a) sum[a] += n[a];
+            ++cnt;
+        }
+        for (int a = 0; a < 3; ++a) out4[4 * c + a] = cnt ? sum[a] / cnt : 0.0;
+        out4[4 * c + 3] = cnt;
+    }
+    return 0;
+}
+
+/* Obstacle avoidance of a boid at pb (section "Boid Motion and Agent Fluid
+ * Interaction"): the mean over the obstacle cells whose centre lies within
+ * the visual range (float32 predicate as the boid pairs) of their mean
+ * normals, those within the protection range weighted near_factor;
+ * returns the count and the increment w_obst * that mean in dv. */
+static int obstacle_term(const or_params *p, const or_obstacles *ob, const or_grid *g, const double *grid4,
+                         const float *pb, float rs2f, float rv2f, double dv[3])
+{
+    double acc[3] = {0, 0, 0};
+    int n = 0;
+    for (long c = 0; c < g->ncells; ++c) {
+        if (grid4[4 * c + 3] == 0.0) continue;
+        const int ix = (int)(c % g->dim[0]), iy = (int)((c / g->dim[0]) % g->dim[1]),
+                  iz = (int)(c / ((long)g->dim[0] * g->dim[1]));
+        const float x[3] = {cell_centre(p, 0, ix), cell_centre(p, 1, iy), cell_centre(p, 2, iz)};
+        const float r2 = r2_f32(pb, x);
+        if (!(r2 < rv2f)) continue;
+        const double w = r2 < rs2f ? ob->near_factor : 1.0;
+        for (int a = 0; a < 3; ++a) acc[a] += w * grid4[4 * c + a];
+        ++n;
+    }
+    for (int a = 0; a < 3; ++a) dv[a] = n ? ob->w_obst * acc[a] / n : 0.0;
+    return n;
+}
+
 int or_step(const or_params *p, int n_fluid, int n_boid,
             const float *fluid_pos, const float *fluid_vel,
             const float *boid_pos, const float *boid_vel, or_outputs *out)
@@ -484,6 +601,14 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
     /* 5. boid rules on the start-of-step snapshot (brute force over boids). */
     float rs = (float)p->r_sep, rv = (float)p->r_vis;
     float rs2f = rs * rs, rv2f = rv * rv;
+    const or_obstacles *ob = (const or_obstacles *)p->obstacles;
+    or_grid gob;
+    double *grid4 = NULL;
+    if (ob) {
+        grid_make(&gob, p->box_min, p->box_max, p->boid_cell_size);
+        grid4 = (double *)calloc((size_t)gob.ncells * 4, sizeof(double));
+        or_obstacle_grid(p, ob, grid4);
+    }
     for (int b = 0; b < nb; ++b) {
         const float *pb = boid_pos + 3 * b;
         double vb[3] = {boid_vel[3 * b], boid_vel[3 * b + 1], boid_vel[3 * b + 2]};
@@ -530,6 +655,14 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
         /* fluid -> boid: v += sph_factor * dt * F_b, F_b the attached particle's acceleration */
         for (int a = 0; a < 3; ++a) vb[a] += p->sph_factor * p->dt * acc[3 * b + a];
         if (out->acc_scale) scale += fabs(p->sph_factor) * p->dt * out->acc_scale[b];
+        /* obstacle avoidance (reading: after the fluid coupling, before the
+         * edge avoidance and the speed limit, which still bound the result) */
+        if (ob) {
+            double dv[3];
+            obstacle_term(p, ob, &gob, grid4, pb, rs2f, rv2f, dv);
+            for (int a = 0; a < 3; ++a) vb[a] += dv[a];
+            scale += fabs(ob->w_obst) * (ob->near_factor > 1.0 ? ob->near_factor : 1.0);
+        }
         /* edge avoidance: steer back into the box */
         for (int a = 0; a < 3; ++a) {
             if (pb[a] < (float)p->box_min[a]) vb[a] += p->edge_turn;
@@ -551,6 +684,8 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
         if (out->boid_nvis) out->boid_nvis[b] = nvis;
         if (out->fb) for (int a = 0; a < 3; ++a) out->fb[3 * b + a] = acc[3 * b + a];
     }
+
+    free(grid4);
 
     /* 6. Euler-Cromer for fluid particles, then damped reflection at the walls. */
     for (int f = 0; f < n_fluid; ++f) {

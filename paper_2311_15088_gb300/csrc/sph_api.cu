@@ -49,6 +49,8 @@ struct sph_handle {
     int* bbig_list;
     unsigned* bbig_count;
     float4* fb;
+    float4* obst;             // obstacle grid over the boid grid (nbcells)
+    float* obst_shapes;       // spheres then boxes (SPH_MAX_OBSTACLES x 10 floats)
     unsigned* err;
     // surrogate: features, network output, exact-path masks
     void* feat;               // BF16 [nb_pad][SPH_MLP_IN]
@@ -300,6 +302,8 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->bbig_list = cv.take<int>(Cb);
     h->bbig_count = cv.take<unsigned>(1);
     h->fb = cv.take<float4>(nb);
+    h->obst = cv.take<float4>(Cb);
+    h->obst_shapes = cv.take<float>((size_t)SPH_MAX_OBSTACLES * 10);
     h->err = cv.take<unsigned>(4);
     h->nb_pad = nb ? (int)((nb + 127) / 128 * 128) : 0;
     h->feat = cv.take<unsigned short>((size_t)h->nb_pad * SPH_MLP_IN);
@@ -799,7 +803,7 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
                                            0, nullptr, h->bbig_list, h->bbig_count, s, &h->launches));
         prof_end(h, s);
         prof_begin(h, SPH_KIND_BOID_RULES, s);
-        CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, h->sc, h->fb, h->bpos, h->bvel, h->pos,
+        CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, h->obst, h->sc, h->fb, h->bpos, h->bvel, h->pos,
                                       h->vel, h->slot_of_boid, h->key, h->rank, h->count, h->err, s,
                                       &h->launches));
         prof_end(h, s);
@@ -1002,7 +1006,7 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
 {
     if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
     if (!out) return fail(h, SPH_ERR_ARG, "out is NULL");
-    if (!h->has_step && field != SPH_FIELD_FALLBACK)
+    if (!h->has_step && field != SPH_FIELD_FALLBACK && field != SPH_FIELD_OBSTACLE_GRID)
         return fail(h, SPH_ERR_STATE, "no step since the state was loaded or staged");
     cudaStream_t s = (cudaStream_t)stream;
     h->last_stream = s;
@@ -1034,6 +1038,10 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
     case SPH_FIELD_NBR_COUNT:
         if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->nbr, n, (int*)dst);
         bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_OBSTACLE_GRID:
+        bytes = (size_t)h->nbcells * 16;
+        if (h->nbcells) CUDA_TRY(h, cudaMemcpyAsync(dst, h->obst, bytes, cudaMemcpyDeviceToDevice, s));
         break;
     case SPH_FIELD_FALLBACK:
         bytes = (size_t)nb * 4;
@@ -1230,5 +1238,48 @@ int sph_mc_tables(unsigned short* edge_table, signed char* tri_table)
 {
     if (mc_tables_host(edge_table, tri_table) != 0)
         return fail(nullptr, SPH_ERR_CUDA, "marching-cubes table generator failed its checks");
+    return SPH_OK;
+}
+
+// ----------------------------------------------------------- obstacles
+
+int sph_set_obstacles(sph_handle* h, const float* spheres, int n_sphere, const float* boxes, int n_box,
+                      float w_obst, float near_factor, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (h->S != 1) return fail(h, SPH_ERR_ARG, "obstacles need a single-scene handle");
+    if (n_sphere < 0 || n_box < 0 || n_sphere + n_box > SPH_MAX_OBSTACLES)
+        return fail(h, SPH_ERR_ARG, "0 <= n_sphere + n_box <= %d", SPH_MAX_OBSTACLES);
+    if ((n_sphere && !spheres) || (n_box && !boxes)) return fail(h, SPH_ERR_ARG, "NULL obstacle array");
+    if (!isfinite(w_obst) || !(near_factor >= 0.0f) || !isfinite(near_factor))
+        return fail(h, SPH_ERR_ARG, "w_obst must be finite, near_factor >= 0");
+    for (int k = 0; k < 4 * n_sphere; ++k)
+        if (!isfinite(spheres[k]) || (k % 4 == 3 && !(spheres[k] > 0.0f)))
+            return fail(h, SPH_ERR_ARG, "sphere %d: non-finite value or radius <= 0", k / 4);
+    for (int k = 0; k < 6 * n_box; ++k)
+        if (!isfinite(boxes[k]) || (k % 6 >= 3 && !(boxes[k] >= boxes[k - 3])))
+            return fail(h, SPH_ERR_ARG, "box %d: non-finite value or max < min", k / 6);
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    StepConst& c = h->consts[0];
+    const int n = n_sphere + n_box;
+    if (n > 0) {
+        CUDA_TRY(h, cudaMemcpyAsync(h->obst_shapes, spheres, sizeof(float) * 4 * (size_t)n_sphere,
+                                    cudaMemcpyHostToDevice, s));
+        if (n_box)
+            CUDA_TRY(h, cudaMemcpyAsync(h->obst_shapes + 4 * n_sphere, boxes, sizeof(float) * 6 * (size_t)n_box,
+                                        cudaMemcpyHostToDevice, s));
+        const float half_diag = 0.866025403784f * h->params[0].boid_cell_size;
+        CUDA_TRY(h, launch_obstacle_grid(c, h->obst_shapes, n_sphere, n_box, half_diag, h->obst, s, &h->launches));
+    } else if (h->nbcells) {
+        CUDA_TRY(h, cudaMemsetAsync(h->obst, 0, (size_t)h->nbcells * sizeof(float4), s));
+    }
+    c.obst_on = n > 0 ? 1 : 0;
+    c.obst_reach = (int)ceilf(h->params[0].r_vis / h->params[0].boid_cell_size) + 1;
+    c.w_obst = w_obst;
+    c.obst_near = near_factor;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_consts, h->consts, sizeof(StepConst), cudaMemcpyHostToDevice, s));
+    // the host copy must outlive the asynchronous copy: wait for it here
+    CUDA_TRY(h, cudaStreamSynchronize(s));
     return SPH_OK;
 }

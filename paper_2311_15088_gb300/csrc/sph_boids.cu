@@ -62,7 +62,8 @@ constexpr int BOID_WARPS = 8;
 
 __global__ void __launch_bounds__(BOID_WARPS * 32)
 k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_s,
-             const unsigned* __restrict__ bstart, Scenes sc, const float4* __restrict__ fb,
+             const unsigned* __restrict__ bstart, const float4* __restrict__ obst, Scenes sc,
+             const float4* __restrict__ fb,
              float4* __restrict__ bpos, float4* __restrict__ bvel, float4* __restrict__ pos_next,
              float4* __restrict__ vel_next, const int* __restrict__ slot_of_boid,
              unsigned* __restrict__ key, unsigned* __restrict__ rank, unsigned* __restrict__ count,
@@ -108,13 +109,50 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
             }
         }
     }
+    // obstacle avoidance: the obstacle-grid cells whose centre lies within
+    // the visual range (the float32 predicate of the boid pairs), their mean
+    // normals weighted obst_near within the protection range; the lanes take
+    // the cells of the box of obst_reach cells around the boid's own
+    float ob[3] = {0.f, 0.f, 0.f};
+    int nob = 0;
+    if (c.obst_on) {
+        bool cl3 = false;
+        int lo[3], n3[3];
+        const float pp[3] = {pb.x, pb.y, pb.z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int cc = cell_coord(pp[a], c.gb.minf[a], c.gb.inv_d, c.gb.dim[a], &cl3);
+            lo[a] = max(cc - c.obst_reach, 0);
+            n3[a] = min(cc + c.obst_reach, c.gb.dim[a] - 1) - lo[a] + 1;
+        }
+        const int total = n3[0] * n3[1] * n3[2];
+        const float d = c.wb.d;
+        for (int k = lane; k < total; k += 32) {
+            const int ix = lo[0] + k % n3[0], iy = lo[1] + (k / n3[0]) % n3[1], iz = lo[2] + k / (n3[0] * n3[1]);
+            const float4 g = __ldg(obst + c.cb_base + ix + c.gb.dim[0] * (iy + c.gb.dim[1] * iz));
+            if (g.w == 0.0f) continue;
+            const float cx = __fadd_rn(__fmul_rn((float)ix + 0.5f, d), c.gb.minf[0]);
+            const float cy = __fadd_rn(__fmul_rn((float)iy + 0.5f, d), c.gb.minf[1]);
+            const float cz = __fadd_rn(__fmul_rn((float)iz + 0.5f, d), c.gb.minf[2]);
+            const float r2 = pair_r2(__fsub_rn(cx, pb.x), __fsub_rn(cy, pb.y), __fsub_rn(cz, pb.z));
+            if (r2 < c.rv2) {
+                const float w = r2 < c.rs2 ? c.obst_near : 1.0f;
+                ob[0] = fmaf(w, g.x, ob[0]);
+                ob[1] = fmaf(w, g.y, ob[1]);
+                ob[2] = fmaf(w, g.z, ob[2]);
+                ++nob;
+            }
+        }
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         cl[a] = warp_sum(cl[a]);
         vs[a] = warp_sum(vs[a]);
         ps[a] = warp_sum(ps[a]);
+        ob[a] = warp_sum(ob[a]);
     }
     nv = warp_sum_i(nv);
+    nob = warp_sum_i(nob);
     if (lane != 0) return;
 
     float v[3] = {vb.x, vb.y, vb.z};
@@ -136,6 +174,12 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
     v[0] = fmaf(c.sph_dt, f.x, v[0]);
     v[1] = fmaf(c.sph_dt, f.y, v[1]);
     v[2] = fmaf(c.sph_dt, f.z, v[2]);
+    // 4b. obstacle avoidance: v += w_obst * (weighted mean of the cells' normals)
+    if (nob > 0) {
+        const float g = c.w_obst / (float)nob;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = fmaf(g, ob[a], v[a]);
+    }
     // 5. edge avoidance
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -171,15 +215,93 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
 }
 
 cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const unsigned* bstart,
-                              const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
+                              const float4* obst, const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
                               float4* pos_next, float4* vel_next, const int* slot_of_boid,
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches)
 {
     if (sc.nb_all <= 0) return cudaSuccess;
     int blocks = (sc.nb_all + BOID_WARPS - 1) / BOID_WARPS;
-    k_boid_rules<<<blocks, BOID_WARPS * 32, 0, s>>>(bpos_s, bvel_s, bstart, sc, fb, bpos, bvel, pos_next,
+    k_boid_rules<<<blocks, BOID_WARPS * 32, 0, s>>>(bpos_s, bvel_s, bstart, obst, sc, fb, bpos, bvel, pos_next,
                                                     vel_next, slot_of_boid, key, rank, count, err);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ obstacles
+
+// The obstacle grid (section "Boid Motion and Agent Fluid Interaction": the
+// normals of the obstacles' meshes are attributed to the cells of an
+// obstacle grid; analytic spheres and boxes stand in for the meshes): a
+// thread per boid-grid cell.  An obstacle counts in a cell when its signed
+// distance at the cell's centre is within half a cell diagonal (float32, in
+// this fixed order); it adds its outward unit normal at the surface point
+// nearest the centre (a box from inside: the normal of its nearest face,
+// the lowest axis on ties).  The cell keeps their mean and count.
+__global__ void __launch_bounds__(256)
+k_obstacle_grid(StepConst c, const float* __restrict__ shapes, int n_sphere, int n_box, float half_diag,
+                float4* __restrict__ grid)
+{
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= c.gb.ncells) return;
+    const int ix = cell % c.gb.dim[0], iy = (cell / c.gb.dim[0]) % c.gb.dim[1],
+              iz = cell / (c.gb.dim[0] * c.gb.dim[1]);
+    const float d = c.wb.d;
+    const float x[3] = {__fadd_rn(__fmul_rn((float)ix + 0.5f, d), c.gb.minf[0]),
+                        __fadd_rn(__fmul_rn((float)iy + 0.5f, d), c.gb.minf[1]),
+                        __fadd_rn(__fmul_rn((float)iz + 0.5f, d), c.gb.minf[2])};
+    float sum[3] = {0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int k = 0; k < n_sphere; ++k) {
+        const float* S = shapes + 4 * k;
+        const float dx = __fsub_rn(x[0], S[0]), dy = __fsub_rn(x[1], S[1]), dz = __fsub_rn(x[2], S[2]);
+        const float q2 = pair_r2(dx, dy, dz);
+        const float dist = __fsub_rn(sqrtf(q2), S[3]);
+        if (!(fabsf(dist) <= half_diag) || !(q2 > 0.0f)) continue;
+        const float inv = 1.0f / sqrtf(q2);
+        sum[0] += dx * inv;
+        sum[1] += dy * inv;
+        sum[2] += dz * inv;
+        ++cnt;
+    }
+    for (int k = 0; k < n_box; ++k) {
+        const float* B = shapes + 4 * n_sphere + 6 * k;
+        float q[3], m[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            q[a] = fmaxf(__fsub_rn(B[a], x[a]), __fsub_rn(x[a], B[3 + a]));
+            m[a] = fmaxf(q[a], 0.0f);
+        }
+        const bool outside = q[0] > 0.0f || q[1] > 0.0f || q[2] > 0.0f;
+        const float dist = outside ? sqrtf(pair_r2(m[0], m[1], m[2])) : fmaxf(q[0], fmaxf(q[1], q[2]));
+        if (!(fabsf(dist) <= half_diag)) continue;
+        float n[3] = {0.f, 0.f, 0.f};
+        if (outside) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) n[a] = x[a] > B[3 + a] ? m[a] : (x[a] < B[a] ? -m[a] : 0.0f);
+            const float inv = 1.0f / dist;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) n[a] *= inv;
+        } else {
+            int ax = 0;
+            if (q[1] > q[ax]) ax = 1;
+            if (q[2] > q[ax]) ax = 2;
+            n[ax] = __fsub_rn(x[ax], B[3 + ax]) >= __fsub_rn(B[ax], x[ax]) ? 1.0f : -1.0f;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sum[a] += n[a];
+        ++cnt;
+    }
+    const float inv = cnt ? 1.0f / (float)cnt : 0.0f;
+    grid[cell] = make_float4(sum[0] * inv, sum[1] * inv, sum[2] * inv, (float)cnt);
+}
+
+cudaError_t launch_obstacle_grid(const StepConst& c, const float* shapes, int n_sphere, int n_box, float half_diag,
+                                 float4* grid, cudaStream_t s, long long* launches)
+{
+    if (c.gb.ncells <= 0) return cudaSuccess;
+    k_obstacle_grid<<<(c.gb.ncells + 255) / 256, 256, 0, s>>>(c, shapes, n_sphere, n_box, half_diag,
+                                                             grid + c.cb_base);
     ++*launches;
     return cudaGetLastError();
 }

@@ -60,6 +60,9 @@ struct StepConst {
     float restitution;
     float rs, rs2, rv2; // boid radii (separation) and squared radii
     float w_sep, w_align, w_coh, sph_dt, v_min, v_max, edge_turn;
+    // obstacle avoidance (sph_set_obstacles): off while obst_on == 0
+    int obst_on, obst_reach;  // reach: boid-grid cells searched each way
+    float w_obst, obst_near;  // gain, weight of cells in the protection range
 };
 
 // get_cell along one axis: floor((p - m) * inv_d) in float32, no contraction,
@@ -380,8 +383,14 @@ cudaError_t launch_neighbor_list(const float4* pos, const unsigned* start, const
 
 cudaError_t launch_boid_keys(const float4* bpos, const Scenes& sc, unsigned* bkey, unsigned* brank,
                              unsigned* bcount, cudaStream_t s, long long* launches);
+// The obstacle grid over the boid grid's cells (one scene): mean outward
+// normal and count of the obstacles whose surface passes within half a
+// cell diagonal of each cell's centre.  shapes: n_sphere x (centre, radius)
+// then n_box x (min, max) floats, device memory.
+cudaError_t launch_obstacle_grid(const StepConst& c, const float* shapes, int n_sphere, int n_box, float half_diag,
+                                 float4* grid, cudaStream_t s, long long* launches);
 cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const unsigned* bstart,
-                              const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
+                              const float4* obst, const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
                               float4* pos_next, float4* vel_next, const int* slot_of_boid,
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches);

@@ -25,6 +25,7 @@ SPH_MULLER3D, SPH_PAPER_LITERAL = 0, 1
 SPH_COUPLE_FORCE = 0
 SPH_DEV_NONFINITE, SPH_DEV_CLAMPED, SPH_DEV_TIMEOUT = 1, 2, 4
 SPH_BOID_EXACT, SPH_BOID_SURROGATE, SPH_BOID_SURROGATE_FALLBACK, SPH_BOID_EXACT_LOCAL = 0, 1, 2, 3
+SPH_MAX_OBSTACLES = 256
 
 FIELDS = {
     "rho": (0, np.float32, 1), "pressure": (1, np.float32, 1), "acc": (2, np.float32, 4),
@@ -32,6 +33,7 @@ FIELDS = {
     "keys": (6, np.uint32, 1), "perm": (7, np.int32, 1), "cell_start": (8, np.uint32, 1),
     "fb": (9, np.float32, 4), "boid_keys": (10, np.uint32, 1), "boid_perm": (11, np.int32, 1),
     "boid_cell_start": (12, np.uint32, 1), "ncand": (13, np.int32, 1), "fallback": (14, np.int32, 1),
+    "obstacle_grid": (15, np.float32, 4),
 }
 
 
@@ -94,6 +96,7 @@ _sig = {
     "sph_marching_cubes": (_i, [_vp, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp, _sz, _vp, ctypes.c_longlong,
                                 _vp, _vp]),
     "sph_mc_tables": (_i, [_vp, _vp]),
+    "sph_set_obstacles": (_i, [_vp, _vp, _i, _vp, _i, ctypes.c_float, ctypes.c_float, _vp]),
     "sph_set_surrogate": (_i, [_vp, _vp, ctypes.c_float, ctypes.c_float]),
     "sph_set_surrogate_bounds": (_i, [_vp, _vp, _vp]),
 }
@@ -336,6 +339,17 @@ def sph_mlp_status(m, stream: int) -> int:
 
 def sph_mlp_launch_count(m) -> int:
     return int(_lib.sph_mlp_launch_count(m))
+
+
+def sph_set_obstacles(h, spheres, boxes, w_obst: float, near_factor: float, stream):
+    """spheres (k, 4) and boxes (k, 6) as host float32 arrays (or None)."""
+    sp = np.ascontiguousarray(np.asarray(spheres if spheres is not None else np.zeros((0, 4)), np.float32)
+                              .reshape(-1, 4))
+    bx = np.ascontiguousarray(np.asarray(boxes if boxes is not None else np.zeros((0, 6)), np.float32)
+                              .reshape(-1, 6))
+    _check(_lib.sph_set_obstacles(h, sp.ctypes.data_as(_vp) if len(sp) else None, len(sp),
+                                  bx.ctypes.data_as(_vp) if len(bx) else None, len(bx), float(w_obst),
+                                  float(near_factor), stream), h)
 
 
 def sph_voxel_grid(params: dict, spacing: float, radius: float):
@@ -597,6 +611,8 @@ class Scene:
             n = self.ncells + 1
         elif name == "boid_cell_start":
             n = self.nbcells + 1
+        elif name == "obstacle_grid":
+            n = self.nbcells
         elif name in ("fb", "boid_keys", "boid_perm", "fallback"):
             n = self.n_boid
         else:
@@ -613,6 +629,11 @@ class Scene:
         out = t.empty((self.n_boid, 4), dtype=t.float32, device=self.device)
         sph_boid_forces(self.handle, mode, out.data_ptr() if out.numel() else None, self.stream)
         return out
+
+    def set_obstacles(self, spheres=None, boxes=None, w_obst: float = 0.05, near_factor: float = 2.0):
+        """Analytic obstacles the boids avoid (spheres (k, 4), boxes (k, 6));
+        none turns obstacle avoidance off."""
+        sph_set_obstacles(self.handle, spheres, boxes, w_obst, near_factor, self.stream)
 
     def voxel_density(self, spacing: float, radius: float, particle_radius: float, counts: bool = True):
         """phi and neighbour counts on the corner grid over the box (sph_voxel_grid):
