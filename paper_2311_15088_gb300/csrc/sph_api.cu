@@ -30,6 +30,7 @@ struct sph_handle {
     float* soa;               // pos_s as three float arrays (x, y, z), soa_stride(n) each
     unsigned *key, *rank;
     int* tmp;
+    int* tmp_id;              // ids beside tmp (the per-cell sort's ranking keys)
     unsigned *count, *cell_start, *scan_part;
     int* big_list;
     unsigned* big_count;
@@ -275,6 +276,7 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->key = cv.take<unsigned>(n);
     h->rank = cv.take<unsigned>(n);
     h->tmp = cv.take<int>(n > C ? n : C);
+    h->tmp_id = cv.take<int>(n);
     h->count = cv.take<unsigned>(C);
     h->cell_start = cv.take<unsigned>(C + 1);
     h->scan_part = cv.take<unsigned>((size_t)scan_parts((int)C) + 1);
@@ -756,13 +758,13 @@ static int bin_state(sph_handle* h, cudaStream_t s, bool consume)
     CUDA_TRY(h, launch_scan(h->count, h->ncells, h->scan_part, h->cell_start, s, &h->launches));
     prof_end(h, s);
     prof_begin(h, SPH_KIND_SCATTER, s);
-    CUDA_TRY(h, launch_scatter(h->key, h->rank, h->cell_start, h->n, h->tmp, s, &h->launches));
+    CUDA_TRY(h, launch_scatter_ids(h->key, h->rank, h->cell_start, h->pos, h->n, h->tmp, h->tmp_id, s,
+                                   &h->launches));
     prof_end(h, s);
     prof_begin(h, SPH_KIND_SORT, s);
-    CUDA_TRY(h, launch_cellsort_slots(h->cell_start, h->key, h->n, h->ncells, h->tmp, h->pos, h->vel, h->pos_s,
-                                      h->vel_s, h->n_boid, h->slot_of_boid, h->big_list, h->big_count, s,
-                                      &h->launches));
-    CUDA_TRY(h, launch_soa(h->pos_s, h->n, h->soa, s, &h->launches));
+    CUDA_TRY(h, launch_cellsort_slots(h->cell_start, h->key, h->n, h->ncells, h->tmp, h->tmp_id, h->pos, h->vel,
+                                      h->pos_s, h->vel_s, h->soa, h->n_boid, h->slot_of_boid, h->big_list,
+                                      h->big_count, s, &h->launches));
     prof_end(h, s);
     if (consume) {
         CUDA_TRY(h, cudaMemsetAsync(h->count, 0, (size_t)h->ncells * sizeof(unsigned), s));

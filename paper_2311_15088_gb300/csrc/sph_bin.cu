@@ -216,6 +216,30 @@ k_scatter(const unsigned* __restrict__ key, const unsigned* __restrict__ rank,
     if (i < n) tmp[start[key[i]] + rank[i]] = i;
 }
 
+// The same, also placing each particle's id (pos.w) beside its index:
+// tmp_id[start[key] + rank] = id, so that the per-cell sort ranks a cell's
+// particles from one contiguous run of ids.
+__global__ void __launch_bounds__(256)
+k_scatter_ids(const unsigned* __restrict__ key, const unsigned* __restrict__ rank,
+              const unsigned* __restrict__ start, const float4* __restrict__ pos, int n, int* __restrict__ tmp,
+              int* __restrict__ tmp_id)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned dst = start[key[i]] + rank[i];
+    tmp[dst] = i;
+    tmp_id[dst] = id_of(pos[i]);
+}
+
+cudaError_t launch_scatter_ids(const unsigned* key, const unsigned* rank, const unsigned* start, const float4* pos,
+                               int n, int* tmp, int* tmp_id, cudaStream_t s, long long* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_scatter_ids<<<(n + 255) / 256, 256, 0, s>>>(key, rank, start, pos, n, tmp, tmp_id);
+    ++*launches;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scatter(const unsigned* key, const unsigned* rank, const unsigned* start, int n,
                            int* tmp, cudaStream_t s, long long* launches)
 {
@@ -296,9 +320,22 @@ k_cellsort_big(const unsigned* __restrict__ start, const int* __restrict__ big_l
                const unsigned* __restrict__ big_count, const int* __restrict__ tmp,
                const float4* __restrict__ pos_in, const float4* __restrict__ vel_in,
                float4* __restrict__ pos_out, float4* __restrict__ vel_out, int nb,
-               int* __restrict__ slot_of_boid)
+               int* __restrict__ slot_of_boid, const int* __restrict__ tmp_id, float* __restrict__ soa,
+               size_t soa_st)
 {
     extern __shared__ unsigned long long sh_kv[];
+    // id of the entry at sorted-scratch position e (from tmp_id when given)
+    auto id_at = [&](unsigned e) { return tmp_id ? tmp_id[e] : id_of(pos_in[tmp[e]]); };
+    auto put = [&](unsigned dst, int src) {
+        const float4 p = pos_in[src];
+        pos_out[dst] = p;
+        vel_out[dst] = vel_in[src];
+        if (soa) {
+            soa[dst] = p.x;
+            soa[soa_st + dst] = p.y;
+            soa[2 * soa_st + dst] = p.z;
+        }
+    };
     const unsigned nbig = *big_count;
     for (unsigned b = blockIdx.x; b < nbig; b += gridDim.x) {
         const int c = big_list[b];
@@ -311,7 +348,7 @@ k_cellsort_big(const unsigned* __restrict__ start, const int* __restrict__ big_l
                 unsigned long long v = ~0ull;
                 if (e < n) {
                     int src = tmp[s0 + e];
-                    v = ((unsigned long long)(unsigned)id_of(pos_in[src]) << 32) | (unsigned)src;
+                    v = ((unsigned long long)(unsigned)id_at(s0 + e) << 32) | (unsigned)src;
                 }
                 sh_kv[e] = v;
             }
@@ -337,19 +374,17 @@ k_cellsort_big(const unsigned* __restrict__ start, const int* __restrict__ big_l
                 int src = (int)(unsigned)(v & 0xffffffffull);
                 int id = (int)(unsigned)(v >> 32);
                 unsigned dst = s0 + (unsigned)e;
-                pos_out[dst] = pos_in[src];
-                vel_out[dst] = vel_in[src];
+                put(dst, src);
                 if (id < nb && slot_of_boid) slot_of_boid[id] = (int)dst;
             }
         } else {
             for (int e = threadIdx.x; e < n; e += BIG_THREADS) {
                 int src = tmp[s0 + e];
-                int id = id_of(pos_in[src]);
+                int id = id_at(s0 + e);
                 int r = 0;
-                for (int k = 0; k < n; ++k) r += id_of(pos_in[tmp[s0 + k]]) < id;
+                for (int k = 0; k < n; ++k) r += id_at(s0 + k) < id;
                 unsigned dst = s0 + (unsigned)r;
-                pos_out[dst] = pos_in[src];
-                vel_out[dst] = vel_in[src];
+                put(dst, src);
                 if (id < nb && slot_of_boid) slot_of_boid[id] = (int)dst;
             }
         }
@@ -383,24 +418,26 @@ cudaError_t launch_cellsort_gather(const unsigned* start, int ncells, const int*
     k_cellsort_gather<<<blocks, SORT_WARPS * 32, 0, s>>>(start, ncells, tmp, pos_in, vel_in, pos_out,
                                                          vel_out, nb, slot_of_boid, big_list, big_count);
     k_cellsort_big<<<BIG_BLOCKS, BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
-        start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid);
+        start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid, nullptr, nullptr, 0);
     *launches += 2;
     return cudaGetLastError();
 }
 
 // One thread per sorted slot: the thread of slot s takes the storage index
-// tmp[s] of its cell, ranks it by particle id against the cell's other
-// entries and moves pos/vel to start[c] + rank.  Cells with more than
-// SLOT_SMALL entries are queued (by the thread of their first slot) for
-// k_cellsort_big.  Suited to grids of small cells (a few particles each).
+// tmp[s] of its cell, ranks its id tmp_id[s] against the cell's other ids
+// (a contiguous run of tmp_id) and moves pos/vel to start[c] + rank, also
+// writing x, y, z to the SoA copy (soa, soa_st floats per axis).  Cells with
+// more than SLOT_SMALL entries are queued (by the thread of their first
+// slot) for k_cellsort_big.  Suited to grids of small cells (a few particles
+// each).
 constexpr int SLOT_SMALL = 64;
 
 __global__ void __launch_bounds__(256)
 k_cellsort_slots(const unsigned* __restrict__ start, const unsigned* __restrict__ key, int n,
-                 const int* __restrict__ tmp, const float4* __restrict__ pos_in,
+                 const int* __restrict__ tmp, const int* __restrict__ tmp_id, const float4* __restrict__ pos_in,
                  const float4* __restrict__ vel_in, float4* __restrict__ pos_out,
-                 float4* __restrict__ vel_out, int nb, int* __restrict__ slot_of_boid,
-                 int* __restrict__ big_list, unsigned* __restrict__ big_count)
+                 float4* __restrict__ vel_out, float* __restrict__ soa, size_t soa_st, int nb,
+                 int* __restrict__ slot_of_boid, int* __restrict__ big_list, unsigned* __restrict__ big_count)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -412,19 +449,22 @@ k_cellsort_slots(const unsigned* __restrict__ start, const unsigned* __restrict_
         if ((unsigned)s == s0) big_list[atomicAdd(big_count, 1u)] = (int)c;
         return;
     }
-    const float4 p = pos_in[src];
-    const int id = id_of(p);
+    const int id = tmp_id[s];
     int r = 0;
-    for (int k = 0; k < nc; ++k) r += id_of(pos_in[tmp[s0 + k]]) < id;
+    for (int k = 0; k < nc; ++k) r += __ldg(tmp_id + s0 + k) < id;
     const unsigned dst = s0 + (unsigned)r;
+    const float4 p = pos_in[src];
     pos_out[dst] = p;
     vel_out[dst] = vel_in[src];
+    soa[dst] = p.x;
+    soa[soa_st + dst] = p.y;
+    soa[2 * soa_st + dst] = p.z;
     if (id < nb && slot_of_boid) slot_of_boid[id] = (int)dst;
 }
 
 cudaError_t launch_cellsort_slots(const unsigned* start, const unsigned* key, int n, int ncells,
-                                  const int* tmp, const float4* pos_in, const float4* vel_in,
-                                  float4* pos_out, float4* vel_out, int nb, int* slot_of_boid,
+                                  const int* tmp, const int* tmp_id, const float4* pos_in, const float4* vel_in,
+                                  float4* pos_out, float4* vel_out, float* soa, int nb, int* slot_of_boid,
                                   int* big_list, unsigned* big_count, cudaStream_t s, long long* launches)
 {
     if (n <= 0 || ncells <= 0) return cudaSuccess;
@@ -432,10 +472,11 @@ cudaError_t launch_cellsort_slots(const unsigned* start, const unsigned* key, in
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(big_count, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    k_cellsort_slots<<<(n + 255) / 256, 256, 0, s>>>(start, key, n, tmp, pos_in, vel_in, pos_out, vel_out, nb,
-                                                     slot_of_boid, big_list, big_count);
+    const size_t st = soa_stride((size_t)n);
+    k_cellsort_slots<<<(n + 255) / 256, 256, 0, s>>>(start, key, n, tmp, tmp_id, pos_in, vel_in, pos_out, vel_out,
+                                                     soa, st, nb, slot_of_boid, big_list, big_count);
     k_cellsort_big<<<BIG_BLOCKS, BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
-        start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid);
+        start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid, tmp_id, soa, st);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -309,6 +309,9 @@ cudaError_t launch_scene_keys(const float4* pos, const Scenes& sc, unsigned* key
                               unsigned* count, unsigned* err, cudaStream_t s, long long* launches);
 cudaError_t launch_scatter(const unsigned* key, const unsigned* rank, const unsigned* start, int n,
                            int* tmp, cudaStream_t s, long long* launches);
+// The same, also tmp_id[dst] = id of the particle (pos.w).
+cudaError_t launch_scatter_ids(const unsigned* key, const unsigned* rank, const unsigned* start, const float4* pos,
+                               int n, int* tmp, int* tmp_id, cudaStream_t s, long long* launches);
 // Per-cell sort by particle id + gather.  big_list (ncells ints) and
 // big_count (one u32) are scratch for the cells too large for one warp.
 cudaError_t launch_cellsort_gather(const unsigned* start, int ncells, const int* tmp,
@@ -317,9 +320,11 @@ cudaError_t launch_cellsort_gather(const unsigned* start, int ncells, const int*
                                    unsigned* big_count, cudaStream_t s, long long* launches);
 // The same with one thread per sorted slot (for grids of small cells); key
 // holds the cell of every storage slot, n the number of particles.
+// tmp_id: the ids beside tmp (launch_scatter_ids); soa: the SoA copy of
+// pos_out (soa_stride(n) floats per axis), written as well.
 cudaError_t launch_cellsort_slots(const unsigned* start, const unsigned* key, int n, int ncells,
-                                  const int* tmp, const float4* pos_in, const float4* vel_in,
-                                  float4* pos_out, float4* vel_out, int nb, int* slot_of_boid,
+                                  const int* tmp, const int* tmp_id, const float4* pos_in, const float4* vel_in,
+                                  float4* pos_out, float4* vel_out, float* soa, int nb, int* slot_of_boid,
                                   int* big_list, unsigned* big_count, cudaStream_t s, long long* launches);
 cudaError_t launch_slot_keys(const unsigned* start, int ncells, unsigned* slot_key, cudaStream_t s,
                              long long* launches);
@@ -338,8 +343,6 @@ struct SoaPos {
 };
 // Elements per axis of the SoA copy of n positions (even).
 __host__ __device__ inline size_t soa_stride(size_t n) { return (n + 1) & ~(size_t)1; }
-// soa[axis * soa_stride(n) + j] = pos[j].{x, y, z}
-cudaError_t launch_soa(const float4* pos, int n, float* soa, cudaStream_t s, long long* launches);
 
 // Launch shape of the neighbour passes (chosen by the autotuner; results do
 // not depend on it).

@@ -154,25 +154,6 @@ k_density(const float4* __restrict__ pos, SoaPos xyz, const unsigned* __restrict
     if (t < sc.n_all) density_at<STREAM>(t, pos, xyz, start, sc, rho, ab, nbr, bits, ncand, err);
 }
 
-// soa[axis * stride + j] = pos[j].{x, y, z}
-__global__ void __launch_bounds__(256)
-k_soa(const float4* __restrict__ pos, int n, size_t stride, float* __restrict__ soa)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const float4 p = pos[j];
-    soa[j] = p.x;
-    soa[stride + j] = p.y;
-    soa[2 * stride + j] = p.z;
-}
-
-cudaError_t launch_soa(const float4* pos, int n, float* soa, cudaStream_t s, long long* launches)
-{
-    if (n <= 0) return cudaSuccess;
-    k_soa<<<(n + 255) / 256, 256, 0, s>>>(pos, n, soa_stride((size_t)n), soa);
-    ++*launches;
-    return cudaGetLastError();
-}
 
 // Only the slots of a list whose length the device holds (the list is built
 // on the device; warps stride over it): a warp per particle, the lanes fetch
