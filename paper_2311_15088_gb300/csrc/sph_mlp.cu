@@ -647,22 +647,48 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
             const float* bias = P + L.b[layer];
             if (layer < 3) {
                 uint8_t* out = gbase + ((layer & 1) ? BUF_A : BUF_B);  // layer 0 -> B, 1 -> A, 2 -> B
-#pragma unroll 1
-                for (int c0 = part * EPI_COLS; c0 < part * EPI_COLS + EPI_COLS; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                // columns c0 .. c0+15 from the registers of their load: bias
+                // (four 16-byte loads), GELU, BF16, then K tile c0 / 64 as two
+                // 16-byte chunks
+                auto emit = [&](const uint32_t (&rv)[16], int c0) {
+                    const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
+                    float bb[16];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 t = __ldg(b4 + j);
+                        bb[4 * j] = t.x;
+                        bb[4 * j + 1] = t.y;
+                        bb[4 * j + 2] = t.z;
+                        bb[4 * j + 3] = t.w;
+                    }
                     uint32_t pk[8];
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu_f(v[j] + __ldg(bias + c0 + j)),
-                                                                      gelu_f(v[j + 1] + __ldg(bias + c0 + j + 1)));
+                        const __nv_bfloat162 h2 =
+                            __floats2bfloat162_rn(gelu_f(__uint_as_float(rv[j]) + bb[j]),
+                                                  gelu_f(__uint_as_float(rv[j + 1]) + bb[j + 1]));
                         pk[j >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
                     }
-                    // columns c0 .. c0+15: K tile c0 / 64, two 16-byte chunks
                     uint8_t* tile = out + (c0 / BK) * A_TILE;
                     const int cc = c0 % BK;
                     *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                };
+                // the next chunk's accumulator load runs while this chunk is worked on
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16);
+                const int cb = part * EPI_COLS;
+                uint32_t ra[16], rb[16];
+                tmem_ld16_async(tb + (uint32_t)cb, ra);
+                tmem_wait16(ra);
+#pragma unroll
+                for (int k = 0; k < EPI_COLS / 16; k += 2) {
+                    const int c0 = cb + 16 * k;
+                    tmem_ld16_async(tb + (uint32_t)(c0 + 16), rb);
+                    emit(ra, c0);
+                    tmem_wait16(rb);
+                    if (k + 2 < EPI_COLS / 16) tmem_ld16_async(tb + (uint32_t)(c0 + 32), ra);
+                    emit(rb, c0 + 16);
+                    if (k + 2 < EPI_COLS / 16) tmem_wait16(ra);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 tc_fence_before();
