@@ -49,32 +49,44 @@ struct GemmEpi {
     unsigned* err;
 };
 
-// erf by formula 7.1.26 of Abramowitz and Stegun, "Handbook of Mathematical
-// Functions": for x >= 0, erf x = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5))))
-// exp(-x^2) with t = 1 / (1 + p x), absolute error <= 1.5e-7; erf is odd.
+// Phi(-|z|) = erfc(|z| / sqrt 2) / 2, the standard normal lower tail, by
+// formula 7.1.26 of Abramowitz and Stegun, "Handbook of Mathematical
+// Functions": erfc x = t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+// t = 1 / (1 + p x), x >= 0, absolute error <= 1.5e-7 (here with x =
+// |z| / sqrt 2: p / sqrt 2 and a_k / 2 folded into the constants).
 // Evaluated in float32 with the hardware reciprocal and exponential
 // approximations, which add a few 1e-7: far below the BF16 rounding of the
-// activations (2^-9 relative).  About half the instructions of the
-// library erff, and the GELU epilogue is what bounds the fused forward pass.
-__device__ __forceinline__ float erf_as(float x)
+// activations (2^-9 relative).  The GELU epilogue bounds the fused forward
+// pass; this form takes about half the instructions of the library erff.
+// Also returns exp(-z^2 / 2) for the derivative.
+__device__ __forceinline__ float phi_lower(float z, float* gauss)
 {
-    const float ax = fabsf(x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
-    float poly = fmaf(t, 1.061405429f, -1.453152027f);
-    poly = fmaf(t, poly, 1.421413741f);
-    poly = fmaf(t, poly, -0.284496736f);
-    poly = fmaf(t, poly, 0.254829592f);
+    const float az = fabsf(z);
+    const float t = __fdividef(1.0f, fmaf(0.23164190f, az, 1.0f));  // p / sqrt 2 = 0.3275911 / 1.41421356
+    float poly = fmaf(t, 0.5307027145f, -0.7265760135f);            // a_k / 2
+    poly = fmaf(t, poly, 0.7107068705f);
+    poly = fmaf(t, poly, -0.142248368f);
+    poly = fmaf(t, poly, 0.127414796f);
     poly *= t;
-    return copysignf(fmaf(-poly, __expf(-ax * ax), 1.0f), x);
+    const float e = __expf(-0.5f * z * z);
+    *gauss = e;
+    return poly * e;
 }
 
-// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative
-// Phi(z) + z phi(z), phi the standard normal density.
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z) and its derivative Phi(z) + z phi(z), phi the standard
+// normal density, with Phi(z) = 1 - Phi(-z) for z >= 0.
+__device__ __forceinline__ float gelu_f(float z)
+{
+    float e;
+    const float lt = phi_lower(z, &e);
+    return z * (z >= 0.0f ? 1.0f - lt : lt);
+}
 
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
-    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.39894228040143268f;
+    float e;
+    const float lt = phi_lower(z, &e);
+    return (z >= 0.0f ? 1.0f - lt : lt) + z * e * 0.39894228040143268f;
 }
 
 __global__ void k_debug_gelu(const float* __restrict__ z, int n, int grad, float* __restrict__ out)
