@@ -124,52 +124,69 @@ k_scan_reduce(const unsigned* __restrict__ in, int n, unsigned* __restrict__ par
     if (threadIdx.x == 0) part[blockIdx.x] = total;
 }
 
-// One block: exclusive scan of the tile totals in place; part[nparts] = total.
+// One block: exclusive scan of the tile totals in place; part[nparts] =
+// total.  1024 values per round: a shuffle scan in each warp, then of the
+// 32 warp totals by the first warp.
 __global__ void __launch_bounds__(1024) k_scan_parts(unsigned* __restrict__ part, int nparts)
 {
-    __shared__ unsigned sh[1024];
-    __shared__ unsigned carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
+    __shared__ unsigned sh_w[32];
+    __shared__ unsigned carry_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned carry = 0;
     for (int base = 0; base < nparts; base += 1024) {
-        int idx = base + threadIdx.x;
-        unsigned v = idx < nparts ? part[idx] : 0u;
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        // Hillis-Steele inclusive scan in shared memory
-        for (int o = 1; o < 1024; o <<= 1) {
-            unsigned y = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0u;
-            __syncthreads();
-            sh[threadIdx.x] += y;
-            __syncthreads();
+        const int idx = base + threadIdx.x;
+        const unsigned v = idx < nparts ? part[idx] : 0u;
+        unsigned x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
         }
-        unsigned incl = sh[threadIdx.x];
-        if (idx < nparts) part[idx] = carry + incl - v;
+        if (lane == 31) sh_w[warp] = x;
         __syncthreads();
-        if (threadIdx.x == 1023) carry += incl;
+        if (warp == 0) {
+            unsigned w = sh_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(FULL, w, o);
+                if (lane >= o) w += y;
+            }
+            sh_w[lane] = w;  // inclusive warp totals
+            if (lane == 31) carry_sh = w;
+        }
+        __syncthreads();
+        const unsigned incl = x + (warp ? sh_w[warp - 1] : 0u);
+        if (idx < nparts) part[idx] = carry + incl - v;
+        carry += carry_sh;
         __syncthreads();
     }
     if (threadIdx.x == 0) part[nparts] = carry;
 }
 
+// Element e of a tile lives at sh[e + e / 32]: one padding word per 32
+// keeps both the coalesced phase (thread t, elements k * 256 + t) and the
+// per-thread phase (thread t, elements 16 t .. 16 t + 15) free of bank
+// conflicts (without it the second phase is a 16-way conflict).
+__device__ __forceinline__ int scan_pad(int e) { return e + (e >> 5); }
+
 __global__ void __launch_bounds__(SCAN_THREADS)
 k_scan_tiles(const unsigned* __restrict__ in, int n, const unsigned* __restrict__ part,
              unsigned* __restrict__ out)
 {
-    __shared__ unsigned sh[SCAN_TILE];
+    __shared__ unsigned sh[SCAN_TILE + SCAN_TILE / 32];
     __shared__ unsigned sh_warp[SCAN_THREADS / 32];
     int base = blockIdx.x * SCAN_TILE;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         int idx = base + k * SCAN_THREADS + threadIdx.x;
-        sh[k * SCAN_THREADS + threadIdx.x] = idx < n ? in[idx] : 0u;
+        sh[scan_pad(k * SCAN_THREADS + threadIdx.x)] = idx < n ? in[idx] : 0u;
     }
     __syncthreads();
     unsigned local[SCAN_ITEMS];
     unsigned sum = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        local[k] = sh[threadIdx.x * SCAN_ITEMS + k];
+        local[k] = sh[scan_pad(threadIdx.x * SCAN_ITEMS + k)];
         sum += local[k];
     }
     unsigned prefix;
@@ -177,14 +194,14 @@ k_scan_tiles(const unsigned* __restrict__ in, int n, const unsigned* __restrict_
     prefix += part[blockIdx.x];
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        sh[threadIdx.x * SCAN_ITEMS + k] = prefix;
+        sh[scan_pad(threadIdx.x * SCAN_ITEMS + k)] = prefix;
         prefix += local[k];
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         int idx = base + k * SCAN_THREADS + threadIdx.x;
-        if (idx < n) out[idx] = sh[k * SCAN_THREADS + threadIdx.x];
+        if (idx < n) out[idx] = sh[scan_pad(k * SCAN_THREADS + threadIdx.x)];
     }
 }
 
