@@ -69,16 +69,17 @@ def test_batch_is_bitwise_the_scenes_run_alone():
         assert np.array_equal(_split(bv, nb)[k], a_bv), f"scene {k} boid velocities"
 
 
-def test_batch_first_step_against_oracle():
-    """Scene 3 of a batch, one step, every field against the oracle (the
-    batch's fields carry global ids; they are mapped back to the scene's)."""
+@pytest.mark.parametrize("k", [3, 1])
+def test_batch_first_step_against_oracle(k):
+    """Scene k of a batch, one step, every field against the oracle (the
+    batch's fields carry global ids; they are mapped back to the scene's);
+    scene 3 has cells of h/2, scene 1 cells of h."""
     scs = _small_batch()
     b = _batch(scs)
     b.step(1)
     g = gpu_outputs(b)
     nf = np.array([len(sc["fluid_pos"]) for sc in scs])
     nb = np.array([len(sc["boid_pos"]) for sc in scs])
-    k = 3
     sc = scs[k]
     B_all = int(nb.sum())
     ids = np.concatenate([nb[:k].sum() + np.arange(nb[k]), B_all + nf[:k].sum() + np.arange(nf[k])])
