@@ -65,7 +65,7 @@ BYTES_PER_CELL_SCAN = 12
 
 # DRAM traffic of the force pass from one ncu capture (bytes per launch) and
 # the sha256 of the kernel source it was taken on; null once the source moved.
-FORCES_TRAFFIC = {"bytes": 125180928 + 119628800, "source_sha256": "2eb3ae0c2f381710991625bf1f4e1105a3d6f3c9712aa9c667418678ccf42199",
+FORCES_TRAFFIC = {"bytes": 125319936 + 118180096, "source_sha256": "c929daa0d062f9fa7f94702589892c622dda811245f82c79c7f9b94e86e6be63",
                   "capture": "ncu, 2,097,152-particle tank released unsettled (bench.py --settle 0)"}
 
 
@@ -443,194 +443,6 @@ def run_batched(a, dev, flush):
         "speedup_vs_loop": (S * a.batch_steps / t_batch) / (S * n_loop / t_loop),
         "cell_size_over_h": frac,
         "ms_per_step_by_cell_size": {str(f): 1e3 * v["t"] / a.batch_steps for f, v in per_cell.items()},
-        "tuning": {"block": best["block"], "use_stream": best["use_stream"], "ms_per_step": best["ms_per_step"]},
-        "mode": "CUDA graph replay of one step; L2 flushed between timed steps",
-    }
-
-
-# ------------------------------------------------------------ surface
-
-def _surface(s, dev, p, warmup=3, reps=10):
-    """Surface reconstruction of the current state (the paper's third stage):
-    voxel density on the corner grid over the box at spacing h/2 (R = h,
-    particle radius h/4), then marching cubes into a device triangle buffer;
-    CUDA-event times (mean of ``reps`` after ``warmup``), the voxel pass's
-    roofline against the FP32 ALU peak (9 flops per candidate tested, 20 per
-    neighbour) and the marching-cubes pass's against the HBM peak (corner
-    values read once, triangles written: compulsory bytes)."""
-    import torch
-
-    from paper_2311_15088_gb300 import sph
-
-    h = float(np.float32(p["h"]))
-    sp, R, r = float(np.float32(h * 0.5)), float(np.float32(h)), float(np.float32(h * 0.25))
-    origin, dims = sph.sph_voxel_grid(p, sp, R)
-    n = dims[0] * dims[1] * dims[2]
-    phi = torch.empty(n, dtype=torch.float32, device=dev)
-    cnt = torch.empty(n, dtype=torch.int32, device=dev)
-    stream = torch.cuda.current_stream(dev).cuda_stream
-    ncubes = (dims[0] - 1) * (dims[1] - 1) * (dims[2] - 1)
-    ws_bytes = sph.sph_mc_workspace_size(dims)
-    ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
-    ws_ptr = (ws.data_ptr() + 255) & ~255
-    cap = 4 << 20
-    tris = torch.empty((cap, 9), dtype=torch.float32, device=dev)
-    ntri = torch.zeros(1, dtype=torch.int32, device=dev)
-
-    def voxel():
-        sph.sph_voxel_density(s.handle, origin, dims, sp, R, r, phi.data_ptr(), cnt.data_ptr(), stream)
-
-    def mc():
-        sph.sph_marching_cubes(phi.data_ptr(), dims, origin, sp, 0.0, ws_ptr, ws_bytes, tris.data_ptr(), cap,
-                               ntri.data_ptr(), stream)
-
-    def timed(fn):
-        for _ in range(warmup):
-            fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1) / reps
-
-    ms_voxel = timed(voxel)  # includes the state's binning
-    ms_mc = timed(mc)
-    total = int(ntri.item())
-    nbrs = float(cnt.to(torch.float64).sum().item())
-    occupied = int((cnt > 0).sum().item())
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    flops = FLOP_CAND * STENCIL_CAND_PER_NBR * nbrs + 20 * nbrs
-    mc_bytes = 4 * n + 36 * min(total, cap)
-    return {"workload": "voxel density + marching cubes of the tank after the timed steps",
-            "spacing": sp, "radius": R, "particle_radius": r, "corners": n, "cubes": ncubes,
-            "corners_with_neighbours": occupied, "mean_neighbours_per_occupied_corner": nbrs / max(occupied, 1),
-            "triangles": total, "voxel_ms": ms_voxel, "mc_ms": ms_mc,
-            "corners_per_s": n / (ms_voxel * 1e-3), "triangles_per_s": total / (ms_mc * 1e-3),
-            "voxel_roofline": {"bound": "alu", "achieved": flops / (ms_voxel * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
-                               "unit": "TFLOP/s", "frac": flops / (ms_voxel * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                               "definition": "27-cell stencil at cell size R: 9 flops x 27/(4pi/3) x neighbours "
-                                             "+ 20 x neighbours; time includes the binning"},
-            "mc_roofline": {"bound": "hbm", "achieved": mc_bytes / (ms_mc * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                            "frac": mc_bytes / (ms_mc * 1e-3) / 1e9 / hbm,
-                            "definition": "4 B per corner read + 36 B per triangle written"}}
-
-
-# --------------------------------------------------------------- CPU oracle
-
-def _slab(fp, fv, bp, bv, lo, hi):
-    m = (fp[:, 0] >= lo) & (fp[:, 0] < hi)
-    mb = (bp[:, 0] >= lo) & (bp[:, 0] < hi)
-    return fp[m], fv[m], bp[mb], bv[mb]
-
-
-def _oracle_rate(p, fp, fv, bp, bv, step_seconds, min_seconds=0.0, steps=None):
-    """Full oracle steps on a centred x-slab of the state.  The slab is grown
-    until one step takes about ``step_seconds``; then ``steps`` steps (or as
-    many as fill ``min_seconds``) are timed.  Returns (particle-steps/s,
-    threads, description, steps, particles, seconds)."""
-    import oracle
-
-    oracle.build()
-    x0, x1 = float(p["box_min"][0]), float(p["box_max"][0])
-    full = x1 - x0
-    w = full * min(1.0, 20000.0 / max(len(fp), 1))
-    for _ in range(8):
-        lo = x0 + 0.5 * (full - w)
-        sample = _slab(fp, fv, bp, bv, lo, lo + w)
-        t = time.perf_counter()
-        oracle.step(p, *sample)
-        t = time.perf_counter() - t
-        if t >= 0.6 * step_seconds or w >= full:
-            break
-        w = min(full, w * min(4.0, step_seconds / max(t, 1e-6)))
-    n_steps, done, t0 = 0, 0, time.perf_counter()
-    while True:
-        oracle.step(p, *sample)
-        n_steps += 1
-        done += len(sample[0])
-        el = time.perf_counter() - t0
-        if (steps is not None and n_steps >= steps) or (steps is None and el >= min_seconds):
-            break
-    desc = (f"full oracle step on the x-slab [{lo:.3f}, {lo + w:.3f}) of the tank: {len(sample[0])} fluid "
-            f"particles and {len(sample[2])} boids, {n_steps} step(s)")
-    return done / el, oracle.num_threads(), desc, n_steps, len(sample[0]), el
-
-
-# ------------------------------------------------------------- batched
-
-def run_batched(a, dev, flush):
-    """256 independent tanks in one handle (every pass one launch over all
-    scenes, the step replayed from a CUDA graph, launch shape autotuned)
-    against a loop that steps each scene's own handle with the same kernels.
-    Returns the "batched" object of the bench line."""
-    import torch
-
-    from paper_2311_15088_gb300 import sph, tune
-    from paper_2311_15088_gb300.sph import Scene
-
-    scs = scenes.batched_tanks()
-    for sc in scs:
-        sc["params"] = _params(sc)
-    nf = [len(sc["fluid_pos"]) for sc in scs]
-    nb = [len(sc["boid_pos"]) for sc in scs]
-    cat = lambda key: np.concatenate([sc[key] for sc in scs])
-    stream = torch.cuda.Stream(dev)
-    with torch.cuda.stream(stream):
-        b = Scene([sc["params"] for sc in scs], nf, nb, device=dev)
-        b.set_state(cat("fluid_pos"), cat("fluid_vel"), cat("boid_pos"), cat("boid_vel"))
-        best = tune.autotune(b, steps=3, cache=None)
-        for _ in range(a.warmup):
-            b.graph_step(1)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(a.batch_steps)]
-        torch.cuda.synchronize(dev)
-        l0 = b.launches
-        for e0, e1 in ev:
-            flush.zero_()
-            e0.record()
-            b.graph_step(1)
-            e1.record()
-        torch.cuda.synchronize(dev)
-        launches = b.launches - l0
-        t_batch = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
-        del b
-        # the same scenes, one handle each, stepped in a host loop
-        loop = []
-        for sc in scs:
-            s1 = Scene(sc["params"], len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
-            s1.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
-            loop.append(s1)
-        for _ in range(a.warmup):
-            for s1 in loop:
-                s1.step(1)
-        n_loop = max(3, a.batch_steps // 3)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_loop)]
-        torch.cuda.synchronize(dev)
-        for e0, e1 in ev:
-            flush.zero_()
-            e0.record()
-            for s1 in loop:
-                sph.sph_step(s1.handle, 1, stream.cuda_stream)
-            e1.record()
-        torch.cuda.synchronize(dev)
-        t_loop = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
-        del loop
-    S = len(scs)
-    return {
-        "workload": f"{S} unit-box dam-breaks, particles log-uniform in [2048, 65536], boids uniform in [8, 256]",
-        "scenes": S, "particles": int(sum(nf)), "boids": int(sum(nb)), "steps": a.batch_steps,
-        "scenes_per_s": S * a.batch_steps / t_batch, "ms_per_step": 1e3 * t_batch / a.batch_steps,
-        "particle_steps_per_s": sum(nf) * a.batch_steps / t_batch, "gpu_launches": launches,
-        "loop_scenes_per_s": S * n_loop / t_loop, "loop_ms_per_step": 1e3 * t_loop / n_loop,
-        "speedup_vs_loop": (S * a.batch_steps / t_batch) / (S * n_loop / t_loop),
         "tuning": {"block": best["block"], "use_stream": best["use_stream"], "ms_per_step": best["ms_per_step"]},
         "mode": "CUDA graph replay of one step; L2 flushed between timed steps",
     }
