@@ -503,6 +503,12 @@ def _mode_report(surrogate, ms, got, fall, q, n_states):
     out["exact_local_equals_exact_full"] = bool(torch.equal(F, torch.cat(got["exact_full"])))
     out["speedup_surrogate_vs_exact_full"] = out["surrogate"]["qps"] / out["exact_full"]["qps"]
     out["speedup_at_5pct_vs_exact_full"] = out["surrogate_fallback"]["qps"] / out["exact_full"]["qps"]
+    # the fastest mode whose measured aggregate error is within 5 %
+    ok = [n for n in ms if out[n]["aggregate_error"] <= 0.05]
+    best = max(ok, key=lambda n: out[n]["qps"])
+    out["fastest_within_5pct"] = {"mode": best, "qps": out[best]["qps"],
+                                  "aggregate_error": out[best]["aggregate_error"],
+                                  "speedup_vs_exact_full": out[best]["qps"] / out["exact_full"]["qps"]}
     return out
 
 
@@ -513,7 +519,7 @@ def run_surrogate(a, dev, big=None):
     (64 states x 1,024 boids of held-out 262,144-particle column runs), and
     on the settled large tank ``big`` (4 states x 16,384 boids, a shift from
     the training distribution).  The network is trained first (untimed) on
-    16 runs x 64 steps of the column with other seeds.  Each per-state time
+    48 runs x 64 steps of the column with other seeds (40 epochs).  Each per-state time
     includes the state's binning, which every mode needs."""
     import torch
 
@@ -522,7 +528,9 @@ def run_surrogate(a, dev, big=None):
                                             SPH_BOID_SURROGATE_FALLBACK, Scene)
 
     mk = lambda sd: scenes.dam_break_column(seed_offset=100 + sd)
-    mlp, info = surrogate.build_and_train(mk, list(range(16)), [16, 17], steps=64)
+    # 48 training runs (3.1M pairs), 2 calibration runs, the evaluation run (40) held out
+    train_runs = list(range(16)) + list(range(18, 40)) + list(range(41, 51))
+    mlp, info = surrogate.build_and_train(mk, train_runs, [16, 17], steps=64, epochs=40)
     sc = mk(40)
     p = _params(sc)
     s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
