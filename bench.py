@@ -316,6 +316,26 @@ def _surface(s, dev, p, warmup=3, reps=10):
 
 # --------------------------------------------------------------- CPU oracle
 
+def _cpu_model() -> str:
+    """The host CPU's name from /proc/cpuinfo (x86: model name; Arm: the
+    implementer and part numbers), else the machine type."""
+    import platform
+
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    impl = [ln.split(":", 1)[1].strip() for ln in info.splitlines() if ln.startswith("CPU implementer")]
+    part = [ln.split(":", 1)[1].strip() for ln in info.splitlines() if ln.startswith("CPU part")]
+    if impl and part:
+        return f"{platform.machine()} implementer {impl[0]} part {part[0]}"
+    return platform.machine()
+
+
 def _slab(fp, fv, bp, bv, lo, hi):
     m = (fp[:, 0] >= lo) & (fp[:, 0] < hi)
     mb = (bp[:, 0] >= lo) & (bp[:, 0] < hi)
@@ -612,7 +632,8 @@ def run_reference(a):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * el / max(steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc + " (initial state: the oracle does not settle it)"},
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc,
+                         "cpu": _cpu_model(), "host_cpus": os.cpu_count()},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -766,7 +787,8 @@ def run_ours(a):
         st = [x.cpu().numpy() if hasattr(x, "cpu") else x for x in s.get_state()]
         rate, cores, sdesc, _steps, _np, _el = _oracle_rate(p, *st, step_seconds=a.cpu_seconds / 3,
                                                             min_seconds=a.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc,
+               "cpu": _cpu_model(), "host_cpus": os.cpu_count()}
 
     nsearch = _neighbor_search(s, dev)
     surface = None if a.no_surface else _surface(s, dev, p, a.warmup)
