@@ -519,14 +519,17 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 // The forward pass of one 128-row tile in one CTA (inference): the input
 // tile and the hidden activations stay in shared memory in the layout the
 // tensor cores read (K-major, 64-column tiles of 128-byte rows with the
-// 128-byte swizzle that TMA writes), the 128 x 256 FP32 accumulator in
-// tensor memory, and the 17 weight tiles of the four layers stream through
-// a two-stage TMA ring.  Warp 16 loads, warp 17 issues the MMAs, warps
-// 0 .. 15 are the epilogue (warp w reads tensor-memory lanes 32 (w % 4) ..
-// and columns 64 (w / 4) .. of the accumulator): bias, GELU, BF16, written
-// straight into the next layer's operand tile; the last layer's 16 columns
-// go to y with their bias.  Same K order and epilogue arithmetic as the
-// per-layer GEMMs, so the same outputs.  Every wait is bounded.
+// 128-byte swizzle that TMA writes), the 128 x 256 FP32 accumulators in
+// tensor memory (two of them, layers alternating), and the 17 weight tiles
+// of the four layers stream through a two-stage TMA ring.  Warp 16 loads,
+// warp 17 issues the MMAs, warps 0 .. 15 are the epilogue (warp w reads
+// tensor-memory lanes 32 (w % 4) .. and, in each 64-column K tile, the 16
+// columns 16 (w / 4) ..): bias, GELU, BF16, written straight into the next
+// layer's operand tile, K tile by K tile, each announced on its own
+// barrier, so that the next layer's MMAs on that K tile start while the
+// epilogue works on the following ones; the last layer's 16 columns go to
+// y with their bias.  The K order and the epilogue arithmetic are those of
+// the per-layer GEMMs that training runs.  Every wait is bounded.
 namespace fused {
 constexpr int KB_IN = (MLP_IN + BK - 1) / BK;   // 5 K tiles of the input
 constexpr int KB_H = MLP_H / BK;                // 4 K tiles of a hidden layer
@@ -537,13 +540,12 @@ constexpr uint32_t BUF_B = BUF_A + KB_IN * A_TILE;  // layer-1 and layer-3 outpu
 constexpr uint32_t RING = BUF_B + KB_H * A_TILE;
 constexpr int STAGES = 2;
 constexpr uint32_t BARS = RING + STAGES * W_TILE;
-// barriers: x_full, full[2], empty[2], acc_full, act_ready; then the TMEM slot
-constexpr uint32_t TOTAL = 1024 + BARS + 8 * 8 + 16;
+// barriers: x_full, full[2], empty[2], acc_full, act_ready[4]; then the TMEM slot
+constexpr uint32_t TOTAL = 1024 + BARS + 8 * 10 + 16;
 constexpr int EPI_WARPS = 16;
 constexpr int LOAD_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
 constexpr int THREADS = 32 * (EPI_WARPS + 2);
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
-constexpr int EPI_COLS = MLP_H / (EPI_WARPS / 4);  // accumulator columns per epilogue warp
 constexpr int TILES = KB_IN + 2 * KB_H + KB_H;  // 17 weight tiles
 }  // namespace fused
 
@@ -565,11 +567,13 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
     const uint32_t bars = base + BARS;
-    const uint32_t x_full = bars, acc_full = bars + 40, act_ready = bars + 48;
+    const uint32_t x_full = bars, acc_full = bars + 40;
     auto full = [&](int s) { return bars + 8u + 8u * (uint32_t)s; };
     auto empty = [&](int s) { return bars + 24u + 8u * (uint32_t)s; };
-    const uint32_t tmem_slot = bars + 64;
-    uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(gbase + BARS + 64);
+    // K tile kt of the hidden activation written (every epilogue thread arrives)
+    auto act_ready = [&](int kt) { return bars + 48u + 8u * (uint32_t)kt; };
+    const uint32_t tmem_slot = bars + 80;
+    uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(gbase + BARS + 80);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM;
@@ -582,10 +586,13 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
             mbar_init(empty(s), 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(act_ready, EPI_THREADS);
+        for (int kt = 0; kt < KB_H; ++kt) mbar_init(act_ready(kt), EPI_THREADS);
         mbar_fence_init();
     }
-    if (warp == LOAD_WARP) tmem_alloc(tmem_slot, 256);
+    // two 128 x 256 FP32 accumulators: layer l accumulates in columns
+    // 256 (l & 1) .., so the next layer's MMAs run while this layer's
+    // epilogue still reads its accumulator
+    if (warp == LOAD_WARP) tmem_alloc(tmem_slot, 2 * MLP_H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -619,16 +626,21 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
         }
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
-            // ---- MMA issue: layer by layer, each after its operand is ready
+            // ---- MMA issue: layer by layer, each K tile of a hidden layer's
+            // input as soon as the epilogue has written it
             bool ok = mbar_wait(x_full, 0, err);
+            tc_fence_after();
             int g = 0;
             for (int layer = 0; layer < 4 && ok; ++layer) {
-                if (layer > 0) ok = mbar_wait(act_ready, (uint32_t)(layer - 1) & 1u, err);
-                tc_fence_after();
                 const uint32_t a_buf = base + ((layer & 1) ? BUF_B : BUF_A);
+                const uint32_t d_tmem = tmem + (uint32_t)((layer & 1) * MLP_H);
                 const int nkb = layer == 0 ? KB_IN : KB_H;
                 const uint32_t idesc = umma_idesc_bf16(BM, layer == 3 ? MLP_OUT : MLP_H);
                 for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
+                    if (layer > 0 && !mbar_wait(act_ready(kb), (uint32_t)(layer - 1) & 1u, err)) {
+                        ok = false;
+                        break;
+                    }
                     const int s = g % STAGES;
                     if (!mbar_wait(full(s), (uint32_t)(g / STAGES) & 1u, err)) {
                         ok = false;
@@ -639,7 +651,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
                     const uint32_t b = base + RING + s * W_TILE;
 #pragma unroll
                     for (int k = 0; k < BK / UK; ++k)
-                        umma_bf16(tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
+                        umma_bf16(d_tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
                                   (uint32_t)((kb | k) != 0));
                     umma_commit(empty(s));
                 }
@@ -686,28 +698,33 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
                     *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 };
-                // the next chunk's accumulator load runs while this chunk is worked on
-                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16);
-                const int cb = part * EPI_COLS;
+                // K tile by K tile (warp part p takes columns 64 kt + 16 p ..
+                // + 15 of each), announcing each tile when written; the next
+                // chunk's accumulator load runs while this chunk is worked on
+                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((layer & 1) * MLP_H);
+                auto col = [&](int kt) { return kt * BK + part * 16; };
+                auto written = [&](int kt) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tc_fence_before();
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(act_ready(kt)) : "memory");
+                };
                 uint32_t ra[16], rb[16];
-                tmem_ld16_async(tb + (uint32_t)cb, ra);
+                tmem_ld16_async(tb + (uint32_t)col(0), ra);
                 tmem_wait16(ra);
 #pragma unroll
-                for (int k = 0; k < EPI_COLS / 16; k += 2) {
-                    const int c0 = cb + 16 * k;
-                    tmem_ld16_async(tb + (uint32_t)(c0 + 16), rb);
-                    emit(ra, c0);
+                for (int kt = 0; kt < KB_H; kt += 2) {
+                    tmem_ld16_async(tb + (uint32_t)col(kt + 1), rb);
+                    emit(ra, col(kt));
+                    written(kt);
                     tmem_wait16(rb);
-                    if (k + 2 < EPI_COLS / 16) tmem_ld16_async(tb + (uint32_t)(c0 + 32), ra);
-                    emit(rb, c0 + 16);
-                    if (k + 2 < EPI_COLS / 16) tmem_wait16(ra);
+                    if (kt + 2 < KB_H) tmem_ld16_async(tb + (uint32_t)col(kt + 2), ra);
+                    emit(rb, col(kt + 1));
+                    written(kt + 1);
+                    if (kt + 2 < KB_H) tmem_wait16(ra);
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tc_fence_before();
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(act_ready) : "memory");
             } else if (part == 0) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16), v);
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((layer & 1) * MLP_H), v);
                 if (row < B) {
                     float4* o = reinterpret_cast<float4*>(y + (size_t)row * MLP_OUT);
 #pragma unroll
@@ -720,7 +737,7 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == LOAD_WARP) tmem_dealloc(tmem, 256);
+    if (warp == LOAD_WARP) tmem_dealloc(tmem, 2 * MLP_H);
 }
 
 }  // namespace sphk
