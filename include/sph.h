@@ -401,8 +401,10 @@ long long sph_mlp_launch_count(sph_mlp* m);
  * Test hook of the activation the network's kernels use: out[i] = GELU(z[i])
  * (grad = 0) or GELU'(z[i]) (grad = 1) for n floats in device memory, GELU
  * the exact-erf form (z Phi(z)), erf evaluated by formula 7.1.26 of
- * Abramowitz and Stegun (absolute error <= 1.5e-7 plus float32 rounding).
- * Errors: SPH_ERR_ARG (NULL pointers, n < 0, grad not 0/1), SPH_ERR_CUDA.
+ * Abramowitz and Stegun (absolute error <= 1.5e-7 plus float32 rounding);
+ * grad = 2: GELU(z[i]) by the packed two-value form of the same formula that
+ * the fused inference kernel uses.
+ * Errors: SPH_ERR_ARG (NULL pointers, n < 0, grad not 0/1/2), SPH_ERR_CUDA.
  */
 int sph_debug_gelu(const float* z, int n, int grad, float* out, void* stream);
 /*

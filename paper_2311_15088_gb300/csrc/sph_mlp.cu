@@ -89,10 +89,48 @@ __device__ __forceinline__ float gelu_grad_f(float z)
     return (z >= 0.0f ? 1.0f - lt : lt) + z * e * 0.39894228040143268f;
 }
 
+// GELU of two values with the packed FP32x2 instructions (the fused
+// forward's epilogue): the same formula as gelu_f, with
+// exp(-z^2 / 2) = 2^(-z^2 log2(e) / 2) on the hardware base-2 exponential
+// and Phi(z) = 1/2 + sign(z) (1/2 - Phi(-|z|)), the sign bit of z moved onto
+// the bracket, so that each step but the reciprocal and the exponential
+// works on both values at once.
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 gelu2_f(float2 z)
+{
+    const float2 az = make_float2(fabsf(z.x), fabsf(z.y));
+    const float2 d = __ffma2_rn(make_float2(0.23164190f, 0.23164190f), az, make_float2(1.0f, 1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y));
+    float2 poly = __ffma2_rn(t, make_float2(0.5307027145f, 0.5307027145f), make_float2(-0.7265760135f, -0.7265760135f));
+    poly = __ffma2_rn(t, poly, make_float2(0.7107068705f, 0.7107068705f));
+    poly = __ffma2_rn(t, poly, make_float2(-0.142248368f, -0.142248368f));
+    poly = __ffma2_rn(t, poly, make_float2(0.127414796f, 0.127414796f));
+    poly = __fmul2_rn(poly, t);
+    // -z^2 log2(e) / 2
+    const float2 a = __fmul2_rn(__fmul2_rn(z, make_float2(-0.72134752f, -0.72134752f)), z);
+    const float2 e = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    const float2 lt = __fmul2_rn(poly, e);                                              // Phi(-|z|)
+    const float2 hb = __ffma2_rn(lt, make_float2(-1.0f, -1.0f), make_float2(0.5f, 0.5f));  // 1/2 - Phi(-|z|)
+    const float2 sh = make_float2(__uint_as_float(__float_as_uint(hb.x) ^ (__float_as_uint(z.x) & 0x80000000u)),
+                                  __uint_as_float(__float_as_uint(hb.y) ^ (__float_as_uint(z.y) & 0x80000000u)));
+    return __fmul2_rn(z, __fadd2_rn(sh, make_float2(0.5f, 0.5f)));
+}
+
 __global__ void k_debug_gelu(const float* __restrict__ z, int n, int grad, float* __restrict__ out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = grad ? gelu_grad_f(z[i]) : gelu_f(z[i]);
+    if (i >= n) return;
+    if (grad == 2) {
+        out[i] = gelu2_f(make_float2(z[i], 0.0f)).x;
+        return;
+    }
+    out[i] = grad ? gelu_grad_f(z[i]) : gelu_f(z[i]);
 }
 
 // Epilogue, in column chunks of EC (32, or NT when NT < 32), through shared
@@ -688,9 +726,9 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
                     uint32_t pk[8];
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
-                        const __nv_bfloat162 h2 =
-                            __floats2bfloat162_rn(gelu_f(__uint_as_float(rv[j]) + bb[j]),
-                                                  gelu_f(__uint_as_float(rv[j + 1]) + bb[j + 1]));
+                        const float2 g = gelu2_f(__fadd2_rn(make_float2(__uint_as_float(rv[j]), __uint_as_float(rv[j + 1])),
+                                                            make_float2(bb[j], bb[j + 1])));
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(g.x, g.y);
                         pk[j >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
                     }
                     uint8_t* tile = out + (c0 / BK) * A_TILE;
@@ -1091,7 +1129,7 @@ long long sph_mlp_launch_count(sph_mlp* m) { return m ? m->launches : 0; }
 
 int sph_debug_gelu(const float* z, int n, int grad, float* out, void* stream)
 {
-    if (!z || !out || n < 0 || (grad != 0 && grad != 1)) return mfail(nullptr, SPH_ERR_ARG, "bad GELU arguments");
+    if (!z || !out || n < 0 || grad < 0 || grad > 2) return mfail(nullptr, SPH_ERR_ARG, "bad GELU arguments");
     if (n == 0) return SPH_OK;
     k_debug_gelu<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(z, n, grad, out);
     MLP_TRY(nullptr, cudaGetLastError());

@@ -14,11 +14,12 @@ def _bf16(a):
     return torch.as_tensor(a, dtype=torch.float32).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("grad", [0, 1])
+@pytest.mark.parametrize("grad", [0, 1, 2])
 def test_gelu_against_exact_erf(grad):
-    """The kernels' GELU (erf by Abramowitz and Stegun 7.1.26 in float32)
-    against the exact-erf GELU in float64, over a dense grid of inputs
-    covering the range the network's pre-activations take and beyond."""
+    """The kernels' GELU (erf by Abramowitz and Stegun 7.1.26 in float32;
+    grad = 2 the packed two-value form of the fused forward) against the
+    exact-erf GELU in float64, over a dense grid of inputs covering the range
+    the network's pre-activations take and beyond."""
     import math
 
     z = np.concatenate([np.linspace(-12.0, 12.0, 200001), [0.0, -0.0, 1e-30, -1e-30, 40.0, -40.0]]).astype(np.float32)
@@ -28,7 +29,7 @@ def test_gelu_against_exact_erf(grad):
     got = out.cpu().double().numpy()
     zz = z.astype(np.float64)
     phi = np.array([0.5 * (1.0 + math.erf(v / math.sqrt(2.0))) for v in zz])
-    ref = zz * phi if grad == 0 else phi + zz * np.exp(-0.5 * zz * zz) / math.sqrt(2.0 * math.pi)
+    ref = zz * phi if grad != 1 else phi + zz * np.exp(-0.5 * zz * zz) / math.sqrt(2.0 * math.pi)
     # |erf error| <= 1.5e-7 (the formula) plus float32 evaluation: 1e-6
     # absolute on Phi, times |z| for GELU
     tol = 1e-6 * np.maximum(1.0, np.abs(zz)) + 1e-6 * np.abs(ref)
