@@ -554,7 +554,8 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 
 // ------------------------------------------------------------- fused forward
 
-// The forward pass of one 128-row tile in one CTA (inference): the input
+// The forward pass of 128-row tiles (inference), one persistent CTA per SM
+// looping over its tiles: the input
 // tile and the hidden activations stay in shared memory in the layout the
 // tensor cores read (K-major, 64-column tiles of 128-byte rows with the
 // 128-byte swizzle that TMA writes), the 128 x 256 FP32 accumulators in
@@ -567,7 +568,10 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 // barrier, so that the next layer's MMAs on that K tile start while the
 // epilogue works on the following ones; the last layer's 16 columns go to
 // y with their bias.  The K order and the epilogue arithmetic are those of
-// the per-layer GEMMs that training runs.  Every wait is bounded.
+// the per-layer GEMMs that training runs.  The next tile's input tile is
+// loaded as soon as the current tile's layer-2 MMAs have read that buffer,
+// and its layer-0 MMAs run while the epilogue still works on the current
+// tile's last layers.  Every wait is bounded.
 namespace fused {
 constexpr int KB_IN = (MLP_IN + BK - 1) / BK;   // 5 K tiles of the input
 constexpr int KB_H = MLP_H / BK;                // 4 K tiles of a hidden layer
@@ -578,8 +582,9 @@ constexpr uint32_t BUF_B = BUF_A + KB_IN * A_TILE;  // layer-1 and layer-3 outpu
 constexpr uint32_t RING = BUF_B + KB_H * A_TILE;
 constexpr int STAGES = 2;
 constexpr uint32_t BARS = RING + STAGES * W_TILE;
-// barriers: x_full, full[2], empty[2], acc_full, act_ready[4]; then the TMEM slot
-constexpr uint32_t TOTAL = 1024 + BARS + 8 * 10 + 16;
+// barriers: x_full, full[2], empty[2], acc_full[0], act_ready[4], a_free,
+// acc_full[1]; then the TMEM slot
+constexpr uint32_t TOTAL = 1024 + BARS + 8 * 12 + 16;
 constexpr int EPI_WARPS = 16;
 constexpr int LOAD_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
 constexpr int THREADS = 32 * (EPI_WARPS + 2);
@@ -605,16 +610,22 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
     const uint32_t bars = base + BARS;
-    const uint32_t x_full = bars, acc_full = bars + 40;
+    const uint32_t x_full = bars;
+    // accumulator a (layers a, a + 2 of every tile) complete: one barrier per
+    // accumulator, so that a barrier never runs two phases ahead of the
+    // epilogue (the next tile's layer 0 needs no epilogue of this tile's
+    // layer 3); the phase of (tile i, layer l) has parity l >> 1
+    auto acc_full = [&](int layer) { return (layer & 1) ? bars + 88u : bars + 40u; };
     auto full = [&](int s) { return bars + 8u + 8u * (uint32_t)s; };
     auto empty = [&](int s) { return bars + 24u + 8u * (uint32_t)s; };
     // K tile kt of the hidden activation written (every epilogue thread arrives)
     auto act_ready = [&](int kt) { return bars + 48u + 8u * (uint32_t)kt; };
-    const uint32_t tmem_slot = bars + 80;
-    uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(gbase + BARS + 80);
+    // the previous tile's layer-2 MMAs are done (its input buffer is free)
+    const uint32_t a_free = bars + 80;
+    const uint32_t tmem_slot = bars + 96;
+    uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(gbase + BARS + 96);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM;
     const ParamLayout L;
 
     if (threadIdx.x == 0) {
@@ -623,7 +634,9 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
             mbar_init(full(s), 1);
             mbar_init(empty(s), 1);
         }
-        mbar_init(acc_full, 1);
+        mbar_init(acc_full(0), 1);
+        mbar_init(acc_full(1), 1);
+        mbar_init(a_free, 1);
         for (int kt = 0; kt < KB_H; ++kt) mbar_init(act_ready(kt), EPI_THREADS);
         mbar_fence_init();
     }
@@ -636,74 +649,102 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
     tc_fence_after();
     const uint32_t tmem = *tmem_slot_ptr;
 
+    // tiles of this CTA: t = blockIdx.x + i gridDim.x, i = 0 .. ntl - 1; the
+    // weight tiles, layers and hidden layers are counted over all of them
+    // (g, 4 i + layer, 3 i + layer), which gives every barrier's phase
+    const int ntiles = (B + BM - 1) / BM;
+    const int ntl = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
     if (warp == LOAD_WARP) {
         if (lane == 0) {
-            // ---- loads: the input tile, then the 17 weight tiles in order
-            mbar_expect_tx(x_full, KB_IN * A_TILE);
-            for (int kb = 0; kb < KB_IN; ++kb) tma_load_2d(&mapX, x_full, base + BUF_A + kb * A_TILE, kb * BK, m0);
-            int issued = 0;
+            // ---- loads: per tile the input tile (once the previous tile's
+            // layer-2 MMAs have read that buffer), then the 17 weight tiles
+            int g = 0, nx = 0;  // weight tiles and input tiles issued
             bool ok = true;
-            for (int g = 0; g < TILES && ok; ++g) {
-                const int s = g % STAGES;
-                if (g >= STAGES && !mbar_wait(empty(s), (uint32_t)((g / STAGES) - 1) & 1u, err)) {
+            for (int i = 0; i < ntl && ok; ++i) {
+                if (i > 0 && !mbar_wait(a_free, (uint32_t)(i - 1) & 1u, err)) {
                     ok = false;
                     break;
                 }
-                const int layer = g < KB_IN ? 0 : 1 + (g - KB_IN) / KB_H;
-                const int kb = g < KB_IN ? g : (g - KB_IN) % KB_H;
-                const CUtensorMap* map = layer == 0 ? &mapW0 : layer == 1 ? &mapW1 : layer == 2 ? &mapW2 : &mapW3;
-                const uint32_t bytes = layer == 3 ? MLP_OUT * BK * 2 : W_TILE;
-                mbar_expect_tx(full(s), bytes);
-                tma_load_2d(map, full(s), base + RING + s * W_TILE, kb * BK, 0);
-                ++issued;
+                const int m0 = (blockIdx.x + i * gridDim.x) * BM;
+                mbar_expect_tx(x_full, KB_IN * A_TILE);
+                for (int kb = 0; kb < KB_IN; ++kb) tma_load_2d(&mapX, x_full, base + BUF_A + kb * A_TILE, kb * BK, m0);
+                ++nx;
+                for (int w = 0; w < TILES; ++w, ++g) {
+                    const int s = g % STAGES;
+                    if (g >= STAGES && !mbar_wait(empty(s), (uint32_t)((g / STAGES) - 1) & 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const int layer = w < KB_IN ? 0 : 1 + (w - KB_IN) / KB_H;
+                    const int kb = w < KB_IN ? w : (w - KB_IN) % KB_H;
+                    const CUtensorMap* map = layer == 0 ? &mapW0 : layer == 1 ? &mapW1 : layer == 2 ? &mapW2 : &mapW3;
+                    const uint32_t bytes = layer == 3 ? MLP_OUT * BK * 2 : W_TILE;
+                    mbar_expect_tx(full(s), bytes);
+                    tma_load_2d(map, full(s), base + RING + s * W_TILE, kb * BK, 0);
+                }
             }
-            if (!ok)  // let the copies in flight land before the CTA goes away
-                for (int g = (issued > STAGES ? issued - STAGES : 0); g < issued; ++g)
-                    mbar_wait(full(g % STAGES), (uint32_t)(g / STAGES) & 1u, err);
-            mbar_wait(x_full, 0, err);
+            if (!ok) {  // let the copies in flight land before the CTA goes away
+                for (int h = (g > STAGES ? g - STAGES : 0); h < g; ++h)
+                    mbar_wait(full(h % STAGES), (uint32_t)(h / STAGES) & 1u, err);
+                if (nx > 0) mbar_wait(x_full, (uint32_t)(nx - 1) & 1u, err);
+            }
         }
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
-            // ---- MMA issue: layer by layer, each K tile of a hidden layer's
-            // input as soon as the epilogue has written it
-            bool ok = mbar_wait(x_full, 0, err);
-            tc_fence_after();
+            // ---- MMA issue: per tile layer by layer, each K tile of a hidden
+            // layer's input as soon as the epilogue has written it.  Layer 0
+            // of the next tile reuses accumulator 0 of layer 2: its epilogue
+            // has read it once every K tile of layer 2's output is announced,
+            // which layer 3's MMAs waited for.
+            bool ok = true;
             int g = 0;
-            for (int layer = 0; layer < 4 && ok; ++layer) {
-                const uint32_t a_buf = base + ((layer & 1) ? BUF_B : BUF_A);
-                const uint32_t d_tmem = tmem + (uint32_t)((layer & 1) * MLP_H);
-                const int nkb = layer == 0 ? KB_IN : KB_H;
-                const uint32_t idesc = umma_idesc_bf16(BM, layer == 3 ? MLP_OUT : MLP_H);
-                for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
-                    if (layer > 0 && !mbar_wait(act_ready(kb), (uint32_t)(layer - 1) & 1u, err)) {
-                        ok = false;
-                        break;
-                    }
-                    const int s = g % STAGES;
-                    if (!mbar_wait(full(s), (uint32_t)(g / STAGES) & 1u, err)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t a = a_buf + kb * A_TILE;
-                    const uint32_t b = base + RING + s * W_TILE;
+            for (int i = 0; i < ntl && ok; ++i) {
+                ok = mbar_wait(x_full, (uint32_t)i & 1u, err);
+                tc_fence_after();
+                for (int layer = 0; layer < 4 && ok; ++layer) {
+                    const uint32_t a_buf = base + ((layer & 1) ? BUF_B : BUF_A);
+                    const uint32_t d_tmem = tmem + (uint32_t)((layer & 1) * MLP_H);
+                    const int nkb = layer == 0 ? KB_IN : KB_H;
+                    const uint32_t idesc = umma_idesc_bf16(BM, layer == 3 ? MLP_OUT : MLP_H);
+                    const uint32_t hpar = (uint32_t)(3 * i + layer - 1) & 1u;
+                    for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
+                        if (layer > 0 && !mbar_wait(act_ready(kb), hpar, err)) {
+                            ok = false;
+                            break;
+                        }
+                        const int s = g % STAGES;
+                        if (!mbar_wait(full(s), (uint32_t)(g / STAGES) & 1u, err)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a = a_buf + kb * A_TILE;
+                        const uint32_t b = base + RING + s * W_TILE;
 #pragma unroll
-                    for (int k = 0; k < BK / UK; ++k)
-                        umma_bf16(d_tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
-                                  (uint32_t)((kb | k) != 0));
-                    umma_commit(empty(s));
+                        for (int k = 0; k < BK / UK; ++k)
+                            umma_bf16(d_tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
+                                      (uint32_t)((kb | k) != 0));
+                        umma_commit(empty(s));
+                    }
+                    if (layer == 2) umma_commit(a_free);  // the input buffer is free once these MMAs are done
+                    umma_commit(acc_full(layer));
                 }
-                umma_commit(acc_full);
             }
-            if (!ok) umma_commit(acc_full);  // so that the epilogue does not wait for nothing
+            if (!ok) {  // so that the epilogue does not wait for nothing
+                umma_commit(acc_full(0));
+                umma_commit(acc_full(1));
+            }
         }
     } else {
         // ---- epilogue warps
         const int q = warp & 3, part = warp >> 2;
         const int r = q * 32 + lane;  // tile row of this thread
-        const int row = m0 + r;
+        bool ok = true;
+        for (int i = 0; i < ntl && ok; ++i)
         for (int layer = 0; layer < 4; ++layer) {
-            const bool ok = mbar_wait(acc_full, (uint32_t)layer & 1u, err);
+            const int row = (blockIdx.x + i * gridDim.x) * BM + r;
+            ok = mbar_wait(acc_full(layer), (uint32_t)(layer >> 1) & 1u, err);
             tc_fence_after();
             if (!ok) break;
             const float* bias = P + L.b[layer];
@@ -904,7 +945,7 @@ static int mlp_forward(sph_mlp* m, const __nv_bfloat16* x, int B, float* y, bool
     return SPH_OK;
 }
 
-// Inference: the four layers in one launch (k_mlp_fused), 128 rows per CTA.
+// Inference: the four layers in one launch (k_mlp_fused), 128-row tiles.
 static int mlp_forward_fused(sph_mlp* m, const __nv_bfloat16* x, int B, float* y, cudaStream_t s)
 {
     const ParamLayout L;
@@ -913,12 +954,19 @@ static int mlp_forward_fused(sph_mlp* m, const __nv_bfloat16* x, int B, float* y
     for (int l = 0; l < 4; ++l)
         MLP_TRY(m, make_map(&mw[l], m->W + L.w[l], L.out[l], L.in[l], L.in[l], L.out[l]));
     static bool attr = false;
+    static int sms = 0;
     if (!attr) {
         MLP_TRY(m, cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused::TOTAL));
+        int dev = 0;
+        MLP_TRY(m, cudaGetDevice(&dev));
+        MLP_TRY(m, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         attr = true;
     }
-    k_mlp_fused<<<(B + BM - 1) / BM, fused::THREADS, fused::TOTAL, s>>>(mx, mw[0], mw[1], mw[2], mw[3], m->P, B, y,
-                                                                        m->err);
+    // persistent: one CTA per SM (the kernel takes one), each looping over
+    // the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int tiles = (B + BM - 1) / BM;
+    const int grid = tiles < sms ? tiles : sms;
+    k_mlp_fused<<<grid, fused::THREADS, fused::TOTAL, s>>>(mx, mw[0], mw[1], mw[2], mw[3], m->P, B, y, m->err);
     ++m->launches;
     MLP_TRY(m, cudaGetLastError());
     return SPH_OK;

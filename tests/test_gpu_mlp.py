@@ -103,6 +103,30 @@ def test_forward_matches_oracle():
     assert np.all(np.abs(y - ref) <= 2e-2 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("tiles", [153, 305, 512])
+def test_forward_many_tiles_matches_oracle(tiles):
+    """The fused forward with more 128-row tiles than SMs (each CTA loops
+    over several tiles, the last ones ragged across CTAs): a sample of rows
+    from every tile against the oracle, and the whole batch against the
+    same rows run as a batch of their own (tile placement changes nothing)."""
+    B = 128 * tiles
+    p = _oracle_params_bf16(31)
+    x = _inputs(B, 32)
+    m = sph.Mlp(B)
+    m.set_params(torch.from_numpy(_pack(p)))
+    xb = _bf16(x).cuda()
+    y = m.forward(xb).double().cpu().numpy()
+    assert m.status() == 0
+    rows = np.arange(5, B, 29)
+    assert len(np.unique(rows // 128)) == tiles
+    ref = omlp.forward(p, x[rows])["y"]
+    assert np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref) <= 2e-2
+    assert np.all(np.abs(y[rows] - ref) <= 2e-2 * np.abs(ref).max())
+    # the last 640 rows as a batch of their own: bit-identical outputs
+    y2 = m.forward(xb[-640:]).cpu().numpy()
+    assert np.array_equal(y2, y[-640:].astype(np.float32))
+
+
 def test_gradients_match_oracle():
     p = _oracle_params_bf16(21)
     x = _inputs(512, 22)
