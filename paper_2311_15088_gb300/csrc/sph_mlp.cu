@@ -555,41 +555,40 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 // ------------------------------------------------------------- fused forward
 
 // The forward pass of 128-row tiles (inference), one persistent CTA per SM
-// looping over its tiles: the input
-// tile and the hidden activations stay in shared memory in the layout the
-// tensor cores read (K-major, 64-column tiles of 128-byte rows with the
-// 128-byte swizzle that TMA writes), the 128 x 256 FP32 accumulators in
-// tensor memory (two of them, layers alternating), and the 17 weight tiles
-// of the four layers stream through a two-stage TMA ring.  Warp 16 loads,
+// with two tiles in flight (slots 0 and 1), so that the tensor cores work
+// on one tile while the epilogue works on the other.  Per slot the input
+// tile and then each hidden layer's output stay in one shared-memory buffer
+// in the layout the tensor cores read (K-major, 64-column tiles of 128-byte
+// rows with the 128-byte swizzle that TMA writes): a layer's epilogue
+// starts once that layer's MMAs have completed, so it writes its output
+// over its input.  Each slot has a 128 x 256 FP32 accumulator in tensor
+// memory (columns 256 j ..).  The 17 weight tiles of the four layers stream
+// through a two-stage TMA ring, once per tile and layer.  Warp 16 loads,
 // warp 17 issues the MMAs, warps 0 .. 15 are the epilogue (warp w reads
 // tensor-memory lanes 32 (w % 4) .. and, in each 64-column K tile, the 16
 // columns 16 (w / 4) ..): bias, GELU, BF16, written straight into the next
-// layer's operand tile, K tile by K tile, each announced on its own
-// barrier, so that the next layer's MMAs on that K tile start while the
-// epilogue works on the following ones; the last layer's 16 columns go to
-// y with their bias.  The K order and the epilogue arithmetic are those of
-// the per-layer GEMMs that training runs.  The next tile's input tile is
-// loaded as soon as the current tile's layer-2 MMAs have read that buffer,
-// and its layer-0 MMAs run while the epilogue still works on the current
-// tile's last layers.  Every wait is bounded.
+// layer's operand tile; the last layer's 16 columns go to y with their
+// bias.  All three take the work items (tile pair, layer, slot) in the
+// same order: for each pair of tiles, layer by layer, slot 0 then slot 1,
+// so the MMAs of one slot's next layer run during the epilogue of the
+// other slot's current layer.  The K order and the epilogue arithmetic are
+// those of the per-layer GEMMs that training runs.  Every wait is bounded.
 namespace fused {
 constexpr int KB_IN = (MLP_IN + BK - 1) / BK;   // 5 K tiles of the input
 constexpr int KB_H = MLP_H / BK;                // 4 K tiles of a hidden layer
 constexpr uint32_t A_TILE = BM * BK * 2;        // 16 KB: 128 rows x 64 BF16
 constexpr uint32_t W_TILE = MLP_H * BK * 2;     // 32 KB: 256 rows x 64 BF16
-constexpr uint32_t BUF_A = 0;                   // input, then layer-2 output
-constexpr uint32_t BUF_B = BUF_A + KB_IN * A_TILE;  // layer-1 and layer-3 outputs
-constexpr uint32_t RING = BUF_B + KB_H * A_TILE;
+constexpr uint32_t BUF = KB_IN * A_TILE;        // 80 KB per slot: the input, then each layer's output
+constexpr uint32_t RING = 2 * BUF;
 constexpr int STAGES = 2;
 constexpr uint32_t BARS = RING + STAGES * W_TILE;
-// barriers: x_full, full[2], empty[2], acc_full[0], act_ready[4], a_free,
-// acc_full[1]; then the TMEM slot
+// barriers: full[2], empty[2], then per slot x_full, buf_free, acc_full,
+// epi_done; then the TMEM slot
 constexpr uint32_t TOTAL = 1024 + BARS + 8 * 12 + 16;
 constexpr int EPI_WARPS = 16;
 constexpr int LOAD_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
 constexpr int THREADS = 32 * (EPI_WARPS + 2);
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
-constexpr int TILES = KB_IN + 2 * KB_H + KB_H;  // 17 weight tiles
 }  // namespace fused
 
 // byte offset of element (r, c) in a K-major 64-column tile with 128-byte swizzle
@@ -610,18 +609,15 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gbase = smem_raw + (base - raw);
     const uint32_t bars = base + BARS;
-    const uint32_t x_full = bars;
-    // accumulator a (layers a, a + 2 of every tile) complete: one barrier per
-    // accumulator, so that a barrier never runs two phases ahead of the
-    // epilogue (the next tile's layer 0 needs no epilogue of this tile's
-    // layer 3); the phase of (tile i, layer l) has parity l >> 1
-    auto acc_full = [&](int layer) { return (layer & 1) ? bars + 88u : bars + 40u; };
-    auto full = [&](int s) { return bars + 8u + 8u * (uint32_t)s; };
-    auto empty = [&](int s) { return bars + 24u + 8u * (uint32_t)s; };
-    // K tile kt of the hidden activation written (every epilogue thread arrives)
-    auto act_ready = [&](int kt) { return bars + 48u + 8u * (uint32_t)kt; };
-    // the previous tile's layer-2 MMAs are done (its input buffer is free)
-    const uint32_t a_free = bars + 80;
+    auto full = [&](int s) { return bars + 8u * (uint32_t)s; };
+    auto empty = [&](int s) { return bars + 16u + 8u * (uint32_t)s; };
+    // slot j: its input tile landed; its buffer read by its last layer's
+    // MMAs; its accumulator complete; its epilogue done (every epilogue
+    // thread arrives: the layer's output written, the accumulator read)
+    auto x_full = [&](int j) { return bars + 32u + 32u * (uint32_t)j; };
+    auto buf_free = [&](int j) { return bars + 40u + 32u * (uint32_t)j; };
+    auto acc_full = [&](int j) { return bars + 48u + 32u * (uint32_t)j; };
+    auto epi_done = [&](int j) { return bars + 56u + 32u * (uint32_t)j; };
     const uint32_t tmem_slot = bars + 96;
     uint32_t* tmem_slot_ptr = reinterpret_cast<uint32_t*>(gbase + BARS + 96);
 
@@ -629,57 +625,65 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
     const ParamLayout L;
 
     if (threadIdx.x == 0) {
-        mbar_init(x_full, 1);
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full(s), 1);
             mbar_init(empty(s), 1);
         }
-        mbar_init(acc_full(0), 1);
-        mbar_init(acc_full(1), 1);
-        mbar_init(a_free, 1);
-        for (int kt = 0; kt < KB_H; ++kt) mbar_init(act_ready(kt), EPI_THREADS);
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(x_full(j), 1);
+            mbar_init(buf_free(j), 1);
+            mbar_init(acc_full(j), 1);
+            mbar_init(epi_done(j), EPI_THREADS);
+        }
         mbar_fence_init();
     }
-    // two 128 x 256 FP32 accumulators: layer l accumulates in columns
-    // 256 (l & 1) .., so the next layer's MMAs run while this layer's
-    // epilogue still reads its accumulator
     if (warp == LOAD_WARP) tmem_alloc(tmem_slot, 2 * MLP_H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot_ptr;
 
-    // tiles of this CTA: t = blockIdx.x + i gridDim.x, i = 0 .. ntl - 1; the
-    // weight tiles, layers and hidden layers are counted over all of them
-    // (g, 4 i + layer, 3 i + layer), which gives every barrier's phase
+    // tiles of this CTA: t = blockIdx.x + i gridDim.x, i = 0 .. ntl - 1; tile
+    // i sits in slot i & 1 as that slot's (i >> 1)-th tile.  Work item it =
+    // 8 p + 2 l + j: pair p, layer l, slot j (tile 2 p + j, skipped past
+    // ntl).  Per slot, its barriers complete one phase per tile (x_full,
+    // buf_free) or per tile and layer (acc_full, epi_done: parity l & 1),
+    // and none can run two phases ahead of its waiter: each next phase
+    // needs an action that follows the wait on the current one.
     const int ntiles = (B + BM - 1) / BM;
     const int ntl = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int items = 8 * ((ntl + 1) / 2);
+    auto tile_row = [&](int i) { return ((int)blockIdx.x + i * (int)gridDim.x) * BM; };
 
     if (warp == LOAD_WARP) {
         if (lane == 0) {
-            // ---- loads: per tile the input tile (once the previous tile's
-            // layer-2 MMAs have read that buffer), then the 17 weight tiles
-            int g = 0, nx = 0;  // weight tiles and input tiles issued
+            // ---- loads, in work-item order: a slot's input tile before its
+            // layer 0 (once the slot's previous tile has left the buffer),
+            // then the item's weight tiles
+            int g = 0, nx[2] = {0, 0};  // weight tiles, input tiles per slot issued
             bool ok = true;
-            for (int i = 0; i < ntl && ok; ++i) {
-                if (i > 0 && !mbar_wait(a_free, (uint32_t)(i - 1) & 1u, err)) {
-                    ok = false;
-                    break;
+            for (int it = 0; it < items && ok; ++it) {
+                const int p = it >> 3, l = (it >> 1) & 3, j = it & 1, i = 2 * p + j;
+                if (i >= ntl) continue;
+                if (l == 0) {
+                    if (p > 0 && !mbar_wait(buf_free(j), (uint32_t)(p - 1) & 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(x_full(j), KB_IN * A_TILE);
+                    for (int kb = 0; kb < KB_IN; ++kb)
+                        tma_load_2d(&mapX, x_full(j), base + j * BUF + kb * A_TILE, kb * BK, tile_row(i));
+                    ++nx[j];
                 }
-                const int m0 = (blockIdx.x + i * gridDim.x) * BM;
-                mbar_expect_tx(x_full, KB_IN * A_TILE);
-                for (int kb = 0; kb < KB_IN; ++kb) tma_load_2d(&mapX, x_full, base + BUF_A + kb * A_TILE, kb * BK, m0);
-                ++nx;
-                for (int w = 0; w < TILES; ++w, ++g) {
+                const CUtensorMap* map = l == 0 ? &mapW0 : l == 1 ? &mapW1 : l == 2 ? &mapW2 : &mapW3;
+                const uint32_t bytes = l == 3 ? MLP_OUT * BK * 2 : W_TILE;
+                const int nkb = l == 0 ? KB_IN : KB_H;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int s = g % STAGES;
                     if (g >= STAGES && !mbar_wait(empty(s), (uint32_t)((g / STAGES) - 1) & 1u, err)) {
                         ok = false;
                         break;
                     }
-                    const int layer = w < KB_IN ? 0 : 1 + (w - KB_IN) / KB_H;
-                    const int kb = w < KB_IN ? w : (w - KB_IN) % KB_H;
-                    const CUtensorMap* map = layer == 0 ? &mapW0 : layer == 1 ? &mapW1 : layer == 2 ? &mapW2 : &mapW3;
-                    const uint32_t bytes = layer == 3 ? MLP_OUT * BK * 2 : W_TILE;
                     mbar_expect_tx(full(s), bytes);
                     tma_load_2d(map, full(s), base + RING + s * W_TILE, kb * BK, 0);
                 }
@@ -687,49 +691,50 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
             if (!ok) {  // let the copies in flight land before the CTA goes away
                 for (int h = (g > STAGES ? g - STAGES : 0); h < g; ++h)
                     mbar_wait(full(h % STAGES), (uint32_t)(h / STAGES) & 1u, err);
-                if (nx > 0) mbar_wait(x_full, (uint32_t)(nx - 1) & 1u, err);
+                for (int j = 0; j < 2; ++j)
+                    if (nx[j] > 0) mbar_wait(x_full(j), (uint32_t)(nx[j] - 1) & 1u, err);
             }
         }
     } else if (warp == MMA_WARP) {
         if (lane == 0) {
-            // ---- MMA issue: per tile layer by layer, each K tile of a hidden
-            // layer's input as soon as the epilogue has written it.  Layer 0
-            // of the next tile reuses accumulator 0 of layer 2: its epilogue
-            // has read it once every K tile of layer 2's output is announced,
-            // which layer 3's MMAs waited for.
+            // ---- MMA issue, in work-item order: layer l of a slot once the
+            // slot's input tile has landed (l = 0) or once its epilogue of
+            // layer l - 1 (of the previous tile for l = 0) is done
             bool ok = true;
             int g = 0;
-            for (int i = 0; i < ntl && ok; ++i) {
-                ok = mbar_wait(x_full, (uint32_t)i & 1u, err);
-                tc_fence_after();
-                for (int layer = 0; layer < 4 && ok; ++layer) {
-                    const uint32_t a_buf = base + ((layer & 1) ? BUF_B : BUF_A);
-                    const uint32_t d_tmem = tmem + (uint32_t)((layer & 1) * MLP_H);
-                    const int nkb = layer == 0 ? KB_IN : KB_H;
-                    const uint32_t idesc = umma_idesc_bf16(BM, layer == 3 ? MLP_OUT : MLP_H);
-                    const uint32_t hpar = (uint32_t)(3 * i + layer - 1) & 1u;
-                    for (int kb = 0; kb < nkb && ok; ++kb, ++g) {
-                        if (layer > 0 && !mbar_wait(act_ready(kb), hpar, err)) {
-                            ok = false;
-                            break;
-                        }
-                        const int s = g % STAGES;
-                        if (!mbar_wait(full(s), (uint32_t)(g / STAGES) & 1u, err)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t a = a_buf + kb * A_TILE;
-                        const uint32_t b = base + RING + s * W_TILE;
-#pragma unroll
-                        for (int k = 0; k < BK / UK; ++k)
-                            umma_bf16(d_tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
-                                      (uint32_t)((kb | k) != 0));
-                        umma_commit(empty(s));
-                    }
-                    if (layer == 2) umma_commit(a_free);  // the input buffer is free once these MMAs are done
-                    umma_commit(acc_full(layer));
+            for (int it = 0; it < items && ok; ++it) {
+                const int p = it >> 3, l = (it >> 1) & 3, j = it & 1, i = 2 * p + j;
+                if (i >= ntl) continue;
+                if (l == 0) {
+                    ok = mbar_wait(x_full(j), (uint32_t)p & 1u, err);
+                    if (ok && p > 0) ok = mbar_wait(epi_done(j), 1u, err);  // layer 3 of the slot's previous tile
+                } else {
+                    ok = mbar_wait(epi_done(j), (uint32_t)(l - 1) & 1u, err);
                 }
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t a_buf = base + j * BUF;
+                const uint32_t d_tmem = tmem + (uint32_t)(j * MLP_H);
+                const int nkb = l == 0 ? KB_IN : KB_H;
+                const uint32_t idesc = umma_idesc_bf16(BM, l == 3 ? MLP_OUT : MLP_H);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (!mbar_wait(full(s), (uint32_t)(g / STAGES) & 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = a_buf + kb * A_TILE;
+                    const uint32_t b = base + RING + s * W_TILE;
+#pragma unroll
+                    for (int k = 0; k < BK / UK; ++k)
+                        umma_bf16(d_tmem, sw128_desc(a + k * UK * 2), sw128_desc(b + k * UK * 2), idesc,
+                                  (uint32_t)((kb | k) != 0));
+                    umma_commit(empty(s));
+                }
+                if (!ok) break;
+                if (l == 3) umma_commit(buf_free(j));  // the slot's buffer is free once these MMAs are done
+                umma_commit(acc_full(j));
             }
             if (!ok) {  // so that the epilogue does not wait for nothing
                 umma_commit(acc_full(0));
@@ -737,19 +742,19 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
             }
         }
     } else {
-        // ---- epilogue warps
+        // ---- epilogue warps, in work-item order
         const int q = warp & 3, part = warp >> 2;
         const int r = q * 32 + lane;  // tile row of this thread
-        bool ok = true;
-        for (int i = 0; i < ntl && ok; ++i)
-        for (int layer = 0; layer < 4; ++layer) {
-            const int row = (blockIdx.x + i * gridDim.x) * BM + r;
-            ok = mbar_wait(acc_full(layer), (uint32_t)(layer >> 1) & 1u, err);
+        for (int it = 0; it < items; ++it) {
+            const int p = it >> 3, l = (it >> 1) & 3, j = it & 1, i = 2 * p + j;
+            if (i >= ntl) continue;
+            const bool ok = mbar_wait(acc_full(j), (uint32_t)l & 1u, err);
             tc_fence_after();
             if (!ok) break;
-            const float* bias = P + L.b[layer];
-            if (layer < 3) {
-                uint8_t* out = gbase + ((layer & 1) ? BUF_A : BUF_B);  // layer 0 -> B, 1 -> A, 2 -> B
+            const float* bias = P + L.b[l];
+            const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(j * MLP_H);
+            if (l < 3) {
+                uint8_t* out = gbase + j * BUF;
                 // columns c0 .. c0+15 from the registers of their load: bias
                 // (four 16-byte loads), GELU, BF16, then K tile c0 / 64 as two
                 // 16-byte chunks
@@ -757,36 +762,30 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
                     const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
                     float bb[16];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float4 t = __ldg(b4 + j);
-                        bb[4 * j] = t.x;
-                        bb[4 * j + 1] = t.y;
-                        bb[4 * j + 2] = t.z;
-                        bb[4 * j + 3] = t.w;
+                    for (int e = 0; e < 4; ++e) {
+                        const float4 t = __ldg(b4 + e);
+                        bb[4 * e] = t.x;
+                        bb[4 * e + 1] = t.y;
+                        bb[4 * e + 2] = t.z;
+                        bb[4 * e + 3] = t.w;
                     }
                     uint32_t pk[8];
 #pragma unroll
-                    for (int j = 0; j < 16; j += 2) {
-                        const float2 g = gelu2_f(__fadd2_rn(make_float2(__uint_as_float(rv[j]), __uint_as_float(rv[j + 1])),
-                                                            make_float2(bb[j], bb[j + 1])));
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(g.x, g.y);
-                        pk[j >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
+                    for (int e = 0; e < 16; e += 2) {
+                        const float2 gv = gelu2_f(__fadd2_rn(make_float2(__uint_as_float(rv[e]), __uint_as_float(rv[e + 1])),
+                                                             make_float2(bb[e], bb[e + 1])));
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(gv.x, gv.y);
+                        pk[e >> 1] = *reinterpret_cast<const uint32_t*>(&h2);
                     }
                     uint8_t* tile = out + (c0 / BK) * A_TILE;
                     const int cc = c0 % BK;
                     *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     *reinterpret_cast<uint4*>(tile + sw128_offset(r, cc + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 };
-                // K tile by K tile (warp part p takes columns 64 kt + 16 p ..
-                // + 15 of each), announcing each tile when written; the next
-                // chunk's accumulator load runs while this chunk is worked on
-                const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((layer & 1) * MLP_H);
+                // warp part p takes columns 64 kt + 16 p .. + 15 of each K
+                // tile kt; the next chunk's accumulator load runs while this
+                // chunk is worked on
                 auto col = [&](int kt) { return kt * BK + part * 16; };
-                auto written = [&](int kt) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    tc_fence_before();
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(act_ready(kt)) : "memory");
-                };
                 uint32_t ra[16], rb[16];
                 tmem_ld16_async(tb + (uint32_t)col(0), ra);
                 tmem_wait16(ra);
@@ -794,24 +793,26 @@ k_mlp_fused(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CU
                 for (int kt = 0; kt < KB_H; kt += 2) {
                     tmem_ld16_async(tb + (uint32_t)col(kt + 1), rb);
                     emit(ra, col(kt));
-                    written(kt);
                     tmem_wait16(rb);
                     if (kt + 2 < KB_H) tmem_ld16_async(tb + (uint32_t)col(kt + 2), ra);
                     emit(rb, col(kt + 1));
-                    written(kt + 1);
                     if (kt + 2 < KB_H) tmem_wait16(ra);
                 }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             } else if (part == 0) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((layer & 1) * MLP_H), v);
+                tmem_ld16(tb, v);
+                const int row = tile_row(i) + r;
                 if (row < B) {
                     float4* o = reinterpret_cast<float4*>(y + (size_t)row * MLP_OUT);
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        o[j / 4] = make_float4(v[j] + __ldg(bias + j), v[j + 1] + __ldg(bias + j + 1),
-                                               v[j + 2] + __ldg(bias + j + 2), v[j + 3] + __ldg(bias + j + 3));
+                    for (int e = 0; e < 16; e += 4)
+                        o[e / 4] = make_float4(v[e] + __ldg(bias + e), v[e + 1] + __ldg(bias + e + 1),
+                                               v[e + 2] + __ldg(bias + e + 2), v[e + 3] + __ldg(bias + e + 3));
                 }
             }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(epi_done(j)) : "memory");
         }
     }
     tc_fence_before();
