@@ -198,9 +198,12 @@ def _work_snapshot(s):
     whose stream overflowed, for the step last run."""
     nc = s.field("ncand").cpu().numpy().astype(np.int64)
     nbr = s.field("nbr_count").cpu().numpy()
+    from paper_2311_15088_gb300.sph import STATS
+    st = s.stats().cpu().numpy()[0]
     return {"candidates": int(nc.sum()), "pairs": int(nbr.astype(np.int64).sum()),
             "overflow_candidates": int(nc[nc > STREAM_CAPACITY].sum()),
-            "nbr_mean": float(nbr.mean()), "nbr_max": int(nbr.max())}
+            "nbr_mean": float(nbr.mean()), "nbr_max": int(nbr.max()),
+            "stats": {k: float(v) for k, v in zip(STATS, st)}}
 
 
 def _source_sha(path):
@@ -809,6 +812,8 @@ def run_ours(a):
                        "neighbours_mean": statistics.mean(w["nbr_mean"] for w in works),
                        "neighbours_max": max(w["nbr_max"] for w in works),
                        "candidates_per_particle": cand / n_all},
+            "diagnostics": {"source": "sph_stats (fluid particles) after the first and the last sampled timed step",
+                            "first": works[0]["stats"], "last": works[-1]["stats"]},
             "roofline": roofline, "hbm": hbm, "passes": passes, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "device_status": status, "neighbor_search": nsearch,
             "batched": batched,

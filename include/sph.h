@@ -299,6 +299,44 @@ int sph_debug_neighbors(sph_handle* h, int* counts, const long long* offsets, in
                         void* stream);
 
 /*
+ * Per-step diagnostics (the step's optional statistics row): for every scene
+ * k, from the state after the most recent step and that step's fields,
+ * out[k * SPH_STATS_N + i] (float64; device, or host with on_host = 1, which
+ * synchronises the stream) with i =
+ *   SPH_STAT_FLUID      fluid particles of the scene
+ *   SPH_STAT_NBR_MEAN   mean neighbour count of its fluid particles (self
+ *                       excluded; section "Neighborhood Search")
+ *   SPH_STAT_NBR_MAX    largest neighbour count of a fluid particle
+ *   SPH_STAT_CELL_MAX   most particles (attached included) in one cell of
+ *                       the step's binning
+ *   SPH_STAT_MOM_X..Z   sum of m v over its fluid particles after the step
+ *   SPH_STAT_KE         kinetic energy (1/2) m sum |v|^2 of the fluid after
+ *                       the step
+ *   SPH_STAT_RHO_MIN, SPH_STAT_RHO_MAX, SPH_STAT_RHO_MEAN
+ *                       the fluid particles' densities of the step
+ *   SPH_STAT_SPEED_MAX  largest fluid speed after the step
+ * (means, density bounds: 0 for a scene without fluid).  Sums are float64 in
+ * a fixed order: the same state gives the same bits, whatever else is in the
+ * batch.  Two kernel launches; no allocation, graph-capturable with
+ * on_host = 0.  Errors: SPH_ERR_ARG (NULL), SPH_ERR_STATE (no step since
+ * the state was loaded), SPH_ERR_CUDA.
+ */
+#define SPH_STATS_N        12
+#define SPH_STAT_FLUID      0
+#define SPH_STAT_NBR_MEAN   1
+#define SPH_STAT_NBR_MAX    2
+#define SPH_STAT_CELL_MAX   3
+#define SPH_STAT_MOM_X      4
+#define SPH_STAT_MOM_Y      5
+#define SPH_STAT_MOM_Z      6
+#define SPH_STAT_KE         7
+#define SPH_STAT_RHO_MIN    8
+#define SPH_STAT_RHO_MAX    9
+#define SPH_STAT_RHO_MEAN  10
+#define SPH_STAT_SPEED_MAX 11
+int sph_stats(sph_handle* h, double* out, int on_host, void* stream);
+
+/*
  * Read (and keep) the sticky device error word into *bits; synchronises the
  * handle's last stream.  sph_clear_status zeroes it (asynchronously).
  */

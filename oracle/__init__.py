@@ -258,3 +258,37 @@ def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, obstacles=None) -> d
     if rc != 0:
         raise ValueError(f"oracle step rejected the parameters (rc={rc})")
     return o
+
+
+STATS = ("fluid", "nbr_mean", "nbr_max", "cell_max", "mom_x", "mom_y", "mom_z", "ke", "rho_min", "rho_max",
+         "rho_mean", "speed_max")
+
+
+def step_stats(p: dict, o: dict, n_boid: int) -> np.ndarray:
+    """The step's diagnostics, each written out from its definition over the
+    outputs ``o`` of one oracle step (``step``) of a scene with ``n_boid``
+    boids, in the order of ``STATS``: the fluid particle count; the mean and
+    largest neighbour count of the fluid particles (self excluded, section
+    "Neighborhood Search"); the most particles in one cell of the step's
+    binning; the momentum sum m v and the kinetic energy sum m |v|^2 / 2 of
+    the fluid after the step; the smallest, largest and mean fluid density
+    of the step; the largest fluid speed after the step.  Means and density
+    bounds are 0 without fluid."""
+    m = float(np.float32(p["mass"]))
+    v = np.asarray(o["new_fluid_vel"], np.float64)
+    nf = v.shape[0]
+    nbr = np.asarray(o["nbr_count"][n_boid:], np.float64)
+    rho = np.asarray(o["rho"][n_boid:], np.float64)
+    occ = np.diff(np.asarray(o["cell_start"], np.int64))
+    speed2 = (v * v).sum(axis=1)
+    out = np.zeros(len(STATS))
+    out[0] = nf
+    out[3] = occ.max() if occ.size else 0
+    if nf:
+        out[1] = nbr.sum() / nf
+        out[2] = nbr.max()
+        out[4:7] = m * v.sum(axis=0)
+        out[7] = 0.5 * m * speed2.sum()
+        out[8], out[9], out[10] = rho.min(), rho.max(), rho.sum() / nf
+        out[11] = np.sqrt(speed2.max())
+    return out

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsph_gb300.so")
 
-SOURCES = ["sph_api.cu", "sph_bin.cu", "sph_physics.cu", "sph_boids.cu", "sph_static.cu", "sph_mlp.cu", "sph_features.cu", "sph_surface.cu"]
+SOURCES = ["sph_api.cu", "sph_bin.cu", "sph_physics.cu", "sph_boids.cu", "sph_static.cu", "sph_mlp.cu", "sph_features.cu", "sph_surface.cu", "sph_stats.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

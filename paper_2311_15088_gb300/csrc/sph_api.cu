@@ -65,6 +65,9 @@ struct sph_handle {
     size_t list_cap;      // per sorted slot
     int* bflag;               // per boid
     int nb_pad;
+    int stats_chunks;         // blocks per scene of the statistics (sph_stats)
+    double* stats_part;       // their float64 partials
+    double* stats_out;        // staging of a host copy (S x SPH_STATS_N)
     sph_mlp* mlp;
     float f_scale, log_err_max;
     const float *feat_lo, *feat_hi;  // the caller's input range (NULL: no check)
@@ -316,6 +319,8 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->noff = cv.take<unsigned>(n + 1);
     h->noff_part = cv.take<unsigned>((size_t)scan_parts((int)n) + 1);
     h->bflag = cv.take<int>(nb);
+    h->stats_part = cv.take<double>((size_t)h->S * h->stats_chunks * STATS_PART);
+    h->stats_out = cv.take<double>((size_t)h->S * STATS_OUT);
     return (size_t)((cv.off + 255) & ~(uintptr_t)255);
 }
 
@@ -452,6 +457,7 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
     h->h_bbase = new (std::nothrow) unsigned[S + 1];
     if (!h->params || !h->consts || !h->h_pbase || !h->h_bbase) return fail(nullptr, SPH_ERR_ARG, "out of host memory");
     long long n = 0, nb = 0, nf = 0, C = 0, Cb = 0;
+    h->stats_chunks = 1;
     for (int k = 0; k < S; ++k) {
         int rc = validate(&params[k], n_fluid[k], n_boid[k]);
         if (rc != SPH_OK) return rc;
@@ -468,6 +474,8 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
         nf += n_fluid[k];
         C += h->consts[k].g.ncells;
         Cb += h->consts[k].gb.ncells;
+        const long long span = std::max((long long)n_fluid[k] + n_boid[k], (long long)h->consts[k].g.ncells);
+        h->stats_chunks = std::max(h->stats_chunks, (int)((span + STATS_CHUNK - 1) / STATS_CHUNK));
         if (n > 2147483647LL || C > 2147483646LL || Cb > 2147483646LL)
             return fail(nullptr, SPH_ERR_OVERFLOW, "the batch exceeds 2^31 particles or cells");
     }
@@ -1096,6 +1104,24 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
     CUDA_TRY(h, cudaGetLastError());
     if (on_host) {
         if (bytes) CUDA_TRY(h, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+    }
+    return SPH_OK;
+}
+
+int sph_stats(sph_handle* h, double* out, int on_host, void* stream)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (!out) return fail(h, SPH_ERR_ARG, "out is NULL");
+    if (!h->has_step) return fail(h, SPH_ERR_STATE, "no step since the state was loaded or staged");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    const size_t bytes = (size_t)h->S * SPH_STATS_N * sizeof(double);
+    double* dst = on_host ? h->stats_out : out;
+    CUDA_TRY(h, launch_stats(h->pos, h->vel, h->rho, h->nbr, h->cell_start, h->sc, h->stats_chunks, h->stats_part,
+                             dst, s, &h->launches));
+    if (on_host) {
+        CUDA_TRY(h, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, s));
         CUDA_TRY(h, cudaStreamSynchronize(s));
     }
     return SPH_OK;

@@ -26,6 +26,9 @@ SPH_COUPLE_FORCE = 0
 SPH_DEV_NONFINITE, SPH_DEV_CLAMPED, SPH_DEV_TIMEOUT = 1, 2, 4
 SPH_BOID_EXACT, SPH_BOID_SURROGATE, SPH_BOID_SURROGATE_FALLBACK, SPH_BOID_EXACT_LOCAL = 0, 1, 2, 3
 SPH_MAX_OBSTACLES = 256
+SPH_STATS_N = 12
+STATS = ("fluid", "nbr_mean", "nbr_max", "cell_max", "mom_x", "mom_y", "mom_z", "ke", "rho_min", "rho_max",
+         "rho_mean", "speed_max")
 
 FIELDS = {
     "rho": (0, np.float32, 1), "pressure": (1, np.float32, 1), "acc": (2, np.float32, 4),
@@ -64,6 +67,7 @@ _sig = {
     "sph_get_fields": (_i, [_vp, _i, _vp, _i, _vp]),
     "sph_debug_neighbors": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "sph_status": (_i, [_vp, ctypes.POINTER(ctypes.c_uint)]),
+    "sph_stats": (_i, [_vp, _vp, _i, _vp]),
     "sph_clear_status": (_i, [_vp, _vp]),
     "sph_last_error": (ctypes.c_char_p, [_vp]),
     "sph_launch_count": (ctypes.c_longlong, [_vp]),
@@ -241,6 +245,10 @@ def sph_get_fields(h, field: int, out_ptr: int, on_host: int, stream: int):
 
 def sph_debug_neighbors(h, counts_ptr: int, offsets_ptr, list_ptr, stream: int):
     _check(_lib.sph_debug_neighbors(h, counts_ptr, offsets_ptr, list_ptr, stream), h)
+
+
+def sph_stats(h, out_ptr: int, on_host: int, stream: int):
+    _check(_lib.sph_stats(h, out_ptr, on_host, stream), h)
 
 
 def sph_status(h) -> int:
@@ -621,6 +629,14 @@ class Scene:
         out = t.empty((n, width) if width > 1 else (n,), dtype=tdtype, device=self.device)
         if out.numel():
             sph_get_fields(self.handle, code, out.data_ptr(), 0, self.stream)
+        return out
+
+    def stats(self):
+        """Per-scene statistics of the most recent step (sph_stats): a float64
+        (scenes, SPH_STATS_N) tensor on the device, columns named by STATS."""
+        t = self.torch
+        out = t.empty((len(self.params_list), SPH_STATS_N), dtype=t.float64, device=self.device)
+        sph_stats(self.handle, out.data_ptr(), 0, self.stream)
         return out
 
     def boid_forces(self, mode: int = 0):
