@@ -78,3 +78,55 @@ def test_internal_forces_conserve_momentum():
     scale = m * np.abs(fv[:, :3]).sum()
     assert scale > 0
     assert np.all(np.abs(mom) <= 1e-3 * scale), (mom, scale)
+
+
+def test_column_settles_under_gravity():
+    """A full-width lattice column (43 x 21 x 43 particles at h/2, the
+    calibrated mass) released under gravity compresses, oscillates and
+    settles: the kinetic energy falls by over 95 % between 1,000 and 12,000
+    steps, every particle stays in the box, and away from the side walls
+    the density grows monotonically with depth.  The continuum balance
+    k d(rho)/dy = -rho g would give d(ln rho)/dy = -g/k; the discretisation
+    (symmetric pressure term with the spiky gradient, density by poly6) is
+    not consistent under the 2.5-fold density variation of this weak
+    equation of state, and the settled column's log-slope is steeper: it is
+    checked to lie between g/k and 3 g/k."""
+    p = scenes.default_params(mass=scenes.f32(1.0))
+    h = float(p["h"])
+    s = scenes.f32(np.float32(p["h"]) / np.float32(2))
+    p["mass"] = scenes.f32(oracle.lattice_mass(p, s))
+    nx, ny = 43, 21
+    rng = scenes.PaperHashRNG(20231115, np.arange(nx * ny * nx))
+    pos = scenes.lattice_block((nx, ny, nx), s, (0.5 * s,) * 3, 0.0, rng)
+    z = np.zeros((0, 4), np.float32)
+    sc = Scene(p, len(pos), 0)
+    sc.set_state(pos, np.zeros_like(pos), z, z)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sc.graph_step(1000)
+        ke0 = float(sc.stats()[0, 7])
+        sc.graph_step(11000)
+        ke1 = float(sc.stats()[0, 7])
+        fp = sc.get_state()[0].cpu().numpy()
+        rho = sc.field("rho").cpu().numpy()
+    torch.cuda.synchronize()
+    assert sc.status() & 1 == 0
+    assert ke1 < 0.05 * ke0, (ke0, ke1)
+    assert fp[:, :3].min() >= 0.0 and fp[:, :3].max() <= 1.0
+    w = float(s) * nx
+    x, y, zz = fp[:, 0], fp[:, 1].astype(np.float64), fp[:, 2]
+    inner = (x > 3 * h) & (x < w - 3 * h) & (zz > 3 * h) & (zz < w - 3 * h)
+    edges = np.arange(h, y[inner].max(), h / 2)  # above the floor's truncated layer
+    slab = np.digitize(y[inner], edges) - 1
+    mids, means = [], []
+    for i in range(len(edges) - 1):
+        sel = slab == i
+        if sel.sum() > 50:
+            mids.append(0.5 * (edges[i] + edges[i + 1]))
+            means.append(rho[inner][sel].mean())
+    mids, means = np.array(mids), np.array(means)
+    assert len(means) >= 4
+    assert np.all(np.diff(means) < 0), means
+    slope = -np.polyfit(mids[:-1], np.log(means[:-1]), 1)[0]  # the top slab is the free surface
+    gk = 9.8 / 3.0
+    assert gk < slope < 3 * gk, slope
