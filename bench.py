@@ -457,7 +457,24 @@ def run_batched(a, dev, flush):
         t_loop = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
         del loop
     S = len(scs)
+    cpu = None
+    if not a.no_cpu_baseline:
+        # the oracle, as it stands, one step of every 16th scene (its cell size)
+        import oracle
+
+        oracle.build()
+        picked = list(range(0, S, 16))
+        t0 = time.perf_counter()
+        for i in picked:
+            sc = scs[i]
+            oracle.step(chosen["params"][i], sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+        el = time.perf_counter() - t0
+        cpu = {"value": len(picked) / el, "unit": "scenes/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "particle_steps_per_s": sum(nf[i] for i in picked) / el,
+               "sample": f"one oracle step of each of {len(picked)} scenes (every 16th), "
+                         f"{sum(nf[i] for i in picked)} fluid particles"}
     return {
+        "cpu_baseline": cpu,
         "workload": f"{S} unit-box dam-breaks, particles log-uniform in [2048, 65536], boids uniform in [8, 256]",
         "scenes": S, "particles": int(sum(nf)), "boids": int(sum(nb)), "steps": a.batch_steps,
         "scenes_per_s": S * a.batch_steps / t_batch, "ms_per_step": 1e3 * t_batch / a.batch_steps,
@@ -535,6 +552,35 @@ def _mode_report(surrogate, ms, got, fall, q, n_states):
     return out
 
 
+def _oracle_surrogate(p, sc):
+    """The oracle, as it stands, on the surrogate's work: stencil features of
+    64 boids of the evaluation column state, the float64 network over
+    65,536 rows (random rows of the feature width: the cost does not depend
+    on the values), and one full oracle step of the state (which computes
+    every boid's exact F_b)."""
+    import oracle
+    from oracle import features, mlp as omlp
+
+    oracle.build()
+    nb = 64
+    t0 = time.perf_counter()
+    features.stencil_features(p, sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"][:nb], sc["boid_vel"][:nb])
+    t_feat = (time.perf_counter() - t0) / nb
+    x = np.random.default_rng(0).normal(size=(65536, omlp.D_IN))
+    params = omlp.init_params(0)
+    t0 = time.perf_counter()
+    omlp.forward(params, x)
+    t_mlp = (time.perf_counter() - t0) / len(x)
+    t0 = time.perf_counter()
+    oracle.step(p, sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    t_step = time.perf_counter() - t0
+    return {"value": 1.0 / (t_feat + t_mlp), "unit": "queries/s", "kind": "oracle", "cores": oracle.num_threads(),
+            "features_qps": 1.0 / t_feat, "network_fp64_qps": 1.0 / t_mlp,
+            "exact_qps": len(sc["boid_pos"]) / t_step,
+            "sample": f"features of {nb} boids; the float64 network on 65,536 rows; one full oracle step of the "
+                      f"{len(sc['fluid_pos'])}-particle state with its {len(sc['boid_pos'])} boids (exact F_b)"}
+
+
 def run_surrogate(a, dev, big=None):
     """Boid-force queries: the surrogate (features + tensor-core MLP), the
     surrogate with its exact fallback at the calibrated 5 % aggregate error,
@@ -566,6 +612,8 @@ def run_surrogate(a, dev, big=None):
     out = {"workload": "65,536 boid-force queries: 64 states x 1,024 boids of a 262,144-particle column run",
            "training": info, "queries": n_states * s.n_boid}
     out.update(_mode_report(surrogate, ms, got, fall, n_states * s.n_boid, n_states))
+    if not a.no_cpu_baseline:
+        out["cpu_baseline"] = _oracle_surrogate(p, sc)
     if big is not None:
         # distribution shift: the settled 2M-particle tank and its 16,384 boids
         big.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
