@@ -536,8 +536,10 @@ def _mode_report(surrogate, ms, got, fall, q, n_states):
     F = torch.cat(got["exact_local"])
     out = {}
     for name in ms:
+        med, p90 = surrogate.per_query_error(torch.cat(got[name]), F)
         out[name] = {"qps": q / (ms[name] / 1e3), "ms_per_state": ms[name] / n_states,
-                     "aggregate_error": surrogate.aggregate_error(torch.cat(got[name]), F)}
+                     "aggregate_error": surrogate.aggregate_error(torch.cat(got[name]), F),
+                     "per_query_error_median": med, "per_query_error_p90": p90}
     for name, fl in fall.items():
         out[name]["fallback_fraction"] = float(torch.cat(fl).mean().item())
     out["exact_local_equals_exact_full"] = bool(torch.equal(F, torch.cat(got["exact_full"])))

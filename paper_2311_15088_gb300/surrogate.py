@@ -145,6 +145,16 @@ def aggregate_error(F_used, F) -> float:
     return float((F_used - F).double().norm() / F.double().norm().clamp_min(1e-30))
 
 
+def per_query_error(F_used, F):
+    """Median and 90th percentile over the queries of |F_used - F| /
+    max(|F|, 0.05 RMS F) (RMS over these queries), the per-query companion
+    of the aggregate error."""
+    import torch
+
+    rel = rel_errors(F_used, F, f_scale_of(F))
+    return float(rel.median()), float(torch.quantile(rel, 0.9))
+
+
 BOUND_MARGIN = 0.1
 
 

@@ -105,3 +105,21 @@ def test_library_mc_tables_equal_the_oracle_generator(lib):
     assert np.array_equal(e.astype(np.int64), oe)
     assert np.array_equal(t.astype(np.int64), ot)
     assert e[8] == 0x80C and list(t[8][:4]) == [2, 3, 11, -1]
+
+
+def test_surrogate_per_query_error_by_hand():
+    """Median and 90th percentile of |dF| / max(|F|, 0.05 RMS F): three
+    queries worked by hand (RMS |F| = sqrt(5/3), floor 0.0645...)."""
+    import math
+
+    import torch
+
+    from paper_2311_15088_gb300 import surrogate
+
+    F = torch.tensor([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0], [0.0, 0.0, 0.0]], dtype=torch.float64)
+    Fu = F + torch.tensor([[0.1, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.01]], dtype=torch.float64)
+    med, p90 = surrogate.per_query_error(Fu, F)
+    floor = 0.05 * math.sqrt(5.0 / 3.0)
+    rel = sorted([0.1, 0.0, 0.01 / floor])
+    assert med == pytest.approx(rel[1], rel=1e-12)
+    assert p90 == pytest.approx(rel[1] + 0.8 * (rel[2] - rel[1]), rel=1e-12)
