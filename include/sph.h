@@ -315,9 +315,10 @@ int sph_debug_neighbors(sph_handle* h, int* counts, const long long* offsets, in
  *   SPH_STAT_RHO_MIN, SPH_STAT_RHO_MAX, SPH_STAT_RHO_MEAN
  *                       the fluid particles' densities of the step
  *   SPH_STAT_SPEED_MAX  largest fluid speed after the step
- * (means, density bounds: 0 for a scene without fluid).  Sums are float64 in
- * a fixed order: the same state gives the same bits, whatever else is in the
- * batch.  Two kernel launches; no allocation, graph-capturable with
+ * (means, density bounds: 0 for a scene without fluid).  Counts and the
+ * neighbour sum are integers, extrema exact; the other sums are float64 over
+ * float32 partial sums of at most 8 values, all in a fixed order: the same
+ * state gives the same bits, whatever else is in the batch.  Two kernel launches; no allocation, graph-capturable with
  * on_host = 0.  Errors: SPH_ERR_ARG (NULL), SPH_ERR_STATE (no step since
  * the state was loaded), SPH_ERR_CUDA.
  */

@@ -436,7 +436,7 @@ cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const flo
 // Per-scene step statistics (sph_stats): blocks of STATS_CHUNK slots write
 // STATS_PART float64 partials each (part: S x chunks x STATS_PART), one block
 // per scene reduces them to STATS_OUT values in out (S x STATS_OUT).
-constexpr int STATS_CHUNK = 8192;
+constexpr int STATS_CHUNK = 2048;
 constexpr int STATS_PART = 12;
 constexpr int STATS_OUT = 12;  // SPH_STATS_N
 cudaError_t launch_stats(const float4* pos, const float4* vel, const float* rho, const int* nbr,
