@@ -554,6 +554,37 @@ def _mode_report(surrogate, ms, got, fall, q, n_states):
     return out
 
 
+def _network_roofline(s, mlp, reps=50):
+    """The trained network alone (the fused tcgen05 forward) on 65,536 rows:
+    the state's 1,024 feature rows tiled 64 times; BF16 dense flops per
+    launch over its CUDA-event time, against the measured BF16 peak."""
+    import torch
+
+    X = s.features().repeat(64, 1).contiguous()
+    for _ in range(3):
+        mlp.forward(X)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        mlp.forward(X)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * X.shape[0] * (272 * 256 + 256 * 256 * 2 + 256 * 16)
+    peak = None
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        pass
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "k_mlp_fused (4 layers, 65,536 rows)", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak if peak else None, "ms_per_launch": ms,
+            "queries_per_s": X.shape[0] / (ms * 1e-3), "flops_per_launch": flops,
+            "peak_source": "measured (bf16 burst)" if peak else None}
+
+
 def _oracle_surrogate(p, sc):
     """The oracle, as it stands, on the surrogate's work: stencil features of
     64 boids of the evaluation column state, the float64 network over
@@ -614,6 +645,7 @@ def run_surrogate(a, dev, big=None):
     out = {"workload": "65,536 boid-force queries: 64 states x 1,024 boids of a 262,144-particle column run",
            "training": info, "queries": n_states * s.n_boid}
     out.update(_mode_report(surrogate, ms, got, fall, n_states * s.n_boid, n_states))
+    out["network_roofline"] = _network_roofline(s, mlp)
     if not a.no_cpu_baseline:
         out["cpu_baseline"] = _oracle_surrogate(p, sc)
     if big is not None:
