@@ -160,13 +160,32 @@ int sph_batch_create(const sph_params* params, const int* n_fluid, const int* n_
                      void* workspace, size_t ws_bytes, sph_handle** out);
 
 /*
- * Launch shape of the two neighbour passes: `block` threads per block (64,
- * 128, 256 or 512) and whether the force pass reuses the candidate bits the
- * density pass records (use_stream = 1) or tests the candidates again
- * (0, the default).  Neither changes any result bit: the per-particle
- * arithmetic and its order are the same.  Errors: SPH_ERR_ARG.
+ * Launch shape of the two neighbour passes (section "Neighbor Search with
+ * Sorting": the density pass and the force pass each search the sorted
+ * grid): `block` threads per block (64, 128, 256 or 512), and where the
+ * force pass takes its pairs from.  use_segments = 1 (the default): the
+ * density pass, which tests every candidate anyway, records each fluid
+ * particle's force pairs as segments (first sorted slot, 32-bit mask) in
+ * walk order, and the force pass reads them instead of testing the
+ * candidates again (512 bytes of workspace per particle hold them; a
+ * particle with more than 64 segments is tested again).  use_segments = 0:
+ * the force pass tests the candidates itself.  Neither choice changes any
+ * result bit: the pairs and their order are the same.  Errors: SPH_ERR_ARG.
  */
-int sph_set_tuning(sph_handle* h, int block, int use_stream);
+int sph_set_tuning(sph_handle* h, int block, int use_segments);
+
+/*
+ * Record the diagnostic fields in later steps: with record = 1 the force
+ * pass also stores each particle's acceleration, touched_by_boid and
+ * boid_influence (listing "Compute acceleration", section "Boid Motion and
+ * Agent Fluid Interaction") for sph_get_fields; with record = 0 (the
+ * default) it does not write them (36 bytes per particle and step less),
+ * and SPH_FIELD_ACC, SPH_FIELD_TOUCHED and SPH_FIELD_INFLUENCE fail with
+ * SPH_ERR_STATE until a step is taken with record = 1.  The step's results
+ * (state, densities, F_b) are the same either way.  A captured step
+ * (sph_graph_step) is captured again after a change.  Errors: SPH_ERR_ARG.
+ */
+int sph_set_diagnostics(sph_handle* h, int record);
 
 /*
  * Load the state: fluid_pos4 / fluid_vel4 hold n_fluid float4 (fluid order),
@@ -266,7 +285,8 @@ int sph_set_surrogate_bounds(sph_handle* h, const float* lo, const float* hi);
  * Copy one field of the most recent step (SPH_FIELD_*) to `out` (device,
  * or host with on_host = 1), sized as listed with the SPH_FIELD_* codes.
  * Errors: SPH_ERR_ARG (unknown field, NULL out), SPH_ERR_STATE (no step
- * since the last sph_set_state), SPH_ERR_CUDA.
+ * since the last sph_set_state; or acc, touched, influence requested after a
+ * step taken without sph_set_diagnostics(h, 1)), SPH_ERR_CUDA.
  */
 int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* stream);
 

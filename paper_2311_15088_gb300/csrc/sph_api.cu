@@ -8,6 +8,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "sph_internal.cuh"
@@ -37,7 +38,9 @@ struct sph_handle {
     float* rho;
     float2* ab;  // (m / rho, p) per sorted slot
     int* nbr;
-    unsigned* bits;
+    float4* prec;             // the force pass's pair record of each sorted slot (2 float4)
+    uint2* seg;               // hit segments of the density pass (SEG_CAP per particle)
+    int* nseg;
     int* ncand;
     float4* acc;
     int* touched;
@@ -72,6 +75,8 @@ struct sph_handle {
     float f_scale, log_err_max;
     const float *feat_lo, *feat_hi;  // the caller's input range (NULL: no check)
     bool has_state, keys_ready, has_step;
+    bool diag;                // record acc, touched, influence in the step (sph_set_diagnostics)
+    bool diag_step;           // the most recent step recorded them
     long long launches;
     cudaStream_t last_stream;
     // per-pass event timing (sph_profile_enable)
@@ -102,6 +107,23 @@ static void prof_end(sph_handle* h, cudaStream_t s)
 }
 
 static thread_local char g_msg[512] = "";
+
+int sphk::sm_count()
+{
+    static std::atomic<int> cache[64];  // per device ordinal; 0 = not queried yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev >= 64) {
+        int v = 0;
+        return cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0 ? v : 1;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
 
 void sphk::set_handleless_error(const char* msg) { snprintf(g_msg, sizeof(g_msg), "%s", msg); }
 
@@ -288,7 +310,9 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->rho = cv.take<float>(n);
     h->ab = cv.take<float2>(n);
     h->nbr = cv.take<int>(n);
-    h->bits = cv.take<unsigned>(n * (size_t)NBR_WORDS);
+    h->prec = cv.take<float4>(2 * n);
+    h->seg = cv.take<uint2>(n * (size_t)SEG_CAP);
+    h->nseg = cv.take<int>(n);
     h->ncand = cv.take<int>(n);
     h->acc = cv.take<float4>(n);
     h->touched = cv.take<int>(n);
@@ -488,7 +512,7 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
     h->ncells = (int)C;
     h->nbcells = (int)Cb;
     h->tune.block = 256;
-    h->tune.use_stream = 0;
+    h->tune.use_seg = 1;
     return SPH_OK;
 }
 
@@ -563,15 +587,27 @@ int sph_create(const sph_params* p, int n_fluid, int n_boid, void* workspace, si
     return sph_batch_create(p, &n_fluid, &n_boid, 1, workspace, ws_bytes, out);
 }
 
-int sph_set_tuning(sph_handle* h, int block, int use_stream)
+int sph_set_tuning(sph_handle* h, int block, int use_segments)
 {
     if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
     if (block != 64 && block != 128 && block != 256 && block != 512)
         return fail(h, SPH_ERR_ARG, "block must be 64, 128, 256 or 512");
-    if (use_stream != 0 && use_stream != 1) return fail(h, SPH_ERR_ARG, "use_stream must be 0 or 1");
+    if (use_segments != 0 && use_segments != 1) return fail(h, SPH_ERR_ARG, "use_segments must be 0 or 1");
     h->tune.block = block;
-    h->tune.use_stream = use_stream;
+    h->tune.use_seg = use_segments;
     if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return SPH_OK;
+}
+
+int sph_set_diagnostics(sph_handle* h, int record)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (record != 0 && record != 1) return fail(h, SPH_ERR_ARG, "record must be 0 or 1");
+    h->diag = record != 0;
+    if (h->graph) {  // the captured step holds the old choice
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
@@ -787,8 +823,8 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
     int rc = bin_state(h, s, true);
     if (rc != SPH_OK) return rc;
     prof_begin(h, SPH_KIND_DENSITY, s);
-    CUDA_TRY(h, launch_density(h->pos_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand, nullptr,
-                               nullptr, h->err, s, &h->launches));
+    CUDA_TRY(h, launch_density(h->pos_s, h->vel_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->prec,
+                               h->nbr, h->seg, h->nseg, h->ncand, nullptr, nullptr, h->err, s, &h->launches));
     prof_end(h, s);
     if (h->list) {
         prof_begin(h, SPH_KIND_LISTS, s);
@@ -798,9 +834,10 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
         prof_end(h, s);
     }
     prof_begin(h, SPH_KIND_FORCES, s);
-    CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
-                              h->list, h->noff, h->list_cap, true, h->slot_of_boid, nullptr, h->fb, h->acc,
-                              h->touched, h->infl, h->pos, h->vel, h->key, h->rank, h->count, h->err, s,
+    CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->prec, h->cell_start, h->seg, h->nseg, h->sc,
+                              h->tune, h->list, h->noff, h->list_cap, true, h->slot_of_boid, nullptr, h->fb,
+                              h->diag ? h->acc : nullptr, h->diag ? h->touched : nullptr,
+                              h->diag ? h->infl : nullptr, h->pos, h->vel, h->key, h->rank, h->count, h->err, s,
                               &h->launches));
     prof_end(h, s);
     if (h->n_boid > 0) {
@@ -820,6 +857,7 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
     }
     h->keys_ready = true;  // the force and boid kernels emitted the next keys
     h->has_step = true;
+    h->diag_step = h->diag;
     return SPH_OK;
 }
 
@@ -887,6 +925,7 @@ int sph_graph_step(sph_handle* h, int nsteps, void* stream)
     }
     h->keys_ready = true;
     h->has_step = true;
+    h->diag_step = h->diag;
     return SPH_OK;
 }
 
@@ -934,9 +973,11 @@ static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_
     CUDA_TRY(h, cudaMemsetAsync(h->need, 0, (size_t)h->n, s));
     CUDA_TRY(h, launch_mark_needed(h->pos_s, h->cell_start, h->sc, h->slot_of_boid, bmask, h->need, s, &h->launches));
     CUDA_TRY(h, launch_compact_needed(h->need, h->n, h->need_list, h->need_len, s, &h->launches));
-    CUDA_TRY(h, launch_density(h->pos_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
-                               h->need_list, h->need_len, h->err, s, &h->launches));
-    CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+    CUDA_TRY(h, launch_density(h->pos_s, h->vel_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, nullptr,
+                               h->nbr, nullptr, nullptr, h->ncand, h->need_list, h->need_len, h->err, s,
+                               &h->launches));
+    CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, nullptr, h->cell_start, nullptr, nullptr,
+                              h->sc, h->tune,
                               nullptr, nullptr, 0, false, h->slot_of_boid, bmask, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                               nullptr, nullptr, h->err, s, &h->launches));
     return SPH_OK;
@@ -958,9 +999,11 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
     float4* out = (float4*)out_f4;
     h->has_step = false;
     if (mode == SPH_BOID_EXACT) {
-        CUDA_TRY(h, launch_density(h->pos_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->nbr, h->bits, h->ncand,
-                                   nullptr, nullptr, h->err, s, &h->launches));
-        CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->cell_start, h->bits, h->ncand, h->sc, h->tune,
+        CUDA_TRY(h, launch_density(h->pos_s, h->vel_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab,
+                                   nullptr, h->nbr, nullptr, nullptr, h->ncand, nullptr, nullptr, h->err, s,
+                                   &h->launches));
+        CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, nullptr, h->cell_start, nullptr,
+                                  nullptr, h->sc, h->tune,
                                   nullptr, nullptr, 0, false, h->slot_of_boid, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
                                   nullptr, nullptr, nullptr, h->err, s, &h->launches));
         return SPH_OK;
@@ -1034,14 +1077,17 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
         bytes = (size_t)n * 4;
         break;
     case SPH_FIELD_ACC:
+        if (!h->diag_step) return fail(h, SPH_ERR_STATE, "acc is recorded only by steps taken with sph_set_diagnostics(h, 1)");
         if (n) k_by_id<float4><<<blocks, 256, 0, s>>>(h->pos, h->acc, n, (float4*)dst);
         bytes = (size_t)n * 16;
         break;
     case SPH_FIELD_TOUCHED:
+        if (!h->diag_step) return fail(h, SPH_ERR_STATE, "touched is recorded only by steps taken with sph_set_diagnostics(h, 1)");
         if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->touched, n, (int*)dst);
         bytes = (size_t)n * 4;
         break;
     case SPH_FIELD_INFLUENCE:
+        if (!h->diag_step) return fail(h, SPH_ERR_STATE, "influence is recorded only by steps taken with sph_set_diagnostics(h, 1)");
         if (n) k_by_id<float4><<<blocks, 256, 0, s>>>(h->pos, h->infl, n, (float4*)dst);
         bytes = (size_t)n * 16;
         break;

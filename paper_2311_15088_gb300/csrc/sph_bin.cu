@@ -272,7 +272,7 @@ constexpr int SORT_WARPS = 8;
 constexpr int SORT_SMEM = 128;     // cells up to this size are ranked by one warp
 constexpr int BIG_THREADS = 1024;  // larger cells: one block, bitonic sort in smem
 constexpr int BIG_CAP = 16384;     // elements of a block sort (128 KiB of smem)
-constexpr int BIG_BLOCKS = 152;
+// blocks of k_cellsort_big: one per multiprocessor (they loop over the queued cells)
 
 // One warp per cell.  tmp[start[c] ..) holds the storage indices of the
 // cell's particles in arbitrary order; each is ranked by particle id and its
@@ -434,7 +434,7 @@ cudaError_t launch_cellsort_gather(const unsigned* start, int ncells, const int*
     int blocks = (ncells + SORT_WARPS - 1) / SORT_WARPS;
     k_cellsort_gather<<<blocks, SORT_WARPS * 32, 0, s>>>(start, ncells, tmp, pos_in, vel_in, pos_out,
                                                          vel_out, nb, slot_of_boid, big_list, big_count);
-    k_cellsort_big<<<BIG_BLOCKS, BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
+    k_cellsort_big<<<sm_count(), BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
         start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid, nullptr, nullptr, 0);
     *launches += 2;
     return cudaGetLastError();
@@ -492,7 +492,7 @@ cudaError_t launch_cellsort_slots(const unsigned* start, const unsigned* key, in
     const size_t st = soa_stride((size_t)n);
     k_cellsort_slots<<<(n + 255) / 256, 256, 0, s>>>(start, key, n, tmp, tmp_id, pos_in, vel_in, pos_out, vel_out,
                                                      soa, st, nb, slot_of_boid, big_list, big_count);
-    k_cellsort_big<<<BIG_BLOCKS, BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
+    k_cellsort_big<<<sm_count(), BIG_THREADS, BIG_CAP * sizeof(unsigned long long), s>>>(
         start, big_list, big_count, tmp, pos_in, vel_in, pos_out, vel_out, nb, slot_of_boid, tmp_id, soa, st);
     *launches += 2;
     return cudaGetLastError();

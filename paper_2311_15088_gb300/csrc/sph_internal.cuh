@@ -329,8 +329,12 @@ cudaError_t launch_cellsort_slots(const unsigned* start, const unsigned* key, in
 cudaError_t launch_slot_keys(const unsigned* start, int ncells, unsigned* slot_key, cudaStream_t s,
                              long long* launches);
 
-// Candidate bits the density pass keeps per particle for the force pass.
-constexpr int NBR_WORDS = 64;
+// Hit segments the density pass keeps per fluid particle for the force
+// pass: at most SEG_CAP (first slot, 32-bit pair mask) entries each.
+constexpr int SEG_CAP = 64;
+
+// Multiprocessors of the current device (queried once per device).
+int sm_count();
 
 // The sorted positions once more as three float arrays (x, y, z of slot j
 // at x[j], y[j], z[j]; 8-byte aligned, so slots 2k, 2k + 1 load as one
@@ -348,23 +352,32 @@ __host__ __device__ inline size_t soa_stride(size_t n) { return (n + 1) & ~(size
 // not depend on it).
 struct Tuning {
     int block;       // threads per block of density / forces (64 .. 512)
-    int use_stream;  // 1: the force pass decodes the density pass's candidate bits
+    int use_seg;     // 1: the density pass records hit segments and the force pass reads them
 };
 
-// Density, neighbour counts and the candidate bit stream (bits: NBR_WORDS
-// words per particle, word-interleaved; ncand: candidates per particle).
-// list (may be NULL = every particle) restricts the pass to the sorted
-// slots list[0 .. *list_len) (device memory, built on the device).
-cudaError_t launch_density(const float4* pos, const SoaPos& xyz, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const int* list,
-                           const unsigned* list_len, unsigned* err, cudaStream_t s, long long* launches);
+// Density, neighbour counts, candidates tested (ncand) and, with seg given
+// and t.use_seg, the hit segments of every fluid particle (seg: SEG_CAP
+// entries per particle, nseg: their number).  list (may be NULL = every
+// particle) restricts the pass to the sorted slots list[0 .. *list_len)
+// (device memory, built on the device); no segments are written then.
+// prec (may be NULL): the force pass's 32-byte record of every particle,
+// (x, y, z, p) and (v, m / rho with the sign bit set for attached
+// particles), read by launch_forces' fluid particles.
+cudaError_t launch_density(const float4* pos, const float4* vel, const SoaPos& xyz, const unsigned* start,
+                           const Scenes& sc, const Tuning& t, float* rho, float2* ab, float4* prec, int* nbr,
+                           uint2* seg, int* nseg, int* ncand, const int* list, const unsigned* list_len,
+                           unsigned* err, cudaStream_t s, long long* launches);
 // The step's force pass: F_b of every boid (bmask NULL) or of the boids with
 // bmask[b] != 0 (their fb.w = 1), a warp per boid, also stored to acc at the
 // attached slot when acc is given; with fluid = true also every fluid
-// particle, integrated into pos_next/vel_next with the next keys emitted
-// (attached particles get touched = 0, influence = 0).  One launch.
+// particle, integrated into pos_next/vel_next with the next keys emitted,
+// its pairs taken from the density pass's hit segments when t.use_seg (the
+// same step's density pass must have written them).  acc, touched, infl:
+// the diagnostic fields, written when given (all three or none; attached
+// particles get touched = 0, influence = 0).  One launch.
 cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* vel, const float* rho, const float2* ab,
-                          const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
+                          const float4* prec, const unsigned* start, const uint2* seg, const int* nseg,
+                          const Scenes& sc,
                           const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
                           bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
                           float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,

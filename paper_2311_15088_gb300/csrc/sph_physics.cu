@@ -22,12 +22,17 @@ namespace sphk {
 
 // ---------------------------------------------------------------- density
 
-// The density pass also records, for every candidate it tests (in walk
-// order), whether the pair enters the force sum (0 < r2 < h2, not two
-// attached particles): bit k of particle i's candidate stream lives in word
-// bits[(k / 32) * n + i].  The force pass then visits only those slots.
-// Particles with more than NBR_WORDS * 32 candidates keep no stream
-// (ncand > capacity) and the force pass tests their candidates again.
+// Hit segments.  The density pass tests every candidate of a fluid
+// particle's walk; it also keeps, for the force pass, which candidates are
+// force pairs (0 < r2 < h2: the neighbours without the particle itself and
+// coincident particles).  Each row of the walk is cut into pieces of at most
+// 32 consecutive slots and every piece with a pair is stored as one segment
+// (first slot, 32-bit mask of its pairs), in walk order, at seg[i * SEG_CAP
+// + k]; nseg[i] is the number of segments (SEG_CAP + 1 and more: the list
+// did not fit, the force pass tests the candidates itself).  The force pass
+// then evaluates the pairs in exactly the walk's order without testing a
+// candidate again, and the lanes of a warp take their next pair together
+// instead of waiting at each row for the lane with the most hits in it.
 //
 // Besides rho_i it stores ab[i] = (m / rho_i, k (rho_i - rho0)): the two
 // per-particle factors of the pair force, so that the force pass divides
@@ -36,122 +41,149 @@ namespace sphk {
 // A fluid particle has no excluded pairs, so its loop counts every hit and
 // subtracts the self pair (always visited: r2 = 0) at the end; the sums
 // take the same terms in the same order as the attached particles' loop.
-template <bool STREAM>
-__device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos, const SoaPos& xyz,
-                                           const unsigned* __restrict__ start,
+template <bool SEG>
+__device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos, const float4* __restrict__ vel,
+                                           const SoaPos& xyz, const unsigned* __restrict__ start,
                                            const Scenes& sc, float* __restrict__ rho, float2* __restrict__ ab,
-                                           int* __restrict__ nbr, unsigned* __restrict__ bits,
+                                           float4* __restrict__ prec, int* __restrict__ nbr,
+                                           uint2* __restrict__ seg, int* __restrict__ nseg,
                                            int* __restrict__ ncand, unsigned* __restrict__ err)
 {
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
     const float h2 = c.h2;
-    const int nb_all = sc.nb_all, n_all = sc.n_all;
+    const int nb_all = sc.nb_all;
     const float4 pi = pos[i];
     const bool att_i = id_of(pi) < nb_all;
     float sum = 0.0f;
     int cnt = 0;
-    unsigned word = 0;
     int nc = 0;
     RowWalk walk(c.g, c.wg, start + c.c_base, pi.x, pi.y, pi.z);
     unsigned s0, s1;
-    if (!STREAM && !att_i) {
+    if (!att_i) {
         // candidates in slot order: an odd first slot alone, then slot
         // pairs (2k, 2k + 1) from the SoA copy, tested side by side with
         // packed float32x2 operations (each component rounded exactly as
-        // the scalar form), then an odd last slot alone
-        auto take = [&](const float4& pj) {
+        // the scalar form), then an odd last slot alone.  m collects the
+        // hits of the current segment (bit = slot - segment start; the
+        // particle itself and coincident particles are among them, the force
+        // pass skips them by r2 == 0).
+        unsigned m = 0;
+        auto take = [&](const float4& pj, unsigned sh) {
             const float r2 = pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
             if (r2 < h2) {
                 const float t = h2 - r2;
                 sum = fmaf(t * t, t, sum);
                 ++cnt;
+                if (SEG) m |= 1u << sh;
             }
         };
         // x_j - x_i as x_j + (-x_i) and h2 - r2 as fma(r2, -1, h2): the
         // same roundings as the subtractions
         const float2 nx2 = make_float2(-pi.x, -pi.x), ny2 = make_float2(-pi.y, -pi.y), nz2 = make_float2(-pi.z, -pi.z);
         const float2 h22 = make_float2(h2, h2), m11 = make_float2(-1.0f, -1.0f);
-        auto take2 = [&](float2 X, float2 Y, float2 Z) {
+        auto take2 = [&](float2 X, float2 Y, float2 Z, unsigned sh) {
             const float2 dx = __fadd2_rn(X, nx2), dy = __fadd2_rn(Y, ny2), dz = __fadd2_rn(Z, nz2);
             const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
             const float2 t = __ffma2_rn(r2, m11, h22);
             const float2 tt = __fmul2_rn(t, t);
+            const unsigned bit = SEG ? 1u << sh : 0u;
             if (r2.x < h2) {
                 sum = fmaf(tt.x, t.x, sum);
                 ++cnt;
+                if (SEG) m |= bit;
             }
             if (r2.y < h2) {
                 sum = fmaf(tt.y, t.y, sum);
                 ++cnt;
+                if (SEG) m |= bit << 1;
             }
         };
         const float2* __restrict__ X2 = reinterpret_cast<const float2*>(xyz.x);
         const float2* __restrict__ Y2 = reinterpret_cast<const float2*>(xyz.y);
         const float2* __restrict__ Z2 = reinterpret_cast<const float2*>(xyz.z);
-        while (walk.next(s0, s1)) {
-            nc += (int)(s1 - s0);
-            unsigned j = s0;
-            if (j & 1u) take(__ldg(pos + j++));
-            const unsigned e = s1 & ~1u;
+        // the slots [a, e) with bits relative to b
+        auto slots = [&](unsigned a, unsigned e, unsigned b) {
+            unsigned j = a;
+            if (j & 1u) {
+                take(__ldg(pos + j), j - b);
+                ++j;
+            }
+            const unsigned e2 = e & ~1u;
             // two slot pairs (four candidates) in flight per iteration
-            for (; j + 4 <= e; j += 4) {
+            for (; j + 4 <= e2; j += 4) {
                 const unsigned k = j >> 1;
                 const float2 xa = __ldg(X2 + k), ya = __ldg(Y2 + k), za = __ldg(Z2 + k);
                 const float2 xb = __ldg(X2 + k + 1), yb = __ldg(Y2 + k + 1), zb = __ldg(Z2 + k + 1);
-                take2(xa, ya, za);
-                take2(xb, yb, zb);
+                take2(xa, ya, za, j - b);
+                take2(xb, yb, zb, j + 2 - b);
             }
-            if (j < e) {
+            if (j < e2) {
                 const unsigned k = j >> 1;
-                take2(__ldg(X2 + k), __ldg(Y2 + k), __ldg(Z2 + k));
+                take2(__ldg(X2 + k), __ldg(Y2 + k), __ldg(Z2 + k), j - b);
                 j += 2;
             }
-            if (j < s1) take(__ldg(pos + j));
+            if (j < e) take(__ldg(pos + j), j - b);
+        };
+        int ns = 0;
+        uint2* __restrict__ mine = SEG ? seg + (size_t)i * SEG_CAP : nullptr;
+        while (walk.next(s0, s1)) {
+            nc += (int)(s1 - s0);
+            if (SEG) {
+                for (unsigned b = s0; b < s1; b += 32u) {
+                    m = 0;
+                    slots(b, min(b + 32u, s1), b);
+                    if (m) {
+                        if (ns < SEG_CAP) mine[ns] = make_uint2(b, m);
+                        ++ns;
+                    }
+                }
+            } else {
+                slots(s0, s1, s0);
+            }
         }
         --cnt;  // the particle itself
+        if (SEG) nseg[i] = ns;
     } else {
         while (walk.next(s0, s1)) {
             for (unsigned j = s0; j < s1; ++j) {
                 const float4 pj = __ldg(pos + j);
                 const float r2 =
                     pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z));
-                const bool hit = r2 < h2;
-                const bool att_pair = att_i && id_of(pj) < nb_all;
-                if (hit && !(att_pair && j != (unsigned)i)) {
+                const bool att_pair = id_of(pj) < nb_all;
+                if (r2 < h2 && !(att_pair && j != (unsigned)i)) {
                     const float t = h2 - r2;
                     sum = fmaf(t * t, t, sum);
                     cnt += j != (unsigned)i;
                 }
-                if (STREAM) {
-                    word |= (unsigned)(hit && r2 != 0.0f && !att_pair) << (nc & 31);
-                    if (((nc + 1) & 31) == 0) {
-                        const int w = nc >> 5;
-                        if (w < NBR_WORDS) bits[(size_t)w * n_all + i] = word;
-                        word = 0;
-                    }
-                }
-                ++nc;
             }
+            nc += (int)(s1 - s0);
         }
-        if (STREAM && (nc & 31) != 0 && (nc >> 5) < NBR_WORDS) bits[(size_t)(nc >> 5) * n_all + i] = word;
+        if (SEG) nseg[i] = 0;  // attached particles are not integrated
     }
     ncand[i] = nc;
     const float r = c.mC6 * sum;
     rho[i] = r;
-    ab[i] = make_float2(c.mass / r, c.k * (r - c.rho0));
+    const float2 abi = make_float2(c.mass / r, c.k * (r - c.rho0));
+    ab[i] = abi;
+    if (prec) {  // the force pass's record of j: (x, y, z, p) and (v, m / rho, negative if attached)
+        const float4 v = __ldg(vel + i);
+        prec[2 * i] = make_float4(pi.x, pi.y, pi.z, abi.y);
+        prec[2 * i + 1] = make_float4(v.x, v.y, v.z, att_i ? -abi.x : abi.x);
+    }
     nbr[i] = cnt;
     if (!isfinite(r)) atomicOr(err, SPH_DEV_NONFINITE);
 }
 
 // Every particle (thread i = slot i).
-template <bool STREAM>
+template <bool SEG>
 __global__ void __launch_bounds__(512, 3)
-k_density(const float4* __restrict__ pos, SoaPos xyz, const unsigned* __restrict__ start, Scenes sc,
-          float* __restrict__ rho, float2* __restrict__ ab, int* __restrict__ nbr, unsigned* __restrict__ bits,
+k_density(const float4* __restrict__ pos, const float4* __restrict__ vel, SoaPos xyz,
+          const unsigned* __restrict__ start, Scenes sc, float* __restrict__ rho, float2* __restrict__ ab,
+          float4* __restrict__ prec, int* __restrict__ nbr, uint2* __restrict__ seg, int* __restrict__ nseg,
           int* __restrict__ ncand, unsigned* __restrict__ err)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < sc.n_all) density_at<STREAM>(t, pos, xyz, start, sc, rho, ab, nbr, bits, ncand, err);
+    if (t < sc.n_all) density_at<SEG>(t, pos, vel, xyz, start, sc, rho, ab, prec, nbr, seg, nseg, ncand, err);
 }
 
 
@@ -217,19 +249,22 @@ k_density_list(const float4* __restrict__ pos, const unsigned* __restrict__ star
     }
 }
 
-cudaError_t launch_density(const float4* pos, const SoaPos& xyz, const unsigned* start, const Scenes& sc, const Tuning& t,
-                           float* rho, float2* ab, int* nbr, unsigned* bits, int* ncand, const int* list,
-                           const unsigned* list_len, unsigned* err, cudaStream_t s, long long* launches)
+cudaError_t launch_density(const float4* pos, const float4* vel, const SoaPos& xyz, const unsigned* start,
+                           const Scenes& sc, const Tuning& t, float* rho, float2* ab, float4* prec, int* nbr,
+                           uint2* seg, int* nseg, int* ncand, const int* list, const unsigned* list_len,
+                           unsigned* err, cudaStream_t s, long long* launches)
 {
     if (sc.n_all <= 0) return cudaSuccess;
     const int all = (sc.n_all + t.block - 1) / t.block;
     if (list) {
-        const int blocks = (sc.n_all + 7) / 8 < 152 * 16 ? (sc.n_all + 7) / 8 : 152 * 16;  // 8 warps each
+        const int cap = 16 * sm_count();  // 8 warps per block, 16 blocks per SM at most
+        const int blocks = (sc.n_all + 7) / 8 < cap ? (sc.n_all + 7) / 8 : cap;
         k_density_list<<<blocks, 256, 0, s>>>(pos, start, sc, rho, ab, nbr, ncand, list, list_len, err);
-    } else if (t.use_stream) {
-        k_density<true><<<all, t.block, 0, s>>>(pos, xyz, start, sc, rho, ab, nbr, bits, ncand, err);
+    } else if (seg && t.use_seg) {
+        k_density<true><<<all, t.block, 0, s>>>(pos, vel, xyz, start, sc, rho, ab, prec, nbr, seg, nseg, ncand, err);
     } else {
-        k_density<false><<<all, t.block, 0, s>>>(pos, xyz, start, sc, rho, ab, nbr, bits, ncand, err);
+        k_density<false><<<all, t.block, 0, s>>>(pos, vel, xyz, start, sc, rho, ab, prec, nbr, seg, nseg, ncand,
+                                                 err);
     }
     ++*launches;
     return cudaGetLastError();
@@ -273,6 +308,15 @@ struct PairTerms {
         fz = __fmaf_rn(sp, dz, __fmul_rn(sv, __fsub_rn(vi.z, vj.z)));
     }
 };
+
+// The 32-byte pair record of a particle, (x, y, z, p) and (v, +-m / rho),
+// in one 256-bit load (records are 32-byte aligned).
+__device__ __forceinline__ void ld_rec(const float4* __restrict__ p, float4& a, float4& b)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
 
 // x_j - x_i, y_j - y_i as one packed addition of (-x_i, -y_i): the same
 // roundings as the subtractions.
@@ -340,17 +384,23 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
 }
 
 // The step's force pass.  The first boid_blocks blocks compute F_b, a warp
-// per boid (boid_fb_warp; F_b also goes to acc at the attached slot); they
-// come first in the grid so that these latency-bound warps run alongside
-// the fluid blocks.  The remaining blocks (fluid_blocks of them, possibly
-// none) take a particle per thread: pair forces with touched_by_boid and
-// boid_influence, gravity, Euler-Cromer integration, damped walls and the
-// next step's cell keys; attached particles only record touched = 0 and
+// per boid (boid_fb_warp; F_b also goes to acc at the attached slot when
+// acc is given); they come first in the grid so that these latency-bound
+// warps run alongside the fluid blocks.  The remaining blocks (fluid_blocks
+// of them, possibly none) take a particle per thread: pair forces with
+// touched_by_boid and boid_influence, gravity, Euler-Cromer integration,
+// damped walls and the next step's cell keys.  A fluid particle takes its
+// pairs from (in this order of preference) the neighbour list, the density
+// pass's hit segments, or a walk that tests the candidates again; all three
+// visit the same pairs in the same order.  acc, touched and infl (the
+// diagnostic fields) are written only when given (acc, touched and infl
+// all given or all NULL); attached particles then record touched = 0 and
 // influence = 0 (attached pairs are excluded).
 __global__ void __launch_bounds__(512)
 k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ vel, const float* __restrict__ rho,
-         const float2* __restrict__ ab, const unsigned* __restrict__ start, const unsigned* __restrict__ bits,
-         const int* __restrict__ ncand, Scenes sc, int use_stream, const unsigned* __restrict__ list,
+         const float2* __restrict__ ab, const float4* __restrict__ prec, const unsigned* __restrict__ start,
+         const uint2* __restrict__ seg,
+         const int* __restrict__ nseg, Scenes sc, const unsigned* __restrict__ list,
          const unsigned* __restrict__ list_off, unsigned list_cap, int boid_blocks,
          const int* __restrict__ slot_of_boid, const int* __restrict__ bmask, float4* __restrict__ fb,
          float4* __restrict__ acc, int* __restrict__ touched, float4* __restrict__ infl,
@@ -382,29 +432,33 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
         T.set(c, pi, __ldg(vel + i), __ldg(ab + i).y);
         rho_i = __ldg(rho + i);
         const float2 nxy = make_float2(-pi.x, -pi.y);
-        // one neighbour j (0 < r2 < h2)
+        // one neighbour j (r2 < h2) from its record (one 32-byte load); the
+        // particle itself and coincident particles (r2 = 0) add nothing
         auto pair = [&](unsigned j) {
-            const float4 pj = __ldg(pos + j);
-            const float2 dxy = dxy_of(pj, nxy);
-            const float dz = __fsub_rn(pj.z, pi.z);
+            float4 q0, q1;
+            ld_rec(prec + 2 * (size_t)j, q0, q1);
+            const float2 dxy = dxy_of(q0, nxy);
+            const float dz = __fsub_rn(q0.z, pi.z);
+            const float r2 = pair_r2(dxy.x, dxy.y, dz);
             float2 fxy;
             float fz;
-            T.add(dxy, dz, pair_r2(dxy.x, dxy.y, dz), __ldg(vel + j), __ldg(ab + j), fxy, fz);
-            axy = __fadd2_rn(axy, fxy);
-            az = __fadd_rn(az, fz);
-            if (id_of(pj) < nb_all) {
-                ++touch;
-                bxy = __fadd2_rn(bxy, fxy);
-                bz = __fadd_rn(bz, fz);
+            T.add(dxy, dz, r2, q1, make_float2(fabsf(q1.w), q0.w), fxy, fz);
+            if (r2 != 0.0f) {
+                axy = __fadd2_rn(axy, fxy);
+                az = __fadd_rn(az, fz);
+                if (__float_as_int(q1.w) < 0) {  // j is attached to a boid
+                    ++touch;
+                    bxy = __fadd2_rn(bxy, fxy);
+                    bz = __fadd_rn(bz, fz);
+                }
             }
         };
-        RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
-        unsigned s0, s1;
         unsigned o0 = 0, o1 = 0;
         if (list) {
             o0 = __ldg(list_off + i);
             o1 = __ldg(list_off + i + 1);
         }
+        const int ns = seg ? __ldg(nseg + i) : SEG_CAP + 1;
         if (list && o1 <= list_cap) {
             // the neighbour list, in walk order (coincident particles skipped)
             for (unsigned k = o0; k < o1; ++k) {
@@ -412,36 +466,22 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
                 const float4 pj = __ldg(pos + j);
                 if (pair_r2(__fsub_rn(pj.x, pi.x), __fsub_rn(pj.y, pi.y), __fsub_rn(pj.z, pi.z)) != 0.0f) pair(j);
             }
-        } else if (use_stream && ncand[i] <= NBR_WORDS * 32) {
-            // decode the density pass's candidate bits, row by row
-            int bitpos = 0, wcur = -1;
-            unsigned wv = 0;
-            while (walk.next(s0, s1)) {
-                unsigned j = s0;
-                while (j < s1) {
-                    const int w = bitpos >> 5, b = bitpos & 31;
-                    if (w != wcur) {
-                        wv = __ldg(bits + (size_t)w * sc.n_all + i);
-                        wcur = w;
-                    }
-                    const unsigned left = s1 - j;
-                    const int take = left < (unsigned)(32 - b) ? (int)left : 32 - b;
-                    unsigned m = wv >> b;
-                    if (take < 32) m &= (1u << take) - 1u;
-                    while (m) {
-                        const int t = __ffs(m) - 1;
-                        m &= m - 1u;
-                        pair(j + (unsigned)t);
-                    }
-                    j += (unsigned)take;
-                    bitpos += take;
-                }
+        } else if (ns <= SEG_CAP) {
+            // the density pass's hit segments: one pair per iteration, the
+            // next segment fetched while the current pair is evaluated
+            const uint2* __restrict__ mine = seg + (size_t)i * SEG_CAP;
+            uint2 cur = ns > 0 ? __ldg(mine) : make_uint2(0u, 0u);
+            int k = 1;
+            while (cur.y) {
+                const unsigned j = cur.x + (unsigned)(__ffs(cur.y) - 1);
+                cur.y &= cur.y - 1u;
+                if (!cur.y && k < ns) cur = __ldg(mine + k++);
+                pair(j);
             }
         } else {
             // test a chunk of up to 32 candidates into a bit mask, then run
-            // the pair code over the set bits: the warp executes the pair
-            // code max(hits) times per chunk instead of once per candidate
-            // (slot pairs from the SoA copy, as in the density pass)
+            // the pair code over the set bits (slot pairs from the SoA copy,
+            // as in the density pass)
             const float h2 = c.h2;
             const float2 nx2 = make_float2(-pi.x, -pi.x), ny2 = make_float2(-pi.y, -pi.y),
                          nz2 = make_float2(-pi.z, -pi.z);
@@ -458,6 +498,8 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
                 const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
                 return (unsigned)(r2.x < h2 && r2.x != 0.0f) | (unsigned)(r2.y < h2 && r2.y != 0.0f) << 1;
             };
+            RowWalk walk(c.g, c.wg, cstart, pi.x, pi.y, pi.z);
+            unsigned s0, s1;
             while (walk.next(s0, s1)) {
                 for (unsigned base = s0; base < s1; base += 32) {
                     const unsigned e = min(base + 32u, s1);
@@ -492,7 +534,7 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
     const float bx = bxy.x, by = bxy.y;
 
     unsigned k_next = 0;
-    if (active) {
+    if (active && touched) {
         touched[i] = touch;
         infl[i] = make_float4(bx * inv_rho, by * inv_rho, bz * inv_rho, 0.0f);
     }
@@ -500,7 +542,7 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
         ax += c.grav[0];
         ay += c.grav[1];
         az += c.grav[2];
-        acc[i] = make_float4(ax, ay, az, 0.0f);
+        if (acc) acc[i] = make_float4(ax, ay, az, 0.0f);
         const float4 vi = __ldg(vel + i);
         float v[3] = {fmaf(ax, c.dt, vi.x), fmaf(ay, c.dt, vi.y), fmaf(az, c.dt, vi.z)};
         float x[3] = {fmaf(v[0], c.dt, pi.x), fmaf(v[1], c.dt, pi.y), fmaf(v[2], c.dt, pi.z)};
@@ -530,7 +572,8 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
 }
 
 cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* vel, const float* rho, const float2* ab,
-                          const unsigned* start, const unsigned* bits, const int* ncand, const Scenes& sc,
+                          const float4* prec, const unsigned* start, const uint2* seg, const int* nseg,
+                          const Scenes& sc,
                           const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
                           bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
                           float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
@@ -542,10 +585,11 @@ cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* ve
     const int boid_blocks = (sc.nb_all + warps - 1) / warps;
     const int fluid_blocks = fluid ? (sc.n_all + t.block - 1) / t.block : 0;
     if (boid_blocks + fluid_blocks == 0) return cudaSuccess;
-    k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(pos, xyz, vel, rho, ab, start, bits, ncand, sc, t.use_stream,
-                                                            list, list_off, cap, boid_blocks, slot_of_boid, bmask,
-                                                            fb, acc, touched, infl, pos_next, vel_next, key, rank,
-                                                            count, err);
+    k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(pos, xyz, vel, rho, ab, prec, start,
+                                                            t.use_seg ? seg : nullptr,
+                                                            nseg, sc, list, list_off, cap, boid_blocks, slot_of_boid,
+                                                            bmask, fb, acc, touched, infl, pos_next, vel_next, key,
+                                                            rank, count, err);
     ++*launches;
     return cudaGetLastError();
 }

@@ -236,7 +236,7 @@ int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys
     if (e == cudaSuccess) {
         k_sort_cells_index<<<(g.ncells + SORT_WARPS - 1) / SORT_WARPS, SORT_WARPS * 32, 0, s>>>(
             cell_start_out, g.ncells, perm_out, big_list, big_count);
-        k_sort_cells_index_big<<<152, BIG_THREADS, 0, s>>>(cell_start_out, big_list, big_count, perm_out);
+        k_sort_cells_index_big<<<sm_count(), BIG_THREADS, 0, s>>>(cell_start_out, big_list, big_count, perm_out);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -78,6 +78,7 @@ _sig = {
     "sph_batch_workspace_size": (_i, [_P, _vp, _vp, _i, ctypes.POINTER(_sz)]),
     "sph_batch_create": (_i, [_P, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_vp)]),
     "sph_set_tuning": (_i, [_vp, _i, _i]),
+    "sph_set_diagnostics": (_i, [_vp, _i]),
     "sph_set_neighbor_lists": (_i, [_vp, _vp, ctypes.c_size_t]),
     "sph_debug_bucket_neighbors": (_i, [_vp, _vp, ctypes.c_size_t, _i, _vp, _vp, _vp]),
     "sph_graph_step": (_i, [_vp, _i, _vp]),
@@ -195,8 +196,12 @@ def sph_batch_create(params_list, n_fluid, n_boid, workspace_ptr: int, ws_bytes:
     return h
 
 
-def sph_set_tuning(h, block: int, use_stream: int):
-    _check(_lib.sph_set_tuning(h, block, use_stream), h)
+def sph_set_tuning(h, block: int, use_segments: int):
+    _check(_lib.sph_set_tuning(h, block, use_segments), h)
+
+
+def sph_set_diagnostics(h, record: int):
+    _check(_lib.sph_set_diagnostics(h, record), h)
 
 
 def sph_set_neighbor_lists(h, pair_buffer_ptr, nbytes: int):
@@ -514,9 +519,10 @@ class Scene:
     Inputs are float32 ``(n, 4)`` arrays (numpy or torch); outputs are torch
     tensors on the device.  All calls use torch's current stream."""
 
-    def __init__(self, params, n_fluid, n_boid, device="cuda"):
+    def __init__(self, params, n_fluid, n_boid, device="cuda", diagnostics=False):
         """One scene (params a dict, counts ints) or a batch (params a list
-        of dicts, counts lists); a batch concatenates the scenes' arrays."""
+        of dicts, counts lists); a batch concatenates the scenes' arrays.
+        diagnostics: the steps record acc, touched and influence."""
         import torch
 
         self.torch = torch
@@ -539,7 +545,10 @@ class Scene:
         self.dims, self.bdims = dims[0], bdims[0]
         self.ncells = int(sum(d[0] * d[1] * d[2] for d in dims))
         self.nbcells = int(sum(d[0] * d[1] * d[2] for d in bdims))
-        self.tuning = (256, 0)  # the library's default (block, use_stream)
+        self.tuning = (256, 1)  # the library's default (block, use_segments)
+        self.diagnostics = False
+        if diagnostics:
+            self.set_diagnostics(True)
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -608,9 +617,14 @@ class Scene:
                                    counts.data_ptr(), dropped.data_ptr(), self.stream)
         return counts, dropped
 
-    def set_tuning(self, block: int, use_stream: int):
-        sph_set_tuning(self.handle, block, use_stream)
-        self.tuning = (int(block), int(use_stream))
+    def set_tuning(self, block: int, use_segments: int):
+        sph_set_tuning(self.handle, block, use_segments)
+        self.tuning = (int(block), int(use_segments))
+
+    def set_diagnostics(self, record: bool):
+        """Record acc, touched and influence in later steps (off by default)."""
+        sph_set_diagnostics(self.handle, int(bool(record)))
+        self.diagnostics = bool(record)
 
     def field(self, name: str):
         t = self.torch

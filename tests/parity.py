@@ -34,7 +34,7 @@ def _ratio(a, b):
 
 
 def run_gpu(p, sc, steps=1, device="cuda"):
-    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=device)
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=device, diagnostics=True)
     s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
     s.step(steps)
     return s

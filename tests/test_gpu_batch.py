@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2311_15088_gb300 import scenes, tune
+from paper_2311_15088_gb300 import scenes, sph, tune
 from paper_2311_15088_gb300.sph import Scene
 
 from parity import compare_step, gpu_outputs, lattice_params, oracle_step
@@ -35,7 +35,7 @@ def _cat(scs, key):
 
 def _batch(scs):
     b = Scene([sc["params"] for sc in scs], [len(sc["fluid_pos"]) for sc in scs],
-              [len(sc["boid_pos"]) for sc in scs])
+              [len(sc["boid_pos"]) for sc in scs], diagnostics=True)
     b.set_state(_cat(scs, "fluid_pos"), _cat(scs, "fluid_vel"), _cat(scs, "boid_pos"), _cat(scs, "boid_vel"))
     return b
 
@@ -125,16 +125,43 @@ def test_graph_replay_equals_step():
     assert b.launches > a.launches * 0.5
 
 
-@pytest.mark.parametrize("block,use_stream", [(64, 0), (128, 1), (256, 1), (512, 0), (512, 1)])
-def test_launch_shape_changes_no_bit(block, use_stream):
+@pytest.mark.parametrize("block,use_segments", [(64, 0), (128, 1), (256, 0), (512, 0), (512, 1)])
+def test_launch_shape_changes_no_bit(block, use_segments):
+    """Block size and the source of the force pass's pairs (hit segments or
+    a second candidate test) change no bit of the state or of the fields."""
     scs = _small_batch()
     ref = _batch(scs)
     ref.step(6)
     t = _batch(scs)
-    t.set_tuning(block, use_stream)
+    t.set_tuning(block, use_segments)
     t.step(6)
     for x, y in zip(ref.get_state(), t.get_state()):
         assert torch.equal(x, y)
+    for name in ("acc", "touched", "influence", "rho", "fb"):
+        assert torch.equal(ref.field(name), t.field(name)), name
+
+
+def test_diagnostics_switch_changes_no_result():
+    """Without diagnostics the step writes no acc, touched or influence (the
+    fields are refused) and its state is bit for bit the recorded step's."""
+    scs = _small_batch()
+    a = _batch(scs)
+    b = Scene([sc["params"] for sc in scs], [len(sc["fluid_pos"]) for sc in scs],
+              [len(sc["boid_pos"]) for sc in scs])
+    b.set_state(_cat(scs, "fluid_pos"), _cat(scs, "fluid_vel"), _cat(scs, "boid_pos"), _cat(scs, "boid_vel"))
+    a.step(5)
+    b.step(5)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert torch.equal(x, y)
+    for name in ("rho", "fb", "nbr_count"):
+        assert torch.equal(a.field(name), b.field(name)), name
+    for name in ("acc", "touched", "influence"):
+        with pytest.raises(sph.SphError):
+            b.field(name)
+    b.set_diagnostics(True)
+    b.step(1)
+    a.step(1)
+    assert torch.equal(a.field("acc"), b.field("acc"))
 
 
 def test_autotuner_restores_state_and_caches(tmp_path):

@@ -44,7 +44,7 @@ def test_obstacle_grid_matches_oracle():
 def test_step_with_obstacles_matches_oracle(cell):
     sc, p = _scene()
     p["cell_size"] = scenes.f32(p["h"] * cell)
-    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), diagnostics=True)
     s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
     s.set_obstacles(SPHERES, BOXES, 0.08, 2.5)
     s.step(1)

@@ -243,7 +243,7 @@ def test_neighbor_lists_bitwise_equal_to_walk(cap):
     sc["boid_pos"][:, 1] *= np.float32(0.4 / 0.6)
     p = sc["params"]
     a = run_gpu(p, sc, steps=20)
-    b = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    b = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), diagnostics=True)
     b.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
     b.step(1)
     pairs = int(b.field("nbr_count").cpu().numpy().astype(np.int64).sum())
