@@ -58,7 +58,7 @@ extern "C" {
 
 /* Bits of the sticky device error word (sph_status). */
 #define SPH_DEV_NONFINITE 1u  /* a density, position or velocity became NaN/Inf  */
-#define SPH_DEV_CLAMPED   2u  /* a position lay outside the grid and was clamped */
+#define SPH_DEV_CLAMPED   2u  /* a fluid position lay outside the tank (or was NaN) when binned; its cell was clamped */
 #define SPH_DEV_TIMEOUT   4u  /* a bounded wait inside a kernel gave up          */
 #define SPH_DEV_LIST_OVERFLOW 8u /* a neighbour list did not fit the pair buffer  */
 
@@ -246,6 +246,19 @@ int sph_graph_step(sph_handle* h, int nsteps, void* stream);
 #define SPH_BOID_SURROGATE_FALLBACK 2
 #define SPH_BOID_EXACT_LOCAL        3
 int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream);
+
+/*
+ * sph_boid_forces through a CUDA graph, one per mode: the first call of a
+ * mode runs plainly (it also does the mode's one-time set-up), the next
+ * captures the call's launches on `stream` (not the legacy default stream)
+ * and every later call replays them: the same forces, bit for bit, for a
+ * fraction of the launch overhead.  A change of stream or out pointer
+ * recaptures; so does sph_set_surrogate, sph_set_surrogate_bounds or
+ * sph_set_tuning.  A state whose cell keys are not yet computed (just
+ * loaded) takes the plain path.  Errors: as sph_boid_forces, and
+ * SPH_ERR_ARG for the default stream.
+ */
+int sph_graph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream);
 
 /*
  * Stencil features of every boid for the CURRENT state (the surrogate's
@@ -441,6 +454,17 @@ void sph_mlp_destroy(sph_mlp* m);
 /* Load parameters (device FP32 vector) and reset the Adam moments. */
 int sph_mlp_set_params(sph_mlp* m, const float* params, void* stream);
 int sph_mlp_get_params(sph_mlp* m, float* params, void* stream);
+/*
+ * The optimiser's state after the last sph_mlp_train_step (or
+ * sph_mlp_gradients): grads, the gradient of the last step, and m1, m2, the
+ * first and second Adam moments (Kingma and Ba; beta1 = 0.9, beta2 = 0.999,
+ * eps = 1e-8 as float32, bias corrections 1 - beta^t rounded once from
+ * double), packed like the parameters (SPH_MLP_PARAMS FP32 each, device,
+ * copied on `stream`); *step (host): the Adam steps taken since the last
+ * sph_mlp_set_params.  For checkpoints and for checking the update against
+ * a reference.  Errors: SPH_ERR_ARG (NULL pointer), SPH_ERR_CUDA.
+ */
+int sph_mlp_get_optimizer_state(sph_mlp* m, float* grads, float* m1, float* m2, long long* step, void* stream);
 /* y[B][16] = MLP(x[B][272]) (device buffers; x 16-byte aligned). */
 int sph_mlp_forward(sph_mlp* m, const void* x_bf16, int B, float* y, void* stream);
 /* Parameter gradients of sum(dy * y) for an upstream gradient dy[B][16]
@@ -582,11 +606,17 @@ int sph_mc_tables(unsigned short* edge_table, signed char* tri_table);
  * stall other streams.
  *
  * For n particles at pos4 (device float4, 16-byte aligned, by index; w
- * ignored) it computes what sph_step's binning computes, with the grid of
- * p->box_min/box_max/cell_size: keys_out[n] the cell key of each particle
- * (by index), perm_out[n] the particle index at each sorted slot (sorted by
- * key, then index), cell_start_out[ncells + 1] the first sorted slot of each
- * cell (device arrays owned by the caller).  Work is enqueued on `stream`.
+ * ignored) it bins them on the grid of sph_step (p->box_min/box_max/
+ * cell_size, section "Neighbor Search with Sorting"): keys_out[n] the cell
+ * key of each particle (by index), perm_out[n] the particle index at each
+ * sorted slot (sorted by key, then index), cell_start_out[ncells + 1] the
+ * first sorted slot of each cell (device arrays owned by the caller).
+ * sph_step orders a cell by particle id instead of index; the two agree
+ * where ids equal indices (a scene without boids whose state was just
+ * loaded).  flags_out (device, 4-byte aligned; NULL: not reported) receives
+ * this call's flag word: SPH_DEV_CLAMPED when a position lay outside the box
+ * (or was NaN) and was binned into the nearest cell.  Work is enqueued on
+ * `stream`.
  *
  * Its scratch is one file-scope device array of SPH_STATIC_SCRATCH_BYTES
  * (about 21 MiB) that every GPU which loads this library holds until the
@@ -595,15 +625,17 @@ int sph_mc_tables(unsigned short* edge_table, signed char* tri_table);
  * sph_last_error(NULL)) before any device work.  The array is shared by all
  * calls on a device and keeps the last call's contents; each call zeroes
  * what must start at zero.  Calls that overlap on the GPU race on it:
- * serialise them.  The first call on a device (with that device current)
- * looks up the array's device address once; make it before any stream
- * capture.  No device memory is allocated or freed.
+ * serialise them.  Every call looks up the array's address on the current
+ * device (nothing is cached across calls, so a reset of the device's context
+ * in between is harmless); the first call on a device may load the library's
+ * device code there, so make it before any stream capture.  No device
+ * memory is allocated or freed.
  */
 #define SPH_STATIC_MAX_PARTICLES (1 << 22)
 #define SPH_STATIC_MAX_CELLS     (1 << 20)
 #define SPH_STATIC_SCRATCH_BYTES (21u << 20)
 int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys_out, int* perm_out,
-                   unsigned* cell_start_out, void* stream);
+                   unsigned* cell_start_out, unsigned* flags_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -87,6 +87,14 @@ def force_loss_grad_y(y: np.ndarray, t: np.ndarray) -> np.ndarray:
     return dy
 
 
+def error_loss_grad_y(y: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """d/dy of the error-head loss mean over samples of 1/2 (y[:, 3] - t)^2
+    (zero outside column 3)."""
+    dy = np.zeros_like(y)
+    dy[:, 3] = (y[:, 3] - t) / len(y)
+    return dy
+
+
 def adam_update(w, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam step (Kingma & Ba): returns the new (w, m, v)."""
     m = beta1 * m + (1 - beta1) * g

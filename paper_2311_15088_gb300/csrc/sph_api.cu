@@ -87,8 +87,24 @@ struct sph_handle {
     cudaGraphExec_t graph;
     cudaStream_t graph_stream;
     long long graph_launches;
+    // captured boid-force calls (sph_graph_boid_forces), one per mode
+    struct {
+        cudaGraphExec_t exec;
+        cudaStream_t stream;
+        float* out;
+        long long launches;
+        bool warm;  // one plain call of this mode has run (one-time set-up done)
+    } bgraph[4];
     char msg[512];
 };
+
+static void drop_boid_graphs(sph_handle* h)
+{
+    for (auto& g : h->bgraph) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+}
 
 static void prof_begin(sph_handle* h, int kind, cudaStream_t s)
 {
@@ -149,7 +165,7 @@ static int fail(sph_handle* h, int code, const char* fmt, ...)
 
 static bool finite_pos(float v) { return isfinite(v) && v > 0.0f; }
 
-static int make_grid(const float mn[3], const float mx[3], float d, GridDesc* g)
+int sphk::make_grid(const float mn[3], const float mx[3], float d, GridDesc* g)
 {
     long long cells = 1;
     for (int a = 0; a < 3; ++a) {
@@ -599,6 +615,7 @@ int sph_set_tuning(sph_handle* h, int block, int use_segments)
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
+    drop_boid_graphs(h);
     return SPH_OK;
 }
 
@@ -647,6 +664,7 @@ void sph_destroy(sph_handle* h)
     if (!h) return;
     prof_free(h);
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    drop_boid_graphs(h);
     free_tables(h);
     delete h;
 }
@@ -936,6 +954,7 @@ int sph_set_surrogate(sph_handle* h, sph_mlp* m, float f_scale, float log_err_ma
     h->mlp = m;
     h->f_scale = f_scale;
     h->log_err_max = log_err_max;
+    drop_boid_graphs(h);  // the captured calls hold the old network and gate
     return SPH_OK;
 }
 
@@ -945,6 +964,7 @@ int sph_set_surrogate_bounds(sph_handle* h, const float* lo, const float* hi)
     if ((lo == nullptr) != (hi == nullptr)) return fail(h, SPH_ERR_ARG, "give both lo and hi, or neither");
     h->feat_lo = lo;
     h->feat_hi = hi;
+    drop_boid_graphs(h);  // the captured calls hold the old range
     return SPH_OK;
 }
 
@@ -983,17 +1003,9 @@ static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_
     return SPH_OK;
 }
 
-int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
+// The launches of one sph_boid_forces call (arguments checked).
+static int enqueue_boid_forces(sph_handle* h, int mode, float* out_f4, cudaStream_t s)
 {
-    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
-    if (mode < SPH_BOID_EXACT || mode > SPH_BOID_EXACT_LOCAL) return fail(h, SPH_ERR_ARG, "unsupported mode %d", mode);
-    if (h->n_boid && (!out_f4 || !aligned16(out_f4))) return fail(h, SPH_ERR_ARG, "out must be 16-byte aligned");
-    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
-    if ((mode == SPH_BOID_SURROGATE || mode == SPH_BOID_SURROGATE_FALLBACK) && !h->mlp)
-        return fail(h, SPH_ERR_STATE, "no surrogate attached (sph_set_surrogate)");
-    cudaStream_t s = (cudaStream_t)stream;
-    h->last_stream = s;
-    if (h->n_boid == 0) return SPH_OK;
     int rc = bin_state(h, s, false);
     if (rc != SPH_OK) return rc;
     float4* out = (float4*)out_f4;
@@ -1012,11 +1024,84 @@ int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
     // surrogate: features -> network -> forces (+ exact path for flagged boids)
     CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, h->feat, s,
                                 &h->launches));
-    rc = sph_mlp_forward(h->mlp, h->feat, h->nb_pad, h->yout, stream);
+    rc = sph_mlp_forward(h->mlp, h->feat, h->nb_pad, h->yout, s);
     if (rc != SPH_OK) return fail(h, rc, "surrogate forward: %s", sph_last_error(nullptr));
     CUDA_TRY(h, launch_surrogate_out(h->yout, h->feat, h->feat_lo, h->feat_hi, h->n_boid, h->f_scale, h->log_err_max,
                                      out, h->bflag, h->err + 1, s, &h->launches));
     if (mode == SPH_BOID_SURROGATE_FALLBACK) return exact_local(h, h->bflag, out, s);
+    return SPH_OK;
+}
+
+static int check_boid_forces(sph_handle* h, int mode, float* out_f4)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (mode < SPH_BOID_EXACT || mode > SPH_BOID_EXACT_LOCAL) return fail(h, SPH_ERR_ARG, "unsupported mode %d", mode);
+    if (h->n_boid && (!out_f4 || !aligned16(out_f4))) return fail(h, SPH_ERR_ARG, "out must be 16-byte aligned");
+    if (!h->has_state) return fail(h, SPH_ERR_STATE, "no state loaded");
+    if ((mode == SPH_BOID_SURROGATE || mode == SPH_BOID_SURROGATE_FALLBACK) && !h->mlp)
+        return fail(h, SPH_ERR_STATE, "no surrogate attached (sph_set_surrogate)");
+    return SPH_OK;
+}
+
+int sph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
+{
+    int rc = check_boid_forces(h, mode, out_f4);
+    if (rc != SPH_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    if (h->n_boid == 0) return SPH_OK;
+    return enqueue_boid_forces(h, mode, out_f4, s);
+}
+
+int sph_graph_boid_forces(sph_handle* h, int mode, float* out_f4, void* stream)
+{
+    int rc = check_boid_forces(h, mode, out_f4);
+    if (rc != SPH_OK) return rc;
+    if (!stream) return fail(h, SPH_ERR_ARG, "a CUDA graph needs a non-default stream");
+    cudaStream_t s = (cudaStream_t)stream;
+    h->last_stream = s;
+    if (h->n_boid == 0) return SPH_OK;
+    auto& g = h->bgraph[mode - SPH_BOID_EXACT];
+    if (g.exec && (g.out != out_f4 || g.stream != s)) {
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+    }
+    if (!g.exec && (!g.warm || !h->keys_ready)) {
+        // a plain call: the first of this mode (one-time set-up of its
+        // kernels), or the state's cell keys are not computed yet
+        rc = enqueue_boid_forces(h, mode, out_f4, s);
+        if (rc == SPH_OK) g.warm = true;
+        return rc;
+    }
+    if (!g.exec) {
+        const int cap = h->prof_cap;
+        h->prof_cap = 0;  // no event records inside the graph
+        const long long before = h->launches;
+        cudaGraph_t graph = nullptr;
+        CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_boid_forces(h, mode, out_f4, s);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        h->prof_cap = cap;
+        g.launches = h->launches - before;
+        h->launches = before;
+        if (rc != SPH_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(h, SPH_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return fail(h, SPH_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        g.out = out_f4;
+        g.stream = s;
+    }
+    if (!h->keys_ready) return enqueue_boid_forces(h, mode, out_f4, s);  // the captured call starts from keys
+    CUDA_TRY(h, cudaGraphLaunch(g.exec, s));
+    h->launches += g.launches;
+    h->has_step = false;
     return SPH_OK;
 }
 

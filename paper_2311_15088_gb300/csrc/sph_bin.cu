@@ -14,8 +14,12 @@ namespace sphk {
 
 // ------------------------------------------------------------------ keys
 
+struct Box {
+    float box_min[3], box_max[3];
+};
+
 __global__ void __launch_bounds__(256)
-k_keys(const float4* __restrict__ pos, int n, GridDesc g, unsigned* __restrict__ key,
+k_keys(const float4* __restrict__ pos, int n, GridDesc g, Box box, unsigned* __restrict__ key,
        unsigned* __restrict__ rank, unsigned* __restrict__ count, unsigned* __restrict__ err)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -24,19 +28,27 @@ k_keys(const float4* __restrict__ pos, int n, GridDesc g, unsigned* __restrict__
     bool clamped = false;
     if (active) {
         float4 p = pos[i];
-        k = cell_key(g, p.x, p.y, p.z, &clamped);
+        bool cl = false;
+        k = cell_key(g, p.x, p.y, p.z, &cl);
         key[i] = k;
+        clamped = outside_box(box, p.x, p.y, p.z);
     }
     unsigned r = agg_increment(count, k, active);
     if (active) rank[i] = r;
     if (__any_sync(FULL, clamped) && (threadIdx.x & 31) == 0) atomicOr(err, SPH_DEV_CLAMPED);
 }
 
-cudaError_t launch_keys(const float4* pos, int n, const GridDesc& g, unsigned* key, unsigned* rank,
-                        unsigned* count, unsigned* err, cudaStream_t s, long long* launches)
+cudaError_t launch_keys(const float4* pos, int n, const GridDesc& g, const float box_min[3], const float box_max[3],
+                        unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
+                        long long* launches)
 {
     if (n <= 0) return cudaSuccess;
-    k_keys<<<(n + 255) / 256, 256, 0, s>>>(pos, n, g, key, rank, count, err);
+    Box box;
+    for (int a = 0; a < 3; ++a) {
+        box.box_min[a] = box_min[a];
+        box.box_max[a] = box_max[a];
+    }
+    k_keys<<<(n + 255) / 256, 256, 0, s>>>(pos, n, g, box, key, rank, count, err);
     ++*launches;
     return cudaGetLastError();
 }
@@ -54,8 +66,11 @@ k_scene_keys(const float4* __restrict__ pos, Scenes sc, unsigned* __restrict__ k
     if (active) {
         const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
         float4 p = pos[i];
-        k = (unsigned)c.c_base + cell_key(c.g, p.x, p.y, p.z, &clamped);
+        bool cl = false;
+        k = (unsigned)c.c_base + cell_key(c.g, p.x, p.y, p.z, &cl);
         key[i] = k;
+        // boid-attached particles follow their boids, which may leave the tank
+        clamped = id_of(p) >= sc.nb_all && outside_box(c, p.x, p.y, p.z);
     }
     unsigned r = agg_increment(count, k, active);
     if (active) rank[i] = r;

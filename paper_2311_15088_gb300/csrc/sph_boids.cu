@@ -207,11 +207,12 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
     const int slot = slot_of_boid[b];
     pos_next[slot] = np;
     vel_next[slot] = nvel;
+    // a boid outside the tank bins its particle into the nearest cell of the
+    // grid (no fluid is there); that is the method's state, not an anomaly
     bool cl2 = false;
     const unsigned k = (unsigned)c.c_base + cell_key(c.g, x[0], x[1], x[2], &cl2);
     key[slot] = k;
     rank[slot] = atomicAdd(&count[k], 1u);
-    if (cl2) atomicOr(err, SPH_DEV_CLAMPED);
 }
 
 cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const unsigned* bstart,

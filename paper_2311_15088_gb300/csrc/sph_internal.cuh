@@ -112,6 +112,17 @@ __device__ __forceinline__ unsigned agg_increment(unsigned* count, unsigned k, b
 
 __device__ __forceinline__ int id_of(const float4& p) { return __float_as_int(p.w); }
 
+// A fluid position outside the tank [box_min, box_max] (or not a number):
+// binning it clamps its cell into the grid, which SPH_DEV_CLAMPED reports.
+// Positions on the box faces are inside (their cell may still round onto
+// the last grid cell, which is no anomaly).
+template <class C>
+__device__ __forceinline__ bool outside_box(const C& c, float x, float y, float z)
+{
+    return !(x >= c.box_min[0] && x <= c.box_max[0] && y >= c.box_min[1] && y <= c.box_max[1] &&
+             z >= c.box_min[2] && z <= c.box_max[2]);
+}
+
 // Scene of element i: the k with base[k] <= i < base[k + 1] (base has S + 1
 // non-decreasing entries, base[0] = 0).  Empty scenes are skipped.
 __device__ __forceinline__ int scene_of(const unsigned* __restrict__ base, int S, unsigned i)
@@ -301,9 +312,15 @@ int scan_parts(int n);
 cudaError_t launch_scan(const unsigned* counts, int n, unsigned* part, unsigned* start,
                         cudaStream_t s, long long* launches);
 
-// Cell keys of one grid (the allocation-free binning).
-cudaError_t launch_keys(const float4* pos, int n, const GridDesc& g, unsigned* key, unsigned* rank,
-                        unsigned* count, unsigned* err, cudaStream_t s, long long* launches);
+// The uniform grid over [mn, mx] with cells of size d (dim = ceil((mx - mn)
+// / d) per axis, inv_d = fl(1 / d)); SPH_ERR_OVERFLOW beyond 2^31 - 2 cells.
+int make_grid(const float mn[3], const float mx[3], float d, GridDesc* g);
+
+// Cell keys of one grid (the allocation-free binning); err gets
+// SPH_DEV_CLAMPED for a position outside [box_min, box_max] or NaN.
+cudaError_t launch_keys(const float4* pos, int n, const GridDesc& g, const float box_min[3], const float box_max[3],
+                        unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
+                        long long* launches);
 // Cell keys of every scene's particles (global keys c_base + local key).
 cudaError_t launch_scene_keys(const float4* pos, const Scenes& sc, unsigned* key, unsigned* rank,
                               unsigned* count, unsigned* err, cudaStream_t s, long long* launches);

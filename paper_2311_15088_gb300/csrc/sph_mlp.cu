@@ -1082,6 +1082,18 @@ int sph_mlp_set_params(sph_mlp* m, const float* params, void* stream)
     return SPH_OK;
 }
 
+int sph_mlp_get_optimizer_state(sph_mlp* m, float* grads, float* m1, float* m2, long long* step, void* stream)
+{
+    if (!m || !grads || !m1 || !m2 || !step) return mfail(m, SPH_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * SPH_MLP_PARAMS;
+    MLP_TRY(m, cudaMemcpyAsync(grads, m->G, bytes, cudaMemcpyDeviceToDevice, s));
+    MLP_TRY(m, cudaMemcpyAsync(m1, m->Mo, bytes, cudaMemcpyDeviceToDevice, s));
+    MLP_TRY(m, cudaMemcpyAsync(m2, m->Vo, bytes, cudaMemcpyDeviceToDevice, s));
+    *step = m->step;
+    return SPH_OK;
+}
+
 int sph_mlp_get_params(sph_mlp* m, float* params, void* stream)
 {
     if (!m || !params) return mfail(m, SPH_ERR_ARG, "NULL argument");
@@ -1144,7 +1156,10 @@ int sph_mlp_train_step(sph_mlp* m, const void* x, const float* target, int B, in
     if (rc != SPH_OK) return rc;
     ++m->step;
     const float b1 = 0.9f, b2 = 0.999f;
-    const float c1 = 1.f - powf(b1, (float)m->step), c2 = 1.f - powf(b2, (float)m->step);
+    // bias corrections 1 - beta^t in double (in float32 the difference
+    // cancels: 1 - 0.999^t loses most of its digits for small t)
+    const float c1 = (float)(1.0 - pow((double)b1, (double)m->step));
+    const float c2 = (float)(1.0 - pow((double)b2, (double)m->step));
     if (phase == 0) {
         // every parameter except the error-head row 3 of W4 and b4[3]
         k_adam<<<256, 256, 0, s>>>(m->P, m->G, m->Mo, m->Vo, 0, L.w[3] + 3 * MLP_H, lr, b1, b2, 1e-8f, c1, c2);

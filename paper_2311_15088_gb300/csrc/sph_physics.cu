@@ -325,7 +325,7 @@ __device__ __forceinline__ float2 dxy_of(const float4& pj, float2 nxy)
     return __fadd2_rn(make_float2(pj.x, pj.y), nxy);
 }
 
-// F_b of boid b (section "Boids and Fluid Interaction"): the acceleration
+// F_b of boid b (section "Boid Motion and Agent Fluid Interaction"): the acceleration
 // of its attached particle from the fluid particles within h.  One warp per
 // boid: the lanes fetch the walk's rows together (WarpRows) and take its
 // candidates by flat index (lane l: candidates l, l + 32, ... in walk
@@ -563,8 +563,10 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
         }
         pos_next[i] = make_float4(x[0], x[1], x[2], pi.w);
         vel_next[i] = make_float4(v[0], v[1], v[2], 0.0f);
-        k_next = (unsigned)c.c_base + cell_key(c.g, x[0], x[1], x[2], &clamped);
+        bool cl = false;
+        k_next = (unsigned)c.c_base + cell_key(c.g, x[0], x[1], x[2], &cl);
         key[i] = k_next;
+        clamped = outside_box(c, x[0], x[1], x[2]);  // NaN only: the walls keep x in the box
     }
     unsigned r = agg_increment(count, k_next, fluid);
     if (fluid) rank[i] = r;

@@ -19,14 +19,14 @@
 // Calls that overlap on the GPU (two streams, two threads) race on the
 // array: serialise them.
 //
-// Set-up: the first call on a device, with that device current, looks up
-// the array's device address with cudaGetSymbolAddress (in host code the
-// symbol is only a host-side stand-in) and caches it for that device; make
-// that first call before any stream capture.
+// Set-up: in host code the array's name is only a host-side stand-in, so
+// every call looks up the array's device address on the current device with
+// cudaGetSymbolAddress (nothing is cached: after a reset of the device's
+// context the module, and the array with it, may sit at a new address).
+// The first call on a device may load the module there; make that first
+// call before any stream capture.
 #include <math.h>
 #include <stdio.h>
-
-#include <mutex>
 
 #include "sph_internal.cuh"
 
@@ -45,10 +45,6 @@ constexpr size_t STATIC_BYTES = STATIC_MISC_OFF + 256;
 static_assert(STATIC_BYTES <= SPH_STATIC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 
 __device__ __align__(256) unsigned char g_static_scratch[SPH_STATIC_SCRATCH_BYTES];
-
-constexpr int MAX_DEVICES = 64;
-std::mutex g_setup_mutex;
-unsigned char* g_scratch_ptr[MAX_DEVICES] = {};
 
 constexpr int SORT_WARPS = 8;
 constexpr int BIG_THREADS = 512;
@@ -132,30 +128,17 @@ k_sort_cells_index_big(const unsigned* __restrict__ start, const int* __restrict
     }
 }
 
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array on the current device, looked up on
+// every call (see the set-up note above).
 int scratch_on_current_device(unsigned char** out, char* msg, size_t msg_len)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        snprintf(msg, msg_len, "cudaGetDevice: %s", cudaGetErrorString(e));
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess || !ptr) {
+        snprintf(msg, msg_len, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
         return SPH_ERR_CUDA;
     }
-    if (dev < 0 || dev >= MAX_DEVICES) {
-        snprintf(msg, msg_len, "device %d beyond the %d devices this entry point supports", dev, MAX_DEVICES);
-        return SPH_ERR_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess || !ptr) {
-            snprintf(msg, msg_len, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
-            return SPH_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(ptr);
-    }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<unsigned char*>(ptr);
     return SPH_OK;
 }
 
@@ -181,7 +164,7 @@ int static_fail_msg(int code)
 extern "C" {
 
 int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys_out, int* perm_out,
-                   unsigned* cell_start_out, void* stream)
+                   unsigned* cell_start_out, unsigned* flags_out, void* stream)
 {
     if (!p) return static_fail(SPH_ERR_ARG, "params is NULL");
     if (n < 0) return static_fail(SPH_ERR_ARG, "n < 0");
@@ -192,28 +175,19 @@ int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys
         return static_fail_msg(SPH_ERR_ARG);
     }
     if (!(p->cell_size > 0.0f) || !isfinite(p->cell_size)) return static_fail(SPH_ERR_ARG, "cell_size must be > 0");
-    GridDesc g;
-    long long cells = 1;
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3; ++a)
         if (!(isfinite(p->box_min[a]) && isfinite(p->box_max[a]) && p->box_max[a] > p->box_min[a]))
             return static_fail(SPH_ERR_ARG, "box_max must exceed box_min on every axis");
-        double d = ceil(((double)p->box_max[a] - (double)p->box_min[a]) / (double)p->cell_size);
-        if (d < 1.0) d = 1.0;
-        if (d > 2147483647.0) return static_fail(SPH_ERR_ARG, "grid too large");
-        g.dim[a] = (int)d;
-        g.minf[a] = p->box_min[a];
-        cells *= (long long)d;
-        if (cells > SPH_STATIC_MAX_CELLS) {
-            snprintf(g_static_msg, sizeof(g_static_msg),
-                     "the grid has more than SPH_STATIC_MAX_CELLS = %d cells", SPH_STATIC_MAX_CELLS);
-            return static_fail_msg(SPH_ERR_ARG);
-        }
+    GridDesc g;  // the grid of sph_step's binning
+    if (make_grid(p->box_min, p->box_max, p->cell_size, &g) != SPH_OK || g.ncells > SPH_STATIC_MAX_CELLS) {
+        snprintf(g_static_msg, sizeof(g_static_msg),
+                 "the grid has more than SPH_STATIC_MAX_CELLS = %d cells", SPH_STATIC_MAX_CELLS);
+        return static_fail_msg(SPH_ERR_ARG);
     }
-    g.ncells = (int)cells;
-    g.inv_d = 1.0f / p->cell_size;
     if (!cell_start_out || (n > 0 && (!pos4 || !keys_out || !perm_out)))
         return static_fail(SPH_ERR_ARG, "a pointer is NULL");
     if (((uintptr_t)pos4 & 15) != 0) return static_fail(SPH_ERR_ARG, "pos4 must be 16-byte aligned");
+    if (((uintptr_t)flags_out & 3) != 0) return static_fail(SPH_ERR_ARG, "flags_out must be 4-byte aligned");
 
     unsigned char* base = nullptr;
     int rc = scratch_on_current_device(&base, g_static_msg, sizeof(g_static_msg));
@@ -229,8 +203,8 @@ int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys
     long long launches = 0;
     cudaError_t e = cudaMemsetAsync(count, 0, (size_t)g.ncells * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(big_count, 0, 8, s);
-    if (e == cudaSuccess) e = launch_keys(reinterpret_cast<const float4*>(pos4), n, g, keys_out, rank, count, err, s,
-                                          &launches);
+    if (e == cudaSuccess) e = launch_keys(reinterpret_cast<const float4*>(pos4), n, g, p->box_min, p->box_max,
+                                          keys_out, rank, count, err, s, &launches);
     if (e == cudaSuccess) e = launch_scan(count, g.ncells, part, cell_start_out, s, &launches);
     if (e == cudaSuccess) e = launch_scatter(keys_out, rank, cell_start_out, n, perm_out, s, &launches);
     if (e == cudaSuccess) {
@@ -239,6 +213,7 @@ int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys
         k_sort_cells_index_big<<<sm_count(), BIG_THREADS, 0, s>>>(cell_start_out, big_list, big_count, perm_out);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess && flags_out) e = cudaMemcpyAsync(flags_out, err, 4, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) {
         snprintf(g_static_msg, sizeof(g_static_msg), "CUDA error: %s", cudaGetErrorString(e));
         return static_fail_msg(SPH_ERR_CUDA);

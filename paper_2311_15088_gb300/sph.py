@@ -64,6 +64,7 @@ _sig = {
     "sph_get_state": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp]),
     "sph_step": (_i, [_vp, _i, _vp]),
     "sph_boid_forces": (_i, [_vp, _i, _vp, _vp]),
+    "sph_graph_boid_forces": (_i, [_vp, _i, _vp, _vp]),
     "sph_get_fields": (_i, [_vp, _i, _vp, _i, _vp]),
     "sph_debug_neighbors": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "sph_status": (_i, [_vp, ctypes.POINTER(ctypes.c_uint)]),
@@ -74,7 +75,7 @@ _sig = {
     "sph_destroy": (None, [_vp]),
     "sph_profile_enable": (_i, [_vp, _i]),
     "sph_profile_read": (_i, [_vp, _vp, _vp, _i]),
-    "sph_bin_static": (_i, [_P, _i, _vp, _vp, _vp, _vp, _vp]),
+    "sph_bin_static": (_i, [_P, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sph_batch_workspace_size": (_i, [_P, _vp, _vp, _i, ctypes.POINTER(_sz)]),
     "sph_batch_create": (_i, [_P, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_vp)]),
     "sph_set_tuning": (_i, [_vp, _i, _i]),
@@ -87,6 +88,7 @@ _sig = {
     "sph_mlp_destroy": (None, [_vp]),
     "sph_mlp_set_params": (_i, [_vp, _vp, _vp]),
     "sph_mlp_get_params": (_i, [_vp, _vp, _vp]),
+    "sph_mlp_get_optimizer_state": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "sph_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
     "sph_mlp_gradients": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
     "sph_mlp_train_step": (_i, [_vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp]),
@@ -232,6 +234,10 @@ def sph_boid_forces(h, mode: int, out_ptr: int, stream: int):
     _check(_lib.sph_boid_forces(h, mode, out_ptr, stream), h)
 
 
+def sph_graph_boid_forces(h, mode: int, out_ptr: int, stream: int):
+    _check(_lib.sph_graph_boid_forces(h, mode, out_ptr, stream), h)
+
+
 def sph_features(h, x_ptr, stream: int):
     _check(_lib.sph_features(h, x_ptr, stream), h)
 
@@ -297,12 +303,14 @@ SPH_STATIC_MAX_PARTICLES = 1 << 22
 SPH_STATIC_MAX_CELLS = 1 << 20
 
 
-def sph_bin_static(params: dict, n: int, pos_ptr, keys_ptr, perm_ptr, cell_start_ptr, stream: int):
-    """Allocation-free binning (no device allocation; fixed static scratch)."""
+def sph_bin_static(params: dict, n: int, pos_ptr, keys_ptr, perm_ptr, cell_start_ptr, stream: int, flags_ptr=None):
+    """Allocation-free binning (no device allocation; fixed static scratch).
+    flags_ptr: optional device word receiving the call's flags."""
     q = dict(params)
     if q.get("mass") is None:
         q["mass"] = 1.0
-    _check(_lib.sph_bin_static(ctypes.byref(make_params(q)), n, pos_ptr, keys_ptr, perm_ptr, cell_start_ptr, stream))
+    _check(_lib.sph_bin_static(ctypes.byref(make_params(q)), n, pos_ptr, keys_ptr, perm_ptr, cell_start_ptr,
+                               flags_ptr, stream))
 
 
 SPH_MLP_IN, SPH_MLP_HIDDEN, SPH_MLP_OUT, SPH_MLP_PARAMS = 272, 256, 16, 205584
@@ -330,6 +338,12 @@ def sph_mlp_set_params(m, params_ptr: int, stream: int):
 
 def sph_mlp_get_params(m, params_ptr: int, stream: int):
     _check(_lib.sph_mlp_get_params(m, params_ptr, stream))
+
+
+def sph_mlp_get_optimizer_state(m, grads_ptr: int, m1_ptr: int, m2_ptr: int, stream: int) -> int:
+    step = ctypes.c_longlong()
+    _check(_lib.sph_mlp_get_optimizer_state(m, grads_ptr, m1_ptr, m2_ptr, ctypes.byref(step), stream))
+    return int(step.value)
 
 
 def sph_mlp_forward(m, x_ptr: int, B: int, y_ptr: int, stream: int):
@@ -486,6 +500,13 @@ class Mlp:
         p = self.torch.empty(SPH_MLP_PARAMS, dtype=self.torch.float32, device=self.device)
         sph_mlp_get_params(self.handle, p.data_ptr(), self.stream)
         return p
+
+    def optimizer_state(self):
+        """(last gradient, first moment, second moment, step count)."""
+        t = self.torch
+        g, m1, m2 = (t.empty(SPH_MLP_PARAMS, dtype=t.float32, device=self.device) for _ in range(3))
+        step = sph_mlp_get_optimizer_state(self.handle, g.data_ptr(), m1.data_ptr(), m2.data_ptr(), self.stream)
+        return g, m1, m2, step
 
     def forward(self, x):
         xp, B = self._pad(x, SPH_MLP_IN, self.torch.bfloat16)
@@ -658,6 +679,18 @@ class Scene:
         t = self.torch
         out = t.empty((self.n_boid, 4), dtype=t.float32, device=self.device)
         sph_boid_forces(self.handle, mode, out.data_ptr() if out.numel() else None, self.stream)
+        return out
+
+    def graph_boid_forces(self, mode: int = 0):
+        """boid_forces replayed from a captured CUDA graph (non-default
+        stream).  Returns this mode's output buffer, which the next call of
+        the same mode overwrites."""
+        t = self.torch
+        bufs = self.__dict__.setdefault("_graph_out", {})
+        if mode not in bufs:
+            bufs[mode] = t.empty((self.n_boid, 4), dtype=t.float32, device=self.device)
+        out = bufs[mode]
+        sph_graph_boid_forces(self.handle, mode, out.data_ptr() if out.numel() else None, self.stream)
         return out
 
     def set_obstacles(self, spheres=None, boxes=None, w_obst: float = 0.05, near_factor: float = 2.0):

@@ -176,3 +176,112 @@ def test_training_fits_a_smooth_target():
     y = m.forward(xb[:512]).double().cpu().numpy()
     ref = omlp.forward(q, _bf16(x[:512]).double().numpy())["y"]
     assert np.linalg.norm(y[:, :3] - ref[:, :3]) / np.linalg.norm(ref[:, :3]) <= 3e-2
+
+
+def _flat(d):
+    return np.concatenate([np.concatenate([d[w].ravel(), d[b].ravel()]) for w, b, _, _ in omlp.LAYERS])
+
+
+def _trained_blocks(phase):
+    """(name, index array into the packed parameters) of what a phase trains:
+    phase 0 every parameter but the error head (row 3 of W4, b4[3]), phase 1
+    the error head only; rows 4..15 of W4 and b4[4..15] (padding outputs)
+    have zero gradient and are left out of the comparison of directions."""
+    idx, o = {}, 0
+    for w, b, n_out, n_in in omlp.LAYERS:
+        W = o + np.arange(n_out * n_in).reshape(n_out, n_in)
+        o += n_out * n_in
+        bb = o + np.arange(n_out)
+        o += n_out
+        if w == "W4":
+            if phase == 0:
+                idx["W4[0:3]"], idx["b4[0:3]"] = W[:3].ravel(), bb[:3]
+            else:
+                idx["W4[3]"], idx["b4[3]"] = W[3], bb[3:4]
+        elif phase == 0:
+            idx[w], idx[b] = W.ravel(), bb
+    trained = np.zeros(o, bool)
+    if phase == 0:
+        trained[:] = True
+        trained[idx_row3(o)] = False
+    else:
+        trained[np.concatenate(list(idx.values()))] = True
+    return idx, trained
+
+
+def idx_row3(total):
+    """Packed indices of the error head: row 3 of W4 and b4[3]."""
+    o = sum(n_out * n_in + n_out for _, _, n_out, n_in in omlp.LAYERS[:3])
+    w4 = o + 3 * omlp.D_H + np.arange(omlp.D_H)
+    b4 = o + omlp.D_OUT * omlp.D_H + 3
+    return np.concatenate([w4, [b4]])
+
+
+@pytest.mark.parametrize("phase", [0, 1])
+def test_train_steps_match_oracle_adam(phase):
+    """Three sph_mlp_train_step calls from fixed parameters and batch, each
+    checked against the FP64 oracle: (1) the step's gradient against the
+    oracle's gradient of the BF16-rounded network at the step's starting
+    weights (cosine >= 0.999 per block, the BF16 bound of
+    test_gradients_match_oracle), (2) the Adam update (first and second
+    moments and the FP32 master weights) element by element against the
+    oracle's adam_update applied to that gradient, within the float32
+    rounding of the kernel's operations, (3) every parameter the phase does
+    not train left bit for bit unchanged, (4) the loss within BF16 accuracy."""
+    B, lr = 512, 2e-3
+    p = _oracle_params_bf16(41)
+    x = _inputs(B, 42)
+    rng = np.random.default_rng(43)
+    t = rng.normal(size=(B, 4))
+    t[:, 3] = rng.uniform(-3, 0, size=B)
+    m = sph.Mlp(B)
+    m.set_params(torch.from_numpy(_pack(p)))
+    xb = _bf16(x).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    b1, b2, eps = (float(np.float32(v)) for v in (0.9, 0.999, 1e-8))
+    blocks, trained = _trained_blocks(phase)
+    w_prev = m.get_params().double().cpu().numpy()
+    m_prev = np.zeros_like(w_prev)
+    v_prev = np.zeros_like(w_prev)
+    for step in (1, 2, 3):
+        loss = float(m.train_step(xb, tt, lr, phase).item())
+        g, m1, m2, k = m.optimizer_state()
+        g, m1, m2 = (a.double().cpu().numpy() for a in (g, m1, m2))
+        w = m.get_params().double().cpu().numpy()
+        assert k == step and m.status() == 0
+        # (1) the gradient against the oracle's of the BF16-rounded network
+        q = _unpack(w_prev)
+        for name, _, _, _ in omlp.LAYERS:
+            q[name] = _bf16(q[name]).double().numpy()
+        c = omlp.forward(q, x)
+        if phase == 0:
+            dy, lref = omlp.force_loss_grad_y(c["y"], t[:, :3]), omlp.force_loss(c["y"], t[:, :3])
+        else:
+            dy = omlp.error_loss_grad_y(c["y"], t[:, 3])
+            lref = 0.5 * float(np.sum((c["y"][:, 3] - t[:, 3]) ** 2)) / B
+        gref = _flat(omlp.backward(q, c, dy))
+        for name, ix in blocks.items():
+            a, b = g[ix], gref[ix]
+            cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b)))
+            assert cos >= 0.999, (step, name, cos)
+        assert abs(loss - lref) <= 2e-2 * lref, (loss, lref)
+        # (2) Adam on the GPU's gradient, element by element
+        wr, mr, vr = omlp.adam_update(w_prev, g, m_prev, v_prev, step, lr, b1, b2, eps)
+        tr = trained
+        assert np.all(np.abs(m1[tr] - mr[tr]) <= 3e-7 * (b1 * np.abs(m_prev[tr]) + (1 - b1) * np.abs(g[tr])) + 1e-38)
+        assert np.all(np.abs(m2[tr] - vr[tr]) <= 4e-7 * (b2 * v_prev[tr] + (1 - b2) * g[tr] ** 2) + 1e-38)
+        upd = np.abs(wr - w_prev)
+        # the update's error: the first moment's (it can cancel, so its
+        # error is relative to its terms, not to itself) carried through
+        # lr / (sqrt(v_hat) + eps), a few float32 roundings of the update,
+        # and the rounding of the new weight
+        dm = 3e-7 * (b1 * np.abs(m_prev) + (1 - b1) * np.abs(g)) / (1 - b1 ** step)
+        tol_w = lr * dm / (np.sqrt(vr / (1 - b2 ** step)) + eps) + 2e-6 * upd + 6e-8 * np.abs(wr) + 1e-38
+        bad = np.nonzero(tr & (np.abs(w - wr) > tol_w))[0]
+        assert len(bad) == 0, (step, len(bad), [(int(i), g[i], m1[i], m2[i], w_prev[i], w[i], wr[i]) for i in bad[:6]])
+        # the update moved the trained parameters by about lr
+        assert 0.3 * lr < np.median(upd[tr][np.abs(g[tr]) > 1e-6]) < 3.0 * lr
+        # (3) untouched parameters and moments
+        assert np.array_equal(w[~tr], w_prev[~tr])
+        assert np.array_equal(m1[~tr], m_prev[~tr]) and np.array_equal(m2[~tr], v_prev[~tr])
+        w_prev, m_prev, v_prev = w, m1, m2

@@ -279,3 +279,27 @@ def test_bucket_grid_ablation(cell):
     c = counts.cpu().numpy()
     assert int(dropped.item()) > 0
     assert np.all(c <= exact) and c.sum() < exact.sum()
+
+
+def test_clamp_flag_marks_fluid_outside_the_tank_only():
+    """SPH_DEV_CLAMPED (2) reports a fluid particle binned outside the tank:
+    particles resting on the faces (box_min, box_max) and boids flying
+    outside the tank do not raise it; a fluid particle loaded outside does."""
+    p = scenes.default_params(mass=scenes.f32(0.01))
+    lo, hi = np.asarray(p["box_min"], np.float32), np.asarray(p["box_max"], np.float32)
+    fp = np.zeros((6, 4), np.float32)
+    fp[0, :3], fp[1, :3] = hi, lo
+    fp[2, :3] = (hi[0], 0.5, 0.5)
+    fp[3, :3] = (0.5, hi[1], 0.5)
+    fp[4, :3] = (0.5, 0.5, hi[2])
+    fp[5, :3] = (0.3, 0.3, 0.3)
+    bp = np.array([[1.4, 0.5, 0.5, 0.0], [0.5, -0.3, 0.5, 0.0]], np.float32)
+    bv = np.array([[0.5, 0.0, 0.0, 0.0], [0.0, -0.5, 0.0, 0.0]], np.float32)
+    s = Scene(p, len(fp), len(bp))
+    s.set_state(fp, np.zeros_like(fp), bp, bv)
+    s.step(3)
+    assert s.status() & 2 == 0
+    fp[5, 0] = np.float32(1.2)
+    s.set_state(fp, np.zeros_like(fp), bp, bv)
+    s.step(1)
+    assert s.status() & 2

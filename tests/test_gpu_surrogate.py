@@ -111,3 +111,92 @@ def test_trained_surrogate_beats_no_network():
     ev = surrogate.evaluate(mlp, Xe, Fe, info["f_scale"], info["threshold"])
     assert ev["aggregate_error_surrogate"] < 0.9 * ev["aggregate_error_mean_predictor"], ev
     assert ev["aggregate_error_with_fallback"] <= ev["aggregate_error_surrogate"]
+
+
+def _time_modes(s, modes, n_states):
+    """Per mode: summed ms of sph_graph_boid_forces (CUDA events on the
+    current stream, after two warm-up calls: the plain one and the capture)
+    over n_states states one step apart, and the forces."""
+    ms = {k: 0.0 for k in modes}
+    got = {k: [] for k in modes}
+    for _ in range(2):
+        for mode in modes.values():
+            s.graph_boid_forces(mode)
+        s.step(1)
+    for _ in range(n_states):
+        for name, mode in modes.items():
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f = s.graph_boid_forces(mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms[name] += e0.elapsed_time(e1)
+            got[name].append(f.clone())
+        s.step(1)
+    return ms, {k: torch.cat(v) for k, v in got.items()}
+
+
+def test_surrogate_gain_within_five_percent_in_distribution():
+    """What the trained network gains over the method without it, on queries
+    it was not trained or calibrated on: trained on 48 runs of the
+    262,144-particle column (64 steps each), error head and fallback
+    threshold calibrated on 2 more, then 32 states x 1,024 boids of a held-out
+    run.  With the gate (error head + input range, the exact F_b where it
+    fires) the aggregate error ||F_used - F||_2 / ||F||_2 stays within 5 %,
+    and the queries per second beat the faster of the two exact modes (full
+    density pass, or densities only where the boids need them); each mode's
+    time includes the state's binning, and every mode is replayed from its
+    captured graph (sph_graph_boid_forces)."""
+    mk = lambda sd: scenes.dam_break_column(seed_offset=100 + sd)
+    train_runs = list(range(16)) + list(range(18, 40)) + list(range(41, 51))
+    mlp, info = surrogate.build_and_train(mk, train_runs, [16, 17], steps=64, epochs=40)
+    assert info["status"] == 0
+    sc = mk(40)
+    p = dict(sc["params"])
+    p["mass"] = sph.sph_lattice_mass(p, sc["lattice_spacing"])  # as the training runs
+    modes = {"exact": SPH_BOID_EXACT, "exact_local": SPH_BOID_EXACT_LOCAL, "gated": SPH_BOID_SURROGATE_FALLBACK}
+    n_states = 32
+    with torch.cuda.stream(torch.cuda.Stream()):
+        s = _scene(sc, p)
+        s.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
+        ms, got = _time_modes(s, modes, n_states)
+    F = got["exact"][:, :3]
+    assert torch.equal(F, got["exact_local"][:, :3])
+    err = surrogate.aggregate_error(got["gated"][:, :3], F)
+    q = n_states * s.n_boid
+    qps = {k: q / (v * 1e-3) for k, v in ms.items()}
+    fallback = float(got["gated"][:, 3].mean().item())
+    speedup = qps["gated"] / max(qps["exact"], qps["exact_local"])
+    print(f"\nsurrogate gain: aggregate error {err:.4f} with {fallback:.2%} falling back; queries/s gated "
+          f"{qps['gated']:.3e}, exact {qps['exact']:.3e}, exact-local {qps['exact_local']:.3e}; "
+          f"speed-up {speedup:.2f}x over the faster exact mode")
+    assert err <= 0.05, err
+    assert speedup > 1.0, (qps, fallback)
+
+
+def test_graph_boid_forces_equal_plain_calls():
+    """Every mode replayed from its captured graph gives the plain call's
+    forces bit for bit, over steps of the state, and a new surrogate
+    setting is seen by the next replay."""
+    sc = _boids_in_fluid()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a, b = _scene(sc), _scene(sc)
+        m = Mlp(512)
+        m.set_params(torch.from_numpy(surrogate.init_params(7)))
+        for s in (a, b):
+            s.set_surrogate(m, 3.0, 0.0)
+        modes = (SPH_BOID_EXACT, SPH_BOID_EXACT_LOCAL, SPH_BOID_SURROGATE, SPH_BOID_SURROGATE_FALLBACK)
+        pairs = []
+        for it in range(4):
+            for mode in modes:
+                pairs.append((a.boid_forces(mode), b.graph_boid_forces(mode).clone()))
+            if it == 2:  # a new gate threshold: recaptured
+                for s in (a, b):
+                    s.set_surrogate(m, 3.0, 1e9)
+            a.step(1)
+            b.step(1)
+    torch.cuda.synchronize()
+    for x, y in pairs:
+        assert torch.equal(x, y)
+    assert pairs[-1][0][:, 3].sum() == 0  # threshold 1e9: nothing falls back

@@ -28,7 +28,7 @@ def _step_binning(p, pos):
             s.field("cell_start").cpu().numpy().view(np.uint32))
 
 
-def _static_binning(p, pos):
+def _static_binning(p, pos, with_flags=False):
     dims = sph.sph_grid_dims(p, 0)
     ncells = dims[0] * dims[1] * dims[2]
     n = len(pos)
@@ -36,10 +36,12 @@ def _static_binning(p, pos):
     keys = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     perm = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     cs = torch.full((ncells + 1,), -1, dtype=torch.int32, device="cuda")
+    flags = torch.full((1,), -1, dtype=torch.int32, device="cuda")
     sph.sph_bin_static(p, n, x.data_ptr(), keys.data_ptr(), perm.data_ptr(), cs.data_ptr(),
-                       torch.cuda.current_stream().cuda_stream)
+                       torch.cuda.current_stream().cuda_stream, flags.data_ptr() if with_flags else None)
     torch.cuda.synchronize()
-    return keys.cpu().numpy().view(np.uint32), perm.cpu().numpy(), cs.cpu().numpy().view(np.uint32)
+    out = (keys.cpu().numpy().view(np.uint32), perm.cpu().numpy(), cs.cpu().numpy().view(np.uint32))
+    return out + (int(flags.item()),) if with_flags else out
 
 
 def _crowded_column():
@@ -67,6 +69,22 @@ def test_static_binning_equals_step_binning_on_two_calls_in_a_row():
         want = _step_binning(p, pos)
         for g, w, name in zip(got, want, ("keys", "perm", "cell_start")):
             assert np.array_equal(g, w), f"{name} differs for {len(pos)} particles"
+
+
+def test_static_binning_reports_positions_outside_the_box():
+    """The call's flag word: 0 for positions inside the box (faces included),
+    SPH_DEV_CLAMPED (2) for one outside; the scratch keeps no flag from the
+    previous call."""
+    sc = scenes.dam_break_small()
+    p = dict(sc["params"], mass=0.01)
+    pos = sc["fluid_pos"].copy()
+    pos[0, :3] = np.asarray(p["box_max"], np.float32)
+    pos[1, :3] = np.asarray(p["box_min"], np.float32)
+    assert _static_binning(p, pos, with_flags=True)[3] == 0
+    pos[2, 0] = np.float32(1.5)
+    assert _static_binning(p, pos, with_flags=True)[3] == sph.SPH_DEV_CLAMPED
+    pos[2, 0] = np.float32(0.5)
+    assert _static_binning(p, pos, with_flags=True)[3] == 0
 
 
 def test_static_binning_rejects_sizes_beyond_its_limits():
