@@ -54,7 +54,13 @@ extern "C" {
 #define SPH_PAPER_LITERAL 1  /* 30/(pi h^4) and 40/(pi h^4), as printed in the paper      */
 
 /* Fluid -> boid coupling modes. */
-#define SPH_COUPLE_FORCE 0   /* v_b += sph_factor * dt * F_b (the only mode implemented) */
+#define SPH_COUPLE_FORCE 0   /* v_b += sph_factor * dt * F_b; the attached particle takes the boid's
+                                velocity every step (it is kinematic) */
+#define SPH_COUPLE_LITERAL 1 /* the paper's velocity update read literally: the attached particle keeps
+                                its own velocity and is integrated like every particle (its fluid
+                                force F_b plus gravity), only its position follows the boid, and
+                                v_b += sph_factor * v_att (section "Boid Motion and Agent Fluid
+                                Interaction"); sph_set_state resets v_att to the boid's velocity */
 
 /* Bits of the sticky device error word (sph_status). */
 #define SPH_DEV_NONFINITE 1u  /* a density, position or velocity became NaN/Inf  */
@@ -79,6 +85,8 @@ extern "C" {
 #define SPH_FIELD_NCAND      13  /* int[n_tot]     candidates the density pass tested, by id */
 #define SPH_FIELD_FALLBACK   14  /* int[n_boid]    1 where the last surrogate call used the exact path */
 #define SPH_FIELD_OBSTACLE_GRID 15 /* float4[nbcells] mean obstacle normal (xyz) and count (w) per boid-grid cell */
+#define SPH_FIELD_ATT_VEL    16  /* float4[n_boid] velocity the attached particle of each boid carries into the
+                                    next step (the boid's with SPH_COUPLE_FORCE, its own with SPH_COUPLE_LITERAL) */
 
 /*
  * Parameters of a scene.  Paper notation: h smoothing length, rho0 rest
@@ -100,7 +108,7 @@ typedef struct sph_params {
     float wall_restitution;    /* walls: x reflected, v_n <- -wall_restitution v_n */
     float r_sep, r_vis, w_sep, w_align, w_coh, sph_factor, v_min, v_max, edge_turn;
     float boid_cell_size;
-    int   coupling_mode;       /* SPH_COUPLE_FORCE */
+    int   coupling_mode;       /* SPH_COUPLE_FORCE (default) or SPH_COUPLE_LITERAL */
 } sph_params;
 
 typedef struct sph_handle sph_handle;

@@ -50,7 +50,7 @@ class OrParams(ctypes.Structure):
         ("sph_factor", ctypes.c_double), ("v_min", ctypes.c_double),
         ("v_max", ctypes.c_double), ("edge_turn", ctypes.c_double),
         ("boid_cell_size", ctypes.c_double), ("coupling_mode", ctypes.c_int),
-        ("obstacles", ctypes.c_void_p),
+        ("obstacles", ctypes.c_void_p), ("att_vel", ctypes.c_void_p),
     ]
 
 
@@ -93,6 +93,7 @@ class OrOutputs(ctypes.Structure):
         ("fb", _D), ("new_boid_pos", _D), ("new_boid_vel", _D), ("boid_vscale", _D),
         ("boid_nsep", _I), ("boid_nvis", _I),
         ("boid_keys", _U), ("boid_perm", _I), ("boid_cell_start", _I),
+        ("new_att_vel", _D),
     ]
 
 
@@ -218,14 +219,15 @@ def obstacle_grid(p: dict, spheres=None, boxes=None) -> np.ndarray:
     return out
 
 
-def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, obstacles=None) -> dict:
+def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, obstacles=None, att_vel=None) -> dict:
     """One oracle step; returns every output as numpy arrays.
 
     Per-particle arrays are indexed by particle id (ids < n_boid are the
     boid-attached particles), per-fluid arrays by fluid index, per-boid
     arrays by boid index.  obstacles: None or a dict(spheres=(k, 4),
     boxes=(k, 6), w_obst, near_factor) of analytic obstacles the boids
-    avoid."""
+    avoid.  att_vel: with the literal coupling (coupling_mode 1), the
+    attached particles' velocities going into the step (None: the boids')."""
     fp, fv, bp, bv = (_xyz(a) for a in (fluid_pos, fluid_vel, boid_pos, boid_vel))
     nf, nb = fp.shape[0], bp.shape[0]
     n = nf + nb
@@ -242,6 +244,7 @@ def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, obstacles=None) -> d
         boid_vscale=np.zeros(nb), boid_nsep=np.zeros(nb, np.int32), boid_nvis=np.zeros(nb, np.int32),
         boid_keys=np.zeros(nb, np.uint32), boid_perm=np.zeros(nb, np.int32),
         boid_cell_start=np.zeros(bdims[0] * bdims[1] * bdims[2] + 1, np.int32),
+        new_att_vel=np.zeros((nb, 3)),
     )
     outs = OrOutputs()
     for name, arr in o.items():
@@ -252,6 +255,10 @@ def step(p: dict, fluid_pos, fluid_vel, boid_pos, boid_vel, obstacles=None) -> d
     if obstacles is not None:
         ob, keep = make_obstacles(**obstacles)
         par.obstacles = ctypes.cast(ctypes.pointer(ob), ctypes.c_void_p)
+    av = None
+    if att_vel is not None:
+        av = _xyz(att_vel)
+        par.att_vel = av.ctypes.data_as(ctypes.c_void_p)
     rc = lib().or_step(ctypes.byref(par), nf, nb, _ptr(fp), _ptr(fv), _ptr(bp), _ptr(bv),
                        ctypes.byref(outs))
     del keep

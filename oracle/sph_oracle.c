@@ -78,8 +78,10 @@ typedef struct {
     double wall_restitution;
     double r_sep, r_vis, w_sep, w_align, w_coh, sph_factor, v_min, v_max, edge_turn;
     double boid_cell_size;
-    int coupling_mode;      /* 0: force coupling (the only mode the oracle states) */
+    int coupling_mode;      /* 0: force coupling; 1: the literal coupling (see or_step) */
     const void *obstacles;  /* const or_obstacles *, or NULL: no obstacle avoidance */
+    const float *att_vel;   /* literal coupling: the attached particles' velocities (n_boid x 3)
+                               going into the step; NULL: the boids' velocities */
 } or_params;
 
 /* Analytic obstacles standing in for the paper's obstacle meshes (section
@@ -105,6 +107,8 @@ typedef struct {
     double *new_boid_pos, *new_boid_vel, *boid_vscale;     /* per boid */
     int *boid_nsep, *boid_nvis;                            /* per boid */
     unsigned *boid_keys; int *boid_perm; int *boid_cell_start;
+    double *new_att_vel;                                   /* per boid, 3: the attached particle's
+                                                              velocity going into the next step */
 } or_outputs;
 
 /* ------------------------------------------------------------------ grid */
@@ -518,19 +522,22 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
             const float *fluid_pos, const float *fluid_vel,
             const float *boid_pos, const float *boid_vel, or_outputs *out)
 {
-    if (p->coupling_mode != 0) return -1;
+    if (p->coupling_mode != 0 && p->coupling_mode != 1) return -1;
+    const int literal = p->coupling_mode == 1;
     const int nb = n_boid, n = n_fluid + n_boid;
     or_grid g;
     grid_make(&g, p->box_min, p->box_max, p->cell_size);
 
-    /* 1. attach a particle to every boid: position and velocity of the boid. */
+    /* 1. attach a particle to every boid: the boid's position; its velocity
+     *    is the boid's (force coupling) or the attached particle's own,
+     *    carried from the previous step (literal coupling). */
     float *x32 = (float *)malloc(sizeof(float) * 3 * (size_t)(n > 0 ? n : 1));
     double *x = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double *v = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     for (int b = 0; b < nb; ++b)
         for (int a = 0; a < 3; ++a) {
             x32[3 * b + a] = boid_pos[3 * b + a];
-            v[3 * b + a] = boid_vel[3 * b + a];
+            v[3 * b + a] = literal && p->att_vel ? p->att_vel[3 * b + a] : boid_vel[3 * b + a];
         }
     for (int f = 0; f < n_fluid; ++f)
         for (int a = 0; a < 3; ++a) {
@@ -652,9 +659,25 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
             for (int a = 0; a < 3; ++a) vb[a] += p->w_coh * (pa[a] - pbd[a]);
             scale += p->w_coh * (sqrt(pam) + sqrt(pn));
         }
-        /* fluid -> boid: v += sph_factor * dt * F_b, F_b the attached particle's acceleration */
-        for (int a = 0; a < 3; ++a) vb[a] += p->sph_factor * p->dt * acc[3 * b + a];
-        if (out->acc_scale) scale += fabs(p->sph_factor) * p->dt * out->acc_scale[b];
+        double vatt[3] = {0.0, 0.0, 0.0};
+        if (literal) {
+            /* literal coupling (section "Boid Motion and Agent Fluid
+             * Interaction", the velocity update with sph_factor): the
+             * attached particle is integrated like every particle, gravity
+             * included (the frame loop integrates all particles before the
+             * boid pass), and the boid adds sph_factor times its velocity */
+            double vs = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                vatt[a] = v[3 * b + a] + p->dt * (acc[3 * b + a] + p->g[a]);
+                vb[a] += p->sph_factor * vatt[a];
+                vs += v[3 * b + a] * v[3 * b + a];
+            }
+            if (out->acc_scale) scale += fabs(p->sph_factor) * (sqrt(vs) + p->dt * (out->acc_scale[b] + gnorm));
+        } else {
+            /* fluid -> boid: v += sph_factor * dt * F_b, F_b the attached particle's acceleration */
+            for (int a = 0; a < 3; ++a) vb[a] += p->sph_factor * p->dt * acc[3 * b + a];
+            if (out->acc_scale) scale += fabs(p->sph_factor) * p->dt * out->acc_scale[b];
+        }
         /* obstacle avoidance (reading: after the fluid coupling, before the
          * edge avoidance and the speed limit, which still bound the result) */
         if (ob) {
@@ -677,6 +700,9 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
             for (int a = 0; a < 3; ++a) vb[a] *= p->v_min / sp;
         }
         if (out->new_boid_vel) for (int a = 0; a < 3; ++a) out->new_boid_vel[3 * b + a] = vb[a];
+        /* the attached particle follows the boid's position into the next
+         * step; its velocity is the boid's (force) or its own (literal) */
+        if (out->new_att_vel) for (int a = 0; a < 3; ++a) out->new_att_vel[3 * b + a] = literal ? vatt[a] : vb[a];
         if (out->new_boid_pos)
             for (int a = 0; a < 3; ++a) out->new_boid_pos[3 * b + a] = pbd[a] + vb[a] * p->dt;
         if (out->boid_vscale) out->boid_vscale[b] = scale;

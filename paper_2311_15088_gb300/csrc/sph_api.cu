@@ -200,7 +200,7 @@ static int validate(const sph_params* p, int n_fluid, int n_boid)
         return fail(nullptr, SPH_ERR_ARG, "gravity must be finite");
     if (p->const_set != SPH_MULLER3D && p->const_set != SPH_PAPER_LITERAL)
         return fail(nullptr, SPH_ERR_ARG, "unknown const_set %d", p->const_set);
-    if (p->coupling_mode != SPH_COUPLE_FORCE)
+    if (p->coupling_mode != SPH_COUPLE_FORCE && p->coupling_mode != SPH_COUPLE_LITERAL)
         return fail(nullptr, SPH_ERR_ARG, "unsupported coupling_mode %d", p->coupling_mode);
     if (!(isfinite(p->wall_restitution) && p->wall_restitution >= 0.0f))
         return fail(nullptr, SPH_ERR_ARG, "wall_restitution must be >= 0");
@@ -282,6 +282,8 @@ static void make_const(const sph_params* p, int n_fluid, int n_boid, StepConst* 
     c->w_align = p->w_align;
     c->w_coh = p->w_coh;
     c->sph_dt = (float)((double)p->sph_factor * (double)p->dt);
+    c->sph_factor = p->sph_factor;
+    c->literal = p->coupling_mode == SPH_COUPLE_LITERAL;
     c->v_min = p->v_min;
     c->v_max = p->v_max;
     c->edge_turn = p->edge_turn;
@@ -429,6 +431,15 @@ __global__ void k_by_id(const float4* __restrict__ pos, const T* __restrict__ fi
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[__float_as_int(pos[i].w)] = field[i];
+}
+
+// The velocity each boid's attached particle carries into the next step
+// (its slot of the step's sorted order).
+__global__ void k_att_vel(const float4* __restrict__ vel, const int* __restrict__ slot_of_boid, int nb,
+                          float4* __restrict__ out)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) out[b] = vel[slot_of_boid[b]];
 }
 
 __global__ void k_pressure_by_id(const float4* __restrict__ pos, const float* __restrict__ rho, Scenes sc,
@@ -868,7 +879,8 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
                                            0, nullptr, h->bbig_list, h->bbig_count, s, &h->launches));
         prof_end(h, s);
         prof_begin(h, SPH_KIND_BOID_RULES, s);
-        CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, h->obst, h->sc, h->fb, h->bpos, h->bvel, h->pos,
+        CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, h->obst, h->sc, h->fb, h->vel_s, h->bpos,
+                                      h->bvel, h->pos,
                                       h->vel, h->slot_of_boid, h->key, h->rank, h->count, h->err, s,
                                       &h->launches));
         prof_end(h, s);
@@ -1179,6 +1191,11 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
     case SPH_FIELD_NBR_COUNT:
         if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->nbr, n, (int*)dst);
         bytes = (size_t)n * 4;
+        break;
+    case SPH_FIELD_ATT_VEL:
+        // the attached particle of boid b has id b: the first nb ids
+        if (nb) k_att_vel<<<(nb + 255) / 256, 256, 0, s>>>(h->vel, h->slot_of_boid, nb, (float4*)dst);
+        bytes = (size_t)nb * 16;
         break;
     case SPH_FIELD_OBSTACLE_GRID:
         bytes = (size_t)h->nbcells * 16;

@@ -63,7 +63,7 @@ constexpr int BOID_WARPS = 8;
 __global__ void __launch_bounds__(BOID_WARPS * 32)
 k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_s,
              const unsigned* __restrict__ bstart, const float4* __restrict__ obst, Scenes sc,
-             const float4* __restrict__ fb,
+             const float4* __restrict__ fb, const float4* __restrict__ vel_s,
              float4* __restrict__ bpos, float4* __restrict__ bvel, float4* __restrict__ pos_next,
              float4* __restrict__ vel_next, const int* __restrict__ slot_of_boid,
              unsigned* __restrict__ key, unsigned* __restrict__ rank, unsigned* __restrict__ count,
@@ -169,11 +169,23 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
 #pragma unroll
         for (int a = 0; a < 3; ++a) v[a] = fmaf(c.w_coh, ps[a] * inv_n, v[a]);
     }
-    // 4. fluid -> boid coupling: v += sph_factor dt F_b
+    // 4. fluid -> boid coupling: v += sph_factor dt F_b; literal coupling:
+    // the attached particle is integrated like every particle (F_b plus
+    // gravity) and v += sph_factor v_att (the paper's velocity update)
     const float4 f = fb[b];
-    v[0] = fmaf(c.sph_dt, f.x, v[0]);
-    v[1] = fmaf(c.sph_dt, f.y, v[1]);
-    v[2] = fmaf(c.sph_dt, f.z, v[2]);
+    float vatt[3] = {0.f, 0.f, 0.f};
+    if (c.literal) {
+        const float4 va = vel_s[slot_of_boid[b]];
+        vatt[0] = fmaf(c.dt, f.x + c.grav[0], va.x);
+        vatt[1] = fmaf(c.dt, f.y + c.grav[1], va.y);
+        vatt[2] = fmaf(c.dt, f.z + c.grav[2], va.z);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = fmaf(c.sph_factor, vatt[a], v[a]);
+    } else {
+        v[0] = fmaf(c.sph_dt, f.x, v[0]);
+        v[1] = fmaf(c.sph_dt, f.y, v[1]);
+        v[2] = fmaf(c.sph_dt, f.z, v[2]);
+    }
     // 4b. obstacle avoidance: v += w_obst * (weighted mean of the cells' normals)
     if (nob > 0) {
         const float g = c.w_obst / (float)nob;
@@ -203,10 +215,11 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
     const float4 nvel = make_float4(v[0], v[1], v[2], 0.0f);
     bpos[b] = np;
     bvel[b] = nvel;
-    // the attached particle follows the boid into the next step
+    // the attached particle follows the boid into the next step: its
+    // position, and its velocity (force coupling) or its own (literal)
     const int slot = slot_of_boid[b];
     pos_next[slot] = np;
-    vel_next[slot] = nvel;
+    vel_next[slot] = c.literal ? make_float4(vatt[0], vatt[1], vatt[2], 0.0f) : nvel;
     // a boid outside the tank bins its particle into the nearest cell of the
     // grid (no fluid is there); that is the method's state, not an anomaly
     bool cl2 = false;
@@ -216,14 +229,15 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
 }
 
 cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const unsigned* bstart,
-                              const float4* obst, const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
+                              const float4* obst, const Scenes& sc, const float4* fb, const float4* vel_s,
+                              float4* bpos, float4* bvel,
                               float4* pos_next, float4* vel_next, const int* slot_of_boid,
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches)
 {
     if (sc.nb_all <= 0) return cudaSuccess;
     int blocks = (sc.nb_all + BOID_WARPS - 1) / BOID_WARPS;
-    k_boid_rules<<<blocks, BOID_WARPS * 32, 0, s>>>(bpos_s, bvel_s, bstart, obst, sc, fb, bpos, bvel, pos_next,
+    k_boid_rules<<<blocks, BOID_WARPS * 32, 0, s>>>(bpos_s, bvel_s, bstart, obst, sc, fb, vel_s, bpos, bvel, pos_next,
                                                     vel_next, slot_of_boid, key, rank, count, err);
     ++*launches;
     return cudaGetLastError();

@@ -60,6 +60,8 @@ struct StepConst {
     float restitution;
     float rs, rs2, rv2; // boid radii (separation) and squared radii
     float w_sep, w_align, w_coh, sph_dt, v_min, v_max, edge_turn;
+    float sph_factor;
+    int literal;        // SPH_COUPLE_LITERAL: the attached particles keep and integrate their own velocity
     // obstacle avoidance (sph_set_obstacles): off while obst_on == 0
     int obst_on, obst_reach;  // reach: boid-grid cells searched each way
     float w_obst, obst_near;  // gain, weight of cells in the protection range
@@ -422,8 +424,11 @@ cudaError_t launch_boid_keys(const float4* bpos, const Scenes& sc, unsigned* bke
 // then n_box x (min, max) floats, device memory.
 cudaError_t launch_obstacle_grid(const StepConst& c, const float* shapes, int n_sphere, int n_box, float half_diag,
                                  float4* grid, cudaStream_t s, long long* launches);
+// vel_s: the particles' sorted velocities of the step (the attached
+// particles' own velocities, read by the literal coupling).
 cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const unsigned* bstart,
-                              const float4* obst, const Scenes& sc, const float4* fb, float4* bpos, float4* bvel,
+                              const float4* obst, const Scenes& sc, const float4* fb, const float4* vel_s,
+                              float4* bpos, float4* bvel,
                               float4* pos_next, float4* vel_next, const int* slot_of_boid,
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches);

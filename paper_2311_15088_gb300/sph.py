@@ -22,7 +22,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 
 SPH_OK, SPH_ERR_ARG, SPH_ERR_CUDA, SPH_ERR_OVERFLOW, SPH_ERR_TIMEOUT, SPH_ERR_STATE = range(6)
 SPH_MULLER3D, SPH_PAPER_LITERAL = 0, 1
-SPH_COUPLE_FORCE = 0
+SPH_COUPLE_FORCE, SPH_COUPLE_LITERAL = 0, 1
 SPH_DEV_NONFINITE, SPH_DEV_CLAMPED, SPH_DEV_TIMEOUT = 1, 2, 4
 SPH_BOID_EXACT, SPH_BOID_SURROGATE, SPH_BOID_SURROGATE_FALLBACK, SPH_BOID_EXACT_LOCAL = 0, 1, 2, 3
 SPH_MAX_OBSTACLES = 256
@@ -36,7 +36,7 @@ FIELDS = {
     "keys": (6, np.uint32, 1), "perm": (7, np.int32, 1), "cell_start": (8, np.uint32, 1),
     "fb": (9, np.float32, 4), "boid_keys": (10, np.uint32, 1), "boid_perm": (11, np.int32, 1),
     "boid_cell_start": (12, np.uint32, 1), "ncand": (13, np.int32, 1), "fallback": (14, np.int32, 1),
-    "obstacle_grid": (15, np.float32, 4),
+    "obstacle_grid": (15, np.float32, 4), "att_vel": (16, np.float32, 4),
 }
 
 
@@ -656,7 +656,7 @@ class Scene:
             n = self.nbcells + 1
         elif name == "obstacle_grid":
             n = self.nbcells
-        elif name in ("fb", "boid_keys", "boid_perm", "fallback"):
+        elif name in ("fb", "boid_keys", "boid_perm", "fallback", "att_vel"):
             n = self.n_boid
         else:
             n = self.n

@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2311_15088_gb300 import scenes
+from paper_2311_15088_gb300 import scenes, sph
 from paper_2311_15088_gb300.sph import Scene
 
 from parity import compare_step, gpu_outputs, lattice_params, oracle_step, run_gpu
@@ -303,3 +303,41 @@ def test_clamp_flag_marks_fluid_outside_the_tank_only():
     s.set_state(fp, np.zeros_like(fp), bp, bv)
     s.step(1)
     assert s.status() & 2
+
+
+@pytest.mark.parametrize("cell", [1.0, 0.5])
+def test_literal_coupling_two_steps(cell):
+    """SPH_COUPLE_LITERAL: the attached particle keeps and integrates its own
+    velocity and the boid adds sph_factor times it.  Step 1 from a loaded
+    state (v_att = v_b) and step 2 from the GPU's state after step 1 (its
+    attached velocities read back) against the oracle, every field at the
+    usual tolerances, and the attached velocity carried into the next step
+    within the fluid velocity's tolerance."""
+    sc = scenes.scaled_block(8000, 120, (0.6, 0.6, 0.6), (0.6, 0.35, 0.6), seed=21)
+    sc["boid_pos"][:, 1] *= np.float32(0.35 / 0.6)
+    p = dict(sc["params"], coupling_mode=sph.SPH_COUPLE_LITERAL, sph_factor=scenes.f32(0.05),
+             cell_size=scenes.f32(sc["params"]["h"] * cell))
+    nb = len(sc["boid_pos"])
+    s = Scene(p, len(sc["fluid_pos"]), nb, diagnostics=True)
+    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+    att = sc["boid_vel"]
+    state = sc
+    g_ = np.float64(np.linalg.norm([np.float32(p["gx"]), np.float32(p["gy"]), np.float32(p["gz"])]))
+    for it in range(2):
+        s.step(1)
+        g = gpu_outputs(s)
+        o = oracle.step(p, state["fluid_pos"], state["fluid_vel"], state["boid_pos"], state["boid_vel"],
+                        att_vel=att)
+        compare_step(p, g, o, nb)
+        ga = s.field("att_vel").cpu().numpy()
+        Sb = o["acc_scale"][:nb] + g_
+        tol = 1e-5 * (np.abs(o["new_att_vel"]) + p["dt"] * Sb[:, None])
+        assert np.all(np.abs(ga[:, :3] - o["new_att_vel"]) <= tol), it
+        # the attached particles move on their own: not the boids' velocities
+        assert np.abs(ga[:, :3] - g["new_boid_vel"]).max() > 1e-3
+        assert s.status() & 1 == 0
+        fp, fv, bp, bv = (t.cpu().numpy() for t in s.get_state())
+        # get_state staged through the scratch arrays: step again from the
+        # state read back (set_state would reset v_att to the boids')
+        state = dict(fluid_pos=fp, fluid_vel=fv, boid_pos=bp, boid_vel=bv)
+        att = ga
