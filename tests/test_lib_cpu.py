@@ -56,7 +56,7 @@ def test_workspace_size_grows_with_particles(lib):
 
 @pytest.mark.parametrize("bad", [
     dict(h=0.0), dict(cell_size=0.01), dict(mass=-1.0), dict(dt=0.0), dict(box_max=(0.0, 1.0, 1.0)),
-    dict(const_set=7), dict(coupling_mode=1), dict(boid_cell_size=0.04), dict(r_sep=0.5),
+    dict(const_set=7), dict(coupling_mode=2), dict(boid_cell_size=0.04), dict(r_sep=0.5),
     dict(v_min=2.0), dict(k=float("nan")), dict(wall_restitution=-1.0),
 ])
 def test_invalid_parameters_are_rejected(lib, bad):
