@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2311_15088_gb300 import scenes, sph, tune
+from paper_2311_15088_gb300 import scenes, shard, sph, tune
 from paper_2311_15088_gb300.sph import Scene
 
 from parity import compare_step, gpu_outputs, lattice_params, oracle_step
@@ -175,3 +175,23 @@ def test_autotuner_restores_state_and_caches(tmp_path):
         assert torch.equal(x, y)
     again = tune.autotune(b, cache=cache)
     assert again["cached"] and again["block"] == best["block"]
+
+
+def test_rank_shares_step_like_the_scenes_alone():
+    """The scene split across two ranks (in one process here: each rank's
+    batch built in turn): every scene on one rank, each rank's batched
+    handle steps its scenes bit for bit as each scene alone, and the gather
+    returns every scene once, in order."""
+    scs = _small_batch()
+    parts = shard.assign([shard.scene_weight(sc) for sc in scs], 2)
+    assert sorted(parts[0] + parts[1]) == list(range(len(scs))) and parts[0] and parts[1]
+    local = {}
+    for r in range(2):
+        rb = shard.RankBatch(scs, parts[r])
+        rb.step(6)
+        local.update(rb.states())
+    out, owner = shard.gather(local, len(scs), 1)
+    for k, want in enumerate(_singles(scs, 6)):
+        assert owner[k] == 0
+        for x, y in zip(out[k], want):
+            assert np.array_equal(x[:, :3], y[:, :3])
