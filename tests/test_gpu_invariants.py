@@ -85,12 +85,15 @@ def test_column_settles_under_gravity():
     calibrated mass) released under gravity compresses, oscillates and
     settles: the kinetic energy falls by over 95 % between 1,000 and 12,000
     steps, every particle stays in the box, and away from the side walls
-    the density grows monotonically with depth.  The continuum balance
-    k d(rho)/dy = -rho g would give d(ln rho)/dy = -g/k; the discretisation
-    (symmetric pressure term with the spiky gradient, density by poly6) is
-    not consistent under the 2.5-fold density variation of this weak
-    equation of state, and the settled column's log-slope is steeper: it is
-    checked to lie between g/k and 3 g/k."""
+    the density grows monotonically with depth.  The symmetric pressure
+    term carries half of the pressure gradient (pinned on the oracle in
+    test_oracle_hydrostatic_pins.py), so the method's balance is
+    (k/2) d(rho)/dy = -rho g: d(ln rho)/dy = -2 g/k.  The settled column's
+    log-slope between h above the floor (the floor layer has no particles
+    below it and packs tighter) and the top slab (the free surface) is
+    checked against 2 g/k within 15 % (the column is only about 4 h tall, so
+    both boundaries reach into the fit: the local slope runs from above 2 g/k
+    near the floor to below it under the surface)."""
     p = scenes.default_params(mass=scenes.f32(1.0))
     h = float(p["h"])
     s = scenes.f32(np.float32(p["h"]) / np.float32(2))
@@ -128,5 +131,6 @@ def test_column_settles_under_gravity():
     assert len(means) >= 4
     assert np.all(np.diff(means) < 0), means
     slope = -np.polyfit(mids[:-1], np.log(means[:-1]), 1)[0]  # the top slab is the free surface
-    gk = 9.8 / 3.0
-    assert gk < slope < 3 * gk, slope
+    two_gk = 2.0 * 9.8 / 3.0
+    print(f"settled column: interior log-slope {slope:.3f} /m, 2 g/k = {two_gk:.3f} /m, slabs {means.round(1)}")
+    assert abs(slope / two_gk - 1.0) <= 0.15, slope
