@@ -52,21 +52,26 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # per particle (n the number density), i.e. C = N * 27 / (4 pi / 3) with N
 # = (4 pi / 3) n h^3 the neighbour count; a candidate test is 9 flops (3 sub,
 # 3 mul / fma, compare), a density pair 5 flops, a force pair 35 flops.
-# "executed" counts instead the candidates the pruned walk actually tests
-# (read back from the library): every candidate in the density pass, and in
-# the force pass every candidate again, or only the overflowing particles'
-# when the candidate-bit stream is on.
+# "executed" counts what the kernels actually do (read back from the
+# library): the density pass tests the candidates of its pruned walk once
+# for both passes and stores the hits as segments; the force pass evaluates
+# the stored pairs (the particle itself included, then discarded) and tests
+# candidates again only for the particles whose segments overflowed.
 FLOP_CAND, FLOP_DENS_PAIR, FLOP_FORCE_PAIR = 9, 5, 35
 STENCIL_CAND_PER_NBR = 27.0 / (4.0 * math.pi / 3.0)
-STREAM_CAPACITY = 64 * 32  # candidate bits stored per particle
-# Compulsory bytes per particle of each pass (float4 pos/vel, float rho ...):
-BYTES = {"scatter": 12, "sort": 68, "density": 24, "forces": 112}
+SEG_CAP = 128  # hit segments stored per particle
+# Compulsory bytes per particle of each pass (the method's minimum, float4
+# pos/vel, float rho): binning key + rank (scatter 12) and the gather of
+# pos, vel (sort 60), density pos in / rho out (20), forces pos, vel, rho in,
+# pos, vel, key out (72).  The kernels move more: the density pass writes
+# the hit segments and pair records the force pass reads (ncu traffic below).
+BYTES = {"scatter": 12, "sort": 60, "density": 20, "forces": 72}
 BYTES_PER_CELL_SCAN = 12
 
-# DRAM traffic of the force pass from one ncu capture (bytes per launch) and
-# the sha256 of the kernel source it was taken on; null once the source moved.
-FORCES_TRAFFIC = {"bytes": 125319936 + 118180096, "source_sha256": "c929daa0d062f9fa7f94702589892c622dda811245f82c79c7f9b94e86e6be63",
-                  "capture": "ncu, 2,097,152-particle tank released unsettled (bench.py --settle 0)"}
+# DRAM traffic per launch of the force and density passes from one ncu
+# capture of the bench's workload, and the sha256 of the kernel source it
+# was taken on; null once the source moved.
+KERNEL_TRAFFIC = {}
 
 
 def _args():
@@ -194,14 +199,18 @@ class ClockSampler:
 # ----------------------------------------------------------- work counts
 
 def _work_snapshot(s):
-    """Candidates tested, neighbour pairs and the candidates of particles
-    whose stream overflowed, for the step last run."""
+    """Candidates tested, neighbour pairs, hit segments stored and the
+    candidates of the particles whose segments overflowed (tested again by
+    the force pass), for the step last run."""
     nc = s.field("ncand").cpu().numpy().astype(np.int64)
     nbr = s.field("nbr_count").cpu().numpy()
+    nseg = s.field("nseg").cpu().numpy().astype(np.int64)
     from paper_2311_15088_gb300.sph import STATS
     st = s.stats().cpu().numpy()[0]
+    over = nseg > SEG_CAP
     return {"candidates": int(nc.sum()), "pairs": int(nbr.astype(np.int64).sum()),
-            "overflow_candidates": int(nc[nc > STREAM_CAPACITY].sum()),
+            "segments": int(nseg[~over].sum()), "overflow_particles": int(over.sum()),
+            "overflow_candidates": int(nc[over].sum()),
             "nbr_mean": float(nbr.mean()), "nbr_max": int(nbr.max()),
             "stats": {k: float(v) for k, v in zip(STATS, st)}}
 
@@ -383,21 +392,30 @@ def _oracle_rate(p, fp, fv, bp, bv, step_seconds, min_seconds=0.0, steps=None):
 def run_batched(a, dev, flush):
     """256 independent tanks in one handle (every pass one launch over all
     scenes, the step replayed from a CUDA graph, launch shape autotuned)
-    against a loop that steps each scene's own handle with the same kernels.
-    The cell size is tuned too, over h/2 and h (it changes the float32
-    summation order, not the results beyond rounding: parity is tested at
-    both); the loop uses the chosen one.  Returns the "batched" object of
-    the bench line."""
+    against a loop that replays each scene's own captured step with the same
+    kernels.  The cell size is tuned too, over h/2 and h (it changes the
+    float32 summation order, not the results beyond rounding: parity is
+    tested at both); the loop uses the chosen one.  Under torchrun the
+    scenes are split across the ranks (greedy bin-pack by particle count,
+    paper_2311_15088_gb300.shard): each rank steps its share, the time is
+    the slowest rank's and scenes/s counts all 256 (strong scaling of this
+    leg).  Returns the "batched" object of the bench line."""
     import torch
 
-    from paper_2311_15088_gb300 import sph, tune
+    from paper_2311_15088_gb300 import shard, sph, tune
     from paper_2311_15088_gb300.sph import Scene
 
-    scs = scenes.batched_tanks()
-    for sc in scs:
+    world, rank, _ = _dist()
+    all_scs = scenes.batched_tanks()
+    for sc in all_scs:
         sc["params"] = _params(sc)
+    S = len(all_scs)
+    weights = [shard.scene_weight(sc) for sc in all_scs]
+    parts = shard.assign(weights, world)
+    scs = [all_scs[k] for k in parts[rank]]
     nf = [len(sc["fluid_pos"]) for sc in scs]
     nb = [len(sc["boid_pos"]) for sc in scs]
+    nf_all = sum(len(sc["fluid_pos"]) for sc in all_scs)
     cat = lambda key: np.concatenate([sc[key] for sc in scs])
     stream = torch.cuda.Stream(dev)
 
@@ -409,6 +427,17 @@ def run_batched(a, dev, flush):
             out.append(q)
         return out
 
+    def timed_steps(fn, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        torch.cuda.synchronize(dev)
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize(dev)
+        return sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+
     per_cell = {}
     with torch.cuda.stream(stream):
         for frac in (0.5, 1.0):
@@ -418,47 +447,36 @@ def run_batched(a, dev, flush):
             best = tune.autotune(b, steps=3, cache=None)
             for _ in range(a.warmup):
                 b.graph_step(1)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(a.batch_steps)]
-            torch.cuda.synchronize(dev)
             l0 = b.launches
-            for e0, e1 in ev:
-                flush.zero_()
-                e0.record()
-                b.graph_step(1)
-                e1.record()
-            torch.cuda.synchronize(dev)
-            per_cell[frac] = {"t": sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3, "launches": b.launches - l0,
-                              "tuning": best, "params": ps}
+            t = timed_steps(lambda: b.graph_step(1), a.batch_steps)
+            launches = b.launches - l0
+            work = _work_snapshot(b)
+            per_cell[frac] = {"t": _max_over_ranks(t, world, dev), "launches": launches, "tuning": best,
+                              "params": ps, "work": work, "ncells": b.ncells}
             del b
         frac = min(per_cell, key=lambda f: per_cell[f]["t"])
         chosen = per_cell[frac]
         t_batch, launches, best = chosen["t"], chosen["launches"], chosen["tuning"]
-        # the same scenes, one handle each, stepped in a host loop
+        # the same scenes, one handle each, each replaying its own captured step
         loop = []
         for sc, q in zip(scs, chosen["params"]):
             s1 = Scene(q, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
             s1.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
-            s1.set_tuning(best["block"], best["use_stream"])
+            s1.set_tuning(best["block"], best["use_segments"])
             loop.append(s1)
-        for _ in range(a.warmup):
+        for _ in range(max(a.warmup, 2)):
             for s1 in loop:
-                s1.step(1)
+                s1.graph_step(1)
         n_loop = max(3, a.batch_steps // 3)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_loop)]
-        torch.cuda.synchronize(dev)
-        for e0, e1 in ev:
-            flush.zero_()
-            e0.record()
+
+        def loop_step():
             for s1 in loop:
-                sph.sph_step(s1.handle, 1, stream.cuda_stream)
-            e1.record()
-        torch.cuda.synchronize(dev)
-        t_loop = sum(e0.elapsed_time(e1) for e0, e1 in ev) / 1e3
+                sph.sph_graph_step(s1.handle, 1, stream.cuda_stream)
+
+        t_loop = _max_over_ranks(timed_steps(loop_step, n_loop), world, dev)
         del loop
-    S = len(scs)
     cpu = None
-    if not a.no_cpu_baseline:
+    if not a.no_cpu_baseline and world == 1:
         # the oracle, as it stands, one step of every 16th scene (its cell size)
         import oracle
 
@@ -466,24 +484,50 @@ def run_batched(a, dev, flush):
         picked = list(range(0, S, 16))
         t0 = time.perf_counter()
         for i in picked:
-            sc = scs[i]
+            sc = all_scs[i]
             oracle.step(chosen["params"][i], sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
         el = time.perf_counter() - t0
+        nf_p = sum(len(all_scs[i]["fluid_pos"]) for i in picked)
         cpu = {"value": len(picked) / el, "unit": "scenes/s", "cores": oracle.num_threads(), "kind": "oracle",
-               "particle_steps_per_s": sum(nf[i] for i in picked) / el,
-               "sample": f"one oracle step of each of {len(picked)} scenes (every 16th), "
-                         f"{sum(nf[i] for i in picked)} fluid particles"}
+               "particle_steps_per_s": nf_p / el,
+               "sample": f"one oracle step of each of {len(picked)} scenes (every 16th), {nf_p} fluid particles"}
+    # rooflines of this rank's batched step (its share of the scenes)
+    ms = 1e3 * t_batch / a.batch_steps
+    w = chosen["work"]
+    n_all = sum(nf) + sum(nb)
+    stencil = STENCIL_CAND_PER_NBR * w["pairs"]
+    flops = 2 * FLOP_CAND * stencil + FLOP_DENS_PAIR * (w["pairs"] + n_all) + FLOP_FORCE_PAIR * w["pairs"]
+    step_bytes = n_all * sum(BYTES.values()) + chosen["ncells"] * BYTES_PER_CELL_SCAN
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     return {
         "cpu_baseline": cpu,
         "workload": f"{S} unit-box dam-breaks, particles log-uniform in [2048, 65536], boids uniform in [8, 256]",
-        "scenes": S, "particles": int(sum(nf)), "boids": int(sum(nb)), "steps": a.batch_steps,
+        "scenes": S, "particles": int(nf_all), "boids": int(sum(len(sc["boid_pos"]) for sc in all_scs)),
+        "steps": a.batch_steps, "ranks": world, "scaling": "strong" if world > 1 else None,
+        "scenes_per_rank": [len(p) for p in parts], "load_imbalance": shard.imbalance(weights, parts),
         "scenes_per_s": S * a.batch_steps / t_batch, "ms_per_step": 1e3 * t_batch / a.batch_steps,
-        "particle_steps_per_s": sum(nf) * a.batch_steps / t_batch, "gpu_launches": launches,
+        "particle_steps_per_s": nf_all * a.batch_steps / t_batch, "gpu_launches": launches,
         "loop_scenes_per_s": S * n_loop / t_loop, "loop_ms_per_step": 1e3 * t_loop / n_loop,
         "speedup_vs_loop": (S * a.batch_steps / t_batch) / (S * n_loop / t_loop),
+        "loop": "each scene's own handle replaying its captured step (sph_graph_step), same kernels",
         "cell_size_over_h": frac,
         "ms_per_step_by_cell_size": {str(f): 1e3 * v["t"] / a.batch_steps for f, v in per_cell.items()},
-        "tuning": {"block": best["block"], "use_stream": best["use_stream"], "ms_per_step": best["ms_per_step"]},
+        "tuning": {"block": best["block"], "use_segments": best["use_segments"], "ms_per_step": best["ms_per_step"]},
+        "roofline": {
+            "alu": {"achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                    "definition": "both neighbour passes' algorithmic flops (27-cell stencil at h) over the whole "
+                                  "step's time, this rank's scenes"},
+            "hbm": {"achieved": step_bytes / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": step_bytes / (ms * 1e-3) / 1e9 / hbm_peak,
+                    "definition": "compulsory bytes per particle-step (binning 72, density 20, forces 72) + 12 B "
+                                  "per cell, over the whole step's time; the small scenes stay in L2"},
+            "neighbours_mean": w["nbr_mean"]},
         "mode": "CUDA graph replay of one step; L2 flushed between timed steps",
     }
 
@@ -494,39 +538,45 @@ HEAD_ONLY = "surrogate_fallback_head_only"
 
 
 def _time_modes(s, modes, n_states, warmup, bounds=None):
-    """Per mode: summed ms of sph_boid_forces over n_states states (one
-    step between states), the forces and the fallback flags.  The mode
-    named HEAD_ONLY runs the fallback with the input-range check off."""
+    """Per mode: summed ms of the boid-force call over n_states states (one
+    step between states), the forces and the fallback flags.  Every mode is
+    replayed from its captured graph (sph_graph_boid_forces, on the current
+    stream, which must not be the default one), except the mode named
+    HEAD_ONLY, the fallback with the input-range check off: switching the
+    range drops the captured calls, so it runs plain calls, in a second pass
+    over the same states (the state is restored from a snapshot)."""
     import torch
 
+    graphed = {k: v for k, v in modes.items() if k != HEAD_ONLY}
     ms = {k: 0.0 for k in modes}
     got = {k: [] for k in modes}
     fall = {k: [] for k in modes if k.startswith("surrogate_fallback")}
+    snapshot = [t.clone() for t in s.get_state()]
 
-    def call(name, mode):
-        if name == HEAD_ONLY:
-            s.set_surrogate_bounds(None)
-        f = s.boid_forces(mode)
-        if name == HEAD_ONLY:
-            s.set_surrogate_bounds(bounds)
-        return f
+    def run(which, call):
+        for _ in range(max(warmup, 2)):  # the plain first call, then the capture
+            for name, mode in which.items():
+                call(mode)
+        for _ in range(n_states):
+            for name, mode in which.items():
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                f = call(mode)
+                e1.record()
+                torch.cuda.synchronize()
+                ms[name] += e0.elapsed_time(e1)
+                got[name].append(f[:, :3].clone())
+                if name in fall:
+                    fall[name].append(f[:, 3].clone())
+            s.step(1)
 
-    for _ in range(warmup):
-        for name, mode in modes.items():
-            call(name, mode)
-    for _ in range(n_states):
-        for name, mode in modes.items():
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            f = call(name, mode)
-            e1.record()
-            torch.cuda.synchronize()
-            ms[name] += e0.elapsed_time(e1)
-            got[name].append(f[:, :3].clone())
-            if name in fall:
-                fall[name].append(f[:, 3].clone())
-        s.step(1)
+    run(graphed, s.graph_boid_forces)
+    if HEAD_ONLY in modes:
+        s.set_state(*snapshot)
+        s.set_surrogate_bounds(None)
+        run({HEAD_ONLY: modes[HEAD_ONLY]}, s.boid_forces)
+        s.set_surrogate_bounds(bounds)
     return ms, got, fall
 
 
@@ -552,6 +602,44 @@ def _mode_report(surrogate, ms, got, fall, q, n_states):
                                   "aggregate_error": out[best]["aggregate_error"],
                                   "speedup_vs_exact_full": out[best]["qps"] / out["exact_full"]["qps"]}
     return out
+
+
+def _features_roofline(s, dev, reps=20):
+    """The surrogate's stencil features (k_features, its own launch timed by
+    the library's event hook): per boid the 4 x 4 x 4 stencil of h-cells
+    gathers every particle of the stencil's box (pos and vel, 32 B each)
+    and writes one 544-byte feature row; against the measured HBM peak
+    (the boxes of neighbouring boids overlap, so much of it hits L2)."""
+    import torch
+
+    from paper_2311_15088_gb300 import sph
+
+    sph.sph_profile_enable(s.handle, 4 * reps + 8)
+    for _ in range(reps):
+        s.features()
+    torch.cuda.synchronize(dev)
+    prof = sph.sph_profile_read(s.handle)
+    sph.sph_profile_enable(s.handle, 0)
+    ms, cnt = prof["features"]
+    ms = ms / max(cnt, 1)
+    # particles in each boid's box: the stencil spans 4 h and one grid cell
+    # of margin on each side
+    p = s.params
+    h, d = float(p["h"]), float(p["cell_size"])
+    box = (4.0 * h + 2.0 * d) ** 3
+    fluid_vol = 1.0  # the column's fluid fills [0, 1]^3 at 262,144 particles
+    per_boid = box * s.n_fluid / fluid_vol * 32 + 544
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = s.n_boid * per_boid / (ms * 1e-3) / 1e9
+    return {"kernel": "k_features", "ms_per_launch": ms, "boids": s.n_boid, "bytes_per_boid": per_boid,
+            "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "bound": "hbm",
+            "definition": "particles of each boid's stencil box (4 h + 2 cells per side, at the column's "
+                          "density) x 32 B gathered + the 544-byte row written"}
 
 
 def _network_roofline(s, mlp, reps=50):
@@ -635,24 +723,33 @@ def run_surrogate(a, dev, big=None):
     mlp, info = surrogate.build_and_train(mk, train_runs, [16, 17], steps=64, epochs=40)
     sc = mk(40)
     p = _params(sc)
-    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
-    s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
-    s.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
     modes = {"exact_full": SPH_BOID_EXACT, "exact_local": SPH_BOID_EXACT_LOCAL, "surrogate": SPH_BOID_SURROGATE,
              "surrogate_fallback": SPH_BOID_SURROGATE_FALLBACK, HEAD_ONLY: SPH_BOID_SURROGATE_FALLBACK}
     n_states = 64
-    ms, got, fall = _time_modes(s, modes, n_states, a.warmup, mlp.bounds)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
+        s.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
+        s.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
+        ms, got, fall = _time_modes(s, modes, n_states, a.warmup, mlp.bounds)
+        feat = _features_roofline(s, dev)
     out = {"workload": "65,536 boid-force queries: 64 states x 1,024 boids of a 262,144-particle column run",
-           "training": info, "queries": n_states * s.n_boid}
+           "training": info, "queries": n_states * s.n_boid,
+           "mode": "each mode replayed from its captured graph (sph_graph_boid_forces)",
+           "features_roofline": feat}
     out.update(_mode_report(surrogate, ms, got, fall, n_states * s.n_boid, n_states))
     out["network_roofline"] = _network_roofline(s, mlp)
     if not a.no_cpu_baseline:
         out["cpu_baseline"] = _oracle_surrogate(p, sc)
     if big is not None:
         # distribution shift: the settled 2M-particle tank and its 16,384 boids
-        big.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
-        nb = 4
-        ms, got, fall = _time_modes(big, modes, nb, 1, mlp.bounds)
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            big.set_surrogate(mlp, info["f_scale"], info["threshold"], mlp.bounds)
+            nb = 4
+            ms, got, fall = _time_modes(big, modes, nb, 2, mlp.bounds)
+        torch.cuda.synchronize(dev)
         out["large_tank"] = {"workload": f"{nb * big.n_boid:,} queries: {nb} states x {big.n_boid:,} boids of the "
                                          "settled 2,097,152-particle tank (trained on the column: a shift)",
                              "queries": nb * big.n_boid}
@@ -810,13 +907,16 @@ def run_ours(a):
     stencil = STENCIL_CAND_PER_NBR * pairs
     force_flops = FLOP_CAND * stencil + FLOP_FORCE_PAIR * pairs
     dens_flops = FLOP_CAND * stencil + FLOP_DENS_PAIR * (pairs + n_all)
-    force_exec = FLOP_CAND * (over if s.tuning[1] else cand) + FLOP_FORCE_PAIR * pairs
+    segs = statistics.mean(w["segments"] for w in works)
+    if s.tuning[1]:  # segments: stored pairs (self included) + overflow tests
+        force_exec = FLOP_FORCE_PAIR * (pairs + nf) + FLOP_CAND * over
+    else:
+        force_exec = FLOP_CAND * cand + FLOP_FORCE_PAIR * pairs
     dens_exec = FLOP_CAND * cand + FLOP_DENS_PAIR * (pairs + n_all)
     achieved = force_flops / (f_ms * 1e-3) / 1e12
     src = os.path.join(ROOT, "paper_2311_15088_gb300", "csrc", "sph_physics.cu")
-    traffic = None
-    if FORCES_TRAFFIC and FORCES_TRAFFIC.get("source_sha256") == _source_sha(src):
-        traffic = FORCES_TRAFFIC["bytes"]
+    src_sha = _source_sha(src)
+    traffic = {k: v["bytes"] for k, v in KERNEL_TRAFFIC.items() if v.get("source_sha256") == src_sha}
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -832,18 +932,28 @@ def run_ours(a):
         if k in passes:
             gbs = n_all * BYTES[k] / (passes[k]["ms_per_step"] * 1e-3) / 1e9
             hbm_pass[k] = {"GB/s": gbs, "frac": gbs / hbm_peak}
+    both = (force_flops + dens_flops) / ((f_ms + d_ms) * 1e-3) / 1e12
     roofline = {
         "bound": "alu", "kernel": "k_forces (pair forces + integration)", "achieved": achieved,
-        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+        "traffic": traffic.get("k_forces"),
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
         "flops_per_launch": force_flops,
         "flops_definition": "27-cell stencil at cell size h: 9 flops x 27/(4pi/3) x neighbours + 35 x neighbours",
         "executed": {"flops_per_launch": force_exec, "achieved": force_exec / (f_ms * 1e-3) / 1e12,
                      "frac": force_exec / (f_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                     "candidates_per_particle": cand / n_all},
+                     "definition": "35 x stored pairs (self included) + 9 x candidates of overflowing particles"
+                                   if s.tuning[1] else "9 x candidates + 35 x pairs",
+                     "candidates_per_particle": cand / n_all,
+                     "segments_per_particle": segs / n_all,
+                     "overflow_particles": statistics.mean(w["overflow_particles"] for w in works)},
         "density_pass": {"achieved": dens_flops / (d_ms * 1e-3) / 1e12,
                          "frac": dens_flops / (d_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                         "executed_frac": dens_exec / (d_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
+                         "executed_frac": dens_exec / (d_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                         "traffic": traffic.get("k_density")},
+        "neighbour_passes": {"achieved": both, "frac": both / FP32_PEAK_TFLOPS,
+                             "definition": "both passes' algorithmic flops over their summed time (the density "
+                                           "pass tests the candidates once for both)"},
     }
     hbm = {"algorithmic_bytes_per_step": step_bytes, "achieved_GBps": step_bytes / (ms_per_step * 1e-3) / 1e9,
            "peak_GBps": hbm_peak, "frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak,
@@ -889,7 +999,7 @@ def run_ours(a):
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "cell_size_over_h": float(np.float32(p["cell_size"]) / np.float32(p["h"])),
-                       "tuning": {"block": s.tuning[0], "use_stream": s.tuning[1]},
+                       "tuning": {"block": s.tuning[0], "use_segments": s.tuning[1]},
                        "force_pass_neighbours": "pair lists" if a.neighbor_lists else "walk",
                        "neighbours_mean": statistics.mean(w["nbr_mean"] for w in works),
                        "neighbours_max": max(w["nbr_max"] for w in works),

@@ -85,6 +85,9 @@ extern "C" {
 #define SPH_FIELD_NCAND      13  /* int[n_tot]     candidates the density pass tested, by id */
 #define SPH_FIELD_FALLBACK   14  /* int[n_boid]    1 where the last surrogate call used the exact path */
 #define SPH_FIELD_OBSTACLE_GRID 15 /* float4[nbcells] mean obstacle normal (xyz) and count (w) per boid-grid cell */
+#define SPH_FIELD_NSEG       17  /* int[n_tot]     hit segments the density pass stored for the force pass,
+                                    by id (0 for attached particles; above 128: the particle's candidates
+                                    are tested again in the force pass) */
 #define SPH_FIELD_ATT_VEL    16  /* float4[n_boid] velocity the attached particle of each boid carries into the
                                     next step (the boid's with SPH_COUPLE_FORCE, its own with SPH_COUPLE_LITERAL) */
 
@@ -175,8 +178,8 @@ int sph_batch_create(const sph_params* params, const int* n_fluid, const int* n_
  * density pass, which tests every candidate anyway, records each fluid
  * particle's force pairs as segments (first sorted slot, 32-bit mask) in
  * walk order, and the force pass reads them instead of testing the
- * candidates again (512 bytes of workspace per particle hold them; a
- * particle with more than 64 segments is tested again).  use_segments = 0:
+ * candidates again (1 KiB of workspace per particle holds them; a
+ * particle with more than 128 segments is tested again).  use_segments = 0:
  * the force pass tests the candidates itself.  Neither choice changes any
  * result bit: the pairs and their order are the same.  Errors: SPH_ERR_ARG.
  */
@@ -397,7 +400,7 @@ long long sph_launch_count(sph_handle* h);
  * (exclusive scan of the cell counts), SPH_KIND_SCATTER, SPH_KIND_SORT
  * (per-cell sort + gather), SPH_KIND_DENSITY, SPH_KIND_FORCES (pair forces
  * + integration + next keys), SPH_KIND_BOID_BIN (boid-grid binning),
- * SPH_KIND_BOID_RULES.  sph_profile_enable(h, n) creates a host-side pool
+ * SPH_KIND_BOID_RULES, SPH_KIND_FEATURES.  sph_profile_enable(h, n) creates a host-side pool
  * of 2n events (n = 0 disables and frees it); while enabled, each pass of
  * sph_step is bracketed by two events recorded on the step's stream, up to
  * n passes.  sph_profile_read synchronises on the last event and writes,
@@ -413,6 +416,7 @@ long long sph_launch_count(sph_handle* h);
 #define SPH_KIND_BOID_BIN   6
 #define SPH_KIND_BOID_RULES 7
 #define SPH_KIND_LISTS      8  /* neighbour lists: offsets scan + fill (when set) */
+#define SPH_KIND_FEATURES   9  /* the surrogate's stencil features (sph_features, surrogate modes) */
 #define SPH_NUM_KINDS       9
 int sph_profile_enable(sph_handle* h, int max_passes);
 int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds);

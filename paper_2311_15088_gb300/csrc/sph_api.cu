@@ -990,7 +990,9 @@ int sph_features(sph_handle* h, void* x_out, void* stream)
     if (h->n_boid == 0) return SPH_OK;
     int rc = bin_state(h, s, false);
     if (rc != SPH_OK) return rc;
+    prof_begin(h, SPH_KIND_FEATURES, s);
     CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, x_out, s, &h->launches));
+    prof_end(h, s);
     h->has_step = false;
     return SPH_OK;
 }
@@ -1034,8 +1036,10 @@ static int enqueue_boid_forces(sph_handle* h, int mode, float* out_f4, cudaStrea
     }
     if (mode == SPH_BOID_EXACT_LOCAL) return exact_local(h, nullptr, out, s);
     // surrogate: features -> network -> forces (+ exact path for flagged boids)
+    prof_begin(h, SPH_KIND_FEATURES, s);
     CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, h->feat, s,
                                 &h->launches));
+    prof_end(h, s);
     rc = sph_mlp_forward(h->mlp, h->feat, h->nb_pad, h->yout, s);
     if (rc != SPH_OK) return fail(h, rc, "surrogate forward: %s", sph_last_error(nullptr));
     CUDA_TRY(h, launch_surrogate_out(h->yout, h->feat, h->feat_lo, h->feat_hi, h->n_boid, h->f_scale, h->log_err_max,
@@ -1204,6 +1208,10 @@ int sph_get_fields(sph_handle* h, int field, void* out, int on_host, void* strea
     case SPH_FIELD_FALLBACK:
         bytes = (size_t)nb * 4;
         if (nb) CUDA_TRY(h, cudaMemcpyAsync(dst, h->bflag, bytes, cudaMemcpyDeviceToDevice, s));
+        break;
+    case SPH_FIELD_NSEG:
+        if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->nseg, n, (int*)dst);
+        bytes = (size_t)n * 4;
         break;
     case SPH_FIELD_NCAND:
         if (n) k_by_id<int><<<blocks, 256, 0, s>>>(h->pos, h->ncand, n, (int*)dst);

@@ -350,7 +350,7 @@ cudaError_t launch_slot_keys(const unsigned* start, int ncells, unsigned* slot_k
 
 // Hit segments the density pass keeps per fluid particle for the force
 // pass: at most SEG_CAP (first slot, 32-bit pair mask) entries each.
-constexpr int SEG_CAP = 64;
+constexpr int SEG_CAP = 128;
 
 // Multiprocessors of the current device (queried once per device).
 int sm_count();

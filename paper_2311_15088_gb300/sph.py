@@ -36,7 +36,7 @@ FIELDS = {
     "keys": (6, np.uint32, 1), "perm": (7, np.int32, 1), "cell_start": (8, np.uint32, 1),
     "fb": (9, np.float32, 4), "boid_keys": (10, np.uint32, 1), "boid_perm": (11, np.int32, 1),
     "boid_cell_start": (12, np.uint32, 1), "ncand": (13, np.int32, 1), "fallback": (14, np.int32, 1),
-    "obstacle_grid": (15, np.float32, 4), "att_vel": (16, np.float32, 4),
+    "obstacle_grid": (15, np.float32, 4), "att_vel": (16, np.float32, 4), "nseg": (17, np.int32, 1),
 }
 
 
@@ -284,7 +284,7 @@ def sph_destroy(h):
     _lib.sph_destroy(h)
 
 
-KINDS = ("keys", "scan", "scatter", "sort", "density", "forces", "boid_bin", "boid_rules", "lists")
+KINDS = ("keys", "scan", "scatter", "sort", "density", "forces", "boid_bin", "boid_rules", "lists", "features")
 
 
 def sph_profile_enable(h, max_passes: int):

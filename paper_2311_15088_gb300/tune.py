@@ -2,8 +2,8 @@
 
 The tuned knobs change no result bit (the per-particle arithmetic and its
 order do not depend on them): the threads per block of the density and
-force passes, and whether the force pass reuses the density pass's
-candidate bits.  For a scene (or batch) the tuner snapshots the state,
+force passes, and whether the force pass takes its pairs from the density
+pass's hit segments or tests the candidates again.  For a scene (or batch) the tuner snapshots the state,
 times a few steps of each candidate shape with CUDA events, restores the
 state, applies the fastest shape and caches the choice in a JSON file keyed
 by the workload's signature (particle, boid and cell counts).
@@ -13,7 +13,7 @@ from __future__ import annotations
 import json
 import os
 
-CANDIDATES = [(b, s) for b in (128, 256, 512) for s in (0, 1)]
+CANDIDATES = [(b, s) for b in (64, 128, 256, 512) for s in (0, 1)]
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_cache.json")
 
 
@@ -35,20 +35,20 @@ def autotune(scene, steps: int = 4, warmup: int = 1, cache: str | None = DEFAULT
              candidates=CANDIDATES, force: bool = False) -> dict:
     """Pick the fastest bit-neutral launch shape for ``scene`` and apply it.
 
-    Returns {"block", "use_stream", "ms_per_step": {shape: ms}, "cached"}.
+    Returns {"block", "use_segments", "ms_per_step": {shape: ms}, "cached"}.
     The scene's state is left exactly as it was."""
     torch = scene.torch
     key = signature(scene)
     table = _load(cache) if cache else {}
     if not force and key in table:
         best = table[key]
-        scene.set_tuning(best["block"], best["use_stream"])
+        scene.set_tuning(best["block"], best["use_segments"])
         return dict(best, cached=True)
     snapshot = [t.clone() for t in scene.get_state()]
     timings = {}
-    for block, use_stream in candidates:
+    for block, use_seg in candidates:
         scene.set_state(*snapshot)
-        scene.set_tuning(block, use_stream)
+        scene.set_tuning(block, use_seg)
         scene.step(warmup)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -56,12 +56,12 @@ def autotune(scene, steps: int = 4, warmup: int = 1, cache: str | None = DEFAULT
         scene.step(steps)
         e1.record()
         torch.cuda.synchronize(scene.device)
-        timings[f"{block}/{use_stream}"] = e0.elapsed_time(e1) / steps
+        timings[f"{block}/{use_seg}"] = e0.elapsed_time(e1) / steps
     best_key = min(timings, key=timings.get)
-    block, use_stream = (int(x) for x in best_key.split("/"))
+    block, use_seg = (int(x) for x in best_key.split("/"))
     scene.set_state(*snapshot)
-    scene.set_tuning(block, use_stream)
-    best = {"block": block, "use_stream": use_stream, "ms_per_step": timings}
+    scene.set_tuning(block, use_seg)
+    best = {"block": block, "use_segments": use_seg, "ms_per_step": timings}
     if cache:
         table = _load(cache)
         table[key] = best

@@ -97,21 +97,23 @@ def test_neighbor_lists_bit_exact(cell):
 @pytest.mark.parametrize("cell", [1.0, 0.5])
 def test_crowded_cells_sort_paths(cell):
     """Crowded cells take the block-sort path of the per-cell sort, and the
-    2,500-particle clump has more candidates per particle than the density
-    pass can record, so the force pass tests them again; order and sums must
-    still match."""
+    5,000-particle clump gives its particles more hit segments than the
+    density pass can store (128 of 32 slots), so the force pass tests their
+    candidates again; order and sums must still match."""
     rng = np.random.default_rng(5)
     p = scenes.default_params(mass=scenes.f32(0.001))
     h = p["h"]
     p["cell_size"] = scenes.f32(h * cell)
-    a = 0.5 + rng.uniform(0, 0.9 * h, size=(2500, 3))       # > 2,048 candidates each
+    a = 0.5 + rng.uniform(0, 0.9 * h, size=(5000, 3))       # > 4,096 candidates each
     b = 0.2 + rng.uniform(0, 0.4 * h, size=(100, 3))        # one crowded cell
     c = rng.uniform(0.05, 0.95, size=(3000, 3))             # sparse background
-    pos = np.zeros((5600, 4), np.float32)
+    pos = np.zeros((8100, 4), np.float32)
     pos[:, :3] = np.concatenate([a, b, c])
     sc = dict(fluid_pos=pos, fluid_vel=np.zeros_like(pos), boid_pos=np.zeros((0, 4), np.float32),
               boid_vel=np.zeros((0, 4), np.float32))
-    _check(p, sc)
+    s, _, _ = _check(p, sc)
+    nseg = s.field("nseg").cpu().numpy()
+    assert (nseg > 128).sum() > 1000 and (nseg <= 128).sum() > 1000
 
 
 def test_edge_cases_small_scenes():
