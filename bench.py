@@ -462,7 +462,7 @@ def run_batched(a, dev, flush):
         for sc, q in zip(scs, chosen["params"]):
             s1 = Scene(q, len(sc["fluid_pos"]), len(sc["boid_pos"]), device=dev)
             s1.set_state(sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])
-            s1.set_tuning(best["block"], best["use_segments"])
+            tune.apply(s1, best)
             loop.append(s1)
         for _ in range(max(a.warmup, 2)):
             for s1 in loop:
@@ -517,7 +517,7 @@ def run_batched(a, dev, flush):
         "loop": "each scene's own handle replaying its captured step (sph_graph_step), same kernels",
         "cell_size_over_h": frac,
         "ms_per_step_by_cell_size": {str(f): 1e3 * v["t"] / a.batch_steps for f, v in per_cell.items()},
-        "tuning": {"block": best["block"], "use_segments": best["use_segments"], "ms_per_step": best["ms_per_step"]},
+        "tuning": {k: best[k] for k in ("block", "use_segments", "pipe_tile", "pipe_block", "ms_per_step")},
         "roofline": {
             "alu": {"achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,

@@ -199,6 +199,34 @@ int sph_set_tuning(sph_handle* h, int block, int use_segments);
 int sph_set_diagnostics(sph_handle* h, int record);
 
 /*
+ * Both neighbour passes in one persistent launch (the batched step's
+ * pass over (scene, tile) work items; section "Experimental Results" tunes
+ * the threads per group of the paper's dispatches).  tile_slots > 0: one
+ * cooperative launch whose resident CTAs take tiles of tile_slots
+ * consecutive sorted slots (runs of cells, across the scenes) from an
+ * atomic queue for the density pass, meet at a grid barrier, then take the
+ * boids (a warp each: F_b) and the tiles again for the force pass; block:
+ * threads per CTA (128 or 256).  The barrier's wait is bounded (about 2^31
+ * SM clock cycles, a second): a CTA that gives up sets SPH_DEV_TIMEOUT and
+ * returns, leaving the step unfinished but the device usable.  Results are
+ * bit for bit those of the separate launches.  tile_slots = 0 (the
+ * default): separate launches.  The neighbour lists (sph_set_neighbor_lists)
+ * take the separate launches.  A captured step is captured again.
+ * Errors: SPH_ERR_ARG (tile_slots not 0 or a multiple of 32 in [32, 65536],
+ * block not 128 or 256).
+ */
+int sph_set_pipeline(sph_handle* h, int tile_slots, int block);
+
+/*
+ * Test hook of the pipeline's bounded wait: with cta >= 0 that CTA of later
+ * fused launches does not arrive at the grid barrier, so every CTA gives up
+ * at its limit and the step ends with SPH_DEV_TIMEOUT set (no fault, the
+ * context stays usable; the step's state is then unspecified: load a state
+ * again).  cta = -1 (the default) turns it off.  Errors: SPH_ERR_ARG.
+ */
+int sph_debug_barrier_skip(sph_handle* h, int cta);
+
+/*
  * Load the state: fluid_pos4 / fluid_vel4 hold n_fluid float4 (fluid order),
  * boid_pos4 / boid_vel4 hold n_boid float4 (boid order).  on_host = 1: host
  * buffers (copied on `stream`, which is synchronised before returning);
@@ -417,6 +445,7 @@ long long sph_launch_count(sph_handle* h);
 #define SPH_KIND_BOID_RULES 7
 #define SPH_KIND_LISTS      8  /* neighbour lists: offsets scan + fill (when set) */
 #define SPH_KIND_FEATURES   9  /* the surrogate's stencil features (sph_features, surrogate modes) */
+#define SPH_KIND_PIPELINE  10  /* both neighbour passes in one launch (sph_set_pipeline) */
 #define SPH_NUM_KINDS       9
 int sph_profile_enable(sph_handle* h, int max_passes);
 int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds);

@@ -40,6 +40,8 @@ struct sph_handle {
     int* nbr;
     float4* prec;             // the force pass's pair record of each sorted slot (2 float4)
     uint2* seg;               // hit segments of the density pass (SEG_CAP per particle)
+    unsigned* pipe_queue;     // the fused pipeline's work counters and barrier (3 words)
+    int skip_cta;             // test hook of the pipeline's barrier (-1: off)
     int* nseg;
     int* ncand;
     float4* acc;
@@ -329,6 +331,7 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->ab = cv.take<float2>(n);
     h->nbr = cv.take<int>(n);
     h->prec = cv.take<float4>(2 * n);
+    h->pipe_queue = cv.take<unsigned>(4);
     h->seg = cv.take<uint2>(n * (size_t)SEG_CAP);
     h->nseg = cv.take<int>(n);
     h->ncand = cv.take<int>(n);
@@ -540,6 +543,8 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
     h->nbcells = (int)Cb;
     h->tune.block = 256;
     h->tune.use_seg = 1;
+    h->tune.pipe_tile = 0;
+    h->tune.pipe_block = 256;
     return SPH_OK;
 }
 
@@ -583,6 +588,7 @@ int sph_batch_create(const sph_params* params, const int* n_fluid, const int* n_
         delete h;
         return rc;
     }
+    h->skip_cta = -1;
     size_t need = carve(h, (uintptr_t)workspace);
     if (ws_bytes < need) {
         free_tables(h);
@@ -627,6 +633,33 @@ int sph_set_tuning(sph_handle* h, int block, int use_segments)
         h->graph = nullptr;
     }
     drop_boid_graphs(h);
+    return SPH_OK;
+}
+
+int sph_set_pipeline(sph_handle* h, int tile_slots, int block)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (tile_slots != 0 && (tile_slots < 32 || tile_slots > 65536 || tile_slots % 32))
+        return fail(h, SPH_ERR_ARG, "tile_slots must be 0 or a multiple of 32 in [32, 65536]");
+    if (block != 128 && block != 256) return fail(h, SPH_ERR_ARG, "block must be 128 or 256");
+    h->tune.pipe_tile = tile_slots;
+    h->tune.pipe_block = block;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return SPH_OK;
+}
+
+int sph_debug_barrier_skip(sph_handle* h, int cta)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (cta < -1) return fail(h, SPH_ERR_ARG, "cta must be >= -1");
+    h->skip_cta = cta;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
     return SPH_OK;
 }
 
@@ -846,11 +879,10 @@ static int bin_state(sph_handle* h, cudaStream_t s, bool consume)
     return SPH_OK;
 }
 
-// Enqueue one step (keys must be ready or are computed first).
-static int enqueue_step(sph_handle* h, cudaStream_t s)
+// The density pass, the neighbour lists (when set) and the force pass as
+// separate launches.
+static int enqueue_neighbor_passes(sph_handle* h, cudaStream_t s)
 {
-    int rc = bin_state(h, s, true);
-    if (rc != SPH_OK) return rc;
     prof_begin(h, SPH_KIND_DENSITY, s);
     CUDA_TRY(h, launch_density(h->pos_s, h->vel_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->prec,
                                h->nbr, h->seg, h->nseg, h->ncand, nullptr, nullptr, h->err, s, &h->launches));
@@ -869,6 +901,27 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
                               h->diag ? h->infl : nullptr, h->pos, h->vel, h->key, h->rank, h->count, h->err, s,
                               &h->launches));
     prof_end(h, s);
+    return SPH_OK;
+}
+
+// Enqueue one step (keys must be ready or are computed first).
+static int enqueue_step(sph_handle* h, cudaStream_t s)
+{
+    int rc = bin_state(h, s, true);
+    if (rc != SPH_OK) return rc;
+    if (h->tune.pipe_tile > 0 && !h->list) {
+        // both neighbour passes in one cooperative launch
+        prof_begin(h, SPH_KIND_PIPELINE, s);
+        CUDA_TRY(h, launch_nbr_pipeline(h->pos_s, soa_of(h), h->vel_s, h->cell_start, h->sc, h->tune, h->rho, h->ab,
+                                        h->prec, h->nbr, h->seg, h->nseg, h->ncand, h->slot_of_boid, h->fb,
+                                        h->diag ? h->acc : nullptr, h->diag ? h->touched : nullptr,
+                                        h->diag ? h->infl : nullptr, h->pos, h->vel, h->key, h->rank, h->count,
+                                        h->pipe_queue, h->skip_cta, h->err, s, &h->launches));
+        prof_end(h, s);
+    } else {
+        int rc2 = enqueue_neighbor_passes(h, s);
+        if (rc2 != SPH_OK) return rc2;
+    }
     if (h->n_boid > 0) {
         prof_begin(h, SPH_KIND_BOID_BIN, s);
         CUDA_TRY(h, cudaMemsetAsync(h->bcount, 0, (size_t)h->nbcells * sizeof(unsigned), s));

@@ -372,6 +372,8 @@ __host__ __device__ inline size_t soa_stride(size_t n) { return (n + 1) & ~(size
 struct Tuning {
     int block;       // threads per block of density / forces (64 .. 512)
     int use_seg;     // 1: the density pass records hit segments and the force pass reads them
+    int pipe_tile;   // > 0: both neighbour passes in one cooperative launch, tiles of this many slots
+    int pipe_block;  // threads per block of that launch (128 or 256)
 };
 
 // Density, neighbour counts, candidates tested (ncand) and, with seg given
@@ -402,6 +404,17 @@ cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* ve
                           float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
                           unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
                           long long* launches);
+// Both neighbour passes in one cooperative launch (t.pipe_tile > 0):
+// density over tiles of sorted slots, a bounded grid barrier
+// (SPH_DEV_TIMEOUT if it gives up), then F_b of the boids and the force
+// pass; bit for bit launch_density + launch_forces.  queue: 3 device words.
+// skip_cta >= 0: test hook, that CTA does not arrive at the barrier.
+cudaError_t launch_nbr_pipeline(const float4* pos, const SoaPos& xyz, const float4* vel, const unsigned* start,
+                                const Scenes& sc, const Tuning& t, float* rho, float2* ab, float4* prec, int* nbr,
+                                uint2* seg, int* nseg, int* ncand, const int* slot_of_boid, float4* fb,
+                                float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
+                                unsigned* key, unsigned* rank, unsigned* count, unsigned* queue, int skip_cta,
+                                unsigned* err, cudaStream_t s, long long* launches);
 // Neighbour lists of every particle at off[i] (exclusive scan of the
 // density pass's counts), in walk order; lists ending beyond cap are
 // skipped and flagged SPH_DEV_LIST_OVERFLOW.

@@ -309,13 +309,32 @@ struct PairTerms {
     }
 };
 
+// Loads of what the density pass wrote (densities, (m/rho, p), pair
+// records, hit segments): through the read-only path when an earlier launch
+// wrote them (COH = false), or as coherent cached loads when the same launch
+// wrote them before a grid barrier and an acquire fence (COH = true, the
+// fused pipeline; the read-only path is not coherent with such writes).
+template <bool COH, class T>
+__device__ __forceinline__ T ldd(const T* p)
+{
+    if constexpr (COH) return __ldca(p);
+    else return __ldg(p);
+}
+
 // The 32-byte pair record of a particle, (x, y, z, p) and (v, +-m / rho),
 // in one 256-bit load (records are 32-byte aligned).
+template <bool COH>
 __device__ __forceinline__ void ld_rec(const float4* __restrict__ p, float4& a, float4& b)
 {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(p));
+    if constexpr (COH)
+        asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                     : "l"(p)
+                     : "memory");
+    else
+        asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+            : "l"(p));
 }
 
 // x_j - x_i, y_j - y_i as one packed addition of (-x_i, -y_i): the same
@@ -331,6 +350,7 @@ __device__ __forceinline__ float2 dxy_of(const float4& pj, float2 nxy)
 // candidates by flat index (lane l: candidates l, l + 32, ... in walk
 // order), each keeping its own sum, and a butterfly adds the 32 sums (a
 // fixed order).
+template <bool COH>
 __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __restrict__ pos,
                                              const float4* __restrict__ vel, const float* __restrict__ rho,
                                              const float2* __restrict__ ab, const unsigned* __restrict__ start,
@@ -342,7 +362,7 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
     const int nb_all = sc.nb_all;
     PairTerms T;
-    T.set(c, pos[i], vel[i], ab[i].y);
+    T.set(c, pos[i], vel[i], ldd<COH>(ab + i).y);
     const float2 nxy = make_float2(-T.pi.x, -T.pi.y);
     const float h2 = c.h2;
     float2 axy = make_float2(0.f, 0.f);
@@ -362,7 +382,7 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
             if (r2 < h2 && r2 != 0.0f && id_of(pj) >= nb_all) {
                 float2 fxy;
                 float fz;
-                T.add(dxy, dz, r2, __ldg(vel + j), __ldg(ab + j), fxy, fz);
+                T.add(dxy, dz, r2, __ldg(vel + j), ldd<COH>(ab + j), fxy, fz);
                 axy = __fadd2_rn(axy, fxy);
                 az = __fadd_rn(az, fz);
             }
@@ -376,44 +396,77 @@ __device__ __forceinline__ void boid_fb_warp(int b, int lane, const float4* __re
         az += __shfl_xor_sync(FULL, az, o);
     }
     if (lane == 0) {
-        const float inv_rho = 1.0f / rho[i];
+        const float inv_rho = 1.0f / ldd<COH>(rho + i);
         const float4 f = make_float4(ax * inv_rho, ay * inv_rho, az * inv_rho, 0.0f);
         fb[b] = make_float4(f.x, f.y, f.z, bmask ? 1.0f : 0.0f);
         if (acc) acc[i] = f;
     }
 }
 
-// The step's force pass.  The first boid_blocks blocks compute F_b, a warp
-// per boid (boid_fb_warp; F_b also goes to acc at the attached slot when
-// acc is given); they come first in the grid so that these latency-bound
-// warps run alongside the fluid blocks.  The remaining blocks (fluid_blocks
-// of them, possibly none) take a particle per thread: pair forces with
-// touched_by_boid and boid_influence, gravity, Euler-Cromer integration,
-// damped walls and the next step's cell keys.  A fluid particle takes its
-// pairs from (in this order of preference) the neighbour list, the density
-// pass's hit segments, or a walk that tests the candidates again; all three
-// visit the same pairs in the same order.  acc, touched and infl (the
-// diagnostic fields) are written only when given (acc, touched and infl
-// all given or all NULL); attached particles then record touched = 0 and
-// influence = 0 (attached pairs are excluded).
-__global__ void __launch_bounds__(512)
-k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ vel, const float* __restrict__ rho,
-         const float2* __restrict__ ab, const float4* __restrict__ prec, const unsigned* __restrict__ start,
-         const uint2* __restrict__ seg,
-         const int* __restrict__ nseg, Scenes sc, const unsigned* __restrict__ list,
-         const unsigned* __restrict__ list_off, unsigned list_cap, int boid_blocks,
-         const int* __restrict__ slot_of_boid, const int* __restrict__ bmask, float4* __restrict__ fb,
-         float4* __restrict__ acc, int* __restrict__ touched, float4* __restrict__ infl,
-         float4* __restrict__ pos_next, float4* __restrict__ vel_next, unsigned* __restrict__ key,
-         unsigned* __restrict__ rank, unsigned* __restrict__ count, unsigned* __restrict__ err)
+// The arguments of the force pass (k_forces and the fused pipeline).
+struct ForceArgs {
+    const float4* __restrict__ pos;
+    SoaPos xyz;
+    const float4* __restrict__ vel;
+    const float* rho;
+    const float2* ab;
+    const float4* prec;
+    const unsigned* __restrict__ start;
+    const uint2* seg;
+    const int* nseg;
+    Scenes sc;
+    const unsigned* __restrict__ list;
+    const unsigned* __restrict__ list_off;
+    unsigned list_cap;
+    const int* __restrict__ slot_of_boid;
+    const int* __restrict__ bmask;
+    float4* __restrict__ fb;
+    float4* __restrict__ acc;
+    int* __restrict__ touched;
+    float4* __restrict__ infl;
+    float4* __restrict__ pos_next;
+    float4* __restrict__ vel_next;
+    unsigned* __restrict__ key;
+    unsigned* __restrict__ rank;
+    unsigned* __restrict__ count;
+    unsigned* __restrict__ err;
+};
+
+// The force pass of sorted slot i (i >= n_all: an idle lane): pair forces
+// with touched_by_boid and boid_influence, gravity, Euler-Cromer
+// integration, damped walls and the next step's cell keys.  A fluid
+// particle takes its pairs from (in this order of preference) the
+// neighbour list, the density pass's hit segments, or a walk that tests the
+// candidates again; all three visit the same pairs in the same order.
+// acc, touched and infl (the diagnostic fields) are written only when given
+// (all three or none); attached particles then record touched = 0 and
+// influence = 0 (attached pairs are excluded).  Every lane of the warp
+// must call it (warp-aggregated counting).
+template <bool COH>
+__device__ __forceinline__ void force_particle(const ForceArgs& a, int i)
 {
-    if ((int)blockIdx.x < boid_blocks) {
-        const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-        if (b < sc.nb_all && !(bmask && !bmask[b]))  // uniform per warp
-            boid_fb_warp(b, threadIdx.x & 31, pos, vel, rho, ab, start, sc, slot_of_boid, bmask, fb, acc);
-        return;
-    }
-    const int i = (blockIdx.x - boid_blocks) * blockDim.x + threadIdx.x;
+    const float4* __restrict__ pos = a.pos;
+    const SoaPos& xyz = a.xyz;
+    const float4* __restrict__ vel = a.vel;
+    const float* rho = a.rho;
+    const float2* ab = a.ab;
+    const float4* prec = a.prec;
+    const unsigned* __restrict__ start = a.start;
+    const uint2* seg = a.seg;
+    const int* nseg = a.nseg;
+    const Scenes& sc = a.sc;
+    const unsigned* __restrict__ list = a.list;
+    const unsigned* __restrict__ list_off = a.list_off;
+    const unsigned list_cap = a.list_cap;
+    float4* __restrict__ acc = a.acc;
+    int* __restrict__ touched = a.touched;
+    float4* __restrict__ infl = a.infl;
+    float4* __restrict__ pos_next = a.pos_next;
+    float4* __restrict__ vel_next = a.vel_next;
+    unsigned* __restrict__ key = a.key;
+    unsigned* __restrict__ rank = a.rank;
+    unsigned* __restrict__ count = a.count;
+    unsigned* __restrict__ err = a.err;
     const bool active = i < sc.n_all;
     const int ii = active ? i : 0;
     const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)ii)];
@@ -429,14 +482,14 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
     bool clamped = false;
     if (fluid) {
         PairTerms T;
-        T.set(c, pi, __ldg(vel + i), __ldg(ab + i).y);
-        rho_i = __ldg(rho + i);
+        T.set(c, pi, __ldg(vel + i), ldd<COH>(ab + i).y);
+        rho_i = ldd<COH>(rho + i);
         const float2 nxy = make_float2(-pi.x, -pi.y);
         // one neighbour j (r2 < h2) from its record (one 32-byte load); the
         // particle itself and coincident particles (r2 = 0) add nothing
         auto pair = [&](unsigned j) {
             float4 q0, q1;
-            ld_rec(prec + 2 * (size_t)j, q0, q1);
+            ld_rec<COH>(prec + 2 * (size_t)j, q0, q1);
             const float2 dxy = dxy_of(q0, nxy);
             const float dz = __fsub_rn(q0.z, pi.z);
             const float r2 = pair_r2(dxy.x, dxy.y, dz);
@@ -458,7 +511,7 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
             o0 = __ldg(list_off + i);
             o1 = __ldg(list_off + i + 1);
         }
-        const int ns = seg ? __ldg(nseg + i) : SEG_CAP + 1;
+        const int ns = seg ? ldd<COH>(nseg + i) : SEG_CAP + 1;
         if (list && o1 <= list_cap) {
             // the neighbour list, in walk order (coincident particles skipped)
             for (unsigned k = o0; k < o1; ++k) {
@@ -470,12 +523,12 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
             // the density pass's hit segments: one pair per iteration, the
             // next segment fetched while the current pair is evaluated
             const uint2* __restrict__ mine = seg + (size_t)i * SEG_CAP;
-            uint2 cur = ns > 0 ? __ldg(mine) : make_uint2(0u, 0u);
+            uint2 cur = ns > 0 ? ldd<COH>(mine) : make_uint2(0u, 0u);
             int k = 1;
             while (cur.y) {
                 const unsigned j = cur.x + (unsigned)(__ffs(cur.y) - 1);
                 cur.y &= cur.y - 1u;
-                if (!cur.y && k < ns) cur = __ldg(mine + k++);
+                if (!cur.y && k < ns) cur = ldd<COH>(mine + k++);
                 pair(j);
             }
         } else {
@@ -573,6 +626,24 @@ k_forces(const float4* __restrict__ pos, SoaPos xyz, const float4* __restrict__ 
     if (__any_sync(FULL, clamped) && (threadIdx.x & 31) == 0) atomicOr(err, SPH_DEV_CLAMPED);
 }
 
+// The step's force pass.  The first boid_blocks blocks compute F_b, a warp
+// per boid (boid_fb_warp; F_b also goes to acc at the attached slot when
+// acc is given); they come first in the grid so that these latency-bound
+// warps run alongside the fluid blocks.  The remaining blocks (possibly
+// none) take a particle per thread (force_particle).
+__global__ void __launch_bounds__(512)
+k_forces(ForceArgs a, int boid_blocks)
+{
+    if ((int)blockIdx.x < boid_blocks) {
+        const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (b < a.sc.nb_all && !(a.bmask && !a.bmask[b]))  // uniform per warp
+            boid_fb_warp<false>(b, threadIdx.x & 31, a.pos, a.vel, a.rho, a.ab, a.start, a.sc, a.slot_of_boid,
+                                a.bmask, a.fb, a.acc);
+        return;
+    }
+    force_particle<false>(a, (blockIdx.x - boid_blocks) * blockDim.x + threadIdx.x);
+}
+
 cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* vel, const float* rho, const float2* ab,
                           const float4* prec, const unsigned* start, const uint2* seg, const int* nseg,
                           const Scenes& sc,
@@ -587,13 +658,152 @@ cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* ve
     const int boid_blocks = (sc.nb_all + warps - 1) / warps;
     const int fluid_blocks = fluid ? (sc.n_all + t.block - 1) / t.block : 0;
     if (boid_blocks + fluid_blocks == 0) return cudaSuccess;
-    k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(pos, xyz, vel, rho, ab, prec, start,
-                                                            t.use_seg ? seg : nullptr,
-                                                            nseg, sc, list, list_off, cap, boid_blocks, slot_of_boid,
-                                                            bmask, fb, acc, touched, infl, pos_next, vel_next, key,
-                                                            rank, count, err);
+    const ForceArgs a{pos, xyz, vel, rho, ab, prec, start, t.use_seg ? seg : nullptr, nseg, sc, list, list_off, cap,
+                      slot_of_boid, bmask, fb, acc, touched, infl, pos_next, vel_next, key, rank, count, err};
+    k_forces<<<boid_blocks + fluid_blocks, t.block, 0, s>>>(a, boid_blocks);
     ++*launches;
     return cudaGetLastError();
+}
+
+// ------------------------------------------------- fused neighbour pipeline
+
+// Both neighbour passes of every scene in one cooperative launch (the
+// batched step's persistent pass): all CTAs are resident and take work
+// items from two atomic queues.  Phase A: tiles of `tile` consecutive
+// sorted slots (a run of cells of one or more scenes; each particle is
+// independent), the density pass.  Then a grid barrier: every CTA arrives
+// and waits for the others, a bounded wait (about 2^31 SM clock cycles, a
+// second) after which it sets SPH_DEV_TIMEOUT and returns.  Phase B: groups
+// of boids (a warp per boid: F_b) first, then the tiles again: the force
+// pass.  queue[0], queue[1]: the phases' item counters, queue[2]: barrier
+// arrivals (zeroed before every launch).  skip_cta >= 0 is a test hook:
+// that CTA does not arrive, so the others give up at their limit.  Results
+// are bit for bit those of the two launches (same per-particle code).
+struct PipeArgs {
+    ForceArgs f;
+    float* rho;
+    float2* ab;
+    float4* prec;
+    int* nbr;
+    uint2* seg;
+    int* nseg;
+    int* ncand;
+    unsigned* queue;
+    int tile;
+    unsigned n_tiles, n_boid_items;
+    int skip_cta;
+};
+
+constexpr long long BARRIER_CYCLES = 1ll << 31;
+
+// Arrive (unless skip) and wait until `expected` CTAs have arrived, at most
+// BARRIER_CYCLES; false (and SPH_DEV_TIMEOUT) when the wait gave up.  The
+// fences order this CTA's writes before its arrival and the other CTAs'
+// writes before this CTA's later loads.
+__device__ __forceinline__ bool grid_barrier(unsigned* arrive, unsigned expected, bool skip, unsigned* err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (!skip) atomicAdd(arrive, 1u);
+        int ok = 1;
+        const long long t0 = clock64();
+        while (atomicAdd(arrive, 0u) < expected) {
+            if (clock64() - t0 > BARRIER_CYCLES) {
+                atomicOr(err, SPH_DEV_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(500);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    __threadfence();
+    return s_ok != 0;
+}
+
+template <bool SEG>
+__global__ void __launch_bounds__(256)
+k_nbr_pipeline(PipeArgs a)
+{
+    __shared__ unsigned s_item;
+    const Scenes& sc = a.f.sc;
+    const int n_all = sc.n_all;
+    for (;;) {  // phase A: density
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.queue[0], 1u);
+        __syncthreads();
+        const unsigned it = s_item;
+        __syncthreads();
+        if (it >= a.n_tiles) break;
+        const int base = (int)it * a.tile, end = min(base + a.tile, n_all);
+        for (int i = base + (int)threadIdx.x; i < end; i += blockDim.x)
+            density_at<SEG>(i, a.f.pos, a.f.vel, a.f.xyz, a.f.start, sc, a.rho, a.ab, a.prec, a.nbr, a.seg, a.nseg,
+                            a.ncand, a.f.err);
+    }
+    if (!grid_barrier(a.queue + 2, gridDim.x, (int)blockIdx.x == a.skip_cta, a.f.err)) return;
+    const int warps = blockDim.x >> 5;
+    for (;;) {  // phase B: F_b of the boids, then the forces
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.queue[1], 1u);
+        __syncthreads();
+        const unsigned it = s_item;
+        __syncthreads();
+        if (it >= a.n_boid_items + a.n_tiles) break;
+        if (it < a.n_boid_items) {
+            const int b = (int)it * warps + (int)(threadIdx.x >> 5);
+            if (b < sc.nb_all)  // uniform per warp
+                boid_fb_warp<true>(b, threadIdx.x & 31, a.f.pos, a.f.vel, a.f.rho, a.f.ab, a.f.start, sc,
+                                   a.f.slot_of_boid, nullptr, a.f.fb, a.f.acc);
+        } else {
+            const int base = (int)(it - a.n_boid_items) * a.tile, end = min(base + a.tile, n_all);
+            for (int o = 0; o < a.tile; o += blockDim.x) {  // every lane takes part
+                const int i = base + o + (int)threadIdx.x;
+                force_particle<true>(a.f, i < end ? i : n_all);
+            }
+        }
+    }
+}
+
+cudaError_t launch_nbr_pipeline(const float4* pos, const SoaPos& xyz, const float4* vel, const unsigned* start,
+                                const Scenes& sc, const Tuning& t, float* rho, float2* ab, float4* prec, int* nbr,
+                                uint2* seg, int* nseg, int* ncand, const int* slot_of_boid, float4* fb,
+                                float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
+                                unsigned* key, unsigned* rank, unsigned* count, unsigned* queue, int skip_cta,
+                                unsigned* err, cudaStream_t s, long long* launches)
+{
+    if (sc.n_all <= 0) return cudaSuccess;
+    const int block = t.pipe_block;
+    const int tile = t.pipe_tile;
+    const bool use_seg = t.use_seg != 0;
+    const ForceArgs f{pos, xyz, vel, rho, ab, prec, start, use_seg ? seg : nullptr, nseg, sc, nullptr, nullptr, 0u,
+                      slot_of_boid, nullptr, fb, acc, touched, infl, pos_next, vel_next, key, rank, count, err};
+    const unsigned n_tiles = (unsigned)((sc.n_all + tile - 1) / tile);
+    const unsigned warps = (unsigned)(block / 32);
+    const unsigned n_boid_items = ((unsigned)sc.nb_all + warps - 1) / warps;
+    const PipeArgs a{f, rho, ab, prec, nbr, seg, nseg, ncand, queue, tile, n_tiles, n_boid_items, skip_cta};
+    void* fn = use_seg ? (void*)k_nbr_pipeline<true> : (void*)k_nbr_pipeline<false>;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const unsigned items = n_tiles + n_boid_items;
+    unsigned grid = (unsigned)per_sm * (unsigned)sm_count();  // every CTA resident
+    if (grid > items) grid = items;
+    e = cudaMemsetAsync(queue, 0, 3 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = use_seg ? cudaLaunchKernelEx(&cfg, k_nbr_pipeline<true>, a) : cudaLaunchKernelEx(&cfg, k_nbr_pipeline<false>, a);
+    ++*launches;
+    return e;
 }
 
 // ---------------------------------------------------------- pair lists

@@ -80,6 +80,8 @@ _sig = {
     "sph_batch_create": (_i, [_P, _vp, _vp, _i, _vp, _sz, ctypes.POINTER(_vp)]),
     "sph_set_tuning": (_i, [_vp, _i, _i]),
     "sph_set_diagnostics": (_i, [_vp, _i]),
+    "sph_set_pipeline": (_i, [_vp, _i, _i]),
+    "sph_debug_barrier_skip": (_i, [_vp, _i]),
     "sph_set_neighbor_lists": (_i, [_vp, _vp, ctypes.c_size_t]),
     "sph_debug_bucket_neighbors": (_i, [_vp, _vp, ctypes.c_size_t, _i, _vp, _vp, _vp]),
     "sph_graph_step": (_i, [_vp, _i, _vp]),
@@ -206,6 +208,14 @@ def sph_set_diagnostics(h, record: int):
     _check(_lib.sph_set_diagnostics(h, record), h)
 
 
+def sph_set_pipeline(h, tile_slots: int, block: int = 256):
+    _check(_lib.sph_set_pipeline(h, tile_slots, block), h)
+
+
+def sph_debug_barrier_skip(h, cta: int):
+    _check(_lib.sph_debug_barrier_skip(h, cta), h)
+
+
 def sph_set_neighbor_lists(h, pair_buffer_ptr, nbytes: int):
     _check(_lib.sph_set_neighbor_lists(h, pair_buffer_ptr, nbytes), h)
 
@@ -284,7 +294,8 @@ def sph_destroy(h):
     _lib.sph_destroy(h)
 
 
-KINDS = ("keys", "scan", "scatter", "sort", "density", "forces", "boid_bin", "boid_rules", "lists", "features")
+KINDS = ("keys", "scan", "scatter", "sort", "density", "forces", "boid_bin", "boid_rules", "lists", "features",
+         "pipeline")
 
 
 def sph_profile_enable(h, max_passes: int):
@@ -567,6 +578,7 @@ class Scene:
         self.ncells = int(sum(d[0] * d[1] * d[2] for d in dims))
         self.nbcells = int(sum(d[0] * d[1] * d[2] for d in bdims))
         self.tuning = (256, 1)  # the library's default (block, use_segments)
+        self.pipeline = (0, 256)  # separate neighbour-pass launches
         self.diagnostics = False
         if diagnostics:
             self.set_diagnostics(True)
@@ -641,6 +653,12 @@ class Scene:
     def set_tuning(self, block: int, use_segments: int):
         sph_set_tuning(self.handle, block, use_segments)
         self.tuning = (int(block), int(use_segments))
+
+    def set_pipeline(self, tile_slots: int, block: int = 256):
+        """Both neighbour passes in one persistent launch over tiles of
+        tile_slots sorted slots (0: separate launches)."""
+        sph_set_pipeline(self.handle, tile_slots, block)
+        self.pipeline = (int(tile_slots), int(block))
 
     def set_diagnostics(self, record: bool):
         """Record acc, touched and influence in later steps (off by default)."""

@@ -125,15 +125,20 @@ def test_graph_replay_equals_step():
     assert b.launches > a.launches * 0.5
 
 
-@pytest.mark.parametrize("block,use_segments", [(64, 0), (128, 1), (256, 0), (512, 0), (512, 1)])
-def test_launch_shape_changes_no_bit(block, use_segments):
-    """Block size and the source of the force pass's pairs (hit segments or
-    a second candidate test) change no bit of the state or of the fields."""
+@pytest.mark.parametrize("block,use_segments,tile,pblock",
+                         [(64, 0, 0, 256), (128, 1, 0, 256), (256, 0, 0, 256), (512, 0, 0, 256), (512, 1, 0, 256),
+                          (256, 1, 32, 128), (256, 1, 512, 256), (256, 0, 2048, 256), (256, 1, 65536, 128)])
+def test_launch_shape_changes_no_bit(block, use_segments, tile, pblock):
+    """Block size, the source of the force pass's pairs (hit segments or a
+    second candidate test) and the fused persistent pipeline (both passes in
+    one cooperative launch over work tiles of any size) change no bit of the
+    state or of the fields."""
     scs = _small_batch()
     ref = _batch(scs)
     ref.step(6)
     t = _batch(scs)
     t.set_tuning(block, use_segments)
+    t.set_pipeline(tile, pblock)
     t.step(6)
     for x, y in zip(ref.get_state(), t.get_state()):
         assert torch.equal(x, y)
@@ -195,3 +200,46 @@ def test_rank_shares_step_like_the_scenes_alone():
         assert owner[k] == 0
         for x, y in zip(out[k], want):
             assert np.array_equal(x[:, :3], y[:, :3])
+
+
+def test_pipeline_graph_replay_equals_step():
+    """The fused pipeline (a cooperative launch) captured in the step's CUDA
+    graph and replayed gives the separate launches' bits."""
+    scs = _small_batch()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a = _batch(scs)
+        a.step(8)
+        b = _batch(scs)
+        b.set_pipeline(1024, 256)
+        b.graph_step(8)
+        sa = [t.cpu().numpy() for t in a.get_state()]
+        sb = [t.cpu().numpy() for t in b.get_state()]
+    torch.cuda.synchronize()
+    for x, y in zip(sa, sb):
+        assert np.array_equal(x, y)
+
+
+def test_pipeline_barrier_wait_gives_up():
+    """A bounded wait that runs out: the test hook keeps CTA 0 from arriving
+    at the pipeline's grid barrier, so every CTA gives up after its limit
+    (about a second), SPH_DEV_TIMEOUT is set and the step returns.  No fault:
+    the context stays usable, and after the hook is cleared and a state is
+    loaded again the scene steps bit for bit like a fresh one."""
+    scs = _small_batch()
+    ref = _batch(scs)
+    ref.step(3)
+    b = _batch(scs)
+    b.set_pipeline(256, 256)
+    b.step(1)
+    assert b.status() & sph.SPH_DEV_TIMEOUT == 0
+    sph.sph_debug_barrier_skip(b.handle, 0)
+    b.step(1)
+    assert b.status() & sph.SPH_DEV_TIMEOUT
+    sph.sph_debug_barrier_skip(b.handle, -1)
+    b.clear_status()
+    b.set_state(_cat(scs, "fluid_pos"), _cat(scs, "fluid_vel"), _cat(scs, "boid_pos"), _cat(scs, "boid_vel"))
+    b.step(3)
+    assert b.status() == 0
+    for x, y in zip(ref.get_state(), b.get_state()):
+        assert torch.equal(x, y)
