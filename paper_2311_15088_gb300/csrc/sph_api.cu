@@ -26,6 +26,8 @@ struct sph_handle {
     Tuning tune;
     int n_fluid, n_boid, n;   // totals over the scenes
     int ncells, nbcells;      // totals over the scenes
+    int nfcells;              // cells of the surrogate's feature grids
+    int4* fgrid;              // their integer sums (count, velocity in 2^-16 fixed point)
     // state (storage order) and the sorted scratch copy
     float4 *pos, *vel, *pos_s, *vel_s;
     float* soa;               // pos_s as three float arrays (x, y, z), soa_stride(n) each
@@ -286,6 +288,8 @@ static void make_const(const sph_params* p, int n_fluid, int n_boid, StepConst* 
     c->sph_dt = (float)((double)p->sph_factor * (double)p->dt);
     c->sph_factor = p->sph_factor;
     c->literal = p->coupling_mode == SPH_COUPLE_LITERAL;
+    for (int a = 0; a < 3; ++a)  // the highest feature cell of a position in the box, plus margins
+        c->fdim[a] = (int)floorf((p->box_max[a] - p->box_min[a]) * c->inv_h) + 1 + 4;
     c->v_min = p->v_min;
     c->v_max = p->v_max;
     c->edge_turn = p->edge_turn;
@@ -332,6 +336,7 @@ static size_t carve(sph_handle* h, uintptr_t base)
     h->nbr = cv.take<int>(n);
     h->prec = cv.take<float4>(2 * n);
     h->pipe_queue = cv.take<unsigned>(4);
+    h->fgrid = cv.take<int4>((size_t)h->nfcells);
     h->seg = cv.take<uint2>(n * (size_t)SEG_CAP);
     h->nseg = cv.take<int>(n);
     h->ncand = cv.take<int>(n);
@@ -510,7 +515,7 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
     h->h_pbase = new (std::nothrow) unsigned[S + 1];
     h->h_bbase = new (std::nothrow) unsigned[S + 1];
     if (!h->params || !h->consts || !h->h_pbase || !h->h_bbase) return fail(nullptr, SPH_ERR_ARG, "out of host memory");
-    long long n = 0, nb = 0, nf = 0, C = 0, Cb = 0;
+    long long n = 0, nb = 0, nf = 0, C = 0, Cb = 0, Cf = 0;
     h->stats_chunks = 1;
     for (int k = 0; k < S; ++k) {
         int rc = validate(&params[k], n_fluid[k], n_boid[k]);
@@ -523,6 +528,8 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
         h->consts[k].b_base = (int)nb;
         h->consts[k].c_base = (int)C;
         h->consts[k].cb_base = (int)Cb;
+        h->consts[k].fc_base = (int)Cf;
+        Cf += (long long)h->consts[k].fdim[0] * h->consts[k].fdim[1] * h->consts[k].fdim[2];
         n += (long long)n_fluid[k] + n_boid[k];
         nb += n_boid[k];
         nf += n_fluid[k];
@@ -530,7 +537,7 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
         Cb += h->consts[k].gb.ncells;
         const long long span = std::max((long long)n_fluid[k] + n_boid[k], (long long)h->consts[k].g.ncells);
         h->stats_chunks = std::max(h->stats_chunks, (int)((span + STATS_CHUNK - 1) / STATS_CHUNK));
-        if (n > 2147483647LL || C > 2147483646LL || Cb > 2147483646LL)
+        if (n > 2147483647LL || C > 2147483646LL || Cb > 2147483646LL || Cf > 2147483646LL)
             return fail(nullptr, SPH_ERR_OVERFLOW, "the batch exceeds 2^31 particles or cells");
     }
     h->h_pbase[S] = (unsigned)n;
@@ -541,6 +548,7 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
     h->n_fluid = (int)nf;
     h->ncells = (int)C;
     h->nbcells = (int)Cb;
+    h->nfcells = (int)Cf;
     h->tune.block = 256;
     h->tune.use_seg = 1;
     h->tune.pipe_tile = 0;
@@ -1044,7 +1052,8 @@ int sph_features(sph_handle* h, void* x_out, void* stream)
     int rc = bin_state(h, s, false);
     if (rc != SPH_OK) return rc;
     prof_begin(h, SPH_KIND_FEATURES, s);
-    CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, x_out, s, &h->launches));
+    CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, h->fgrid, h->nfcells,
+                                x_out, s, &h->launches));
     prof_end(h, s);
     h->has_step = false;
     return SPH_OK;
@@ -1090,8 +1099,8 @@ static int enqueue_boid_forces(sph_handle* h, int mode, float* out_f4, cudaStrea
     if (mode == SPH_BOID_EXACT_LOCAL) return exact_local(h, nullptr, out, s);
     // surrogate: features -> network -> forces (+ exact path for flagged boids)
     prof_begin(h, SPH_KIND_FEATURES, s);
-    CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, h->feat, s,
-                                &h->launches));
+    CUDA_TRY(h, launch_features(h->pos_s, h->vel_s, h->cell_start, h->bpos, h->bvel, h->sc, h->fgrid, h->nfcells,
+                                h->feat, s, &h->launches));
     prof_end(h, s);
     rc = sph_mlp_forward(h->mlp, h->feat, h->nb_pad, h->yout, s);
     if (rc != SPH_OK) return fail(h, rc, "surrogate forward: %s", sph_last_error(nullptr));

@@ -30,135 +30,97 @@
 
 namespace sphk {
 
-// One block of FT = 256 threads per boid, every sum in a fixed order:
-//   1. the rows (y, z) of particle-grid cells under the stencil's box (one
-//      cell of margin) get their slot ranges loaded in parallel, and a block
-//      scan of their lengths numbers the box's particles 0 .. total-1;
-//   2. thread t takes particles t, t + FT, ... (four at a time, their loads
-//      issued together): a particle of a stencil
-//      cell adds 1 and its velocity in 2^-16 fixed point to the cell's
-//      shared integer sums (integer sums do not depend on the order; they
-//      hold while a cell's mean speed stays below 2^15 / count m/s, beyond
-//      any flow of these scenes), and a particle within h of the boid adds
-//      its kernel moments to the thread's own sums;
-//   3. the moments are reduced by a butterfly in each warp, then warp by warp.
-constexpr int FT = 256;
-constexpr int FROWS = 512;  // rows of the box (d >= h/4: at most 19 x 19 with margins)
+// Stencil features in two launches:
+//   1. k_feature_grid (K8): every fluid particle adds 1 and its velocity (in
+//      2^-16 fixed point) to the integer sums of its feature cell, kept for
+//      the box plus two cells of margin on every side (a boid in the box
+//      has its whole stencil there; integer sums do not depend on the
+//      order, and they hold while a cell's mean speed stays below
+//      2^15 / count m/s, beyond any flow of these scenes);
+//   2. k_features (K9): a warp per boid reads its 4 x 4 x 4 cells from the
+//      grid (cells outside it are zeros) and walks the particle grid around
+//      it for the kernel moments (WarpRows: the lanes take the walk's
+//      candidates by flat index, each keeping its own sums, then a
+//      butterfly adds the 32 sums in a fixed order).
 constexpr float VFIX = 65536.0f;
+constexpr int FW = 8;  // warps per block of k_features
 
-__global__ void __launch_bounds__(FT)
+__global__ void __launch_bounds__(256)
+k_feature_grid(const float4* __restrict__ pos, const float4* __restrict__ vel, Scenes sc, int4* __restrict__ grid)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= sc.n_all) return;
+    const float4 p = pos[i];
+    if (id_of(p) < sc.nb_all) return;  // fluid particles only
+    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+    // feature cell floor((x - m) inv_h), shifted by the two-cell margin
+    const float fx = floorf(__fmul_rn(__fsub_rn(p.x, c.g.minf[0]), c.inv_h)) + 2.0f;
+    const float fy = floorf(__fmul_rn(__fsub_rn(p.y, c.g.minf[1]), c.inv_h)) + 2.0f;
+    const float fz = floorf(__fmul_rn(__fsub_rn(p.z, c.g.minf[2]), c.inv_h)) + 2.0f;
+    if (!(fx >= 0.f && fx < (float)c.fdim[0] && fy >= 0.f && fy < (float)c.fdim[1] && fz >= 0.f &&
+          fz < (float)c.fdim[2]))
+        return;  // more than two cells outside the box (no boid of the box sees it)
+    const int q = c.fc_base + (int)fx + c.fdim[0] * ((int)fy + c.fdim[1] * (int)fz);
+    const float4 v = __ldg(vel + i);
+    atomicAdd(&grid[q].x, 1);
+    atomicAdd(&grid[q].y, __float2int_rn(v.x * VFIX));
+    atomicAdd(&grid[q].z, __float2int_rn(v.y * VFIX));
+    atomicAdd(&grid[q].w, __float2int_rn(v.z * VFIX));
+}
+
+__global__ void __launch_bounds__(FW * 32)
 k_features(const float4* __restrict__ pos, const float4* __restrict__ vel, const unsigned* __restrict__ start,
            const float4* __restrict__ bpos, const float4* __restrict__ bvel, Scenes sc,
-           __nv_bfloat16* __restrict__ x)
+           const int4* __restrict__ grid, __nv_bfloat16* __restrict__ x)
 {
-    __shared__ unsigned row_s0[FROWS];
-    __shared__ unsigned row_pre[FROWS + 1];
-    __shared__ int cnt[64], vsum[64][3];
-    __shared__ float red[FT / 32][8];
-    const int b = blockIdx.x;
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * FW + (int)(threadIdx.x >> 5);
+    if (b >= sc.nb_all) return;  // the whole warp
     const StepConst& c = sc.c[scene_of(sc.bbase, sc.S, (unsigned)b)];
     const float4 pb = bpos[b], vb = bvel[b];
     const float p[3] = {pb.x, pb.y, pb.z};
     float c0[3], centre_off[3];
-    int lo[3], hi[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float t = __fmul_rn(__fsub_rn(p[a], c.g.minf[a]), c.inv_h);
         c0[a] = floorf(__fsub_rn(t, 1.5f));
         centre_off[a] = __fsub_rn(__fsub_rn(t, c0[a]), 2.0f);
-        // particle-grid cells under [c0 h, (c0 + 4) h) (relative to m), +-1 cell
-        const float e0 = __fmul_rn(__fmul_rn(c0[a], c.h), c.g.inv_d);
-        const float e1 = __fmul_rn(__fmul_rn(c0[a] + 4.0f, c.h), c.g.inv_d);
-        lo[a] = (int)fmaxf(floorf(e0) - 1.0f, 0.0f);
-        hi[a] = (int)fminf(floorf(e1) + 1.0f, (float)(c.g.dim[a] - 1));
     }
-    const int ny = hi[1] - lo[1] + 1, nz = hi[2] - lo[2] + 1;
-    int nrows = (lo[0] <= hi[0] && ny > 0 && nz > 0) ? ny * nz : 0;
-    nrows = nrows < FROWS ? nrows : FROWS;  // a box this large only arises for far-off boids
-    const unsigned* cstart = start + c.c_base;
-    // ---- 1: row ranges and their prefix sums (rows past nrows count 0)
-    const int nscan = (nrows + 31) & ~31;
-    for (int r = tid; r < nscan; r += FT) {
-        unsigned len = 0;
-        if (r < nrows) {
-            const int y = lo[1] + r % ny, z = lo[2] + r / ny;
-            const unsigned rk = (unsigned)c.g.dim[0] * ((unsigned)y + (unsigned)c.g.dim[1] * (unsigned)z);
-            const unsigned s0 = __ldg(cstart + rk + lo[0]);
-            row_s0[r] = s0;
-            len = __ldg(cstart + rk + hi[0] + 1) - s0;
-        }
-        row_pre[r + 1] = len;
-    }
-    if (tid == 0) row_pre[0] = 0;
-    if (tid < 64) {
-        cnt[tid] = 0;
-        vsum[tid][0] = vsum[tid][1] = vsum[tid][2] = 0;
-    }
-    __syncthreads();
-    if (tid < 32) {  // inclusive scan of row_pre[1 .. FROWS] by one warp
-        unsigned carry = 0;
-        for (int base = 1; base <= nscan; base += 32) {
-            unsigned v = row_pre[base + tid];
+    __nv_bfloat16* row = x + (size_t)b * SPH_MLP_IN;
+    // ---- the 64 stencil cells from the grid (two per lane)
+    const float dens_unit = c.mass / (c.h * c.h * c.h * c.rho0);
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned u = __shfl_up_sync(FULL, v, o);
-                if (tid >= o) v += u;
-            }
-            row_pre[base + tid] = v + carry;
-            carry += __shfl_sync(FULL, v, 31);
-        }
+    for (int k = 0; k < 2; ++k) {
+        const int q = lane + 32 * k;
+        const float gx = c0[0] + (float)(q & 3) + 2.0f, gy = c0[1] + (float)((q >> 2) & 3) + 2.0f,
+                    gz = c0[2] + (float)(q >> 4) + 2.0f;
+        int4 v = make_int4(0, 0, 0, 0);
+        if (gx >= 0.f && gx < (float)c.fdim[0] && gy >= 0.f && gy < (float)c.fdim[1] && gz >= 0.f &&
+            gz < (float)c.fdim[2])
+            v = __ldg(grid + c.fc_base + (int)gx + c.fdim[0] * ((int)gy + c.fdim[1] * (int)gz));
+        const float inv = v.x ? 1.0f / ((float)v.x * VFIX) : 0.0f;
+        row[4 * q + 0] = __float2bfloat16_rn((float)v.x * dens_unit);
+        row[4 * q + 1] = __float2bfloat16_rn((float)v.y * inv);
+        row[4 * q + 2] = __float2bfloat16_rn((float)v.z * inv);
+        row[4 * q + 3] = __float2bfloat16_rn((float)v.w * inv);
     }
-    __syncthreads();
-    const unsigned total = row_pre[nrows];
+    // ---- kernel moments over the fluid particles within h of the boid
     const float h2 = c.h2;
     float mo[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // poly6, S0, S1 (3), S2 (3)
-    // ---- 2: every particle of the box once, four per thread at a time (the
-    // positions and velocities of the four are loaded before any is used)
-    constexpr int U = 4;
-    for (unsigned g0 = tid; g0 < total; g0 += FT * U) {
-        unsigned js[U];
-        float4 ps[U], vs[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const unsigned g = g0 + (unsigned)(u * FT);
-            js[u] = 0xffffffffu;
-            if (g < total) {
-                int lo_r = 0, hi_r = nrows;  // row r with row_pre[r] <= g < row_pre[r + 1]
-                while (hi_r - lo_r > 1) {
-                    const int mid = (lo_r + hi_r) >> 1;
-                    if (row_pre[mid] <= g) lo_r = mid;
-                    else hi_r = mid;
-                }
-                js[u] = row_s0[lo_r] + (g - row_pre[lo_r]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (js[u] != 0xffffffffu) {
-                ps[u] = __ldg(pos + js[u]);
-                vs[u] = __ldg(vel + js[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (js[u] == 0xffffffffu) continue;
-            const float4 pj = ps[u], vj = vs[u];
+    WarpRows rows(c.g, c.wg, start + c.c_base, pb.x, pb.y, pb.z);
+    for (int bt = 0; 32 * bt < rows.nrows; ++bt) {
+        rows.batch(bt);
+        const unsigned total = rows.flatten();
+        for (unsigned k0 = 0; k0 < total; k0 += 32) {
+            const unsigned k = k0 + (unsigned)lane;
+            const unsigned j = rows.slot(k < total ? k : total - 1);
+            if (k >= total) continue;
+            const float4 pj = __ldg(pos + j);
             if (id_of(pj) < sc.nb_all) continue;  // fluid particles only
-            const float fx = floorf(__fmul_rn(__fsub_rn(pj.x, c.g.minf[0]), c.inv_h)) - c0[0];
-            const float fy = floorf(__fmul_rn(__fsub_rn(pj.y, c.g.minf[1]), c.inv_h)) - c0[1];
-            const float fz = floorf(__fmul_rn(__fsub_rn(pj.z, c.g.minf[2]), c.inv_h)) - c0[2];
-            const bool in = fx >= 0.f && fx < 4.f && fy >= 0.f && fy < 4.f && fz >= 0.f && fz < 4.f;
-            if (in) {
-                const int q = (int)fx + 4 * ((int)fy + 4 * (int)fz);
-                atomicAdd(&cnt[q], 1);
-                atomicAdd(&vsum[q][0], __float2int_rn(vj.x * VFIX));
-                atomicAdd(&vsum[q][1], __float2int_rn(vj.y * VFIX));
-                atomicAdd(&vsum[q][2], __float2int_rn(vj.z * VFIX));
-            }
             const float dx = __fsub_rn(pj.x, pb.x), dy = __fsub_rn(pj.y, pb.y), dz = __fsub_rn(pj.z, pb.z);
             const float r2 = pair_r2(dx, dy, dz);
             if (r2 < h2) {
+                const float4 vj = __ldg(vel + j);
                 const float u2 = h2 - r2;
                 mo[0] += u2 * u2 * u2;
                 const float rr = sqrtf(r2);
@@ -176,50 +138,36 @@ k_features(const float4* __restrict__ pos, const float4* __restrict__ vel, const
             }
         }
     }
-    // ---- 3: moments
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mo[k] += __shfl_xor_sync(FULL, mo[k], o);
     }
-    if ((tid & 31) == 0) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) red[tid >> 5][k] = mo[k];
-    }
-    __syncthreads();
-    __nv_bfloat16* row = x + (size_t)b * SPH_MLP_IN;
-    if (tid < 64) {
-        const int n = cnt[tid];
-        const float dens = (float)n * (c.mass / (c.h * c.h * c.h * c.rho0));
-        const float inv = n ? 1.0f / ((float)n * VFIX) : 0.0f;
-        row[4 * tid + 0] = __float2bfloat16_rn(dens);
-        row[4 * tid + 1] = __float2bfloat16_rn((float)vsum[tid][0] * inv);
-        row[4 * tid + 2] = __float2bfloat16_rn((float)vsum[tid][1] * inv);
-        row[4 * tid + 3] = __float2bfloat16_rn((float)vsum[tid][2] * inv);
-    } else if (tid < 64 + (SPH_MLP_IN - 256)) {
-        const int m = tid - 64;
-        float tot[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            float acc = 0.0f;
-            for (int w = 0; w < FT / 32; ++w) acc += red[w][k];
-            tot[k] = acc;
-        }
+    if (lane < SPH_MLP_IN - 256) {
+        const int m = lane;
         const float kn = c.mass / (c.rho0 * c.h * c.h * c.h);
         float v = 0.0f;
         if (m < 3) v = m == 0 ? vb.x : (m == 1 ? vb.y : vb.z);
         else if (m < 6) v = centre_off[m - 3];
-        else if (m == 6) v = c.mC6 * (tot[0] + h2 * h2 * h2) / c.rho0;
-        else if (m < 14) v = kn * tot[m - 6];
+        else if (m == 6) v = c.mC6 * (mo[0] + h2 * h2 * h2) / c.rho0;
+        else if (m < 14) v = kn * mo[m - 6];
         row[256 + m] = __float2bfloat16_rn(v);
     }
 }
 
 cudaError_t launch_features(const float4* pos, const float4* vel, const unsigned* start, const float4* bpos,
-                            const float4* bvel, const Scenes& sc, void* x, cudaStream_t s, long long* launches)
+                            const float4* bvel, const Scenes& sc, int4* grid, int nfcells, void* x, cudaStream_t s,
+                            long long* launches)
 {
     if (sc.nb_all <= 0) return cudaSuccess;
-    k_features<<<sc.nb_all, FT, 0, s>>>(pos, vel, start, bpos, bvel, sc, (__nv_bfloat16*)x);
+    cudaError_t e = cudaMemsetAsync(grid, 0, (size_t)nfcells * sizeof(int4), s);
+    if (e != cudaSuccess) return e;
+    if (sc.n_all > 0) {
+        k_feature_grid<<<(sc.n_all + 255) / 256, 256, 0, s>>>(pos, vel, sc, grid);
+        ++*launches;
+    }
+    k_features<<<(sc.nb_all + FW - 1) / FW, FW * 32, 0, s>>>(pos, vel, start, bpos, bvel, sc, grid,
+                                                              (__nv_bfloat16*)x);
     ++*launches;
     return cudaGetLastError();
 }

@@ -61,7 +61,11 @@ struct StepConst {
     float rs, rs2, rv2; // boid radii (separation) and squared radii
     float w_sep, w_align, w_coh, sph_dt, v_min, v_max, edge_turn;
     float sph_factor;
-    int literal;        // SPH_COUPLE_LITERAL: the attached particles keep and integrate their own velocity
+    int literal;
+    // the surrogate's feature grid (cells of h anchored at box_min, cell
+    // floor((x - m) inv_h), two cells of margin on every side): dims, and
+    // the scene's first cell in the handle's feature grid
+    int fdim[3], fc_base;        // SPH_COUPLE_LITERAL: the attached particles keep and integrate their own velocity
     // obstacle avoidance (sph_set_obstacles): off while obst_on == 0
     int obst_on, obst_reach;  // reach: boid-grid cells searched each way
     float w_obst, obst_near;  // gain, weight of cells in the protection range
@@ -446,9 +450,12 @@ cudaError_t launch_boid_rules(const float4* bpos_s, const float4* bvel_s, const 
                               unsigned* key, unsigned* rank, unsigned* count, unsigned* err,
                               cudaStream_t s, long long* launches);
 
-// Surrogate inputs and outputs (sph_features.cu).
+// Surrogate inputs and outputs (sph_features.cu).  The feature grid pass
+// (every fluid particle into the integer sums of its feature cell; grid:
+// nfcells int4, zeroed here) and the features of every boid (a warp each).
 cudaError_t launch_features(const float4* pos, const float4* vel, const unsigned* start, const float4* bpos,
-                            const float4* bvel, const Scenes& sc, void* x, cudaStream_t s, long long* launches);
+                            const float4* bvel, const Scenes& sc, int4* grid, int nfcells, void* x, cudaStream_t s,
+                            long long* launches);
 cudaError_t launch_mark_needed(const float4* pos, const unsigned* start, const Scenes& sc, const int* slot_of_boid,
                                const int* bmask, unsigned char* need, cudaStream_t s, long long* launches);
 // list[0 .. *len) = the slots with need[slot] != 0 (order unspecified); *len
