@@ -44,9 +44,26 @@ METRIC = "particle-steps/sec at 2M particles (HBM roofline %)"
 UNIT = "particle-steps/s"
 SETTLE = 200
 
-# FP32 peak of the ALU-bound passes: 152 SMs x 128 FP32 lanes x 2 flops (FMA)
-# x 2070 MHz (maximum SM clock).
+# FP32 peak of the ALU-bound passes: SMs x 128 FP32 lanes x 2 flops (FMA) x
+# the maximum SM clock.  Set by _set_fp32_peak from the device's SM count and
+# the measured peaks' maximum clock once the device is known; the nominal
+# GB300 figure (152 SMs, 2070 MHz) until then.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP32_PEAK_SOURCE = "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+
+
+def _set_fp32_peak(dev):
+    global FP32_PEAK_TFLOPS, FP32_PEAK_SOURCE
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    FP32_PEAK_TFLOPS = sms * 128 * 2 * mhz * 1e6 / 1e12
+    FP32_PEAK_SOURCE = f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
 # Algorithmic work per particle-step, as the method defines it: each pass
 # tests the candidates of the 27-cell stencil of cell size h, C = 27 n h^3
 # per particle (n the number density), i.e. C = N * 27 / (4 pi / 3) with N
@@ -835,6 +852,7 @@ def run_ours(a):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    _set_fp32_peak(dev)
     if world > 1:
         import torch.distributed as dist
 
@@ -941,7 +959,7 @@ def run_ours(a):
         "bound": "alu", "kernel": "k_forces (pair forces + integration)", "achieved": achieved,
         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
         "traffic": traffic.get("k_forces"),
-        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+        "peak_source": FP32_PEAK_SOURCE,
         "flops_per_launch": force_flops,
         "flops_definition": "27-cell stencil at cell size h: 9 flops x 27/(4pi/3) x neighbours + 35 x neighbours",
         "executed": {"flops_per_launch": force_exec, "achieved": force_exec / (f_ms * 1e-3) / 1e12,

@@ -428,7 +428,8 @@ long long sph_launch_count(sph_handle* h);
  * (exclusive scan of the cell counts), SPH_KIND_SCATTER, SPH_KIND_SORT
  * (per-cell sort + gather), SPH_KIND_DENSITY, SPH_KIND_FORCES (pair forces
  * + integration + next keys), SPH_KIND_BOID_BIN (boid-grid binning),
- * SPH_KIND_BOID_RULES, SPH_KIND_FEATURES.  sph_profile_enable(h, n) creates a host-side pool
+ * SPH_KIND_BOID_RULES, SPH_KIND_LISTS, SPH_KIND_FEATURES, SPH_KIND_PIPELINE
+ * (SPH_NUM_KINDS kinds).  sph_profile_enable(h, n) creates a host-side pool
  * of 2n events (n = 0 disables and frees it); while enabled, each pass of
  * sph_step is bracketed by two events recorded on the step's stream, up to
  * n passes.  sph_profile_read synchronises on the last event and writes,
@@ -446,7 +447,7 @@ long long sph_launch_count(sph_handle* h);
 #define SPH_KIND_LISTS      8  /* neighbour lists: offsets scan + fill (when set) */
 #define SPH_KIND_FEATURES   9  /* the surrogate's stencil features (sph_features, surrogate modes) */
 #define SPH_KIND_PIPELINE  10  /* both neighbour passes in one launch (sph_set_pipeline) */
-#define SPH_NUM_KINDS       9
+#define SPH_NUM_KINDS      11
 int sph_profile_enable(sph_handle* h, int max_passes);
 int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds);
 
