@@ -87,6 +87,11 @@ struct sph_handle {
     cudaEvent_t* prof_ev;
     int* prof_kind;
     int prof_cap, prof_n;
+    // the step's side stream: the boids' binning, F_b and rules run there,
+    // alongside the fluid passes (forked from and joined back into the
+    // caller's stream every step)
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_dens, ev_join;
     // captured step (sph_graph_step)
     cudaGraphExec_t graph;
     cudaStream_t graph_stream;
@@ -108,6 +113,16 @@ static void drop_boid_graphs(sph_handle* h)
         if (g.exec) cudaGraphExecDestroy(g.exec);
         g.exec = nullptr;
     }
+}
+
+static void destroy_side(sph_handle* h)
+{
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_dens) cudaEventDestroy(h->ev_dens);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
+    h->ev_fork = h->ev_dens = h->ev_join = nullptr;
+    h->side = nullptr;
 }
 
 static void prof_begin(sph_handle* h, int kind, cudaStream_t s)
@@ -608,7 +623,16 @@ int sph_batch_create(const sph_params* params, const int* n_fluid, const int* n_
     if (e == cudaSuccess) e = cudaMemcpy(h->d_bbase, h->h_bbase, sizeof(unsigned) * (size_t)(S + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->err, 0, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = prepare_kernels();
+    if (e == cudaSuccess && h->n_boid > 0) {
+        // default priority: a higher one lets the F_b warps take SMs from the
+        // fluid blocks early and slows the force pass by more than it saves
+        e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_dens, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
+        destroy_side(h);
         free_tables(h);
         delete h;
         return fail(nullptr, SPH_ERR_CUDA, "uploading the scene tables: %s", cudaGetErrorString(e));
@@ -717,6 +741,7 @@ void sph_destroy(sph_handle* h)
     prof_free(h);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     drop_boid_graphs(h);
+    destroy_side(h);
     free_tables(h);
     delete h;
 }
@@ -753,9 +778,10 @@ int sph_profile_read(sph_handle* h, double* ms, long long* passes, int nkinds)
         ms[k] = 0.0;
         passes[k] = 0;
     }
-    if (h->prof_n > 0) CUDA_TRY(h, cudaEventSynchronize(h->prof_ev[2 * h->prof_n - 1]));
     for (int i = 0; i < h->prof_n; ++i) {
         float t = 0.0f;
+        // passes on the side stream may end after later passes of the caller's stream
+        CUDA_TRY(h, cudaEventSynchronize(h->prof_ev[2 * i + 1]));
         CUDA_TRY(h, cudaEventElapsedTime(&t, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
         int k = h->prof_kind[i];
         if (k < nkinds) {
@@ -887,9 +913,35 @@ static int bin_state(sph_handle* h, cudaStream_t s, bool consume)
     return SPH_OK;
 }
 
+// The boids' binning (the boid state only) on stream s.
+static int enqueue_boid_bin(sph_handle* h, cudaStream_t s)
+{
+    prof_begin(h, SPH_KIND_BOID_BIN, s);
+    CUDA_TRY(h, cudaMemsetAsync(h->bcount, 0, (size_t)h->nbcells * sizeof(unsigned), s));
+    CUDA_TRY(h, launch_boid_keys(h->bpos, h->sc, h->bkey, h->brank, h->bcount, s, &h->launches));
+    CUDA_TRY(h, launch_scan(h->bcount, h->nbcells, h->bscan_part, h->bstart, s, &h->launches));
+    CUDA_TRY(h, launch_scatter(h->bkey, h->brank, h->bstart, h->n_boid, h->btmp, s, &h->launches));
+    CUDA_TRY(h, launch_cellsort_gather(h->bstart, h->nbcells, h->btmp, h->bpos, h->bvel, h->bpos_s, h->bvel_s, 0,
+                                       nullptr, h->bbig_list, h->bbig_count, s, &h->launches));
+    prof_end(h, s);
+    return SPH_OK;
+}
+
+// The boid rules (needs F_b and the boids' binning) on stream s.
+static cudaError_t launch_rules(sph_handle* h, cudaStream_t s)
+{
+    return launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, h->obst, h->sc, h->fb, h->vel_s, h->bpos, h->bvel,
+                             h->pos, h->vel, h->slot_of_boid, h->key, h->rank, h->count, h->err, s, &h->launches);
+}
+
 // The density pass, the neighbour lists (when set) and the force pass as
-// separate launches.
-static int enqueue_neighbor_passes(sph_handle* h, cudaStream_t s)
+// separate launches.  split: the F_b warps and the boid rules run on the
+// side stream once the densities exist, alongside the fluid blocks of the
+// force pass on s (they write disjoint slots: the fluid blocks write the
+// fluid particles' next state and keys, the boid rules the boids' and their
+// attached particles'; both only add to the cell counts), and s waits for
+// them before it goes on.
+static int enqueue_neighbor_passes(sph_handle* h, cudaStream_t s, bool split)
 {
     prof_begin(h, SPH_KIND_DENSITY, s);
     CUDA_TRY(h, launch_density(h->pos_s, h->vel_s, soa_of(h), h->cell_start, h->sc, h->tune, h->rho, h->ab, h->prec,
@@ -902,22 +954,46 @@ static int enqueue_neighbor_passes(sph_handle* h, cudaStream_t s)
                                       &h->launches));
         prof_end(h, s);
     }
+    if (split) {
+        CUDA_TRY(h, cudaEventRecord(h->ev_dens, s));
+        CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_dens, 0));
+        prof_begin(h, SPH_KIND_BOID_RULES, h->side);
+        CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->prec, h->cell_start, h->seg,
+                                  h->nseg, h->sc, h->tune, h->list, h->noff, h->list_cap, true, false,
+                                  h->slot_of_boid, nullptr, h->fb, h->diag ? h->acc : nullptr, nullptr, nullptr,
+                                  h->pos, h->vel, h->key, h->rank, h->count, h->err, h->side, &h->launches));
+        CUDA_TRY(h, launch_rules(h, h->side));
+        prof_end(h, h->side);
+        CUDA_TRY(h, cudaEventRecord(h->ev_join, h->side));
+    }
     prof_begin(h, SPH_KIND_FORCES, s);
     CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, h->prec, h->cell_start, h->seg, h->nseg, h->sc,
-                              h->tune, h->list, h->noff, h->list_cap, true, h->slot_of_boid, nullptr, h->fb,
+                              h->tune, h->list, h->noff, h->list_cap, !split, true, h->slot_of_boid, nullptr, h->fb,
                               h->diag ? h->acc : nullptr, h->diag ? h->touched : nullptr,
                               h->diag ? h->infl : nullptr, h->pos, h->vel, h->key, h->rank, h->count, h->err, s,
                               &h->launches));
     prof_end(h, s);
+    if (split) CUDA_TRY(h, cudaStreamWaitEvent(s, h->ev_join, 0));
     return SPH_OK;
 }
 
-// Enqueue one step (keys must be ready or are computed first).
+// Enqueue one step (keys must be ready or are computed first).  With boids
+// and separate neighbour-pass launches, the boids' binning, F_b and rules
+// run on the side stream, forked from s at the start of the step and joined
+// back before it ends; the per-thread arithmetic is that of the serial order.
 static int enqueue_step(sph_handle* h, cudaStream_t s)
 {
+    const bool pipe = h->tune.pipe_tile > 0 && !h->list;
+    const bool split = h->n_boid > 0 && h->side && !pipe;
+    if (split) {
+        CUDA_TRY(h, cudaEventRecord(h->ev_fork, s));
+        CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        int rc = enqueue_boid_bin(h, h->side);
+        if (rc != SPH_OK) return rc;
+    }
     int rc = bin_state(h, s, true);
     if (rc != SPH_OK) return rc;
-    if (h->tune.pipe_tile > 0 && !h->list) {
+    if (pipe) {
         // both neighbour passes in one cooperative launch
         prof_begin(h, SPH_KIND_PIPELINE, s);
         CUDA_TRY(h, launch_nbr_pipeline(h->pos_s, soa_of(h), h->vel_s, h->cell_start, h->sc, h->tune, h->rho, h->ab,
@@ -927,23 +1003,14 @@ static int enqueue_step(sph_handle* h, cudaStream_t s)
                                         h->pipe_queue, h->skip_cta, h->err, s, &h->launches));
         prof_end(h, s);
     } else {
-        int rc2 = enqueue_neighbor_passes(h, s);
+        int rc2 = enqueue_neighbor_passes(h, s, split);
         if (rc2 != SPH_OK) return rc2;
     }
-    if (h->n_boid > 0) {
-        prof_begin(h, SPH_KIND_BOID_BIN, s);
-        CUDA_TRY(h, cudaMemsetAsync(h->bcount, 0, (size_t)h->nbcells * sizeof(unsigned), s));
-        CUDA_TRY(h, launch_boid_keys(h->bpos, h->sc, h->bkey, h->brank, h->bcount, s, &h->launches));
-        CUDA_TRY(h, launch_scan(h->bcount, h->nbcells, h->bscan_part, h->bstart, s, &h->launches));
-        CUDA_TRY(h, launch_scatter(h->bkey, h->brank, h->bstart, h->n_boid, h->btmp, s, &h->launches));
-        CUDA_TRY(h, launch_cellsort_gather(h->bstart, h->nbcells, h->btmp, h->bpos, h->bvel, h->bpos_s, h->bvel_s,
-                                           0, nullptr, h->bbig_list, h->bbig_count, s, &h->launches));
-        prof_end(h, s);
+    if (h->n_boid > 0 && !split) {
+        rc = enqueue_boid_bin(h, s);
+        if (rc != SPH_OK) return rc;
         prof_begin(h, SPH_KIND_BOID_RULES, s);
-        CUDA_TRY(h, launch_boid_rules(h->bpos_s, h->bvel_s, h->bstart, h->obst, h->sc, h->fb, h->vel_s, h->bpos,
-                                      h->bvel, h->pos,
-                                      h->vel, h->slot_of_boid, h->key, h->rank, h->count, h->err, s,
-                                      &h->launches));
+        CUDA_TRY(h, launch_rules(h, s));
         prof_end(h, s);
     }
     h->keys_ready = true;  // the force and boid kernels emitted the next keys
@@ -1074,7 +1141,7 @@ static int exact_local(sph_handle* h, const int* bmask, float4* out, cudaStream_
                                &h->launches));
     CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, nullptr, h->cell_start, nullptr, nullptr,
                               h->sc, h->tune,
-                              nullptr, nullptr, 0, false, h->slot_of_boid, bmask, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                              nullptr, nullptr, 0, true, false, h->slot_of_boid, bmask, out, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                               nullptr, nullptr, h->err, s, &h->launches));
     return SPH_OK;
 }
@@ -1092,7 +1159,7 @@ static int enqueue_boid_forces(sph_handle* h, int mode, float* out_f4, cudaStrea
                                    &h->launches));
         CUDA_TRY(h, launch_forces(h->pos_s, soa_of(h), h->vel_s, h->rho, h->ab, nullptr, h->cell_start, nullptr,
                                   nullptr, h->sc, h->tune,
-                                  nullptr, nullptr, 0, false, h->slot_of_boid, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                  nullptr, nullptr, 0, true, false, h->slot_of_boid, nullptr, out, nullptr, nullptr, nullptr, nullptr, nullptr,
                                   nullptr, nullptr, nullptr, h->err, s, &h->launches));
         return SPH_OK;
     }

@@ -399,12 +399,14 @@ cudaError_t launch_density(const float4* pos, const float4* vel, const SoaPos& x
 // its pairs taken from the density pass's hit segments when t.use_seg (the
 // same step's density pass must have written them).  acc, touched, infl:
 // the diagnostic fields, written when given (all three or none; attached
-// particles get touched = 0, influence = 0).  One launch.
+// particles get touched = 0, influence = 0).  boids: the F_b warps of the
+// boids (bmask NULL = all) take part; fluid: the fluid blocks (pair forces,
+// integration, next keys) take part.  One launch.
 cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* vel, const float* rho, const float2* ab,
                           const float4* prec, const unsigned* start, const uint2* seg, const int* nseg,
                           const Scenes& sc,
                           const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
-                          bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
+                          bool boids, bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
                           float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
                           unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
                           long long* launches);

@@ -73,8 +73,7 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
             if (r2 < h2) {
                 const float t = h2 - r2;
                 sum = fmaf(t * t, t, sum);
-                ++cnt;
-                if (SEG) m |= 1u << sh;
+                if (SEG) m |= 1u << sh; else ++cnt;
             }
         };
         // x_j - x_i as x_j + (-x_i) and h2 - r2 as fma(r2, -1, h2): the
@@ -89,13 +88,11 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
             const unsigned bit = SEG ? 1u << sh : 0u;
             if (r2.x < h2) {
                 sum = fmaf(tt.x, t.x, sum);
-                ++cnt;
-                if (SEG) m |= bit;
+                if (SEG) m |= bit; else ++cnt;
             }
             if (r2.y < h2) {
                 sum = fmaf(tt.y, t.y, sum);
-                ++cnt;
-                if (SEG) m |= bit << 1;
+                if (SEG) m |= bit << 1; else ++cnt;
             }
         };
         const float2* __restrict__ X2 = reinterpret_cast<const float2*>(xyz.x);
@@ -133,6 +130,7 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
                     m = 0;
                     slots(b, min(b + 32u, s1), b);
                     if (m) {
+                        cnt += __popc(m);
                         if (ns < SEG_CAP) mine[ns] = make_uint2(b, m);
                         ++ns;
                     }
@@ -648,14 +646,14 @@ cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* ve
                           const float4* prec, const unsigned* start, const uint2* seg, const int* nseg,
                           const Scenes& sc,
                           const Tuning& t, const unsigned* list, const unsigned* list_off, size_t list_cap,
-                          bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
+                          bool boids, bool fluid, const int* slot_of_boid, const int* bmask, float4* fb,
                           float4* acc, int* touched, float4* infl, float4* pos_next, float4* vel_next,
                           unsigned* key, unsigned* rank, unsigned* count, unsigned* err, cudaStream_t s,
                           long long* launches)
 {
     const unsigned cap = list_cap > 0xffffffffu ? 0xffffffffu : (unsigned)list_cap;
     const int warps = t.block / 32;
-    const int boid_blocks = (sc.nb_all + warps - 1) / warps;
+    const int boid_blocks = boids ? (sc.nb_all + warps - 1) / warps : 0;
     const int fluid_blocks = fluid ? (sc.n_all + t.block - 1) / t.block : 0;
     if (boid_blocks + fluid_blocks == 0) return cudaSuccess;
     const ForceArgs a{pos, xyz, vel, rho, ab, prec, start, t.use_seg ? seg : nullptr, nseg, sc, list, list_off, cap,
