@@ -86,9 +86,18 @@ BYTES = {"scatter": 12, "sort": 60, "density": 20, "forces": 72}
 BYTES_PER_CELL_SCAN = 12
 
 # DRAM traffic per launch of the force and density passes from one ncu
-# capture of the bench's workload, and the sha256 of the kernel source it
-# was taken on; null once the source moved.
-KERNEL_TRAFFIC = {}
+# capture of the bench's workload, and the sha256 of the kernel sources
+# (sph_physics.cu, sph_internal.cuh) it was taken on; null once they moved.
+# Capture: the launch list (gpu__time_duration, dram__bytes_read/write, one
+# pass) of `bench.py --steps 20 --warmup 3 --no-cpu-baseline --e2e-steps 2
+# --no-batch --no-surrogate --no-surface`, mean over the 21 launches of the
+# timed steps after 200 settling steps (k_forces: the fluid launches).
+KERNEL_TRAFFIC = {
+    "k_forces": {"bytes": 740.7e6, "read": 667.0e6, "write": 73.7e6,
+                 "source_sha256": "ef49e7f402f63b2207cf486b78b103b84de88adf4e8dae2c7a4fb4c9ed228ecf"},
+    "k_density": {"bytes": 889.2e6, "read": 286.5e6, "write": 602.7e6,
+                  "source_sha256": "ef49e7f402f63b2207cf486b78b103b84de88adf4e8dae2c7a4fb4c9ed228ecf"},
+}
 
 
 def _args():
@@ -232,8 +241,12 @@ def _work_snapshot(s):
             "stats": {k: float(v) for k, v in zip(STATS, st)}}
 
 
-def _source_sha(path):
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+def _source_sha(*paths):
+    """sha256 over the concatenated bytes of the kernel sources."""
+    h = hashlib.sha256()
+    for path in paths:
+        h.update(open(path, "rb").read())
+    return h.hexdigest()
 
 
 # ------------------------------------------------------- neighbour search
@@ -924,6 +937,9 @@ def run_ours(a):
     over = statistics.mean(w["overflow_candidates"] for w in works)
     n_all = nf + nb
     passes = {k: {"ms_per_step": ms / max(cnt, 1), "launch_groups": cnt} for k, (ms, cnt) in prof.items() if cnt}
+    if nb:
+        passes["note"] = ("boid_bin and boid_rules (F_b + rules) run on the step's side stream alongside the "
+                          "fluid passes: their times are spans that overlap density and forces")
     f_ms = passes["forces"]["ms_per_step"]
     d_ms = passes["density"]["ms_per_step"]
     stencil = STENCIL_CAND_PER_NBR * pairs
@@ -936,8 +952,8 @@ def run_ours(a):
         force_exec = FLOP_CAND * cand + FLOP_FORCE_PAIR * pairs
     dens_exec = FLOP_CAND * cand + FLOP_DENS_PAIR * (pairs + n_all)
     achieved = force_flops / (f_ms * 1e-3) / 1e12
-    src = os.path.join(ROOT, "paper_2311_15088_gb300", "csrc", "sph_physics.cu")
-    src_sha = _source_sha(src)
+    src_sha = _source_sha(*(os.path.join(ROOT, "paper_2311_15088_gb300", "csrc", f)
+                            for f in ("sph_physics.cu", "sph_internal.cuh")))
     traffic = {k: v["bytes"] for k, v in KERNEL_TRAFFIC.items() if v.get("source_sha256") == src_sha}
     peaks = {}
     try:

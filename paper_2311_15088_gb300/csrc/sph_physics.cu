@@ -24,12 +24,13 @@ namespace sphk {
 
 // Hit segments.  The density pass tests every candidate of a fluid
 // particle's walk; it also keeps, for the force pass, which candidates are
-// force pairs (0 < r2 < h2: the neighbours without the particle itself and
-// coincident particles).  Each row of the walk is cut into pieces of at most
-// 32 consecutive slots and every piece with a pair is stored as one segment
-// (first slot, 32-bit mask of its pairs), in walk order, at seg[i * SEG_CAP
-// + k]; nseg[i] is the number of segments (SEG_CAP + 1 and more: the list
-// did not fit, the force pass tests the candidates itself).  The force pass
+// within h (r2 < h2: the particle itself and coincident particles among
+// them; the force pass skips those by r2 == 0).  Each row of the walk is cut
+// into pieces of at most 32 consecutive slots and every piece with a hit is
+// stored as one segment (first slot, 32-bit mask of its hits), in walk
+// order, at seg[i * SEG_CAP + k]; nseg[i] is the number of segments
+// (SEG_CAP + 1 and more: the list did not fit, the force pass tests the
+// candidates itself).  The neighbour count is the hits' popcount less one.  The force pass
 // then evaluates the pairs in exactly the walk's order without testing a
 // candidate again, and the lanes of a warp take their next pair together
 // instead of waiting at each row for the lane with the most hits in it.
