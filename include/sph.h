@@ -249,6 +249,12 @@ int sph_get_state(sph_handle* h, float* fluid_pos4, float* fluid_vel4,
  * boid rules (start-of-step snapshot, rules in the listed order, then
  * v_b += sph_factor dt F_b, edge avoidance, speed limit, x_b += v_b dt);
  * Euler-Cromer integration of the fluid with damped wall reflection.
+ * With boids (and without the fused pipeline of sph_set_pipeline), the
+ * boids' binning, F_b and rules run on a stream the handle owns, forked from
+ * `stream` at the start of each step and joined back into it before the
+ * step ends: to the caller the work is ordered on `stream` as if it ran
+ * there alone (a capture of `stream` takes the side branch with it), and the
+ * results are bit for bit those of the serial order.
  * Errors: SPH_ERR_ARG (nsteps < 0), SPH_ERR_STATE (no state loaded),
  * SPH_ERR_CUDA.  Device-side anomalies set bits of the error word.
  */

@@ -49,23 +49,56 @@ __global__ void __launch_bounds__(256)
 k_feature_grid(const float4* __restrict__ pos, const float4* __restrict__ vel, Scenes sc, int4* __restrict__ grid)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= sc.n_all) return;
-    const float4 p = pos[i];
-    if (id_of(p) < sc.nb_all) return;  // fluid particles only
-    const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
-    // feature cell floor((x - m) inv_h), shifted by the two-cell margin
-    const float fx = floorf(__fmul_rn(__fsub_rn(p.x, c.g.minf[0]), c.inv_h)) + 2.0f;
-    const float fy = floorf(__fmul_rn(__fsub_rn(p.y, c.g.minf[1]), c.inv_h)) + 2.0f;
-    const float fz = floorf(__fmul_rn(__fsub_rn(p.z, c.g.minf[2]), c.inv_h)) + 2.0f;
-    if (!(fx >= 0.f && fx < (float)c.fdim[0] && fy >= 0.f && fy < (float)c.fdim[1] && fz >= 0.f &&
-          fz < (float)c.fdim[2]))
-        return;  // more than two cells outside the box (no boid of the box sees it)
-    const int q = c.fc_base + (int)fx + c.fdim[0] * ((int)fy + c.fdim[1] * (int)fz);
-    const float4 v = __ldg(vel + i);
-    atomicAdd(&grid[q].x, 1);
-    atomicAdd(&grid[q].y, __float2int_rn(v.x * VFIX));
-    atomicAdd(&grid[q].z, __float2int_rn(v.y * VFIX));
-    atomicAdd(&grid[q].w, __float2int_rn(v.z * VFIX));
+    const unsigned lane = threadIdx.x & 31u;
+    int q = -1;  // feature cell of this lane's particle, -1: none
+    int4 v = make_int4(0, 0, 0, 0);
+    if (i < sc.n_all) {
+        const float4 p = pos[i];
+        if (id_of(p) >= sc.nb_all) {  // fluid particles only
+            const StepConst& c = sc.c[scene_of(sc.pbase, sc.S, (unsigned)i)];
+            // feature cell floor((x - m) inv_h), shifted by the two-cell margin
+            const float fx = floorf(__fmul_rn(__fsub_rn(p.x, c.g.minf[0]), c.inv_h)) + 2.0f;
+            const float fy = floorf(__fmul_rn(__fsub_rn(p.y, c.g.minf[1]), c.inv_h)) + 2.0f;
+            const float fz = floorf(__fmul_rn(__fsub_rn(p.z, c.g.minf[2]), c.inv_h)) + 2.0f;
+            // more than two cells outside the box: no boid of the box sees it
+            if (fx >= 0.f && fx < (float)c.fdim[0] && fy >= 0.f && fy < (float)c.fdim[1] && fz >= 0.f &&
+                fz < (float)c.fdim[2]) {
+                q = c.fc_base + (int)fx + c.fdim[0] * ((int)fy + c.fdim[1] * (int)fz);
+                const float4 u = __ldg(vel + i);
+                v = make_int4(1, __float2int_rn(u.x * VFIX), __float2int_rn(u.y * VFIX), __float2int_rn(u.z * VFIX));
+            }
+        }
+    }
+    // Consecutive sorted particles mostly share a cell: the lanes of a run
+    // of equal q add their sums (integer prefix sums of the warp, the run's
+    // sum = the prefix at its last lane minus the prefix before its first)
+    // and the run's last lane adds them to the grid.
+    const int qp = __shfl_up_sync(FULL, q, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || qp != q);
+    int4 incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(FULL, incl.x, o), b = __shfl_up_sync(FULL, incl.y, o);
+        const int c = __shfl_up_sync(FULL, incl.z, o), d = __shfl_up_sync(FULL, incl.w, o);
+        if (lane >= (unsigned)o) {
+            incl.x += a;
+            incl.y += b;
+            incl.z += c;
+            incl.w += d;
+        }
+    }
+    const int head = 31 - __clz(heads & (0xffffffffu >> (31u - lane)));  // first lane of this lane's run
+    const int src = head > 0 ? head - 1 : 0;
+    int4 before = make_int4(__shfl_sync(FULL, incl.x, src), __shfl_sync(FULL, incl.y, src),
+                            __shfl_sync(FULL, incl.z, src), __shfl_sync(FULL, incl.w, src));
+    if (head == 0) before = make_int4(0, 0, 0, 0);
+    const bool tail = lane == 31u || ((heads >> (lane + 1u)) & 1u);
+    if (tail && q >= 0) {
+        atomicAdd(&grid[q].x, incl.x - before.x);
+        atomicAdd(&grid[q].y, incl.y - before.y);
+        atomicAdd(&grid[q].z, incl.z - before.z);
+        atomicAdd(&grid[q].w, incl.w - before.w);
+    }
 }
 
 __global__ void __launch_bounds__(FW * 32)
