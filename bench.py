@@ -547,7 +547,7 @@ def run_batched(a, dev, flush):
         "loop": "each scene's own handle replaying its captured step (sph_graph_step), same kernels",
         "cell_size_over_h": frac,
         "ms_per_step_by_cell_size": {str(f): 1e3 * v["t"] / a.batch_steps for f, v in per_cell.items()},
-        "tuning": {k: best[k] for k in ("block", "use_segments", "pipe_tile", "pipe_block", "ms_per_step")},
+        "tuning": {k: best[k] for k in ("block", "use_segments", "ppt", "pipe_tile", "pipe_block", "ms_per_step")},
         "roofline": {
             "alu": {"achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": flops / (ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
@@ -1037,7 +1037,7 @@ def run_ours(a):
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "cell_size_over_h": float(np.float32(p["cell_size"]) / np.float32(p["h"])),
-                       "tuning": {"block": s.tuning[0], "use_segments": s.tuning[1]},
+                       "tuning": {"block": s.tuning[0], "use_segments": s.tuning[1], "ppt": s.ppt},
                        "force_pass_neighbours": "pair lists" if a.neighbor_lists else "walk",
                        "neighbours_mean": statistics.mean(w["nbr_mean"] for w in works),
                        "neighbours_max": max(w["nbr_max"] for w in works),

@@ -186,6 +186,15 @@ int sph_batch_create(const sph_params* params, const int* n_fluid, const int* n_
 int sph_set_tuning(sph_handle* h, int block, int use_segments);
 
 /*
+ * Particles per thread of the two neighbour passes' separate launches (the
+ * trade-off of section "Experimental Results": fewer threads, each taking
+ * several particles): ppt = 1 (the default), 2 or 4; thread t of a grid of
+ * T threads takes particles t, t + T, ...  No result bit changes.  The fused
+ * pipeline (sph_set_pipeline) takes its own tiles.  Errors: SPH_ERR_ARG.
+ */
+int sph_set_particles_per_thread(sph_handle* h, int ppt);
+
+/*
  * Record the diagnostic fields in later steps: with record = 1 the force
  * pass also stores each particle's acceleration, touched_by_boid and
  * boid_influence (listing "Compute acceleration", section "Boid Motion and

@@ -566,6 +566,7 @@ static int layout_scenes(sph_handle* h, const sph_params* params, const int* n_f
     h->nfcells = (int)Cf;
     h->tune.block = 256;
     h->tune.use_seg = 1;
+    h->tune.ppt = 1;
     h->tune.pipe_tile = 0;
     h->tune.pipe_block = 256;
     return SPH_OK;
@@ -660,6 +661,19 @@ int sph_set_tuning(sph_handle* h, int block, int use_segments)
     if (use_segments != 0 && use_segments != 1) return fail(h, SPH_ERR_ARG, "use_segments must be 0 or 1");
     h->tune.block = block;
     h->tune.use_seg = use_segments;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    drop_boid_graphs(h);
+    return SPH_OK;
+}
+
+int sph_set_particles_per_thread(sph_handle* h, int ppt)
+{
+    if (!h) return fail(nullptr, SPH_ERR_ARG, "handle is NULL");
+    if (ppt != 1 && ppt != 2 && ppt != 4) return fail(h, SPH_ERR_ARG, "ppt must be 1, 2 or 4");
+    h->tune.ppt = ppt;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;

@@ -378,6 +378,7 @@ struct Tuning {
     int use_seg;     // 1: the density pass records hit segments and the force pass reads them
     int pipe_tile;   // > 0: both neighbour passes in one cooperative launch, tiles of this many slots
     int pipe_block;  // threads per block of that launch (128 or 256)
+    int ppt;         // particles per thread of the separate neighbour-pass launches (1, 2 or 4)
 };
 
 // Density, neighbour counts, candidates tested (ncand) and, with seg given

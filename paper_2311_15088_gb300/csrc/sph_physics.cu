@@ -181,8 +181,11 @@ k_density(const float4* __restrict__ pos, const float4* __restrict__ vel, SoaPos
           float4* __restrict__ prec, int* __restrict__ nbr, uint2* __restrict__ seg, int* __restrict__ nseg,
           int* __restrict__ ncand, unsigned* __restrict__ err)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < sc.n_all) density_at<SEG>(t, pos, vel, xyz, start, sc, rho, ab, prec, nbr, seg, nseg, ncand, err);
+    // particles t, t + T, t + 2T, ... (T the threads of the grid: a grid of
+    // n / ppt threads gives each thread ppt particles)
+    const int T = gridDim.x * blockDim.x;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < sc.n_all; t += T)
+        density_at<SEG>(t, pos, vel, xyz, start, sc, rho, ab, prec, nbr, seg, nseg, ncand, err);
 }
 
 
@@ -254,7 +257,8 @@ cudaError_t launch_density(const float4* pos, const float4* vel, const SoaPos& x
                            unsigned* err, cudaStream_t s, long long* launches)
 {
     if (sc.n_all <= 0) return cudaSuccess;
-    const int all = (sc.n_all + t.block - 1) / t.block;
+    const int per_block = t.block * (t.ppt > 1 ? t.ppt : 1);
+    const int all = (sc.n_all + per_block - 1) / per_block;
     if (list) {
         const int cap = 16 * sm_count();  // 8 warps per block, 16 blocks per SM at most
         const int blocks = (sc.n_all + 7) / 8 < cap ? (sc.n_all + 7) / 8 : cap;
@@ -640,7 +644,12 @@ k_forces(ForceArgs a, int boid_blocks)
                                 a.bmask, a.fb, a.acc);
         return;
     }
-    force_particle<false>(a, (blockIdx.x - boid_blocks) * blockDim.x + threadIdx.x);
+    // particles base + lane, base stepping over the fluid blocks' threads; the
+    // trip count is the block's, so every lane of a warp takes part in each
+    // call (force_particle's warp-aggregated count)
+    const int T = ((int)gridDim.x - boid_blocks) * (int)blockDim.x;
+    for (int base = ((int)blockIdx.x - boid_blocks) * (int)blockDim.x; base < a.sc.n_all; base += T)
+        force_particle<false>(a, base + (int)threadIdx.x);
 }
 
 cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* vel, const float* rho, const float2* ab,
@@ -655,7 +664,8 @@ cudaError_t launch_forces(const float4* pos, const SoaPos& xyz, const float4* ve
     const unsigned cap = list_cap > 0xffffffffu ? 0xffffffffu : (unsigned)list_cap;
     const int warps = t.block / 32;
     const int boid_blocks = boids ? (sc.nb_all + warps - 1) / warps : 0;
-    const int fluid_blocks = fluid ? (sc.n_all + t.block - 1) / t.block : 0;
+    const int per_block = t.block * (t.ppt > 1 ? t.ppt : 1);
+    const int fluid_blocks = fluid ? (sc.n_all + per_block - 1) / per_block : 0;
     if (boid_blocks + fluid_blocks == 0) return cudaSuccess;
     const ForceArgs a{pos, xyz, vel, rho, ab, prec, start, t.use_seg ? seg : nullptr, nseg, sc, list, list_off, cap,
                       slot_of_boid, bmask, fb, acc, touched, infl, pos_next, vel_next, key, rank, count, err};

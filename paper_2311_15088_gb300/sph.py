@@ -81,6 +81,7 @@ _sig = {
     "sph_set_tuning": (_i, [_vp, _i, _i]),
     "sph_set_diagnostics": (_i, [_vp, _i]),
     "sph_set_pipeline": (_i, [_vp, _i, _i]),
+    "sph_set_particles_per_thread": (_i, [_vp, _i]),
     "sph_debug_barrier_skip": (_i, [_vp, _i]),
     "sph_set_neighbor_lists": (_i, [_vp, _vp, ctypes.c_size_t]),
     "sph_debug_bucket_neighbors": (_i, [_vp, _vp, ctypes.c_size_t, _i, _vp, _vp, _vp]),
@@ -206,6 +207,10 @@ def sph_set_tuning(h, block: int, use_segments: int):
 
 def sph_set_diagnostics(h, record: int):
     _check(_lib.sph_set_diagnostics(h, record), h)
+
+
+def sph_set_particles_per_thread(h, ppt: int):
+    _check(_lib.sph_set_particles_per_thread(h, ppt), h)
 
 
 def sph_set_pipeline(h, tile_slots: int, block: int = 256):
@@ -578,6 +583,7 @@ class Scene:
         self.ncells = int(sum(d[0] * d[1] * d[2] for d in dims))
         self.nbcells = int(sum(d[0] * d[1] * d[2] for d in bdims))
         self.tuning = (256, 1)  # the library's default (block, use_segments)
+        self.ppt = 1
         self.pipeline = (0, 256)  # separate neighbour-pass launches
         self.diagnostics = False
         if diagnostics:
@@ -653,6 +659,11 @@ class Scene:
     def set_tuning(self, block: int, use_segments: int):
         sph_set_tuning(self.handle, block, use_segments)
         self.tuning = (int(block), int(use_segments))
+
+    def set_particles_per_thread(self, ppt: int):
+        """Particles per thread of the separate neighbour-pass launches."""
+        sph_set_particles_per_thread(self.handle, ppt)
+        self.ppt = int(ppt)
 
     def set_pipeline(self, tile_slots: int, block: int = 256):
         """Both neighbour passes in one persistent launch over tiles of

@@ -125,19 +125,21 @@ def test_graph_replay_equals_step():
     assert b.launches > a.launches * 0.5
 
 
-@pytest.mark.parametrize("block,use_segments,tile,pblock",
-                         [(64, 0, 0, 256), (128, 1, 0, 256), (256, 0, 0, 256), (512, 0, 0, 256), (512, 1, 0, 256),
-                          (256, 1, 32, 128), (256, 1, 512, 256), (256, 0, 2048, 256), (256, 1, 65536, 128)])
-def test_launch_shape_changes_no_bit(block, use_segments, tile, pblock):
-    """Block size, the source of the force pass's pairs (hit segments or a
-    second candidate test) and the fused persistent pipeline (both passes in
-    one cooperative launch over work tiles of any size) change no bit of the
-    state or of the fields."""
+@pytest.mark.parametrize("block,use_segments,ppt,tile,pblock",
+                         [(64, 0, 1, 0, 256), (128, 1, 2, 0, 256), (256, 0, 4, 0, 256), (512, 0, 1, 0, 256),
+                          (512, 1, 4, 0, 256), (64, 1, 2, 0, 256), (256, 1, 1, 32, 128), (256, 1, 1, 512, 256),
+                          (256, 0, 2, 2048, 256), (256, 1, 1, 65536, 128)])
+def test_launch_shape_changes_no_bit(block, use_segments, ppt, tile, pblock):
+    """Block size, particles per thread, the source of the force pass's
+    pairs (hit segments or a second candidate test) and the fused persistent
+    pipeline (both passes in one cooperative launch over work tiles of any
+    size) change no bit of the state or of the fields."""
     scs = _small_batch()
     ref = _batch(scs)
     ref.step(6)
     t = _batch(scs)
     t.set_tuning(block, use_segments)
+    t.set_particles_per_thread(ppt)
     t.set_pipeline(tile, pblock)
     t.step(6)
     for x, y in zip(ref.get_state(), t.get_state()):
