@@ -462,7 +462,7 @@ cudaError_t launch_cellsort_gather(const unsigned* start, int ncells, const int*
 // more than SLOT_SMALL entries are queued (by the thread of their first
 // slot) for k_cellsort_big.  Suited to grids of small cells (a few particles
 // each).
-constexpr int SLOT_SMALL = 64;
+constexpr int SLOT_SMALL = 128;  // compressed fluid fills h/2 cells with 60-100 particles
 
 __global__ void __launch_bounds__(256)
 k_cellsort_slots(const unsigned* __restrict__ start, const unsigned* __restrict__ key, int n,
