@@ -1505,7 +1505,7 @@ int sph_voxel_density(sph_handle* h, const float* origin, const int* dims, float
 
 struct McLayout {
     long long ncubes;
-    size_t cnt, off, part, total;
+    size_t tile_off, tile_count, count, total;
 };
 
 static int mc_layout(const int* dims, McLayout* L)
@@ -1515,10 +1515,11 @@ static int mc_layout(const int* dims, McLayout* L)
     if ((long long)dims[0] * dims[1] * dims[2] > 2147483647LL || n > 2147483647LL / 5) return SPH_ERR_OVERFLOW;
     L->ncubes = n;
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    L->cnt = 0;
-    L->off = up((size_t)n * sizeof(unsigned));
-    L->part = L->off + up(((size_t)n + 1) * sizeof(unsigned));
-    L->total = L->part + up(((size_t)(n > 0 ? scan_parts((int)n) : 0) + 1) * sizeof(unsigned));
+    const size_t nt = (size_t)(n > 0 ? mc_tiles(n) : 1);
+    L->tile_off = 0;
+    L->tile_count = up(nt * sizeof(unsigned long long));
+    L->count = L->tile_count + up(nt * sizeof(unsigned));
+    L->total = L->count + 256;
     return SPH_OK;
 }
 
@@ -1551,12 +1552,12 @@ int sph_marching_cubes(const float* phi, const int* dims, const float* origin, f
     if (e != cudaSuccess) return fail(nullptr, SPH_ERR_CUDA, "marching-cubes tables: %s", cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t* w = (uint8_t*)workspace;
-    unsigned* off = (unsigned*)(w + L.off);
+    unsigned* count = (unsigned*)(w + L.count);
     long long launches = 0;
-    e = launch_marching_cubes(phi, dims, origin, spacing, iso, (unsigned*)(w + L.cnt), off, (unsigned*)(w + L.part),
-                              tris, (unsigned long long)max_tris, s, &launches);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ntri, off + L.ncubes, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
+    e = launch_marching_cubes(phi, dims, origin, spacing, iso, (unsigned*)(w + L.tile_count),
+                              (unsigned long long*)(w + L.tile_off), count, tris, (unsigned long long)max_tris, s,
+                              &launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ntri, count, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return fail(nullptr, SPH_ERR_CUDA, "marching cubes: %s", cudaGetErrorString(e));
     return SPH_OK;
 }

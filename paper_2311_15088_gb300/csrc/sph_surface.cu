@@ -314,46 +314,27 @@ __device__ __forceinline__ int cube_case(const float* __restrict__ phi, const Mc
     return ci;
 }
 
-__global__ void __launch_bounds__(256)
-k_mc_count(const float* __restrict__ phi, McGrid g, unsigned* __restrict__ cnt)
-{
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int cx = g.nx - 1, cy = g.ny - 1;
-    const long long n = (long long)cx * cy * (g.nz - 1);
-    if (c >= n) return;
-    float val[8];
-    const int ci = cube_case(phi, g, (int)(c % cx), (int)((c / cx) % cy), (int)(c / ((long long)cx * cy)), val);
-    cnt[c] = c_mc_ntri[ci];
-}
-
 // Edge endpoints, the one of smaller coordinate first, and the vertex
 // offsets (bit 0: +x, bit 1: +y, bit 2: +z) of the numbering above.
 __constant__ unsigned char c_mc_lo[12] = {0, 1, 3, 0, 4, 5, 7, 4, 0, 1, 2, 3};
 __constant__ unsigned char c_mc_hi[12] = {1, 2, 2, 3, 5, 6, 6, 7, 4, 5, 6, 7};
 __constant__ unsigned char c_mc_off[8] = {0, 1, 3, 2, 4, 5, 7, 6};
 
-__global__ void __launch_bounds__(256)
-k_mc_emit(const float* __restrict__ phi, McGrid g, const unsigned* __restrict__ off, float* __restrict__ tris,
-          unsigned long long cap)
+// The triangles of cube c (index ii, case ci, corner values val) from
+// output slot o0 on (slots at or past cap are not written).
+__device__ __forceinline__ void mc_emit_cube(const McGrid& g, const int ii[3], int ci, const float val[8],
+                                             unsigned long long o0, float* __restrict__ tris,
+                                             unsigned long long cap)
 {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int cx = g.nx - 1, cy = g.ny - 1;
-    const long long n = (long long)cx * cy * (g.nz - 1);
-    if (c >= n) return;
-    const unsigned o0 = off[c], o1 = off[c + 1];
-    if (o0 == o1) return;
-    const int ii[3] = {(int)(c % cx), (int)((c / cx) % cy), (int)(c / ((long long)cx * cy))};
-    float val[8];
-    const int ci = cube_case(phi, g, ii[0], ii[1], ii[2], val);
     float lo[3], hi[3];  // the cube's corner coordinates, fl(origin + fl(i * spacing))
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         lo[a] = __fadd_rn(__fmul_rn((float)ii[a], g.spacing), g.origin[a]);
         hi[a] = __fadd_rn(__fmul_rn((float)(ii[a] + 1), g.spacing), g.origin[a]);
     }
-    const int nt = (int)(o1 - o0);
+    const int nt = c_mc_ntri[ci];
     for (int k = 0; k < nt; ++k) {
-        const unsigned long long slot = (unsigned long long)o0 + (unsigned long long)k;
+        const unsigned long long slot = o0 + (unsigned long long)k;
         if (slot >= cap) return;
         float* out = tris + 9ull * slot;
         for (int q = 0; q < 3; ++q) {
@@ -372,9 +353,142 @@ k_mc_emit(const float* __restrict__ phi, McGrid g, const unsigned* __restrict__ 
     }
 }
 
+// Marching cubes in three launches, without a wait between blocks: tiles
+// of MC_TILE consecutive cubes (a block each) count their triangles and
+// store the tile's total; one block scans the tile totals into tile
+// offsets (and the grand total); then each tile recounts its cubes, scans
+// them within the block and writes its triangles from its tile's offset.
+// The output is in cube order, as if the counts had been scanned over the
+// whole grid.
+constexpr int MC_T = 256, MC_C = 4, MC_TILE = MC_T * MC_C;
+
+// Cases and triangle counts of this thread's cubes c0 .. c0 + MC_C - 1
+// (beyond n: none); returns the thread's total.
+__device__ __forceinline__ unsigned mc_thread_cases(const float* __restrict__ phi, const McGrid& g, long long n,
+                                                    long long c0, int ci[MC_C])
+{
+    const int cx = g.nx - 1, cy = g.ny - 1;
+    unsigned mine = 0;
+#pragma unroll
+    for (int k = 0; k < MC_C; ++k) {
+        ci[k] = 0;
+        const long long c = c0 + k;
+        if (c < n) {
+            float val[8];
+            ci[k] = cube_case(phi, g, (int)(c % cx), (int)((c / cx) % cy), (int)(c / ((long long)cx * cy)), val);
+            mine += c_mc_ntri[ci[k]];
+        }
+    }
+    return mine;
+}
+
+// Exclusive prefix of v over the block (MC_T threads) and the block total.
+__device__ __forceinline__ unsigned mc_block_scan(unsigned v, unsigned* s_warp, unsigned& total)
+{
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    unsigned inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(FULL, inc, o);
+        if (lane >= (unsigned)o) inc += u;
+    }
+    if (lane == 31u) s_warp[warp] = inc;
+    __syncthreads();
+    unsigned before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < MC_T / 32; ++w) {
+        const unsigned t = s_warp[w];
+        before += (unsigned)w < warp ? t : 0u;
+        all += t;
+    }
+    total = all;
+    return before + inc - v;
+}
+
+__global__ void __launch_bounds__(MC_T)
+k_mc_tile_counts(const float* __restrict__ phi, McGrid g, unsigned* __restrict__ tile_count)
+{
+    __shared__ unsigned s_warp[MC_T / 32];
+    const long long n = (long long)(g.nx - 1) * (g.ny - 1) * (g.nz - 1);
+    int ci[MC_C];
+    const unsigned mine =
+        mc_thread_cases(phi, g, n, (long long)blockIdx.x * MC_TILE + (long long)threadIdx.x * MC_C, ci);
+    unsigned total;
+    mc_block_scan(mine, s_warp, total);
+    if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
+}
+
+// One block: tile_off[t] = sum of tile_count[0 .. t-1] (64-bit), and the
+// grand total (saturated to 0xfffffffe) in *total_out.
+__global__ void __launch_bounds__(1024)
+k_mc_tile_scan(const unsigned* __restrict__ tile_count, int ntiles, unsigned long long* __restrict__ tile_off,
+               unsigned* __restrict__ total_out)
+{
+    __shared__ unsigned long long s_warp[32];
+    __shared__ unsigned long long s_carry;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ntiles; base += 1024) {
+        const int t = base + (int)threadIdx.x;
+        const unsigned long long v = t < ntiles ? tile_count[t] : 0ull;
+        unsigned long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(FULL, inc, o);
+            if (lane >= (unsigned)o) inc += u;
+        }
+        if (lane == 31u) s_warp[warp] = inc;
+        __syncthreads();
+        unsigned long long before = 0, all = 0;
+        for (int w = 0; w < 32; ++w) {
+            const unsigned long long x = s_warp[w];
+            before += (unsigned)w < warp ? x : 0ull;
+            all += x;
+        }
+        const unsigned long long carry = s_carry;
+        if (t < ntiles) tile_off[t] = carry + before + inc - v;
+        __syncthreads();  // every thread has read s_warp and s_carry
+        if (threadIdx.x == 0) s_carry = carry + all;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long tot = s_carry;
+        *total_out = tot > 0xfffffffeull ? 0xfffffffeu : (unsigned)tot;
+    }
+}
+
+__global__ void __launch_bounds__(MC_T)
+k_mc_tile_emit(const float* __restrict__ phi, McGrid g, const unsigned long long* __restrict__ tile_off,
+               float* __restrict__ tris, unsigned long long cap)
+{
+    __shared__ unsigned s_warp[MC_T / 32];
+    const int cx = g.nx - 1, cy = g.ny - 1;
+    const long long n = (long long)cx * cy * (g.nz - 1);
+    const long long c0 = (long long)blockIdx.x * MC_TILE + (long long)threadIdx.x * MC_C;
+    int ci[MC_C];
+    const unsigned mine = mc_thread_cases(phi, g, n, c0, ci);
+    unsigned total;
+    const unsigned excl = mc_block_scan(mine, s_warp, total);
+    unsigned long long o = tile_off[blockIdx.x] + excl;
+#pragma unroll
+    for (int k = 0; k < MC_C; ++k) {
+        const int nt = c_mc_ntri[ci[k]];
+        if (nt == 0) continue;
+        const long long c = c0 + k;
+        const int ii[3] = {(int)(c % cx), (int)((c / cx) % cy), (int)(c / ((long long)cx * cy))};
+        float val[8];
+        cube_case(phi, g, ii[0], ii[1], ii[2], val);
+        mc_emit_cube(g, ii, ci[k], val, o, tris, cap);
+        o += (unsigned long long)nt;
+    }
+}
+
+long long mc_tiles(long long ncubes) { return (ncubes + MC_TILE - 1) / MC_TILE; }
+
 cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const float origin[3], float spacing,
-                                  float iso, unsigned* cnt, unsigned* off, unsigned* part, float* tris,
-                                  unsigned long long cap, cudaStream_t s, long long* launches)
+                                  float iso, unsigned* tile_count, unsigned long long* tile_off, unsigned* total,
+                                  float* tris, unsigned long long cap, cudaStream_t s, long long* launches)
 {
     McGrid g;
     g.nx = dims[0];
@@ -384,16 +498,12 @@ cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const flo
     g.spacing = spacing;
     g.iso = iso;
     const long long n = (long long)(g.nx - 1) * (g.ny - 1) * (g.nz - 1);
-    if (n <= 0) return cudaMemsetAsync(off, 0, sizeof(unsigned), s);
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    k_mc_count<<<blocks, 256, 0, s>>>(phi, g, cnt);
-    ++*launches;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = launch_scan(cnt, (int)n, part, off, s, launches);
-    if (e != cudaSuccess) return e;
-    k_mc_emit<<<blocks, 256, 0, s>>>(phi, g, off, tris, cap);
-    ++*launches;
+    if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(unsigned), s);
+    const long long nt = mc_tiles(n);
+    k_mc_tile_counts<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, tile_count);
+    k_mc_tile_scan<<<1, 1024, 0, s>>>(tile_count, (int)nt, tile_off, total);
+    k_mc_tile_emit<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, tile_off, tris, cap);
+    *launches += 3;
     return cudaGetLastError();
 }
 
