@@ -124,6 +124,8 @@ def _args():
     ap.add_argument("--mlp-throughput", action="store_true",
                     help="only time the surrogate network's forward pass on 65,536 queries (features of "
                          "the 262,144-particle column's 1,024 boids, tiled), untrained weights")
+    ap.add_argument("--cell-x", type=float, default=None,
+                    help="particle-grid cell size along x over h for the main leg (default: the workload's)")
     ap.add_argument("--settle", type=int, default=None,
                     help="settling steps of the large tank before the boids are released (default 200)")
     return ap.parse_args()
@@ -419,6 +421,11 @@ def _oracle_rate(p, fp, fv, bp, bv, step_seconds, min_seconds=0.0, steps=None):
 
 # ------------------------------------------------------------- batched
 
+# Cell shapes the batched leg tries (cell size over h along y and z, along
+# x), each with the autotuner; the fastest is kept.
+CELL_SHAPES = ((0.5, 0.5), (1.0, 1.0), (1.0, 0.5), (1.0, 0.34))
+
+
 def run_batched(a, dev, flush):
     """256 independent tanks in one handle (every pass one launch over all
     scenes, the step replayed from a CUDA graph, launch shape autotuned)
@@ -449,11 +456,12 @@ def run_batched(a, dev, flush):
     cat = lambda key: np.concatenate([sc[key] for sc in scs])
     stream = torch.cuda.Stream(dev)
 
-    def with_cell(frac):
+    def with_cell(frac, frac_x):
         out = []
         for sc in scs:
             q = dict(sc["params"])
             q["cell_size"] = float(np.float32(np.float32(q["h"]) * np.float32(frac)))
+            q["cell_size_x"] = float(np.float32(np.float32(q["h"]) * np.float32(frac_x)))
             out.append(q)
         return out
 
@@ -470,8 +478,8 @@ def run_batched(a, dev, flush):
 
     per_cell = {}
     with torch.cuda.stream(stream):
-        for frac in (0.5, 1.0):
-            ps = with_cell(frac)
+        for frac in CELL_SHAPES:
+            ps = with_cell(*frac)
             b = Scene(ps, nf, nb, device=dev)
             b.set_state(cat("fluid_pos"), cat("fluid_vel"), cat("boid_pos"), cat("boid_vel"))
             best = tune.autotune(b, steps=3, cache=None)
@@ -545,8 +553,8 @@ def run_batched(a, dev, flush):
         "loop_scenes_per_s": S * n_loop / t_loop, "loop_ms_per_step": 1e3 * t_loop / n_loop,
         "speedup_vs_loop": (S * a.batch_steps / t_batch) / (S * n_loop / t_loop),
         "loop": "each scene's own handle replaying its captured step (sph_graph_step), same kernels",
-        "cell_size_over_h": frac,
-        "ms_per_step_by_cell_size": {str(f): 1e3 * v["t"] / a.batch_steps for f, v in per_cell.items()},
+        "cell_size_over_h": frac[0], "cell_size_x_over_h": frac[1],
+        "ms_per_step_by_cell_size": {f"{f[0]}/{f[1]}": 1e3 * v["t"] / a.batch_steps for f, v in per_cell.items()},
         "tuning": {k: best[k] for k in ("block", "use_segments", "ppt", "pipe_tile", "pipe_block", "ms_per_step")},
         "roofline": {
             "alu": {"achieved": flops / (ms * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -875,6 +883,8 @@ def run_ours(a):
         settle = a.settle
         desc = desc.replace(f"settled {SETTLE} steps", f"settled {settle} steps")
     p = _params(sc)
+    if a.cell_x is not None:
+        p["cell_size_x"] = float(np.float32(np.float32(p["h"]) * np.float32(a.cell_x)))
     nf, nb = len(sc["fluid_pos"]), len(sc["boid_pos"])
     z = np.zeros((0, 4), np.float32)
 
@@ -1037,6 +1047,8 @@ def run_ours(a):
                        "l2": "flushed between timed steps (256 MiB write outside the step events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "cell_size_over_h": float(np.float32(p["cell_size"]) / np.float32(p["h"])),
+                       "cell_size_x_over_h": float(np.float32(p.get("cell_size_x") or p["cell_size"])
+                                                   / np.float32(p["h"])),
                        "tuning": {"block": s.tuning[0], "use_segments": s.tuning[1], "ppt": s.ppt},
                        "force_pass_neighbours": "pair lists" if a.neighbor_lists else "walk",
                        "neighbours_mean": statistics.mean(w["nbr_mean"] for w in works),

@@ -112,6 +112,7 @@ typedef struct sph_params {
     float r_sep, r_vis, w_sep, w_align, w_coh, sph_factor, v_min, v_max, edge_turn;
     float boid_cell_size;
     int   coupling_mode;       /* SPH_COUPLE_FORCE (default) or SPH_COUPLE_LITERAL */
+    float cell_size_x;         /* particle-grid cell size along x; 0: cell_size (cubic cells) */
 } sph_params;
 
 typedef struct sph_handle sph_handle;

@@ -50,7 +50,7 @@ class OrParams(ctypes.Structure):
         ("sph_factor", ctypes.c_double), ("v_min", ctypes.c_double),
         ("v_max", ctypes.c_double), ("edge_turn", ctypes.c_double),
         ("boid_cell_size", ctypes.c_double), ("coupling_mode", ctypes.c_int),
-        ("obstacles", ctypes.c_void_p), ("att_vel", ctypes.c_void_p),
+        ("obstacles", ctypes.c_void_p), ("att_vel", ctypes.c_void_p), ("cell_size_x", ctypes.c_double),
     ]
 
 
@@ -131,6 +131,7 @@ def make_params(p: dict) -> OrParams:
     o.box_max[:] = [float(np.float32(v)) for v in p["box_max"]]
     o.const_set = int(p["const_set"])
     o.coupling_mode = int(p["coupling_mode"])
+    o.cell_size_x = float(np.float32(p.get("cell_size_x") or 0.0))
     return o
 
 

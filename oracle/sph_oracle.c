@@ -82,6 +82,7 @@ typedef struct {
     const void *obstacles;  /* const or_obstacles *, or NULL: no obstacle avoidance */
     const float *att_vel;   /* literal coupling: the attached particles' velocities (n_boid x 3)
                                going into the step; NULL: the boids' velocities */
+    double cell_size_x;     /* particle-grid cell size along x; 0: cell_size */
 } or_params;
 
 /* Analytic obstacles standing in for the paper's obstacle meshes (section
@@ -117,26 +118,36 @@ typedef struct {
     int dim[3];
     long ncells;
     float minf[3];
-    float inv_d;
+    float inv_d, inv_dx;    /* 1/d along y and z, 1/dx along x */
 } or_grid;
 
 /* Number of cells per axis: dim = ceil((max - min) / d) (section
- * "Neighborhood Search"; the product dim_x dim_y dim_z is the cell count). */
-static void grid_make(or_grid *g, const double mn[3], const double mx[3], double d)
+ * "Neighborhood Search"; the product dim_x dim_y dim_z is the cell count),
+ * with cell size dx along x and d along y and z. */
+static void grid_make_x(or_grid *g, const double mn[3], const double mx[3], double dx, double d)
 {
     for (int a = 0; a < 3; ++a) {
-        int n = (int)ceil((mx[a] - mn[a]) / d);
+        int n = (int)ceil((mx[a] - mn[a]) / (a == 0 ? dx : d));
         g->dim[a] = n < 1 ? 1 : n;
         g->minf[a] = (float)mn[a];
     }
     g->ncells = (long)g->dim[0] * g->dim[1] * g->dim[2];
     g->inv_d = 1.0f / (float)d;
+    g->inv_dx = 1.0f / (float)dx;
 }
+
+static void grid_make(or_grid *g, const double mn[3], const double mx[3], double d)
+{
+    grid_make_x(g, mn, mx, d, d);
+}
+
+/* The particle grid's cell size along x. */
+static double cell_x(const or_params *p) { return p->cell_size_x > 0.0 ? p->cell_size_x : p->cell_size; }
 
 /* get_cell along one axis: floor((p - m) / d), in float32, clamped. */
 static int cell_coord(const or_grid *g, int a, float x)
 {
-    float t = (x - g->minf[a]) * g->inv_d;
+    float t = (x - g->minf[a]) * (a == 0 ? g->inv_dx : g->inv_d);
     float c = floorf(t);
     if (!(c >= 0.0f)) return 0;
     if (c >= (float)(g->dim[a] - 1)) return g->dim[a] - 1;
@@ -224,7 +235,7 @@ static void force_constants(const or_params *p, double *cp, double *cv)
 typedef struct {
     const or_grid *g;
     const int *perm, *cell_start;
-    int reach;
+    int reach, reach_x;     /* along y and z, along x */
 } or_walk;
 
 static int walk_reach(double h, double d) { return (int)ceil(h / d) + 1; }
@@ -234,10 +245,10 @@ static int walk_reach(double h, double d) { return (int)ceil(h / d) + 1; }
         int cx_ = cell_coord((W)->g, 0, (XI)[0]);                                \
         int cy_ = cell_coord((W)->g, 1, (XI)[1]);                                \
         int cz_ = cell_coord((W)->g, 2, (XI)[2]);                                \
-        const int R_ = (W)->reach;                                               \
+        const int R_ = (W)->reach, RX_ = (W)->reach_x;                           \
         for (int dz_ = -R_; dz_ <= R_; ++dz_)                                    \
             for (int dy_ = -R_; dy_ <= R_; ++dy_)                                \
-                for (int dx_ = -R_; dx_ <= R_; ++dx_) {                          \
+                for (int dx_ = -RX_; dx_ <= RX_; ++dx_) {                        \
                     int x_ = cx_ + dx_, y_ = cy_ + dy_, z_ = cz_ + dz_;          \
                     if (x_ < 0 || x_ >= (W)->g->dim[0] || y_ < 0 ||              \
                         y_ >= (W)->g->dim[1] || z_ < 0 || z_ >= (W)->g->dim[2])  \
@@ -271,7 +282,8 @@ int or_num_threads(void)
 int or_grid_dims(const or_params *p, int which, int dims[3])
 {
     or_grid g;
-    grid_make(&g, p->box_min, p->box_max, which ? p->boid_cell_size : p->cell_size);
+    if (which) grid_make(&g, p->box_min, p->box_max, p->boid_cell_size);
+    else grid_make_x(&g, p->box_min, p->box_max, cell_x(p), p->cell_size);
     for (int a = 0; a < 3; ++a) dims[a] = g.dim[a];
     return 0;
 }
@@ -333,7 +345,8 @@ int or_bin(const or_params *p, int which, int n, const float *pos3,
            unsigned *keys, int *perm, int *cell_start)
 {
     or_grid g;
-    grid_make(&g, p->box_min, p->box_max, which ? p->boid_cell_size : p->cell_size);
+    if (which) grid_make(&g, p->box_min, p->box_max, p->boid_cell_size);
+    else grid_make_x(&g, p->box_min, p->box_max, cell_x(p), p->cell_size);
     counting_sort(&g, n, pos3, keys, perm, cell_start);
     return 0;
 }
@@ -346,12 +359,12 @@ int or_neighbors(const or_params *p, int n, int n_att, const float *pos3,
                  int *counts, const long *offsets, int *list)
 {
     or_grid g;
-    grid_make(&g, p->box_min, p->box_max, p->cell_size);
+    grid_make_x(&g, p->box_min, p->box_max, cell_x(p), p->cell_size);
     unsigned *keys = (unsigned *)malloc(sizeof(unsigned) * (size_t)(n > 0 ? n : 1));
     int *perm = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     int *cs = (int *)malloc(sizeof(int) * (size_t)(g.ncells + 1));
     counting_sort(&g, n, pos3, keys, perm, cs);
-    or_walk w = {&g, perm, cs, walk_reach(p->h, p->cell_size)};
+    or_walk w = {&g, perm, cs, walk_reach(p->h, p->cell_size), walk_reach(p->h, cell_x(p))};
     float hf = (float)p->h, h2f = hf * hf;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < n; ++i) {
@@ -526,7 +539,7 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
     const int literal = p->coupling_mode == 1;
     const int nb = n_boid, n = n_fluid + n_boid;
     or_grid g;
-    grid_make(&g, p->box_min, p->box_max, p->cell_size);
+    grid_make_x(&g, p->box_min, p->box_max, cell_x(p), p->cell_size);
 
     /* 1. attach a particle to every boid: the boid's position; its velocity
      *    is the boid's (force coupling) or the attached particle's own,
@@ -551,7 +564,7 @@ int or_step(const or_params *p, int n_fluid, int n_boid,
     int *perm = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
     int *cs = (int *)malloc(sizeof(int) * (size_t)(g.ncells + 1));
     counting_sort(&g, n, x32, keys, perm, cs);
-    or_walk w = {&g, perm, cs, walk_reach(p->h, p->cell_size)};
+    or_walk w = {&g, perm, cs, walk_reach(p->h, p->cell_size), walk_reach(p->h, cell_x(p))};
     float hf = (float)p->h, h2f = hf * hf;
 
     /* 3. density (self term included) and pressure. */

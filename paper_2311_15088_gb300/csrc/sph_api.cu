@@ -184,11 +184,11 @@ static int fail(sph_handle* h, int code, const char* fmt, ...)
 
 static bool finite_pos(float v) { return isfinite(v) && v > 0.0f; }
 
-int sphk::make_grid(const float mn[3], const float mx[3], float d, GridDesc* g)
+int sphk::make_grid_x(const float mn[3], const float mx[3], float dx, float d, GridDesc* g)
 {
     long long cells = 1;
     for (int a = 0; a < 3; ++a) {
-        double n = ceil(((double)mx[a] - (double)mn[a]) / (double)d);
+        double n = ceil(((double)mx[a] - (double)mn[a]) / (double)(a == 0 ? dx : d));
         if (n < 1.0) n = 1.0;
         if (n > 2147483647.0) return SPH_ERR_OVERFLOW;
         g->dim[a] = (int)n;
@@ -198,8 +198,12 @@ int sphk::make_grid(const float mn[3], const float mx[3], float d, GridDesc* g)
     }
     g->ncells = (int)cells;
     g->inv_d = 1.0f / d;
+    g->inv_dx = 1.0f / dx;
     return SPH_OK;
 }
+
+// The particle grid's cell size along x (cell_size_x, 0: cell_size).
+static float cell_x(const sph_params* p) { return p->cell_size_x > 0.0f ? p->cell_size_x : p->cell_size; }
 
 static int validate(const sph_params* p, int n_fluid, int n_boid)
 {
@@ -210,6 +214,8 @@ static int validate(const sph_params* p, int n_fluid, int n_boid)
         return fail(nullptr, SPH_ERR_ARG, "h, rho0, mass and dt must be finite and > 0");
     if (!(isfinite(p->cell_size) && p->cell_size >= 0.25f * p->h))
         return fail(nullptr, SPH_ERR_ARG, "cell_size must be >= h/4");
+    if (!(isfinite(p->cell_size_x) && (p->cell_size_x == 0.0f || p->cell_size_x >= 0.125f * p->h)))
+        return fail(nullptr, SPH_ERR_ARG, "cell_size_x must be 0 or >= h/8");
     if (!(isfinite(p->k) && p->k >= 0.0f) || !(isfinite(p->mu) && p->mu >= 0.0f))
         return fail(nullptr, SPH_ERR_ARG, "k and mu must be finite and >= 0");
     for (int a = 0; a < 3; ++a)
@@ -233,7 +239,7 @@ static int validate(const sph_params* p, int n_fluid, int n_boid)
           isfinite(p->edge_turn)))
         return fail(nullptr, SPH_ERR_ARG, "boid weights must be finite");
     GridDesc g;
-    if (make_grid(p->box_min, p->box_max, p->cell_size, &g) != SPH_OK)
+    if (make_grid_x(p->box_min, p->box_max, cell_x(p), p->cell_size, &g) != SPH_OK)
         return fail(nullptr, SPH_ERR_OVERFLOW, "particle grid has more than 2^31 cells");
     if (make_grid(p->box_min, p->box_max, p->boid_cell_size, &g) != SPH_OK)
         return fail(nullptr, SPH_ERR_OVERFLOW, "boid grid has more than 2^31 cells");
@@ -244,13 +250,13 @@ static int validate(const sph_params* p, int n_fluid, int n_boid)
 // cells of size d: reach2 = r2 (1 + 1e-5) exceeds the exact squared
 // distance of any pair that passes the float32 predicate, and margin covers
 // the rounding of cell boundaries (8 ulps of the largest coordinate + 1e-5 d).
-static WalkBounds make_bounds(const sph_params* p, float r2, float d)
+static WalkBounds make_bounds(const sph_params* p, float r2, float d, float dx)
 {
     float extent = d;
     for (int a = 0; a < 3; ++a) extent = fmaxf(extent, fmaxf(fabsf(p->box_min[a]), fabsf(p->box_max[a])) + d);
     const float ulp = nextafterf(extent, INFINITY) - extent;
     WalkBounds w;
-    w.margin = 8.0f * ulp + 1e-5f * d;
+    w.margin = 8.0f * ulp + 1e-5f * fminf(d, dx);
     w.reach2 = r2 * (1.0f + 1e-5f);
     w.reach = sqrtf(w.reach2) + w.margin;
     w.d = d;
@@ -260,10 +266,10 @@ static WalkBounds make_bounds(const sph_params* p, float r2, float d)
 static void make_const(const sph_params* p, int n_fluid, int n_boid, StepConst* c)
 {
     memset(c, 0, sizeof(*c));
-    make_grid(p->box_min, p->box_max, p->cell_size, &c->g);
+    make_grid_x(p->box_min, p->box_max, cell_x(p), p->cell_size, &c->g);
     make_grid(p->box_min, p->box_max, p->boid_cell_size, &c->gb);
-    c->wg = make_bounds(p, p->h * p->h, p->cell_size);
-    c->wb = make_bounds(p, p->r_vis * p->r_vis, p->boid_cell_size);
+    c->wg = make_bounds(p, p->h * p->h, p->cell_size, cell_x(p));
+    c->wb = make_bounds(p, p->r_vis * p->r_vis, p->boid_cell_size, p->boid_cell_size);
     c->n = n_fluid + n_boid;
     c->nb = n_boid;  // bases and nb_all are filled in by layout_scenes
     const double pi = 3.14159265358979323846;
@@ -495,7 +501,8 @@ int sph_grid_dims(const sph_params* p, int which, int dims[3])
     GridDesc g;
     float d = which ? p->boid_cell_size : p->cell_size;
     if (!(d > 0.0f)) return fail(nullptr, SPH_ERR_ARG, "cell size must be > 0");
-    if (make_grid(p->box_min, p->box_max, d, &g) != SPH_OK) return fail(nullptr, SPH_ERR_OVERFLOW, "grid too large");
+    if (make_grid_x(p->box_min, p->box_max, which ? d : cell_x(p), d, &g) != SPH_OK)
+        return fail(nullptr, SPH_ERR_OVERFLOW, "grid too large");
     for (int a = 0; a < 3; ++a) dims[a] = g.dim[a];
     return SPH_OK;
 }
@@ -1497,7 +1504,7 @@ int sph_voxel_density(sph_handle* h, const float* origin, const int* dims, float
     v.R2 = radius * radius;
     v.invR2 = (float)(1.0 / (double)v.R2);
     v.r = particle_radius;
-    v.wb = make_bounds(&h->params[0], v.R2, h->params[0].cell_size);
+    v.wb = make_bounds(&h->params[0], v.R2, h->params[0].cell_size, cell_x(&h->params[0]));
     CUDA_TRY(h, launch_voxel_density(h->pos_s, h->cell_start, h->sc, v, phi, counts, s, &h->launches));
     h->has_step = false;
     return SPH_OK;

@@ -13,12 +13,16 @@ namespace sphk {
 constexpr unsigned FULL = 0xffffffffu;
 
 // A uniform grid over the box (section "Neighborhood Search"): dim cells per
-// axis, float32 origin and reciprocal cell size used by get_cell.
+// axis, float32 origin and reciprocal cell sizes used by get_cell (inv_dx
+// along x, inv_d along y and z; equal unless the cells are made narrower
+// along x, the axis along which a row of cells is one contiguous run of
+// sorted slots).
 struct GridDesc {
     int dim[3];
     int ncells;
     float minf[3];
     float inv_d;
+    float inv_dx;
 };
 
 // Conservative search bounds of a grid walk: any particle j with
@@ -85,7 +89,7 @@ __device__ __forceinline__ int cell_coord(float x, float mn, float inv_d, int di
 // hash(c) = c_x + dim_x (c_y + dim_y c_z).
 __device__ __forceinline__ unsigned cell_key(const GridDesc& g, float x, float y, float z, bool* clamped)
 {
-    int cx = cell_coord(x, g.minf[0], g.inv_d, g.dim[0], clamped);
+    int cx = cell_coord(x, g.minf[0], g.inv_dx, g.dim[0], clamped);
     int cy = cell_coord(y, g.minf[1], g.inv_d, g.dim[1], clamped);
     int cz = cell_coord(z, g.minf[2], g.inv_d, g.dim[2], clamped);
     return (unsigned)cx + (unsigned)g.dim[0] * ((unsigned)cy + (unsigned)g.dim[1] * (unsigned)cz);
@@ -210,8 +214,8 @@ struct RowWalk {
             // sqrt(ryz) relatively, far inside margin (>= 1e-5 d, d >= h/4)
             const float xr = fmaf(ryz, rsqrtf(ryz), wb.margin);
             bool cl = false;
-            const int x0 = cell_coord(px - xr, g.minf[0], g.inv_d, g.dim[0], &cl);
-            const int x1 = cell_coord(px + xr, g.minf[0], g.inv_d, g.dim[0], &cl);
+            const int x0 = cell_coord(px - xr, g.minf[0], g.inv_dx, g.dim[0], &cl);
+            const int x1 = cell_coord(px + xr, g.minf[0], g.inv_dx, g.dim[0], &cl);
             const unsigned rowk = (unsigned)g.dim[0] * ((unsigned)yy + (unsigned)g.dim[1] * (unsigned)z);
             s0 = __ldg(start + rowk + x0);
             s1 = __ldg(start + rowk + x1 + 1);
@@ -259,8 +263,8 @@ struct WarpRows {
             if (rz > 0.0f && ryz > 0.0f) {
                 const float xr = fmaf(ryz, rsqrtf(ryz), wb.margin);
                 bool cl = false;
-                const int x0 = cell_coord(px - xr, g.minf[0], g.inv_d, g.dim[0], &cl);
-                const int x1 = cell_coord(px + xr, g.minf[0], g.inv_d, g.dim[0], &cl);
+                const int x0 = cell_coord(px - xr, g.minf[0], g.inv_dx, g.dim[0], &cl);
+                const int x1 = cell_coord(px + xr, g.minf[0], g.inv_dx, g.dim[0], &cl);
                 const unsigned rowk = (unsigned)g.dim[0] * ((unsigned)yy + (unsigned)g.dim[1] * (unsigned)z);
                 s0 = __ldg(start + rowk + x0);
                 s1 = __ldg(start + rowk + x1 + 1);
@@ -318,9 +322,14 @@ int scan_parts(int n);
 cudaError_t launch_scan(const unsigned* counts, int n, unsigned* part, unsigned* start,
                         cudaStream_t s, long long* launches);
 
-// The uniform grid over [mn, mx] with cells of size d (dim = ceil((mx - mn)
-// / d) per axis, inv_d = fl(1 / d)); SPH_ERR_OVERFLOW beyond 2^31 - 2 cells.
-int make_grid(const float mn[3], const float mx[3], float d, GridDesc* g);
+// The uniform grid over [mn, mx] with cells of size dx along x and d along
+// y and z (dim = ceil((mx - mn) / size) per axis, inv = fl(1 / size));
+// SPH_ERR_OVERFLOW beyond 2^31 - 2 cells.  make_grid: dx = d.
+int make_grid_x(const float mn[3], const float mx[3], float dx, float d, GridDesc* g);
+inline int make_grid(const float mn[3], const float mx[3], float d, GridDesc* g)
+{
+    return make_grid_x(mn, mx, d, d, g);
+}
 
 // Cell keys of one grid (the allocation-free binning); err gets
 // SPH_DEV_CLAMPED for a position outside [box_min, box_max] or NaN.

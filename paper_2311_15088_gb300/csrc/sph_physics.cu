@@ -898,14 +898,14 @@ k_bucket_count(const float4* __restrict__ pos, const unsigned* __restrict__ star
     const float4 pi = pos[i];
     const bool att_i = id_of(pi) < sc.nb_all;
     bool cl = false;
-    const int cx = cell_coord(pi.x, c.g.minf[0], c.g.inv_d, c.g.dim[0], &cl);
+    const int cx = cell_coord(pi.x, c.g.minf[0], c.g.inv_dx, c.g.dim[0], &cl);
     const int cy = cell_coord(pi.y, c.g.minf[1], c.g.inv_d, c.g.dim[1], &cl);
     const int cz = cell_coord(pi.z, c.g.minf[2], c.g.inv_d, c.g.dim[2], &cl);
-    const int R = (int)ceilf(c.h * c.g.inv_d);
+    const int R = (int)ceilf(c.h * c.g.inv_d), Rx = (int)ceilf(c.h * c.g.inv_dx);
     int n = 0;
     for (int z = max(cz - R, 0); z <= min(cz + R, c.g.dim[2] - 1); ++z)
         for (int y = max(cy - R, 0); y <= min(cy + R, c.g.dim[1] - 1); ++y)
-            for (int x = max(cx - R, 0); x <= min(cx + R, c.g.dim[0] - 1); ++x) {
+            for (int x = max(cx - Rx, 0); x <= min(cx + Rx, c.g.dim[0] - 1); ++x) {
                 const unsigned key = (unsigned)c.c_base + (unsigned)x +
                                      (unsigned)c.g.dim[0] * ((unsigned)y + (unsigned)c.g.dim[1] * (unsigned)z);
                 const unsigned m = min(__ldg(tracker + key), (unsigned)cap);

@@ -179,7 +179,8 @@ int sph_bin_static(const sph_params* p, int n, const float* pos4, unsigned* keys
         if (!(isfinite(p->box_min[a]) && isfinite(p->box_max[a]) && p->box_max[a] > p->box_min[a]))
             return static_fail(SPH_ERR_ARG, "box_max must exceed box_min on every axis");
     GridDesc g;  // the grid of sph_step's binning
-    if (make_grid(p->box_min, p->box_max, p->cell_size, &g) != SPH_OK || g.ncells > SPH_STATIC_MAX_CELLS) {
+    const float dx = p->cell_size_x > 0.0f ? p->cell_size_x : p->cell_size;
+    if (make_grid_x(p->box_min, p->box_max, dx, p->cell_size, &g) != SPH_OK || g.ncells > SPH_STATIC_MAX_CELLS) {
         snprintf(g_static_msg, sizeof(g_static_msg),
                  "the grid has more than SPH_STATIC_MAX_CELLS = %d cells", SPH_STATIC_MAX_CELLS);
         return static_fail_msg(SPH_ERR_ARG);

@@ -73,8 +73,8 @@ def default_params(**overrides) -> dict:
     h = 0.0457, rest density 1000, gas constant 3, viscosity 3.5, dt = 1e-3,
     gravity -9.8 along y (y is up), cell size h/2 (the grid cell is a free
     parameter of the method; h/2 lets the walk clip each particle's search
-    to its h-sphere), wall restitution 0.75, boid radii 2h / 4h / 4h and the
-    boid weights below.
+    to its h-sphere; cell_size_x = 0: the same along x), wall restitution
+    0.75, boid radii 2h / 4h / 4h and the boid weights below.
     ``mass`` must be supplied by the caller (it depends on the layout).
     """
     h = f32(0.0457)
@@ -88,7 +88,7 @@ def default_params(**overrides) -> dict:
         w_sep=f32(0.05), w_align=f32(0.05), w_coh=f32(0.005),
         sph_factor=1.0, v_min=f32(0.05), v_max=1.0, edge_turn=f32(0.05),
         boid_cell_size=f32(np.float32(4) * np.float32(h)),
-        coupling_mode=0,
+        coupling_mode=0, cell_size_x=0.0,
     )
     p.update(overrides)
     for key, val in list(p.items()):
@@ -203,10 +203,13 @@ def large_tank(seed_offset=0, n=2_097_152, n_boid=16_384, n_schools=8):
     """2,097,152 particles uniform in the lower 40% ([0,4]x[0,0.8]x[0,2]) of
     a 4x2x2 tank, mass = rest density * fluid volume / n.  The boids (8
     schools) are returned separately; the workload settles the fluid first
-    and releases them afterwards."""
+    and releases them afterwards.  The grid's cells are h/2 along y and z
+    and h/8 along x (a row of cells is one run of sorted slots, so narrow x
+    cells clip each row of a particle's walk closer to its h-sphere)."""
     lo, hi = (0.0, 0.0, 0.0), (4.0, 0.8, 2.0)
     vol = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2])
-    p = default_params(box_max=(4.0, 2.0, 2.0), mass=f32(1000.0 * vol / n))
+    h = np.float32(default_params()["h"])
+    p = default_params(box_max=(4.0, 2.0, 2.0), mass=f32(1000.0 * vol / n), cell_size_x=f32(h / np.float32(8)))
     seed = BASE_SEED + 2 + seed_offset
     rng = PaperHashRNG(seed, n_boid + np.arange(n))
     pos = uniform_block(lo, hi, rng)

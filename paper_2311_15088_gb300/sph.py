@@ -49,7 +49,7 @@ class SphParams(ctypes.Structure):
         ("r_sep", ctypes.c_float), ("r_vis", ctypes.c_float), ("w_sep", ctypes.c_float),
         ("w_align", ctypes.c_float), ("w_coh", ctypes.c_float), ("sph_factor", ctypes.c_float),
         ("v_min", ctypes.c_float), ("v_max", ctypes.c_float), ("edge_turn", ctypes.c_float),
-        ("boid_cell_size", ctypes.c_float), ("coupling_mode", ctypes.c_int),
+        ("boid_cell_size", ctypes.c_float), ("coupling_mode", ctypes.c_int), ("cell_size_x", ctypes.c_float),
     ]
 
 
@@ -139,6 +139,8 @@ def make_params(p: dict) -> SphParams:
             getattr(s, name)[:] = [float(v) for v in p[name]]
         elif ctype is ctypes.c_int:
             setattr(s, name, int(p[name]))
+        elif name == "cell_size_x":
+            setattr(s, name, float(p.get(name, 0.0)))
         else:
             setattr(s, name, float(p[name]))
     return s

@@ -43,6 +43,19 @@ def test_dam_break_4096_first_step(cell):
     _check(p, sc)
 
 
+@pytest.mark.parametrize("cell,cell_x", [(0.5, 0.25), (1.0, 0.5), (0.5, 0.125)])
+def test_narrow_x_cells_first_step(cell, cell_x):
+    """Cells narrower along x than along y and z: keys, order, neighbour
+    sets and every field of the step as with cubic cells."""
+    sc = scenes.scaled_block(12000, 300, (0.6, 0.6, 0.6), (0.6, 0.4, 0.6), seed=78)
+    sc["boid_pos"][:, 1] *= np.float32(0.4 / 0.6)
+    p = dict(sc["params"])
+    p["cell_size"] = scenes.f32(p["h"] * cell)
+    p["cell_size_x"] = scenes.f32(p["h"] * cell_x)
+    _s, _g, o = _check(p, sc)
+    assert o["touched"].sum() > 1000
+
+
 def test_dam_break_4096_after_80_gpu_steps():
     """Run the GPU 80 steps (the column collapses and compresses), then one
     more step on the GPU and in the oracle from the GPU's state."""

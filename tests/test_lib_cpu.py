@@ -57,7 +57,8 @@ def test_workspace_size_grows_with_particles(lib):
 @pytest.mark.parametrize("bad", [
     dict(h=0.0), dict(cell_size=0.01), dict(mass=-1.0), dict(dt=0.0), dict(box_max=(0.0, 1.0, 1.0)),
     dict(const_set=7), dict(coupling_mode=2), dict(boid_cell_size=0.04), dict(r_sep=0.5),
-    dict(v_min=2.0), dict(k=float("nan")), dict(wall_restitution=-1.0),
+    dict(v_min=2.0), dict(k=float("nan")), dict(wall_restitution=-1.0), dict(cell_size_x=0.001),
+    dict(cell_size_x=float("inf")),
 ])
 def test_invalid_parameters_are_rejected(lib, bad):
     with pytest.raises(lib.SphError) as e:
@@ -82,6 +83,10 @@ def test_grid_dims_match_oracle(lib, orc):
     assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0), cell_size=h), 0) == (88, 44, 44)
     assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0)), 0) == (176, 88, 88)
     assert lib.sph_grid_dims(_p(box_max=(4.0, 2.0, 2.0)), 1) == (22, 11, 11)
+    q = _p(box_max=(4.0, 2.0, 2.0), cell_size_x=h / 4)
+    dx = np.float64(np.float32(q["cell_size_x"]))
+    assert lib.sph_grid_dims(q, 0) == orc.grid_dims(q, 0) == (int(np.ceil(4.0 / dx)), 88, 88)
+    assert lib.sph_grid_dims(q, 1) == (22, 11, 11)  # the boid grid keeps cubic cells
 
 
 @pytest.mark.parametrize("spacing", [0.02285, 1.0 / 64, 0.03])

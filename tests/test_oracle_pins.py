@@ -122,6 +122,44 @@ def test_grid_neighbors_equal_brute_force(orc, n, n_att, cell):
             assert not any(j < n_att for j in l1[o1[i]:o1[i + 1]])
 
 
+@pytest.mark.parametrize("cell,cell_x", [(0.5, 0.25), (1.0, 0.2), (0.34, 0.125)])
+def test_grid_neighbors_equal_brute_force_narrow_x_cells(orc, cell, cell_x):
+    """Cells narrower along x than along y and z (the walk then reaches
+    ceil(h / dx) + 1 cells along x): still exactly the all-pairs set, with
+    particles squeezed into the corners."""
+    sc = scenes.scaled_block(2000, 20, (1.0, 1.0, 1.0), (1.0, 1.0, 1.0), seed=9)
+    pos = sc["fluid_pos"].copy()
+    k = 600
+    pos[:k, :3] = np.where(pos[:k, :3] < 0.5, pos[:k, :3] * 0.08, 1.0 - (1.0 - pos[:k, :3]) * 0.08)
+    h = sc["params"]["h"]
+    p = dict(sc["params"], cell_size=scenes.f32(h * cell), cell_size_x=scenes.f32(h * cell_x))
+    c1, o1, l1 = orc.neighbors(p, pos, 20)
+    c2, o2, l2 = orc.neighbors(p, pos, 20, brute=True)
+    assert np.array_equal(c1, c2)
+    assert _sets(c1, o1, l1) == _sets(c2, o2, l2)
+    assert c1.sum() > 10 * len(pos)
+
+
+def test_narrow_x_cells_sort_by_the_x_cell(orc):
+    """With cells h/4 wide along x and h/2 along y and z, a particle's key
+    is floor((x - m) / dx) + dim_x (floor((y - m) / d) + dim_y floor((z - m)
+    / d)) in float32, and dim_x = ceil(extent / dx)."""
+    p = _params()
+    h = np.float32(p["h"])
+    p = dict(p, cell_size=scenes.f32(h / 2), cell_size_x=scenes.f32(h / 4), box_max=(1.0, 0.5, 0.5))
+    dims = orc.grid_dims(p, 0)
+    assert dims[0] == int(np.ceil(1.0 / np.float64(np.float32(h / 4))))
+    assert dims[1] == int(np.ceil(0.5 / np.float64(np.float32(h / 2))))
+    rng = np.random.default_rng(3)
+    pos = _p4(rng.uniform(0.0, [1.0, 0.5, 0.5], size=(500, 3)).astype(np.float32))
+    keys, perm, cs = orc.bin_particles(p, pos)
+    inv_dx, inv_d = np.float32(1) / np.float32(h / 4), np.float32(1) / np.float32(h / 2)
+    cx = np.minimum(np.floor(pos[:, 0] * inv_dx), dims[0] - 1).astype(np.int64)
+    cy = np.minimum(np.floor(pos[:, 1] * inv_d), dims[1] - 1).astype(np.int64)
+    cz = np.minimum(np.floor(pos[:, 2] * inv_d), dims[2] - 1).astype(np.int64)
+    assert np.array_equal(keys, cx + dims[0] * (cy + dims[1] * cz))
+
+
 def test_lattice_ties_at_exactly_h(orc):
     """Unjittered lattice of spacing h/2: pairs at exactly r = h in real
     arithmetic are decided by the float predicate; grid and brute force agree."""
