@@ -1512,7 +1512,7 @@ int sph_voxel_density(sph_handle* h, const float* origin, const int* dims, float
 
 struct McLayout {
     long long ncubes;
-    size_t tile_off, tile_count, count, total;
+    size_t tile_off, tile_count, count, cases, total;
 };
 
 static int mc_layout(const int* dims, McLayout* L)
@@ -1526,7 +1526,8 @@ static int mc_layout(const int* dims, McLayout* L)
     L->tile_off = 0;
     L->tile_count = up(nt * sizeof(unsigned long long));
     L->count = L->tile_count + up(nt * sizeof(unsigned));
-    L->total = L->count + 256;
+    L->cases = L->count + 256;
+    L->total = L->cases + up((size_t)(n > 0 ? n : 1));
     return SPH_OK;
 }
 
@@ -1561,7 +1562,7 @@ int sph_marching_cubes(const float* phi, const int* dims, const float* origin, f
     uint8_t* w = (uint8_t*)workspace;
     unsigned* count = (unsigned*)(w + L.count);
     long long launches = 0;
-    e = launch_marching_cubes(phi, dims, origin, spacing, iso, (unsigned*)(w + L.tile_count),
+    e = launch_marching_cubes(phi, dims, origin, spacing, iso, (unsigned char*)(w + L.cases), (unsigned*)(w + L.tile_count),
                               (unsigned long long*)(w + L.tile_off), count, tris, (unsigned long long)max_tris, s,
                               &launches);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ntri, count, sizeof(unsigned), cudaMemcpyDeviceToDevice, s);

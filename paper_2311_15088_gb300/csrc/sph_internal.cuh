@@ -495,14 +495,15 @@ cudaError_t launch_voxel_density(const float4* pos, const unsigned* start, const
 int mc_tables_host(unsigned short* edge, signed char* tri);
 // Copy the tables to the current device's constant memory (once per device).
 cudaError_t mc_upload_tables();
-// Tiles of consecutive cubes: per-tile counts, one scan of the tile
-// totals, then the triangles from each tile's offset (three launches).
-// tile_count and tile_off hold mc_tiles(ncubes) words; *total receives the
-// triangle count.
+// Tiles of consecutive cubes: per-tile counts (each cube's case byte kept
+// in cases[ncubes]), one scan of the tile totals, then the triangles from
+// each tile's offset (three launches).  tile_count and tile_off hold
+// mc_tiles(ncubes) words; *total receives the triangle count.
 long long mc_tiles(long long ncubes);
 cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const float origin[3], float spacing,
-                                  float iso, unsigned* tile_count, unsigned long long* tile_off, unsigned* total,
-                                  float* tris, unsigned long long cap, cudaStream_t s, long long* launches);
+                                  float iso, unsigned char* cases, unsigned* tile_count,
+                                  unsigned long long* tile_off, unsigned* total, float* tris,
+                                  unsigned long long cap, cudaStream_t s, long long* launches);
 
 // Per-scene step statistics (sph_stats): blocks of STATS_CHUNK slots write
 // STATS_PART float64 partials each (part: S x chunks x STATS_PART), one block

@@ -363,9 +363,9 @@ __device__ __forceinline__ void mc_emit_cube(const McGrid& g, const int ii[3], i
 constexpr int MC_T = 256, MC_C = 4, MC_TILE = MC_T * MC_C;
 
 // Cases and triangle counts of this thread's cubes c0 .. c0 + MC_C - 1
-// (beyond n: none); returns the thread's total.
+// (beyond n: none); returns the thread's total and stores each case byte.
 __device__ __forceinline__ unsigned mc_thread_cases(const float* __restrict__ phi, const McGrid& g, long long n,
-                                                    long long c0, int ci[MC_C])
+                                                    long long c0, int ci[MC_C], unsigned char* __restrict__ cases)
 {
     const int cx = g.nx - 1, cy = g.ny - 1;
     unsigned mine = 0;
@@ -376,6 +376,7 @@ __device__ __forceinline__ unsigned mc_thread_cases(const float* __restrict__ ph
         if (c < n) {
             float val[8];
             ci[k] = cube_case(phi, g, (int)(c % cx), (int)((c / cx) % cy), (int)(c / ((long long)cx * cy)), val);
+            cases[c] = (unsigned char)ci[k];
             mine += c_mc_ntri[ci[k]];
         }
     }
@@ -406,13 +407,14 @@ __device__ __forceinline__ unsigned mc_block_scan(unsigned v, unsigned* s_warp, 
 }
 
 __global__ void __launch_bounds__(MC_T)
-k_mc_tile_counts(const float* __restrict__ phi, McGrid g, unsigned* __restrict__ tile_count)
+k_mc_tile_counts(const float* __restrict__ phi, McGrid g, unsigned char* __restrict__ cases,
+                 unsigned* __restrict__ tile_count)
 {
     __shared__ unsigned s_warp[MC_T / 32];
     const long long n = (long long)(g.nx - 1) * (g.ny - 1) * (g.nz - 1);
     int ci[MC_C];
     const unsigned mine =
-        mc_thread_cases(phi, g, n, (long long)blockIdx.x * MC_TILE + (long long)threadIdx.x * MC_C, ci);
+        mc_thread_cases(phi, g, n, (long long)blockIdx.x * MC_TILE + (long long)threadIdx.x * MC_C, ci, cases);
     unsigned total;
     mc_block_scan(mine, s_warp, total);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
@@ -459,15 +461,20 @@ k_mc_tile_scan(const unsigned* __restrict__ tile_count, int ntiles, unsigned lon
 }
 
 __global__ void __launch_bounds__(MC_T)
-k_mc_tile_emit(const float* __restrict__ phi, McGrid g, const unsigned long long* __restrict__ tile_off,
-               float* __restrict__ tris, unsigned long long cap)
+k_mc_tile_emit(const float* __restrict__ phi, McGrid g, const unsigned char* __restrict__ cases,
+               const unsigned long long* __restrict__ tile_off, float* __restrict__ tris, unsigned long long cap)
 {
     __shared__ unsigned s_warp[MC_T / 32];
     const int cx = g.nx - 1, cy = g.ny - 1;
     const long long n = (long long)cx * cy * (g.nz - 1);
     const long long c0 = (long long)blockIdx.x * MC_TILE + (long long)threadIdx.x * MC_C;
     int ci[MC_C];
-    const unsigned mine = mc_thread_cases(phi, g, n, c0, ci);
+    unsigned mine = 0;  // the cases the count pass stored
+#pragma unroll
+    for (int k = 0; k < MC_C; ++k) {
+        ci[k] = c0 + k < n ? (int)__ldg(cases + c0 + k) : 0;
+        mine += c_mc_ntri[ci[k]];
+    }
     unsigned total;
     const unsigned excl = mc_block_scan(mine, s_warp, total);
     unsigned long long o = tile_off[blockIdx.x] + excl;
@@ -487,8 +494,9 @@ k_mc_tile_emit(const float* __restrict__ phi, McGrid g, const unsigned long long
 long long mc_tiles(long long ncubes) { return (ncubes + MC_TILE - 1) / MC_TILE; }
 
 cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const float origin[3], float spacing,
-                                  float iso, unsigned* tile_count, unsigned long long* tile_off, unsigned* total,
-                                  float* tris, unsigned long long cap, cudaStream_t s, long long* launches)
+                                  float iso, unsigned char* cases, unsigned* tile_count,
+                                  unsigned long long* tile_off, unsigned* total, float* tris,
+                                  unsigned long long cap, cudaStream_t s, long long* launches)
 {
     McGrid g;
     g.nx = dims[0];
@@ -500,9 +508,9 @@ cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const flo
     const long long n = (long long)(g.nx - 1) * (g.ny - 1) * (g.nz - 1);
     if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(unsigned), s);
     const long long nt = mc_tiles(n);
-    k_mc_tile_counts<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, tile_count);
+    k_mc_tile_counts<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, cases, tile_count);
     k_mc_tile_scan<<<1, 1024, 0, s>>>(tile_count, (int)nt, tile_off, total);
-    k_mc_tile_emit<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, tile_off, tris, cap);
+    k_mc_tile_emit<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, cases, tile_off, tris, cap);
     *launches += 3;
     return cudaGetLastError();
 }
