@@ -93,10 +93,10 @@ BYTES_PER_CELL_SCAN = 12
 # --no-batch --no-surrogate --no-surface`, mean over the 21 launches of the
 # timed steps after 200 settling steps (k_forces: the fluid launches).
 KERNEL_TRAFFIC = {
-    "k_forces": {"bytes": 740.7e6, "read": 667.0e6, "write": 73.7e6,
-                 "source_sha256": "ef49e7f402f63b2207cf486b78b103b84de88adf4e8dae2c7a4fb4c9ed228ecf"},
-    "k_density": {"bytes": 889.2e6, "read": 286.5e6, "write": 602.7e6,
-                  "source_sha256": "ef49e7f402f63b2207cf486b78b103b84de88adf4e8dae2c7a4fb4c9ed228ecf"},
+    "k_forces": {"bytes": 720.3e6, "read": 642.9e6, "write": 77.4e6,
+                 "source_sha256": "1b3aeb22006f35fc5dede13736a1a9b6efe583cc18787b1105b07cad88f8ad48"},
+    "k_density": {"bytes": 864.4e6, "read": 289.5e6, "write": 574.9e6,
+                  "source_sha256": "1b3aeb22006f35fc5dede13736a1a9b6efe583cc18787b1105b07cad88f8ad48"},
 }
 
 
