@@ -67,6 +67,8 @@ extern "C" {
 #define SPH_DEV_CLAMPED   2u  /* a fluid position lay outside the tank (or was NaN) when binned; its cell was clamped */
 #define SPH_DEV_TIMEOUT   4u  /* a bounded wait inside a kernel gave up          */
 #define SPH_DEV_LIST_OVERFLOW 8u /* a neighbour list did not fit the pair buffer  */
+#define SPH_DEV_BOUNDS   16u  /* bounds-checked builds only: a sorted-slot index of a walk or of
+                                 a hit segment was out of range; the access was skipped   */
 
 /* Fields that sph_get_fields can return (one per call). */
 #define SPH_FIELD_RHO         0  /* float[n_tot]   density, by particle id                 */
@@ -523,6 +525,15 @@ int sph_mlp_get_params(sph_mlp* m, float* params, void* stream);
  * a reference.  Errors: SPH_ERR_ARG (NULL pointer), SPH_ERR_CUDA.
  */
 int sph_mlp_get_optimizer_state(sph_mlp* m, float* grads, float* m1, float* m2, long long* step, void* stream);
+/*
+ * Restore the Adam moments and step count of a checkpoint (after
+ * sph_mlp_set_params, which resets them): with the parameters, m1, m2 and
+ * step as sph_mlp_get_optimizer_state gave them, the next train steps are
+ * bit for bit those the saved network would have taken.  Device FP32
+ * vectors of SPH_MLP_PARAMS, copied on `stream`.  Errors: SPH_ERR_ARG (NULL
+ * pointer, step < 0), SPH_ERR_CUDA.
+ */
+int sph_mlp_set_optimizer_state(sph_mlp* m, const float* m1, const float* m2, long long step, void* stream);
 /* y[B][16] = MLP(x[B][272]) (device buffers; x 16-byte aligned). */
 int sph_mlp_forward(sph_mlp* m, const void* x_bf16, int B, float* y, void* stream);
 /* Parameter gradients of sum(dy * y) for an upstream gradient dy[B][16]

@@ -12,6 +12,17 @@ namespace sphk {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Bounds checks of the bounds-checked build (compiled with -DSPH_CHECK, a
+// stand-in for a memory sanitizer): an index i outside [0, n) sets
+// SPH_DEV_BOUNDS in the error word and the access is skipped.  In the
+// normal build the check compiles to nothing.
+#ifdef SPH_CHECK
+#define SPH_IN_BOUNDS(i, n, err) \
+    ((unsigned)(i) < (unsigned)(n) ? true : (atomicOr((err), SPH_DEV_BOUNDS), false))
+#else
+#define SPH_IN_BOUNDS(i, n, err) true
+#endif
+
 // A uniform grid over the box (section "Neighborhood Search"): dim cells per
 // axis, float32 origin and reciprocal cell sizes used by get_cell (inv_dx
 // along x, inv_d along y and z; equal unless the cells are made narrower

@@ -1094,6 +1094,18 @@ int sph_mlp_get_optimizer_state(sph_mlp* m, float* grads, float* m1, float* m2, 
     return SPH_OK;
 }
 
+int sph_mlp_set_optimizer_state(sph_mlp* m, const float* m1, const float* m2, long long step, void* stream)
+{
+    if (!m || !m1 || !m2) return mfail(m, SPH_ERR_ARG, "NULL argument");
+    if (step < 0) return mfail(m, SPH_ERR_ARG, "step must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(float) * SPH_MLP_PARAMS;
+    MLP_TRY(m, cudaMemcpyAsync(m->Mo, m1, bytes, cudaMemcpyDeviceToDevice, s));
+    MLP_TRY(m, cudaMemcpyAsync(m->Vo, m2, bytes, cudaMemcpyDeviceToDevice, s));
+    m->step = step;
+    return SPH_OK;
+}
+
 int sph_mlp_get_params(sph_mlp* m, float* params, void* stream)
 {
     if (!m || !params) return mfail(m, SPH_ERR_ARG, "NULL argument");

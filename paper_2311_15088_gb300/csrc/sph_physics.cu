@@ -125,6 +125,7 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
         int ns = 0;
         uint2* __restrict__ mine = SEG ? seg + (size_t)i * SEG_CAP : nullptr;
         while (walk.next(s0, s1)) {
+            if (!SPH_IN_BOUNDS(s1 - 1u, sc.n_all, err)) break;  // the row's last slot
             nc += (int)(s1 - s0);
             if (SEG) {
                 for (unsigned b = s0; b < s1; b += 32u) {
@@ -144,6 +145,7 @@ __device__ __forceinline__ void density_at(int i, const float4* __restrict__ pos
         if (SEG) nseg[i] = ns;
     } else {
         while (walk.next(s0, s1)) {
+            if (!SPH_IN_BOUNDS(s1 - 1u, sc.n_all, err)) break;
             for (unsigned j = s0; j < s1; ++j) {
                 const float4 pj = __ldg(pos + j);
                 const float r2 =
@@ -491,6 +493,7 @@ __device__ __forceinline__ void force_particle(const ForceArgs& a, int i)
         // one neighbour j (r2 < h2) from its record (one 32-byte load); the
         // particle itself and coincident particles (r2 = 0) add nothing
         auto pair = [&](unsigned j) {
+            if (!SPH_IN_BOUNDS(j, sc.n_all, err)) return;  // a hit segment's slot
             float4 q0, q1;
             ld_rec<COH>(prec + 2 * (size_t)j, q0, q1);
             const float2 dxy = dxy_of(q0, nxy);

@@ -15,7 +15,9 @@ import os
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsph_gb300.so")
+# SPH_GB300_LIB may name the bounds-checked build of the same library
+_LIB_PATH = os.environ.get("SPH_GB300_LIB") or os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                             "libsph_gb300.so")
 if not os.path.exists(_LIB_PATH):
     raise ImportError(f"{_LIB_PATH} is missing: build it with `python -m paper_2311_15088_gb300.build`")
 _lib = ctypes.CDLL(_LIB_PATH)
@@ -23,7 +25,7 @@ _lib = ctypes.CDLL(_LIB_PATH)
 SPH_OK, SPH_ERR_ARG, SPH_ERR_CUDA, SPH_ERR_OVERFLOW, SPH_ERR_TIMEOUT, SPH_ERR_STATE = range(6)
 SPH_MULLER3D, SPH_PAPER_LITERAL = 0, 1
 SPH_COUPLE_FORCE, SPH_COUPLE_LITERAL = 0, 1
-SPH_DEV_NONFINITE, SPH_DEV_CLAMPED, SPH_DEV_TIMEOUT = 1, 2, 4
+SPH_DEV_NONFINITE, SPH_DEV_CLAMPED, SPH_DEV_TIMEOUT, SPH_DEV_LIST_OVERFLOW, SPH_DEV_BOUNDS = 1, 2, 4, 8, 16
 SPH_BOID_EXACT, SPH_BOID_SURROGATE, SPH_BOID_SURROGATE_FALLBACK, SPH_BOID_EXACT_LOCAL = 0, 1, 2, 3
 SPH_MAX_OBSTACLES = 256
 SPH_STATS_N = 12
@@ -92,6 +94,7 @@ _sig = {
     "sph_mlp_set_params": (_i, [_vp, _vp, _vp]),
     "sph_mlp_get_params": (_i, [_vp, _vp, _vp]),
     "sph_mlp_get_optimizer_state": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
+    "sph_mlp_set_optimizer_state": (_i, [_vp, _vp, _vp, ctypes.c_longlong, _vp]),
     "sph_mlp_forward": (_i, [_vp, _vp, _i, _vp, _vp]),
     "sph_mlp_gradients": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
     "sph_mlp_train_step": (_i, [_vp, _vp, _vp, _i, _i, ctypes.c_float, _vp, _vp]),
@@ -358,6 +361,10 @@ def sph_mlp_get_params(m, params_ptr: int, stream: int):
     _check(_lib.sph_mlp_get_params(m, params_ptr, stream))
 
 
+def sph_mlp_set_optimizer_state(m, m1_ptr: int, m2_ptr: int, step: int, stream: int):
+    _check(_lib.sph_mlp_set_optimizer_state(m, m1_ptr, m2_ptr, int(step), stream))
+
+
 def sph_mlp_get_optimizer_state(m, grads_ptr: int, m1_ptr: int, m2_ptr: int, stream: int) -> int:
     step = ctypes.c_longlong()
     _check(_lib.sph_mlp_get_optimizer_state(m, grads_ptr, m1_ptr, m2_ptr, ctypes.byref(step), stream))
@@ -525,6 +532,24 @@ class Mlp:
         g, m1, m2 = (t.empty(SPH_MLP_PARAMS, dtype=t.float32, device=self.device) for _ in range(3))
         step = sph_mlp_get_optimizer_state(self.handle, g.data_ptr(), m1.data_ptr(), m2.data_ptr(), self.stream)
         return g, m1, m2, step
+
+    def state_dict(self):
+        """A training checkpoint of plain tensors (device copies): the FP32
+        parameters, both Adam moments and the step count."""
+        _g, m1, m2, step = self.optimizer_state()
+        return {"params": self.get_params(), "adam_m1": m1, "adam_m2": m2,
+                "adam_step": self.torch.tensor(step, dtype=self.torch.int64)}
+
+    def load_state_dict(self, sd):
+        """Restore a checkpoint of state_dict: later train steps are bit for
+        bit those the saved network would have taken."""
+        t = self.torch
+        self.set_params(sd["params"])
+        m1 = t.as_tensor(sd["adam_m1"], dtype=t.float32, device=self.device).contiguous()
+        m2 = t.as_tensor(sd["adam_m2"], dtype=t.float32, device=self.device).contiguous()
+        assert m1.numel() == SPH_MLP_PARAMS and m2.numel() == SPH_MLP_PARAMS
+        self._moments = (m1, m2)  # alive until the copies on the stream have run
+        sph_mlp_set_optimizer_state(self.handle, m1.data_ptr(), m2.data_ptr(), int(sd["adam_step"]), self.stream)
 
     def forward(self, x):
         xp, B = self._pad(x, SPH_MLP_IN, self.torch.bfloat16)

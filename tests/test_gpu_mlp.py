@@ -285,3 +285,30 @@ def test_train_steps_match_oracle_adam(phase):
         assert np.array_equal(w[~tr], w_prev[~tr])
         assert np.array_equal(m1[~tr], m_prev[~tr]) and np.array_equal(m2[~tr], v_prev[~tr])
         w_prev, m_prev, v_prev = w, m1, m2
+
+
+def test_checkpoint_resumes_training_bit_for_bit(tmp_path):
+    """Two Adam steps, a checkpoint (state_dict through torch.save), two more
+    steps; a fresh network loaded from the checkpoint takes the same two
+    steps: parameters and both moments bit for bit equal."""
+    B, lr = 256, 1e-3
+    x = _bf16(_inputs(B, 52)).cuda()
+    rng = np.random.default_rng(53)
+    t = torch.from_numpy(rng.normal(size=(B, 4)).astype(np.float32)).cuda()
+    a = sph.Mlp(B)
+    a.set_params(torch.from_numpy(_pack(_oracle_params_bf16(51))))
+    for _ in range(2):
+        a.train_step(x, t, lr)
+    path = tmp_path / "mlp.pt"
+    torch.save({k: v.cpu() for k, v in a.state_dict().items()}, path)
+    for _ in range(2):
+        a.train_step(x, t, lr)
+    b = sph.Mlp(B)
+    b.load_state_dict(torch.load(path))
+    for _ in range(2):
+        b.train_step(x, t, lr)
+    sa, sb = a.state_dict(), b.state_dict()
+    assert int(sa["adam_step"]) == int(sb["adam_step"]) == 4
+    for k in ("params", "adam_m1", "adam_m2"):
+        assert torch.equal(sa[k], sb[k]), k
+    assert a.status() == 0 and b.status() == 0

@@ -28,7 +28,7 @@ def _check(p, sc):
     g = gpu_outputs(s)
     o = oracle_step(p, sc)
     compare_step(p, g, o, nb)
-    assert s.status() & 1 == 0
+    assert s.status() & (sph.SPH_DEV_NONFINITE | sph.SPH_DEV_BOUNDS) == 0
     return s, g, o
 
 
