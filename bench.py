@@ -93,10 +93,10 @@ BYTES_PER_CELL_SCAN = 12
 # --no-batch --no-surrogate --no-surface`, mean over the 21 launches of the
 # timed steps after 200 settling steps (k_forces: the fluid launches).
 KERNEL_TRAFFIC = {
-    "k_forces": {"bytes": 720.3e6, "read": 642.9e6, "write": 77.4e6,
-                 "source_sha256": "1b3aeb22006f35fc5dede13736a1a9b6efe583cc18787b1105b07cad88f8ad48"},
-    "k_density": {"bytes": 864.4e6, "read": 289.5e6, "write": 574.9e6,
-                  "source_sha256": "1b3aeb22006f35fc5dede13736a1a9b6efe583cc18787b1105b07cad88f8ad48"},
+    "k_forces": {"bytes": 720.4e6, "read": 643.0e6, "write": 77.4e6,
+                 "source_sha256": "6b796b8c825557b856e8bbf3bfed9d904664eaa34e59dceed01518a5c17eb9c8"},
+    "k_density": {"bytes": 864.2e6, "read": 289.4e6, "write": 574.8e6,
+                  "source_sha256": "6b796b8c825557b856e8bbf3bfed9d904664eaa34e59dceed01518a5c17eb9c8"},
 }
 
 

@@ -360,7 +360,7 @@ __device__ __forceinline__ void mc_emit_cube(const McGrid& g, const int ii[3], i
 // them within the block and writes its triangles from its tile's offset.
 // The output is in cube order, as if the counts had been scanned over the
 // whole grid.
-constexpr int MC_T = 256, MC_C = 4, MC_TILE = MC_T * MC_C;
+constexpr int MC_T = 256, MC_C = 1, MC_TILE = MC_T * MC_C;
 
 // Cases and triangle counts of this thread's cubes c0 .. c0 + MC_C - 1
 // (beyond n: none); returns the thread's total and stores each case byte.

@@ -88,7 +88,7 @@ def _field(seed, dims, kind):
                                            ("noise", (65, 2, 9), 0.05), ("spheres", (103, 101, 99), 0.0)])
 def test_marching_cubes_matches_oracle(kind, dims, iso):
     """Count, order and vertices against the oracle; the last grid has
-    about a million cubes (about a thousand tiles of the tile scan)."""
+    about a million cubes (about four thousand tiles of the tile scan)."""
     phi = _field(len(kind) + dims[0], dims, kind)
     origin, sp = np.array([-1.0, -0.5, 0.25], np.float32), np.float32(0.0625)
     tris, total = sph.marching_cubes(torch.from_numpy(phi).cuda(), dims, origin, float(sp), iso)
