@@ -644,10 +644,11 @@ int sph_voxel_density(sph_handle* h, const float origin[3], const int dims[3], f
  * order; triangles wind so that their right-hand normal points to the side
  * below iso.  At most max_tris are written; *ntri (a device unsigned)
  * receives the total, which may exceed max_tris (saturated at 0xfffffffe).
- * Three launches: the triangle counts of tiles of 256 cubes, one scan of
- * the tile totals, then each tile's triangles from its offset.  workspace: device memory
- * of sph_mc_workspace_size bytes, 256-byte aligned, owned by the caller.
- * The first call on a device copies the tables to its constant memory
+ * Three launches: the triangle counts of tiles of 1,024 cubes, one scan of
+ * the tile totals, then each tile's triangles from its offset, spread
+ * evenly over the tile's threads.  workspace: device memory of
+ * sph_mc_workspace_size bytes, 256-byte aligned, owned by the caller.
+ * The first call on a device copies the tables to its memory
  * (synchronously); make it before any stream capture.  Errors: SPH_ERR_ARG
  * (NULL, misaligned, too small a workspace, spacing not > 0, iso not
  * finite), SPH_ERR_OVERFLOW (more than 2^31 - 1 corners or (2^31 - 1) / 5

@@ -26,8 +26,10 @@
 // cube order (each cube's in table order) into the caller's buffer.
 //
 // The tables are generated on the host at first use (mc_case, below) from
-// the cube's numbering and copied to each device's constant memory before
-// the first marching-cubes launch on it.
+// the cube's numbering and copied to each device before the first
+// marching-cubes launch on it: the edge table to constant memory, the
+// triangle table and counts to global memory (the threads of a warp index
+// them by different cases, which the constant cache would serialise).
 #include <math.h>
 #include <string.h>
 
@@ -38,8 +40,8 @@
 namespace sphk {
 
 __constant__ unsigned short c_mc_edge[256];
-__constant__ signed char c_mc_tri[256][16];
-__constant__ unsigned char c_mc_ntri[256];
+__device__ signed char c_mc_tri[256][16];
+__device__ unsigned char c_mc_ntri[256];
 
 // ------------------------------------------------------ table generation
 
@@ -300,88 +302,103 @@ struct McGrid {
     float origin[3], spacing, iso;
 };
 
-__device__ __forceinline__ int cube_case(const float* __restrict__ phi, const McGrid& g, int ix, int iy, int iz,
-                                         float val[8])
+// Index of corner (ix, iy, iz) and coordinates of cube c, in 32-bit
+// arithmetic: a corner grid holds fewer than 2^31 corners (checked before
+// any launch).
+__device__ __forceinline__ unsigned mc_corner(const McGrid& g, int ix, int iy, int iz)
 {
-    int ci = 0;
+    return (unsigned)ix + (unsigned)g.nx * ((unsigned)iy + (unsigned)g.ny * (unsigned)iz);
+}
+
+__device__ __forceinline__ void mc_cube_coords(const McGrid& g, unsigned c, int ii[3])
+{
+    const unsigned cx = (unsigned)(g.nx - 1), cy = (unsigned)(g.ny - 1);
+    const unsigned r = c / cx, z = r / cy;
+    ii[0] = (int)(c - r * cx);
+    ii[1] = (int)(r - z * cy);
+    ii[2] = (int)z;
+}
+
+// The values at the eight vertices of cube ii, and the cube's case.
+__device__ __forceinline__ void cube_values(const float* __restrict__ phi, const McGrid& g, const int ii[3],
+                                            float val[8])
+{
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
         const int ox = (v == 1 || v == 2 || v == 5 || v == 6), oy = (v == 2 || v == 3 || v == 6 || v == 7),
                   oz = v >= 4;
-        val[v] = __ldg(phi + (ix + ox) + (long long)g.nx * ((iy + oy) + (long long)g.ny * (iz + oz)));
-        ci |= (val[v] < g.iso) << v;
+        val[v] = __ldg(phi + mc_corner(g, ii[0] + ox, ii[1] + oy, ii[2] + oz));
     }
+}
+
+__device__ __forceinline__ int cube_case(const McGrid& g, const float val[8])
+{
+    int ci = 0;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) ci |= (val[v] < g.iso) << v;
     return ci;
 }
 
 // Edge endpoints, the one of smaller coordinate first, and the vertex
-// offsets (bit 0: +x, bit 1: +y, bit 2: +z) of the numbering above.
-__constant__ unsigned char c_mc_lo[12] = {0, 1, 3, 0, 4, 5, 7, 4, 0, 1, 2, 3};
-__constant__ unsigned char c_mc_hi[12] = {1, 2, 2, 3, 5, 6, 6, 7, 4, 5, 6, 7};
-__constant__ unsigned char c_mc_off[8] = {0, 1, 3, 2, 4, 5, 7, 6};
+// offsets (bit 0: +x, bit 1: +y, bit 2: +z) of the numbering above, packed
+// three bits per entry so that a lookup is a shift (entry k of a table:
+// (bits >> 3 k) & 7), with no memory access.
+constexpr unsigned char MC_LO[12] = {0, 1, 3, 0, 4, 5, 7, 4, 0, 1, 2, 3};
+constexpr unsigned char MC_HI[12] = {1, 2, 2, 3, 5, 6, 6, 7, 4, 5, 6, 7};
+constexpr unsigned char MC_OFF[8] = {0, 1, 3, 2, 4, 5, 7, 6};
 
-// The triangles of cube c (index ii, case ci, corner values val) from
-// output slot o0 on (slots at or past cap are not written).
-__device__ __forceinline__ void mc_emit_cube(const McGrid& g, const int ii[3], int ci, const float val[8],
-                                             unsigned long long o0, float* __restrict__ tris,
-                                             unsigned long long cap)
+template <int N>
+constexpr unsigned long long mc_pack3(const unsigned char (&t)[N])
 {
+    unsigned long long b = 0;
+    for (int k = 0; k < N; ++k) b |= (unsigned long long)t[k] << (3 * k);
+    return b;
+}
+constexpr unsigned long long MC_LO3 = mc_pack3(MC_LO), MC_HI3 = mc_pack3(MC_HI), MC_OFF3 = mc_pack3(MC_OFF);
+
+// Triangle k of cube ii (case ci), written to out[0 .. 9); each vertex
+// reads its edge's two corner values from phi.
+__device__ __forceinline__ void mc_emit_tri(const float* __restrict__ phi, const McGrid& g, const int ii[3], int ci,
+                                            int k, float* __restrict__ out)
+{
+    // corner of offset bits b (bit 0: +x, bit 1: +y, bit 2: +z)
+    auto corner = [&](int b) {
+        return __ldg(phi + mc_corner(g, ii[0] + (b & 1), ii[1] + ((b >> 1) & 1), ii[2] + (b >> 2)));
+    };
     float lo[3], hi[3];  // the cube's corner coordinates, fl(origin + fl(i * spacing))
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         lo[a] = __fadd_rn(__fmul_rn((float)ii[a], g.spacing), g.origin[a]);
         hi[a] = __fadd_rn(__fmul_rn((float)(ii[a] + 1), g.spacing), g.origin[a]);
     }
-    const int nt = c_mc_ntri[ci];
-    for (int k = 0; k < nt; ++k) {
-        const unsigned long long slot = o0 + (unsigned long long)k;
-        if (slot >= cap) return;
-        float* out = tris + 9ull * slot;
-        for (int q = 0; q < 3; ++q) {
-            const int e = c_mc_tri[ci][3 * k + q];
-            const int v1 = c_mc_lo[e], v2 = c_mc_hi[e];
-            const float f1 = val[v1], f2 = val[v2];
-            const float t = __fdiv_rn(__fsub_rn(g.iso, f1), __fsub_rn(f2, f1));
-            const int b1 = c_mc_off[v1], b2 = c_mc_off[v2];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float p1 = (b1 >> a) & 1 ? hi[a] : lo[a];
-                const float p2 = (b2 >> a) & 1 ? hi[a] : lo[a];
-                out[3 * q + a] = __fadd_rn(p1, __fmul_rn(t, __fsub_rn(p2, p1)));
-            }
+    for (int q = 0; q < 3; ++q) {
+        const int e = __ldg(&c_mc_tri[ci][3 * k + q]);
+        const int v1 = (int)(MC_LO3 >> (3 * e)) & 7, v2 = (int)(MC_HI3 >> (3 * e)) & 7;
+        const int b1 = (int)(MC_OFF3 >> (3 * v1)) & 7, b2 = (int)(MC_OFF3 >> (3 * v2)) & 7;
+        const float f1 = corner(b1), f2 = corner(b2);
+        const float t = __fdiv_rn(__fsub_rn(g.iso, f1), __fsub_rn(f2, f1));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float p1 = (b1 >> a) & 1 ? hi[a] : lo[a];
+            const float p2 = (b2 >> a) & 1 ? hi[a] : lo[a];
+            out[3 * q + a] = __fadd_rn(p1, __fmul_rn(t, __fsub_rn(p2, p1)));
         }
     }
 }
 
-// Marching cubes in three launches, without a wait between blocks: tiles
-// of MC_TILE consecutive cubes (a block each) count their triangles and
-// store the tile's total; one block scans the tile totals into tile
-// offsets (and the grand total); then each tile recounts its cubes, scans
-// them within the block and writes its triangles from its tile's offset.
-// The output is in cube order, as if the counts had been scanned over the
-// whole grid.
-constexpr int MC_T = 256, MC_C = 1, MC_TILE = MC_T * MC_C;
-
-// Cases and triangle counts of this thread's cubes c0 .. c0 + MC_C - 1
-// (beyond n: none); returns the thread's total and stores each case byte.
-__device__ __forceinline__ unsigned mc_thread_cases(const float* __restrict__ phi, const McGrid& g, long long n,
-                                                    long long c0, int ci[MC_C], unsigned char* __restrict__ cases)
-{
-    const int cx = g.nx - 1, cy = g.ny - 1;
-    unsigned mine = 0;
-#pragma unroll
-    for (int k = 0; k < MC_C; ++k) {
-        ci[k] = 0;
-        const long long c = c0 + k;
-        if (c < n) {
-            float val[8];
-            ci[k] = cube_case(phi, g, (int)(c % cx), (int)((c / cx) % cy), (int)(c / ((long long)cx * cy)), val);
-            cases[c] = (unsigned char)ci[k];
-            mine += c_mc_ntri[ci[k]];
-        }
-    }
-    return mine;
-}
+// Marching cubes in three launches, without a wait between blocks, over
+// tiles of MC_TILE consecutive cubes (MC_CPT per thread of an MC_T-thread
+// block).  k_mc_tile_counts (a block per tile) stores every cube's case
+// byte and the tile's triangle total; k_mc_tile_scan (one block) turns the
+// totals into the tiles' offsets and the grand total; k_mc_tile_emit (a
+// block per tile with triangles) scans the tile's counts in shared memory
+// and then spreads the tile's triangles evenly over its threads: triangle q
+// of the tile belongs to the cube u with pre[u] <= q < pre[u + 1] (a binary
+// search of the scan), and a warp's 32 consecutive triangles go out through
+// shared memory as one contiguous run.  The output is in cube order, as if
+// the counts had been scanned over the whole grid.
+constexpr int MC_T = 256, MC_CPT = 4, MC_TILE = MC_T * MC_CPT;
 
 // Exclusive prefix of v over the block (MC_T threads) and the block total.
 __device__ __forceinline__ unsigned mc_block_scan(unsigned v, unsigned* s_warp, unsigned& total)
@@ -406,88 +423,150 @@ __device__ __forceinline__ unsigned mc_block_scan(unsigned v, unsigned* s_warp, 
     return before + inc - v;
 }
 
+// Thread t takes cubes c0 + t + k MC_T (k < MC_CPT): all their corner loads
+// first (a thread past the end loads cube 0's), then their cases.
 __global__ void __launch_bounds__(MC_T)
 k_mc_tile_counts(const float* __restrict__ phi, McGrid g, unsigned char* __restrict__ cases,
                  unsigned* __restrict__ tile_count)
 {
-    __shared__ unsigned s_warp[MC_T / 32];
-    const long long n = (long long)(g.nx - 1) * (g.ny - 1) * (g.nz - 1);
-    int ci[MC_C];
-    const unsigned mine =
-        mc_thread_cases(phi, g, n, (long long)blockIdx.x * MC_TILE + (long long)threadIdx.x * MC_C, ci, cases);
-    unsigned total;
-    mc_block_scan(mine, s_warp, total);
-    if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
+    __shared__ unsigned s_sum[MC_T / 32];
+    const unsigned n = (unsigned)(g.nx - 1) * (unsigned)(g.ny - 1) * (unsigned)(g.nz - 1);
+    const unsigned c0 = blockIdx.x * MC_TILE + threadIdx.x;
+    float val[MC_CPT][8];
+#pragma unroll
+    for (int k = 0; k < MC_CPT; ++k) {
+        const unsigned c = c0 + k * MC_T;
+        int ii[3];
+        mc_cube_coords(g, c < n ? c : 0u, ii);
+        cube_values(phi, g, ii, val[k]);
+    }
+    unsigned mine = 0;
+#pragma unroll
+    for (int k = 0; k < MC_CPT; ++k) {
+        const unsigned c = c0 + k * MC_T;
+        if (c < n) {
+            const int ci = cube_case(g, val[k]);
+            cases[c] = (unsigned char)ci;
+            mine += __ldg(c_mc_ntri + ci);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(FULL, mine, o);
+    if ((threadIdx.x & 31u) == 0) s_sum[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+#pragma unroll
+        for (int w = 0; w < MC_T / 32; ++w) tot += s_sum[w];
+        tile_count[blockIdx.x] = tot;
+    }
 }
 
-// One block: tile_off[t] = sum of tile_count[0 .. t-1] (64-bit), and the
-// grand total (saturated to 0xfffffffe) in *total_out.
+// One block of 1024 threads: thread t sums its run of consecutive tile
+// totals, the block scans those sums, and the thread writes its tiles'
+// offsets (64-bit); the grand total, saturated to 0xfffffffe, goes to
+// *total_out.
 __global__ void __launch_bounds__(1024)
 k_mc_tile_scan(const unsigned* __restrict__ tile_count, int ntiles, unsigned long long* __restrict__ tile_off,
                unsigned* __restrict__ total_out)
 {
     __shared__ unsigned long long s_warp[32];
-    __shared__ unsigned long long s_carry;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
+    const int per = (ntiles + 1023) / 1024;
+    const int a = (int)threadIdx.x * per, e = min(a + per, ntiles);
+    unsigned long long mine = 0;
+    for (int t0 = a; t0 < e; t0 += 8) {  // eight loads in flight
+        unsigned x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = t0 + j < e ? __ldg(tile_count + t0 + j) : 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mine += x[j];
+    }
+    unsigned long long inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(FULL, inc, o);
+        if (lane >= (unsigned)o) inc += u;
+    }
+    if (lane == 31u) s_warp[warp] = inc;
     __syncthreads();
-    for (int base = 0; base < ntiles; base += 1024) {
-        const int t = base + (int)threadIdx.x;
-        const unsigned long long v = t < ntiles ? tile_count[t] : 0ull;
-        unsigned long long inc = v;
+    if (warp == 0) {
+        unsigned long long x = s_warp[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long u = __shfl_up_sync(FULL, inc, o);
-            if (lane >= (unsigned)o) inc += u;
+            const unsigned long long u = __shfl_up_sync(FULL, x, o);
+            if (lane >= (unsigned)o) x += u;
         }
-        if (lane == 31u) s_warp[warp] = inc;
-        __syncthreads();
-        unsigned long long before = 0, all = 0;
-        for (int w = 0; w < 32; ++w) {
-            const unsigned long long x = s_warp[w];
-            before += (unsigned)w < warp ? x : 0ull;
-            all += x;
-        }
-        const unsigned long long carry = s_carry;
-        if (t < ntiles) tile_off[t] = carry + before + inc - v;
-        __syncthreads();  // every thread has read s_warp and s_carry
-        if (threadIdx.x == 0) s_carry = carry + all;
-        __syncthreads();
+        s_warp[lane] = x;  // inclusive over the warps
     }
-    if (threadIdx.x == 0) {
-        const unsigned long long tot = s_carry;
+    __syncthreads();
+    unsigned long long run = (warp ? s_warp[warp - 1] : 0ull) + inc - mine;
+    for (int t = a; t < e; ++t) {
+        tile_off[t] = run;
+        run += __ldg(tile_count + t);
+    }
+    if (threadIdx.x == 1023) {
+        const unsigned long long tot = s_warp[31];
         *total_out = tot > 0xfffffffeull ? 0xfffffffeu : (unsigned)tot;
     }
 }
 
 __global__ void __launch_bounds__(MC_T)
 k_mc_tile_emit(const float* __restrict__ phi, McGrid g, const unsigned char* __restrict__ cases,
-               const unsigned long long* __restrict__ tile_off, float* __restrict__ tris, unsigned long long cap)
+               const unsigned* __restrict__ tile_count, const unsigned long long* __restrict__ tile_off,
+               float* __restrict__ tris, unsigned long long cap)
 {
+    if (__ldg(tile_count + blockIdx.x) == 0) return;  // a tile without triangles (uniform)
     __shared__ unsigned s_warp[MC_T / 32];
-    const int cx = g.nx - 1, cy = g.ny - 1;
-    const long long n = (long long)cx * cy * (g.nz - 1);
-    const long long c0 = (long long)blockIdx.x * MC_TILE + (long long)threadIdx.x * MC_C;
-    int ci[MC_C];
-    unsigned mine = 0;  // the cases the count pass stored
+    __shared__ unsigned s_pre[MC_TILE + 1];
+    __shared__ unsigned char s_case[MC_TILE];
+    __shared__ float s_out[MC_T / 32][32 * 9];
+    const unsigned n = (unsigned)(g.nx - 1) * (unsigned)(g.ny - 1) * (unsigned)(g.nz - 1);
+    const unsigned c0 = blockIdx.x * MC_TILE;
+    // this thread's MC_CPT consecutive cubes: their case bytes in one load
+    // (the case array is padded to 256 bytes), those past the end as case 0
+    const unsigned cb = c0 + MC_CPT * threadIdx.x;
+    static_assert(MC_CPT == 4, "one 4-byte load of case bytes");
+    const uchar4 q4 = cb < n ? __ldg(reinterpret_cast<const uchar4*>(cases + cb)) : make_uchar4(0, 0, 0, 0);
+    const int cc[MC_CPT] = {q4.x, q4.y, q4.z, q4.w};
+    unsigned pre[MC_CPT], local = 0;
 #pragma unroll
-    for (int k = 0; k < MC_C; ++k) {
-        ci[k] = c0 + k < n ? (int)__ldg(cases + c0 + k) : 0;
-        mine += c_mc_ntri[ci[k]];
+    for (int k = 0; k < MC_CPT; ++k) {
+        const int ci = cb + k < n ? cc[k] : 0;
+        s_case[MC_CPT * threadIdx.x + k] = (unsigned char)ci;
+        pre[k] = local;
+        local += __ldg(c_mc_ntri + ci);
     }
     unsigned total;
-    const unsigned excl = mc_block_scan(mine, s_warp, total);
-    unsigned long long o = tile_off[blockIdx.x] + excl;
+    const unsigned excl = mc_block_scan(local, s_warp, total);
 #pragma unroll
-    for (int k = 0; k < MC_C; ++k) {
-        const int nt = c_mc_ntri[ci[k]];
-        if (nt == 0) continue;
-        const long long c = c0 + k;
-        const int ii[3] = {(int)(c % cx), (int)((c / cx) % cy), (int)(c / ((long long)cx * cy))};
-        float val[8];
-        cube_case(phi, g, ii[0], ii[1], ii[2], val);
-        mc_emit_cube(g, ii, ci[k], val, o, tris, cap);
-        o += (unsigned long long)nt;
+    for (int k = 0; k < MC_CPT; ++k) s_pre[MC_CPT * threadIdx.x + k] = excl + pre[k];
+    if (threadIdx.x == 0) s_pre[MC_TILE] = total;
+    __syncthreads();
+    const unsigned long long base = tile_off[blockIdx.x];
+    if (base >= cap) return;
+    const unsigned lim = cap - base < (unsigned long long)total ? (unsigned)(cap - base) : total;
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    float* const buf = s_out[warp];
+    for (unsigned q0 = warp * 32u; q0 < lim; q0 += MC_T) {  // warp-uniform
+        const unsigned q = q0 + lane;
+        if (q < lim) {
+            int lo = 0, hi = MC_TILE;  // s_pre[lo] <= q < s_pre[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_pre[mid] <= q) lo = mid;
+                else hi = mid;
+            }
+            int ii[3];
+            mc_cube_coords(g, c0 + (unsigned)lo, ii);
+            mc_emit_tri(phi, g, ii, s_case[lo], (int)(q - s_pre[lo]), buf + 9 * lane);
+        }
+        __syncwarp();
+        // the warp's triangles q0 .. q0 + m - 1 are one contiguous run
+        const unsigned m = min(32u, lim - q0);
+        float* __restrict__ dst = tris + 9ull * (base + q0);
+        for (unsigned f = lane; f < 9 * m; f += 32) dst[f] = buf[f];
+        __syncwarp();
     }
 }
 
@@ -507,10 +586,10 @@ cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const flo
     g.iso = iso;
     const long long n = (long long)(g.nx - 1) * (g.ny - 1) * (g.nz - 1);
     if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(unsigned), s);
-    const long long nt = mc_tiles(n);
+    const int nt = (int)mc_tiles(n);
     k_mc_tile_counts<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, cases, tile_count);
-    k_mc_tile_scan<<<1, 1024, 0, s>>>(tile_count, (int)nt, tile_off, total);
-    k_mc_tile_emit<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, cases, tile_off, tris, cap);
+    k_mc_tile_scan<<<1, 1024, 0, s>>>(tile_count, nt, tile_off, total);
+    k_mc_tile_emit<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, cases, tile_count, tile_off, tris, cap);
     *launches += 3;
     return cudaGetLastError();
 }
