@@ -399,6 +399,7 @@ __device__ __forceinline__ void mc_emit_tri(const float* __restrict__ phi, const
 // shared memory as one contiguous run.  The output is in cube order, as if
 // the counts had been scanned over the whole grid.
 constexpr int MC_T = 256, MC_CPT = 4, MC_TILE = MC_T * MC_CPT;
+constexpr int MC_SPLIT = 4;  // emit blocks per tile (blockIdx.y): each takes every MC_SPLIT-th run of MC_T triangles
 
 // Exclusive prefix of v over the block (MC_T threads) and the block total.
 __device__ __forceinline__ unsigned mc_block_scan(unsigned v, unsigned* s_warp, unsigned& total)
@@ -548,7 +549,7 @@ k_mc_tile_emit(const float* __restrict__ phi, McGrid g, const unsigned char* __r
     const unsigned lim = cap - base < (unsigned long long)total ? (unsigned)(cap - base) : total;
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     float* const buf = s_out[warp];
-    for (unsigned q0 = warp * 32u; q0 < lim; q0 += MC_T) {  // warp-uniform
+    for (unsigned q0 = blockIdx.y * MC_T + warp * 32u; q0 < lim; q0 += MC_T * MC_SPLIT) {  // warp-uniform
         const unsigned q = q0 + lane;
         if (q < lim) {
             int lo = 0, hi = MC_TILE;  // s_pre[lo] <= q < s_pre[hi]
@@ -589,7 +590,7 @@ cudaError_t launch_marching_cubes(const float* phi, const int dims[3], const flo
     const int nt = (int)mc_tiles(n);
     k_mc_tile_counts<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, cases, tile_count);
     k_mc_tile_scan<<<1, 1024, 0, s>>>(tile_count, nt, tile_off, total);
-    k_mc_tile_emit<<<(unsigned)nt, MC_T, 0, s>>>(phi, g, cases, tile_count, tile_off, tris, cap);
+    k_mc_tile_emit<<<dim3((unsigned)nt, MC_SPLIT), MC_T, 0, s>>>(phi, g, cases, tile_count, tile_off, tris, cap);
     *launches += 3;
     return cudaGetLastError();
 }
