@@ -204,6 +204,26 @@ def test_host_buffers_round_trip():
         assert np.array_equal(a.numpy(), b.cpu().numpy())
 
 
+def test_pageable_host_buffers_round_trip():
+    """Host buffers that are not page-locked round-trip like page-locked
+    ones: both give the device path's state bit for bit."""
+    sc = scenes.dam_break_small(n_side=10, n_boid=8)
+    p = lattice_params(sc)
+    s = Scene(p, len(sc["fluid_pos"]), len(sc["boid_pos"]))
+    host = [torch.from_numpy(a.copy()) for a in (sc["fluid_pos"], sc["fluid_vel"], sc["boid_pos"], sc["boid_vel"])]
+    assert not any(t.is_pinned() for t in host)
+    s.set_state_host(*host)
+    s.step(3)
+    outs = [torch.empty_like(t) for t in host]
+    s.get_state_host(outs)
+    pinned = [torch.empty_like(t).pin_memory() for t in host]
+    s.get_state_host(pinned)
+    dev = run_gpu(p, sc, steps=3).get_state()
+    for a, b, c in zip(outs, pinned, dev):
+        assert np.array_equal(a.numpy(), c.cpu().numpy())
+        assert np.array_equal(b.numpy(), c.cpu().numpy())
+
+
 def test_nonfinite_input_sets_status_bit():
     sc = scenes.dam_break_small(n_side=8, n_boid=4)
     p = lattice_params(sc)
