@@ -27,9 +27,10 @@
 //
 // The tables are generated on the host at first use (mc_case, below) from
 // the cube's numbering and copied to each device before the first
-// marching-cubes launch on it: the edge table to constant memory, the
-// triangle table and counts to global memory (the threads of a warp index
-// them by different cases, which the constant cache would serialise).
+// marching-cubes launch on it: the triangle table and counts go to global
+// memory (the threads of a warp index them by different cases, which the
+// constant cache would serialise); the edge table stays on the host
+// (sph_mc_tables).
 #include <math.h>
 #include <string.h>
 
@@ -39,7 +40,6 @@
 
 namespace sphk {
 
-__constant__ unsigned short c_mc_edge[256];
 __device__ signed char c_mc_tri[256][16];
 __device__ unsigned char c_mc_ntri[256];
 
@@ -235,8 +235,7 @@ cudaError_t mc_upload_tables()
     if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_upload_mutex);
     if (g_uploaded[dev]) return cudaSuccess;
-    e = cudaMemcpyToSymbol(c_mc_edge, t.edge, sizeof(t.edge));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_mc_tri, t.tri, sizeof(t.tri));
+    e = cudaMemcpyToSymbol(c_mc_tri, t.tri, sizeof(t.tri));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_mc_ntri, t.ntri, sizeof(t.ntri));
     if (e == cudaSuccess) g_uploaded[dev] = true;
     return e;
@@ -391,15 +390,17 @@ __device__ __forceinline__ void mc_emit_tri(const float* __restrict__ phi, const
 // tiles of MC_TILE consecutive cubes (MC_CPT per thread of an MC_T-thread
 // block).  k_mc_tile_counts (a block per tile) stores every cube's case
 // byte and the tile's triangle total; k_mc_tile_scan (one block) turns the
-// totals into the tiles' offsets and the grand total; k_mc_tile_emit (a
-// block per tile with triangles) scans the tile's counts in shared memory
-// and then spreads the tile's triangles evenly over its threads: triangle q
+// totals into the tiles' offsets and the grand total; k_mc_tile_emit
+// (MC_SPLIT blocks per tile with triangles) scans the tile's counts in
+// shared memory in each block and then spreads the tile's triangles evenly
+// over the threads of its blocks: triangle q
 // of the tile belongs to the cube u with pre[u] <= q < pre[u + 1] (a binary
 // search of the scan), and a warp's 32 consecutive triangles go out through
 // shared memory as one contiguous run.  The output is in cube order, as if
 // the counts had been scanned over the whole grid.
 constexpr int MC_T = 256, MC_CPT = 4, MC_TILE = MC_T * MC_CPT;
-constexpr int MC_SPLIT = 4;  // emit blocks per tile (blockIdx.y): each takes every MC_SPLIT-th run of MC_T triangles
+// emit blocks per tile (blockIdx.y); block y takes the runs of MC_T triangles y, y + MC_SPLIT, ...
+constexpr int MC_SPLIT = 4;
 
 // Exclusive prefix of v over the block (MC_T threads) and the block total.
 __device__ __forceinline__ unsigned mc_block_scan(unsigned v, unsigned* s_warp, unsigned& total)
