@@ -116,6 +116,21 @@ def test_marching_cubes_capacity_and_degenerate_grids():
         sph.marching_cubes(d, dims, np.zeros(3, np.float32), -0.1, 0.0)
 
 
+@pytest.mark.parametrize("cap", [1, 31, 33, 257, 777, 1025, 2600])
+def test_marching_cubes_capacity_cuts_any_run(cap):
+    """A capacity inside a warp's run of 32 triangles, across the emit
+    blocks' runs of 256 and across tiles: the buffer holds exactly the
+    first cap triangles of the full output."""
+    dims = (40, 33, 29)
+    phi = torch.from_numpy(_field(7, dims, "spheres")).cuda()
+    origin = np.array([-1.0, -0.5, 0.25], np.float32)
+    full, total = sph.marching_cubes(phi, dims, origin, 0.0625, 0.0)
+    assert total > 2600
+    part, total2 = sph.marching_cubes(phi, dims, origin, 0.0625, 0.0, max_tris=cap)
+    assert total2 == total and len(part) == cap
+    assert torch.equal(part, full[:cap])
+
+
 def test_dam_break_surface_is_closed_and_oriented():
     """GPU voxel density then GPU marching cubes on the dam-break column:
     the corner grid extends past the box, so the mesh must be closed; the
