@@ -80,34 +80,42 @@ k_boid_rules(const float4* __restrict__ bpos_s, const float4* __restrict__ bvel_
     float vs[3] = {0.f, 0.f, 0.f};  // alignment: sum of v_j
     float ps[3] = {0.f, 0.f, 0.f};  // cohesion: sum of (p_j - p_b)
     int nv = 0;
+    // boid j at pj with velocity vj (vj is used only within r_vis)
+    auto take = [&](const float4& pj, const float4& vj) {
+        const float dx = __fsub_rn(pj.x, pb.x);
+        const float dy_ = __fsub_rn(pj.y, pb.y);
+        const float dz_ = __fsub_rn(pj.z, pb.z);
+        const float r2 = pair_r2(dx, dy_, dz_);
+        if (r2 < c.rs2) {
+            float w = 1.0f - sqrtf(r2) / c.rs;
+            w = fminf(fmaxf(w, 0.0f), 1.0f);
+            cl[0] -= dx * w;
+            cl[1] -= dy_ * w;
+            cl[2] -= dz_ * w;
+        }
+        if (r2 < c.rv2) {
+            vs[0] += vj.x;
+            vs[1] += vj.y;
+            vs[2] += vj.z;
+            ps[0] += dx;
+            ps[1] += dy_;
+            ps[2] += dz_;
+            ++nv;
+        }
+    };
     RowWalk walk(c.gb, c.wb, bstart + c.cb_base, pb.x, pb.y, pb.z);
     unsigned s0, s1;
     while (walk.next(s0, s1)) {
-        for (unsigned j = s0 + lane; j < s1; j += 32) {
-            if (j == (unsigned)s) continue;
-            const float4 pj = bpos_s[j];
-            const float dx = __fsub_rn(pj.x, pb.x);
-            const float dy_ = __fsub_rn(pj.y, pb.y);
-            const float dz_ = __fsub_rn(pj.z, pb.z);
-            const float r2 = pair_r2(dx, dy_, dz_);
-            if (r2 < c.rs2) {
-                float w = 1.0f - sqrtf(r2) / c.rs;
-                w = fminf(fmaxf(w, 0.0f), 1.0f);
-                cl[0] -= dx * w;
-                cl[1] -= dy_ * w;
-                cl[2] -= dz_ * w;
-            }
-            if (r2 < c.rv2) {
-                const float4 vj = bvel_s[j];
-                vs[0] += vj.x;
-                vs[1] += vj.y;
-                vs[2] += vj.z;
-                ps[0] += dx;
-                ps[1] += dy_;
-                ps[2] += dz_;
-                ++nv;
-            }
+        // lane l takes slots s0 + l, s0 + l + 32, ... in that order, two
+        // at a time so that both candidates' loads are in flight together
+        unsigned j = s0 + lane;
+        for (; j + 32 < s1; j += 64) {
+            const float4 pa = bpos_s[j], va = bvel_s[j];
+            const float4 pc = bpos_s[j + 32], vc = bvel_s[j + 32];
+            if (j != (unsigned)s) take(pa, va);
+            if (j + 32 != (unsigned)s) take(pc, vc);
         }
+        if (j < s1 && j != (unsigned)s) take(bpos_s[j], bvel_s[j]);
     }
     // obstacle avoidance: the obstacle-grid cells whose centre lies within
     // the visual range (the float32 predicate of the boid pairs), their mean
